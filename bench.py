@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""HGMM build + register throughput on one GB300 (or N independent replicas).
+
+Workload (one "step"): two consecutive frames of a simulated 64-beam spinning
+LiDAR (0.2 deg azimuth step, +-15 deg elevation, 100 m range, N(0, 0.02^2) m
+range noise) in a seeded synthetic urban scene (ground, 20 boxes of 5-20 m,
+30 poles); the second frame after 1 m of forward motion and <= 2 deg of yaw.
+A step builds the depth-4 GMM tree (4680 nodes, 8 EM iterations per level)
+of the first frame and registers the second frame to it with 30 rounds of
+the adaptive E-step (Algorithm 1) and the Mahalanobis M-step (Eq. 9-16).
+
+value   = (target points + source points) per second through build +
+          register, Mpts/s, summed over ranks (each rank registers its own
+          independently seeded pair: weak scaling, no collective on the path)
+e2e     = the same metric through hgmm_register_pair_host with pinned host
+          buffers: host->device copies of both clouds and the device->host
+          read of T inside the timed region
+roofline: the kernel with the largest share of device time, its average
+          CUDA-event duration (library event profiler, same stream) against
+          its algorithmic work per launch
+cpu_baseline / --impl reference: the FP64 numpy oracle on a bounded sample
+          of the same workload (1/8 of each cloud, depth 3 so the points per
+          leaf match, 30 rounds), single-threaded, on this machine's host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEPTH = 4
+ITERS = 30
+WORKLOAD = "lidar64_consecutive_frames_depth4_30it"
+METRIC = "HGMM build+register Mpts/s"
+L2_FLUSH_BYTES = 512 << 20
+
+# algorithmic work per processed point for each kernel of the path
+# (bytes of DRAM traffic a perfect kernel needs, FP32 flops with FMA = 2)
+KERNEL_WORK = {
+    "estep": {"bytes": 16, "flops": 355, "unit": "target point"},
+    "assign": {"bytes": 20, "flops": 160, "unit": "target point"},
+    "scatter": {"bytes": 44, "flops": 0, "unit": "target point"},
+    "descend": {"bytes": 16, "flops": None, "unit": "source point"},
+}
+DESCEND_FLOPS_PER_LEVEL = 8 * 18 + 8 * 2 + 8  # 8 child scores, 8 exp2 + sum, rcp
+DESCEND_FLOPS_FIXED = 18 + 12  # transform, fixed-point conversion
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle leg
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import hgmm_oracle as O
+from paper_1807_02587_gb300 import synth
+p = synth.lidar_pair({seed})
+rng = np.random.default_rng(12345)
+tgt = p["tgt"][rng.permutation(p["tgt"].shape[0])[: p["tgt"].shape[0] // 8]]
+src = p["src"][rng.permutation(p["src"].shape[0])[: p["src"].shape[0] // 8]]
+tgt = tgt.astype(np.float32).astype(np.float64)
+src = src.astype(np.float32).astype(np.float64)
+times = []
+for k in range({reps}):
+    t0 = time.perf_counter()
+    tree = O.build_tree(tgt, O.Params(depth=3))
+    O.register(tree, src, iters={iters})
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times, "n": int(tgt.shape[0] + src.shape[0])}}))
+"""
+
+
+def run_oracle(reps, seed=0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, seed=seed, reps=reps, iters=ITERS)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_desc():
+    return ("FP64 numpy oracle, 1/8 random subsample of each frame (~11.6k + 11.6k points), "
+            "depth 3 (same points per leaf as depth 4 on the full frame), 8 EM iterations "
+            "per level, 30 registration rounds; one thread (OMP/BLAS threads = 1)")
+
+
+def reference_main(args, rank, world):
+    if rank != 0:
+        return 0
+    res = run_oracle(args.warmup + args.steps, seed=args.seed)
+    ts = res["times"][args.warmup:]
+    ms = 1e3 * float(np.mean(ts))
+    val = res["n"] / (ms / 1e3) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpts/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + "_sampled", "points_per_step": res["n"]},
+        "cpu_baseline": {"value": val, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+                         "sample": oracle_sample_desc()},
+        "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def gpu_main(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    from paper_1807_02587_gb300 import binding as B
+    from paper_1807_02587_gb300 import synth
+
+    pair = synth.lidar_pair(args.seed + rank)
+    tgt4 = synth.to_float4(pair["tgt"])
+    src4 = synth.to_float4(pair["src"])
+    n_t, n_s = tgt4.shape[0], src4.shape[0]
+    tgt = torch.from_numpy(tgt4).cuda()
+    src = torch.from_numpy(src4).cuda()
+    tree = B.Tree(max(n_t, n_s), DEPTH)
+    prm = B.params()
+    s = torch.cuda.Stream()
+    T_out = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+
+    def step():
+        tree.build(tgt, DEPTH, prm, stream=s)
+        tree.register(src, None, ITERS, stream=s, T_out=T_out)
+
+    # correctness gate + warm-up (eager)
+    step()
+    tree.sync(s)
+    T0 = T_out.cpu().numpy().copy()
+    for _ in range(args.warmup):
+        step()
+    tree.sync(s)
+    # per-kernel profile of two eager steps (event pairs around every launch)
+    tree.profile(True)
+    step()
+    step()
+    prof = tree.profile_read()
+    tree.profile(False)
+    launches_per_step = sum(c for _, c in prof.values()) // 2
+
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            step()
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        assert np.allclose(T_out.cpu().numpy(), T0, atol=1e-9), "graph replay changed the result"
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        with torch.cuda.stream(s):
+            flush.zero_()
+        starts[k].record(s)
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+        ends[k].record(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    tree.sync(s)
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms_step = float(np.mean(ms))
+
+    # end to end through the host-buffer entry point
+    tgt_h = torch.from_numpy(tgt4).pin_memory()
+    src_h = torch.from_numpy(src4).pin_memory()
+    for _ in range(2):
+        B.hgmm_register_pair_host(tree.handle, tgt_h, src_h, DEPTH, prm, None, ITERS, stream=s)
+    e2e_ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(s):
+            flush.zero_()
+        s.synchronize()
+        t0 = time.perf_counter()
+        T_h = B.hgmm_register_pair_host(tree.handle, tgt_h, src_h, DEPTH, prm, None, ITERS, stream=s)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_step = float(np.mean(e2e_ms))
+
+    pts = float(n_t + n_s)
+    tot = torch.tensor([pts, ms_step, e2e_step], dtype=torch.float64, device="cuda")
+    if world > 1:
+        pts_all = tot[:1].clone()
+        dist.all_reduce(pts_all, op=dist.ReduceOp.SUM)
+        mx = tot[1:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        pts_tot, ms_max, e2e_max = float(pts_all[0]), float(mx[0]), float(mx[1])
+    else:
+        pts_tot, ms_max, e2e_max = pts, ms_step, e2e_step
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    hbm_peak, peak_kind = _peaks()
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    clk_mhz = clk["sm_mhz"] or 2070.0
+    fp32_peak_tflops = sm_count * 128 * 2 * clk_mhz * 1e6 / 1e12
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / max(prof[dom][1], 1)
+    total_prof = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms_total_2steps": round(v[0], 4), "launches_2steps": v[1],
+                   "share": round(v[0] / total_prof, 4)} for k, v in prof.items() if v[1]}
+    roof = {"kernel": dom, "avg_launch_us": dom_ms * 1e3}
+    work = KERNEL_WORK.get(dom)
+    units = n_t if (work and work["unit"] == "target point") else n_s
+    if dom == "descend":
+        lv = _descend_levels(B, tree, src4, DEPTH)
+        flops_pt = DESCEND_FLOPS_FIXED + DESCEND_FLOPS_PER_LEVEL * lv
+        roof.update(bound="alu", achieved=flops_pt * units / (dom_ms / 1e3) / 1e12,
+                    peak=fp32_peak_tflops, unit="TFLOP/s",
+                    note=f"FP32 flops/point {flops_pt:.0f} (avg {lv:.2f} levels visited); "
+                         f"peak = {sm_count} SM x 128 lanes x 2 x {clk_mhz:.0f} MHz")
+    elif work is not None and work["flops"] and \
+            work["flops"] / work["bytes"] > fp32_peak_tflops * 1e12 / (hbm_peak * 1e9):
+        roof.update(bound="alu", achieved=work["flops"] * units / (dom_ms / 1e3) / 1e12,
+                    peak=fp32_peak_tflops, unit="TFLOP/s",
+                    note=f"FP32 flops/point {work['flops']}; peak = {sm_count} SM x 128 x 2 x "
+                         f"{clk_mhz:.0f} MHz")
+    elif work is not None:
+        roof.update(bound="hbm", achieved=work["bytes"] * units / (dom_ms / 1e3) / 1e9,
+                    peak=hbm_peak, unit="GB/s", note=f"{peak_kind} HBM copy bandwidth")
+    else:
+        roof.update(bound="alu", achieved=None, peak=None, unit=None,
+                    note="no algorithmic model for this kernel")
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    hbm_equiv = None
+    if dom in KERNEL_WORK:
+        hbm_equiv = KERNEL_WORK[dom]["bytes"] * units / (dom_ms / 1e3) / 1e9
+    roof["hbm_gbs_equivalent"] = hbm_equiv
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        res = run_oracle(1, seed=args.seed)
+        t = res["times"][0]
+        cpu = {"value": res["n"] / t / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+               "sample": oracle_sample_desc(), "seconds": t}
+
+    c = (np.trace(T0[:3, :3].T @ pair["T_gt"][:3, :3]) - 1.0) / 2.0
+    rot_err = float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
+    line = {
+        "metric": METRIC, "value": pts_tot / (ms_max / 1e3) / 1e6, "unit": "Mpts/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_target": n_t, "n_source": n_s, "depth": DEPTH,
+                   "J": 8, "em_iters": prm.em_iters, "reg_iters": ITERS,
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                   "cuda_graph": graph is not None, "parallelism": f"replicas{world}"},
+        "pairs_per_s": world / (ms_max / 1e3),
+        "e2e": {"value": pts_tot / (e2e_max / 1e3) / 1e6, "unit": "Mpts/s",
+                "h2d_bytes_per_step": int(16 * (n_t + n_s)), "d2h_bytes_per_step": 128,
+                "ms_per_step": e2e_max},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "launches_per_step": int(launches_per_step),
+        "roofline": roof,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "accuracy": {"rot_err_deg_vs_truth": rot_err,
+                     "trans_err_m_vs_truth": float(np.linalg.norm(T0[:3, 3] - pair["T_gt"][:3, 3])),
+                     "e2e_equals_device_path": bool(np.array_equal(T_h, T0))},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _descend_levels(B, tree, src4, depth):
+    """Average number of tree levels the descent visits per source point in
+    the last round (from the association levels of the exported moments)."""
+    m = tree.reg_moments()
+    sizes = [8 ** (l + 1) for l in range(depth)]
+    offs = np.cumsum([0] + sizes)
+    mass = np.array([m[offs[l]:offs[l + 1], 0].sum() for l in range(depth)])
+    if mass.sum() <= 0:
+        return float(depth)
+    return float(np.sum(mass * (np.arange(depth) + 1)) / mass.sum())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_main(args, rank, world)
+    return gpu_main(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

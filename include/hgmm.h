@@ -1,0 +1,167 @@
+/*
+ * hgmm.h - C ABI of the GB300 (sm_103a) hierarchical-GMM registration path.
+ *
+ * Method: Eckart, Kim, Kautz, "Fast and Accurate Point Cloud Registration
+ * using Trees of Gaussian Mixtures" (arXiv 1807.02587).
+ *
+ *   - hgmm_build     : the GMM-tree construction the paper relies on
+ *                      (Sec. 3 last paragraph, Sec. 4.1 first paragraph): a
+ *                      top-down hierarchy of 8-component GMM nodes, each level
+ *                      fitted by EM (Eq. 2, Eq. 3) on the points that the
+ *                      level above assigned to each parent.
+ *   - hgmm_register  : the registration EM loop (Eq. 1, Eq. 4-7): the
+ *                      adaptive tree-search E-step of Algorithm 1 with the
+ *                      complexity criterion of Sec. 4.1, then the M-step of
+ *                      Eq. 9-16 (PCA form of the Mahalanobis distance, weighted
+ *                      point-to-plane least squares after Low), solved in FP64.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 (HGMM_OK) or one of the negative HGMM_E* codes below.
+ *     hgmm_strerror() gives a one-line message.  A failing call leaves its
+ *     outputs unspecified and the tree reusable.
+ *   - Points are float32 quadruples (x, y, z, pad): n rows of 16 bytes, the
+ *     pointer 16-byte aligned.  "d_" pointers are device memory owned by the
+ *     caller; "h_" pointers are host memory owned by the caller.
+ *   - Transforms are 4x4 row-major float64 matrices T = [R t; 0 1] that map a
+ *     source point z to R z + t in the model (tree) frame: the tree is built
+ *     on cloud Z1, the source is Z2 (Eq. 1).
+ *   - Streams are passed as void* (a cudaStream_t; NULL = legacy default
+ *     stream).  Asynchronous calls only enqueue work; results are valid
+ *     after the stream is synchronised.  Calls on one tree must not overlap
+ *     (they share the tree's device scratch); different trees are independent.
+ *   - The tree lives on the device that was current at hgmm_tree_create and
+ *     every call must run with that device current.
+ *   - No entry point except hgmm_tree_create / hgmm_tree_destroy allocates or
+ *     frees device memory, so build + register can be captured in a CUDA graph.
+ */
+#ifndef HGMM_H
+#define HGMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HGMM_OK 0
+#define HGMM_EINVAL (-1)      /* bad argument: n < 8, J != 8, depth out of range, misaligned pointer */
+#define HGMM_ENOMEM (-2)      /* device allocation failed (hgmm_tree_create only) */
+#define HGMM_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define HGMM_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define HGMM_EDEGENERATE (-5) /* the 6x6 normal equations were singular; T kept */
+#define HGMM_ENONFINITE (-6)  /* the input cloud holds NaN or Inf coordinates */
+#define HGMM_ECAPACITY (-7)   /* n or depth exceeds what the tree was created for */
+
+#define HGMM_J 8          /* components per GMM node (Sec. 4.1) */
+#define HGMM_MAX_DEPTH 5  /* deepest supported tree: 8 + 64 + ... + 32768 nodes */
+
+typedef struct hgmm_tree hgmm_tree; /* opaque, device-resident, library-owned */
+
+/* Build parameters.  The paper fixes J = 8 and lambda_c = 0.01 (Sec. 4.1);
+ * the others are this library's readings of the build it cites.
+ *   em_iters  : EM iterations per tree level (K, default 8).
+ *   n_min     : a child whose expected point count falls below n_min dies
+ *               (weight 0) unless it is its parent's heaviest child (default 8).
+ *   lam_c     : complexity threshold lambda_c of Algorithm 1 (default 0.01).
+ *   eps_rel   : covariances get eps*I with eps = (eps_rel * extent)^2, extent
+ *               = bounding-box diagonal of the modelled cloud (default 1e-3).
+ *   precision : 0 = FP32 moment sums with compensated (Kahan/TwoSum)
+ *               accumulation (default); 1 = plain FP32 sums (for comparison). */
+typedef struct hgmm_params {
+    int32_t em_iters;
+    float n_min;
+    float lam_c;
+    float eps_rel;
+    int32_t precision;
+    int32_t reserved[3];
+} hgmm_params;
+
+/* Per-node record written by hgmm_tree_export: 16 float64 per node,
+ * [pi, mu_x, mu_y, mu_z, S_xx, S_xy, S_xz, S_yy, S_yz, S_zz, live, count,
+ *  complexity, lambda_1, lambda_2, lambda_3]. */
+#define HGMM_NODE_DOUBLES 16
+
+void hgmm_params_default(hgmm_params* p);
+
+/* Allocate a tree able to model up to max_points points with up to max_depth
+ * levels, plus all scratch that build and register need (device memory on
+ * the current device).  *out receives the handle.  Errors: HGMM_EINVAL,
+ * HGMM_ENOMEM, HGMM_ECUDA. */
+int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out);
+void hgmm_tree_destroy(hgmm_tree* t);
+
+/* Build the GMM tree of cloud d_points (n x 4 float32, device) with `depth`
+ * levels (level l holds 8^(l+1) nodes) and J components per node (must be
+ * 8).  p may be NULL for the defaults.  Enqueued on `stream`; non-finite
+ * input is reported by hgmm_sync as HGMM_ENONFINITE.
+ * Errors: HGMM_EINVAL (n < 8, J != 8, depth not in [1, max_depth],
+ * unaligned pointer), HGMM_ECAPACITY, HGMM_ECUDA. */
+int hgmm_build(hgmm_tree* t, const float* d_points, int64_t n, int32_t depth,
+               int32_t J, const hgmm_params* p, void* stream);
+
+/* Register source cloud d_src (n x 4 float32, device) to the tree: `iters`
+ * EM rounds of Algorithm 1 + Eq. 9-16 starting from d_T_init (16 float64,
+ * device, row-major; NULL = identity).  lam_c < 0 uses the build's lambda_c;
+ * lam_c = 0 disables the early stop (the paper's "GMM-Tree" variant).  The
+ * final T is written to d_T_out (16 float64, device).  If d_T_hist is not
+ * NULL it receives the T after every round (iters x 16 float64, device).
+ * Errors: HGMM_EINVAL, HGMM_ECUDA; singular normal equations are reported by
+ * hgmm_sync as HGMM_EDEGENERATE (T is then left unchanged in that round). */
+int hgmm_register(hgmm_tree* t, const float* d_src, int64_t n,
+                  const double* d_T_init, int32_t iters, float lam_c,
+                  void* stream, double* d_T_out, double* d_T_hist);
+
+/* Synchronise `stream` and return the first error the device recorded for
+ * this tree since the last hgmm_sync (HGMM_OK if none); clears it. */
+int hgmm_sync(hgmm_tree* t, void* stream);
+
+/* End-to-end convenience for callers holding host buffers: copy target and
+ * source (n x 4 float32 each, host; pinned memory is fastest) to the tree's
+ * device staging buffers, build the target's tree, register the source from
+ * h_T_init (NULL = identity) and copy the result to h_T_out (16 float64,
+ * host).  Synchronous.  Errors: as hgmm_build, hgmm_register, hgmm_sync. */
+int hgmm_register_pair_host(hgmm_tree* t, const float* h_tgt, int64_t n_tgt,
+                            const float* h_src, int64_t n_src, int32_t depth,
+                            const hgmm_params* p, const double* h_T_init,
+                            int32_t iters, void* stream, double* h_T_out);
+
+/* ---- checking / export (synchronous, host outputs) ---- */
+
+/* Node records of `level` (8^(level+1) nodes x HGMM_NODE_DOUBLES) of the
+ * last build; cap = capacity of h_nodes in doubles. */
+int hgmm_tree_export(hgmm_tree* t, int32_t level, double* h_nodes, int64_t cap);
+
+/* Node index within `level` of every input point after that level's hand-off
+ * (argmax child), in the caller's original point order (n int32). */
+int hgmm_debug_labels(hgmm_tree* t, int32_t level, int32_t* h_labels, int64_t cap);
+
+/* Root statistics of the last build: [n, mu(3), Sigma(6 upper), extent, eps]
+ * (12 float64). */
+int hgmm_debug_root(hgmm_tree* t, double* h_root12);
+
+/* Registration moments of the LAST round of the last hgmm_register: per node
+ * of every level (levels concatenated) [M0, M1_x, M1_y, M1_z] float64 with M1
+ * = sum gamma z' in the model frame (Algorithm 1, Eq. 9). */
+int hgmm_debug_reg_moments(hgmm_tree* t, double* h_m, int64_t cap);
+
+/* ---- per-kernel timing (tracing) ----
+ * hgmm_profile(t, 1) clears and starts recording a CUDA event pair around
+ * every kernel this tree launches (on the launch stream); hgmm_profile(t, 0)
+ * stops.  hgmm_profile_read synchronises the device and returns, for kernel
+ * id k in [0, HGMM_PROF_KERNELS), its name, the summed event time in ms and
+ * the number of launches recorded.  Recording adds an event pair per launch;
+ * it is meant for measurement runs, not for graph capture. */
+#define HGMM_PROF_KERNELS 16
+int hgmm_profile(hgmm_tree* t, int32_t enable);
+int hgmm_profile_read(hgmm_tree* t, int32_t kernel, const char** name, double* total_ms,
+                      int64_t* launches);
+
+/* Total node count of a tree of `depth` levels (8 + 64 + ... + 8^depth). */
+int64_t hgmm_node_count(int32_t depth);
+
+const char* hgmm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGMM_H */

@@ -1,0 +1,295 @@
+"""Thin ctypes binding of ``include/hgmm.h``.
+
+Argument marshalling only: every function below forwards to the entry point
+of the same name in ``_lib/libhgmm.so``, passing raw device pointers taken
+from PyTorch tensors (PyTorch owns the caller's device memory and streams) or
+host pointers from numpy arrays.  There is no fallback: if the compiled
+library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libhgmm.so")
+
+HGMM_OK = 0
+HGMM_EINVAL = -1
+HGMM_ENOMEM = -2
+HGMM_ECUDA = -3
+HGMM_ETIMEOUT = -4
+HGMM_EDEGENERATE = -5
+HGMM_ENONFINITE = -6
+HGMM_ECAPACITY = -7
+HGMM_J = 8
+HGMM_MAX_DEPTH = 5
+HGMM_NODE_DOUBLES = 16
+
+
+class HgmmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class hgmm_params(ctypes.Structure):
+    _fields_ = [("em_iters", ctypes.c_int32), ("n_min", ctypes.c_float),
+                ("lam_c", ctypes.c_float), ("eps_rel", ctypes.c_float),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(
+            f"{_LIB_PATH} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    P = ctypes.POINTER
+    sig = {
+        "hgmm_params_default": (None, [P(hgmm_params)]),
+        "hgmm_tree_create": (ctypes.c_int, [i64, i32, P(vp)]),
+        "hgmm_tree_destroy": (None, [vp]),
+        "hgmm_build": (ctypes.c_int, [vp, vp, i64, i32, i32, P(hgmm_params), vp]),
+        "hgmm_register": (ctypes.c_int, [vp, vp, i64, vp, i32, f32, vp, vp, vp]),
+        "hgmm_sync": (ctypes.c_int, [vp, vp]),
+        "hgmm_register_pair_host": (ctypes.c_int, [vp, vp, i64, vp, i64, i32, P(hgmm_params),
+                                                   vp, i32, vp, vp]),
+        "hgmm_tree_export": (ctypes.c_int, [vp, i32, vp, i64]),
+        "hgmm_debug_labels": (ctypes.c_int, [vp, i32, vp, i64]),
+        "hgmm_debug_root": (ctypes.c_int, [vp, vp]),
+        "hgmm_debug_reg_moments": (ctypes.c_int, [vp, vp, i64]),
+        "hgmm_node_count": (i64, [i32]),
+        "hgmm_profile": (ctypes.c_int, [vp, i32]),
+        "hgmm_profile_read": (ctypes.c_int, [vp, i32, P(ctypes.c_char_p), P(ctypes.c_double),
+                                             P(ctypes.c_int64)]),
+        "hgmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _LIB_PATH
+
+
+def strerror(code: int) -> str:
+    return _lib.hgmm_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != HGMM_OK:
+        raise HgmmError(rc, where)
+
+
+def params(em_iters=8, n_min=8.0, lam_c=0.01, eps_rel=1e-3, precision=0) -> hgmm_params:
+    p = hgmm_params()
+    _lib.hgmm_params_default(ctypes.byref(p))
+    p.em_iters, p.n_min, p.lam_c, p.eps_rel, p.precision = em_iters, n_min, lam_c, eps_rel, precision
+    return p
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_points(x, name):
+    if x.dtype != __import__("torch").float32 or x.dim() != 2 or x.shape[1] != 4:
+        raise ValueError(f"{name}: expected an (N, 4) float32 tensor")
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _dptr(x):
+    return ctypes.c_void_p(0 if x is None else x.data_ptr())
+
+
+# ---------------------------------------------------------------- entry points
+def hgmm_node_count(depth: int) -> int:
+    return int(_lib.hgmm_node_count(int(depth)))
+
+
+def hgmm_tree_create(max_points: int, max_depth: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_lib.hgmm_tree_create(int(max_points), int(max_depth), ctypes.byref(h)),
+           "hgmm_tree_create")
+    return h
+
+
+def hgmm_tree_destroy(h) -> None:
+    _lib.hgmm_tree_destroy(h)
+
+
+def hgmm_build(h, points, depth: int, J: int = HGMM_J, prm: hgmm_params | None = None,
+               stream=None) -> None:
+    _check(_lib.hgmm_build(h, _dev_points(points, "points"), points.shape[0], int(depth),
+                           int(J), None if prm is None else ctypes.byref(prm),
+                           _stream_ptr(stream)), "hgmm_build")
+
+
+def hgmm_register(h, src, T_init=None, iters: int = 30, lam_c: float = -1.0, stream=None,
+                  T_out=None, T_hist=None):
+    """Returns the device tensor T_out (4x4 float64)."""
+    import torch
+    if T_out is None:
+        T_out = torch.empty((4, 4), dtype=torch.float64, device=src.device)
+    for name, x in (("T_init", T_init), ("T_out", T_out), ("T_hist", T_hist)):
+        if x is not None and (x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous()):
+            raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
+    _check(_lib.hgmm_register(h, _dev_points(src, "src"), src.shape[0], _dptr(T_init),
+                              int(iters), float(lam_c), _stream_ptr(stream), _dptr(T_out),
+                              _dptr(T_hist)), "hgmm_register")
+    return T_out
+
+
+def hgmm_sync(h, stream=None) -> None:
+    _check(_lib.hgmm_sync(h, _stream_ptr(stream)), "hgmm_sync")
+
+
+def _host_points(x, name):
+    if hasattr(x, "data_ptr"):  # torch CPU tensor (possibly pinned)
+        if x.dtype != __import__("torch").float32 or x.dim() != 2 or x.shape[1] != 4 \
+                or x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous (N, 4) float32 host tensor")
+        return ctypes.c_void_p(x.data_ptr()), x.shape[0]
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 4:
+        raise ValueError(f"{name}: expected (N, 4) float32")
+    return ctypes.c_void_p(a.ctypes.data), a.shape[0], a
+
+
+def hgmm_register_pair_host(h, tgt, src, depth: int, prm: hgmm_params | None = None,
+                            T_init=None, iters: int = 30, stream=None) -> np.ndarray:
+    t_ptr, n_t, *keep_t = _host_points(tgt, "tgt")
+    s_ptr, n_s, *keep_s = _host_points(src, "src")
+    Ti = None if T_init is None else np.ascontiguousarray(T_init, dtype=np.float64)
+    out = np.empty((4, 4), dtype=np.float64)
+    _check(_lib.hgmm_register_pair_host(
+        h, t_ptr, n_t, s_ptr, n_s, int(depth), None if prm is None else ctypes.byref(prm),
+        None if Ti is None else ctypes.c_void_p(Ti.ctypes.data), int(iters),
+        _stream_ptr(stream), ctypes.c_void_p(out.ctypes.data)), "hgmm_register_pair_host")
+    del keep_t, keep_s
+    return out
+
+
+def hgmm_tree_export(h, level: int, n_nodes: int) -> np.ndarray:
+    out = np.empty((n_nodes, HGMM_NODE_DOUBLES), dtype=np.float64)
+    _check(_lib.hgmm_tree_export(h, int(level), ctypes.c_void_p(out.ctypes.data), out.size),
+           "hgmm_tree_export")
+    return out
+
+
+def hgmm_debug_labels(h, level: int, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.int32)
+    _check(_lib.hgmm_debug_labels(h, int(level), ctypes.c_void_p(out.ctypes.data), n),
+           "hgmm_debug_labels")
+    return out
+
+
+def hgmm_debug_root(h) -> np.ndarray:
+    out = np.empty(12, dtype=np.float64)
+    _check(_lib.hgmm_debug_root(h, ctypes.c_void_p(out.ctypes.data)), "hgmm_debug_root")
+    return out
+
+
+def hgmm_debug_reg_moments(h, n_nodes: int) -> np.ndarray:
+    out = np.empty((n_nodes, 4), dtype=np.float64)
+    _check(_lib.hgmm_debug_reg_moments(h, ctypes.c_void_p(out.ctypes.data), out.size),
+           "hgmm_debug_reg_moments")
+    return out
+
+
+HGMM_PROF_KERNELS = 16
+
+
+def hgmm_profile(h, enable: bool) -> None:
+    _check(_lib.hgmm_profile(h, 1 if enable else 0), "hgmm_profile")
+
+
+def hgmm_profile_read(h) -> dict:
+    """{kernel name: (total ms, launches)} of the launches recorded since
+    hgmm_profile(h, True)."""
+    out = {}
+    for k in range(HGMM_PROF_KERNELS):
+        name = ctypes.c_char_p()
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _check(_lib.hgmm_profile_read(h, k, ctypes.byref(name), ctypes.byref(ms),
+                                      ctypes.byref(cnt)), "hgmm_profile_read")
+        out[name.value.decode()] = (ms.value, cnt.value)
+    return out
+
+
+# ---------------------------------------------------------------- convenience
+class Tree:
+    """Owns one hgmm_tree (device memory sized for max_points / max_depth)."""
+
+    def __init__(self, max_points: int, max_depth: int = 4):
+        self.handle = hgmm_tree_create(max_points, max_depth)
+        self.max_points = max_points
+        self.max_depth = max_depth
+        self.n = 0
+        self.depth = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hgmm_tree_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, points, depth: int, prm: hgmm_params | None = None, stream=None):
+        hgmm_build(self.handle, points, depth, HGMM_J, prm, stream)
+        self.n, self.depth = int(points.shape[0]), int(depth)
+        return self
+
+    def register(self, src, T_init=None, iters: int = 30, lam_c: float = -1.0, stream=None,
+                 T_out=None, T_hist=None):
+        return hgmm_register(self.handle, src, T_init, iters, lam_c, stream, T_out, T_hist)
+
+    def sync(self, stream=None):
+        hgmm_sync(self.handle, stream)
+
+    def export(self, level: int) -> dict:
+        m = 8 ** (level + 1)
+        a = hgmm_tree_export(self.handle, level, m)
+        S = np.empty((m, 3, 3))
+        iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+        for k, (i, j) in enumerate(iu):
+            S[:, i, j] = a[:, 4 + k]
+            S[:, j, i] = a[:, 4 + k]
+        return {"pi": a[:, 0], "mu": a[:, 1:4], "Sigma": S, "live": a[:, 10] > 0.5,
+                "count": a[:, 11].astype(np.int64), "complexity": a[:, 12], "lam": a[:, 13:16]}
+
+    def labels(self, level: int) -> np.ndarray:
+        return hgmm_debug_labels(self.handle, level, self.n)
+
+    def root(self) -> dict:
+        r = hgmm_debug_root(self.handle)
+        S = np.array([[r[4], r[5], r[6]], [r[5], r[7], r[8]], [r[6], r[8], r[9]]])
+        return {"n": r[0], "mu": r[1:4], "Sigma": S, "extent": r[10], "eps": r[11]}
+
+    def profile(self, enable: bool):
+        hgmm_profile(self.handle, enable)
+
+    def profile_read(self) -> dict:
+        return hgmm_profile_read(self.handle)
+
+    def reg_moments(self) -> np.ndarray:
+        return hgmm_debug_reg_moments(self.handle, hgmm_node_count(self.depth))

@@ -1,0 +1,343 @@
+// C ABI of the HGMM library: tree lifetime, argument checking, the
+// host-buffer convenience call and the export / checking entry points.
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+#include "hgmm_internal.cuh"
+
+using namespace hgmm;
+
+namespace {
+
+bool ok(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    fprintf(stderr, "hgmm: %s: %s\n", what, cudaGetErrorString(e));
+    return false;
+}
+
+template <typename T>
+bool dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return true;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) == cudaSuccess;
+}
+
+void clear_prof(hgmm_tree* t) {
+    for (auto& r : t->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    t->prof.clear();
+}
+
+const char* const kKernelNames[HGMM_PROF_KERNELS] = {
+    "root_partial", "root_final", "init_children", "make_items", "fill_items", "estep",
+    "mstep", "assign", "child_offsets", "scatter", "finalize", "reg_init", "descend",
+    "reg_mstep", "copy_T", "labels"};
+
+void free_tree(hgmm_tree* t) {
+    if (!t) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(t->device);
+    clear_prof(t);
+    void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
+                    t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
+                    t->item_off, t->root, t->root_part, t->status, t->reg_acc, t->reg_part,
+                    t->reg_counter, t->reg_T, t->reg_Rt, t->reg_dbg, t->stage_tgt,
+                    t->stage_src, t->stage_T};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int l = 0; l < HGMM_MAX_DEPTH; ++l)
+        if (t->perm[l]) cudaFree(t->perm[l]);
+    cudaSetDevice(cur);
+    delete t;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int check_device(const hgmm_tree* t) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return HGMM_ECUDA;
+    return cur == t->device ? HGMM_OK : HGMM_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t hgmm_node_count(int32_t depth) {
+    if (depth < 1 || depth > HGMM_MAX_DEPTH) return 0;
+    return level_offset(depth);  // sum of 8^(l+1) for l < depth
+}
+
+void hgmm_params_default(hgmm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->em_iters = 8;
+    p->n_min = 8.0f;
+    p->lam_c = 0.01f;
+    p->eps_rel = 1e-3f;
+    p->precision = 0;
+}
+
+const char* hgmm_strerror(int code) {
+    switch (code) {
+        case HGMM_OK: return "ok";
+        case HGMM_EINVAL: return "invalid argument";
+        case HGMM_ENOMEM: return "device allocation failed";
+        case HGMM_ECUDA: return "CUDA error";
+        case HGMM_ETIMEOUT: return "device wait timed out";
+        case HGMM_EDEGENERATE: return "singular normal equations";
+        case HGMM_ENONFINITE: return "non-finite input coordinates";
+        case HGMM_ECAPACITY: return "size exceeds the tree's capacity";
+        default: return "unknown error";
+    }
+}
+
+int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
+    if (!out) return HGMM_EINVAL;
+    *out = nullptr;
+    if (max_points < 8 || max_points > (int64_t(1) << 30) || max_depth < 1 ||
+        max_depth > HGMM_MAX_DEPTH)
+        return HGMM_EINVAL;
+    hgmm_tree* t = new hgmm_tree();
+    if (!ok(cudaGetDevice(&t->device), "cudaGetDevice")) { delete t; return HGMM_ECUDA; }
+    cudaDeviceProp prop;
+    if (!ok(cudaGetDeviceProperties(&prop, t->device), "cudaGetDeviceProperties")) {
+        delete t;
+        return HGMM_ECUDA;
+    }
+    t->n_sm = prop.multiProcessorCount;
+    t->cap = max_points;
+    t->max_depth = max_depth;
+    t->max_nodes = level_offset(max_depth);
+    // widest parent level: level max_depth-2 (8^(max_depth-1) nodes), or the root
+    const int64_t parents = max_depth >= 2 ? level_size(max_depth - 2) : 1;
+    t->max_items = (max_points + TILE - 1) / TILE + parents;
+    t->est_grid = t->n_sm * 2;
+    t->reg_grid = t->n_sm * 4;
+    const int64_t nb = (t->max_nodes + MSTEP_THREADS - 1) / MSTEP_THREADS;
+    bool good = true;
+    good &= dalloc(&t->est, t->max_nodes);
+    good &= dalloc(&t->stat, t->max_nodes);
+    good &= dalloc(&t->seg_start, t->max_nodes);
+    good &= dalloc(&t->seg_count, t->max_nodes);
+    good &= dalloc(&t->pts[0], max_points);
+    good &= dalloc(&t->pts[1], max_points);
+    for (int l = 0; l < max_depth; ++l) good &= dalloc(&t->perm[l], max_points);
+    good &= dalloc(&t->codes, max_points);
+    good &= dalloc(&t->items, t->max_items);
+    good &= dalloc(&t->item_range, 2 * std::max<int64_t>(parents, 1));
+    good &= dalloc(&t->meta, 4);
+    good &= dalloc(&t->partials, t->max_items * NPART);
+    good &= dalloc(&t->item_cnt, t->max_items * 8);
+    good &= dalloc(&t->item_off, t->max_items * 8);
+    good &= dalloc(&t->root, 1);
+    good &= dalloc(&t->root_part, int64_t(t->est_grid) * 32);
+    good &= dalloc(&t->status, 1);
+    good &= dalloc(&t->reg_acc, 4 * t->max_nodes);
+    good &= dalloc(&t->reg_part, 27 * nb);
+    good &= dalloc(&t->reg_counter, 1);
+    good &= dalloc(&t->reg_T, 16);
+    good &= dalloc(&t->reg_Rt, 12);
+    good &= dalloc(&t->reg_dbg, 4 * t->max_nodes);
+    good &= dalloc(&t->stage_tgt, max_points);
+    good &= dalloc(&t->stage_src, max_points);
+    good &= dalloc(&t->stage_T, 32);
+    if (!good) {
+        free_tree(t);
+        return HGMM_ENOMEM;
+    }
+    good &= ok(cudaMemset(t->status, 0, sizeof(int)), "cudaMemset");
+    good &= ok(cudaMemset(t->reg_counter, 0, sizeof(unsigned)), "cudaMemset");
+    good &= ok(cudaMemset(t->reg_acc, 0, 4 * t->max_nodes * sizeof(unsigned long long)), "cudaMemset");
+    good &= ok(cudaMemset(t->stat, 0, t->max_nodes * sizeof(NodeStat)), "cudaMemset");
+    good &= ok(cudaMemset(t->seg_count, 0, t->max_nodes * sizeof(int)), "cudaMemset");
+    good &= ok(cudaMemset(t->seg_start, 0, t->max_nodes * sizeof(int)), "cudaMemset");
+    good &= ok(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (!good) {
+        free_tree(t);
+        return HGMM_ECUDA;
+    }
+    *out = t;
+    return HGMM_OK;
+}
+
+void hgmm_tree_destroy(hgmm_tree* t) { free_tree(t); }
+
+int hgmm_build(hgmm_tree* t, const float* d_points, int64_t n, int32_t depth, int32_t J,
+               const hgmm_params* p, void* stream) {
+    if (!t || !d_points) return HGMM_EINVAL;
+    if (J != HGMM_J || n < 8 || depth < 1 || depth > HGMM_MAX_DEPTH) return HGMM_EINVAL;
+    if (!aligned16(d_points)) return HGMM_EINVAL;
+    if (n > t->cap || depth > t->max_depth) return HGMM_ECAPACITY;
+    if (int rc = check_device(t)) return rc;
+    hgmm_params prm;
+    if (p) {
+        prm = *p;
+        if (prm.em_iters < 0 || prm.em_iters > 1000 || !(prm.eps_rel >= 0.f) ||
+            !(prm.n_min >= 0.f) || !(prm.lam_c >= 0.f))
+            return HGMM_EINVAL;
+    } else {
+        hgmm_params_default(&prm);
+    }
+    t->n = n;
+    t->depth = depth;
+    t->prm = prm;
+    t->built = true;
+    return hgmm_build_impl(t, reinterpret_cast<const float4*>(d_points), n, depth, prm,
+                           static_cast<cudaStream_t>(stream));
+}
+
+int hgmm_register(hgmm_tree* t, const float* d_src, int64_t n, const double* d_T_init,
+                  int32_t iters, float lam_c, void* stream, double* d_T_out, double* d_T_hist) {
+    if (!t || !d_src || n < 1 || iters < 0 || !t->built) return HGMM_EINVAL;
+    if (!aligned16(d_src)) return HGMM_EINVAL;
+    if (n > (int64_t(1) << 31) - 1) return HGMM_ECAPACITY;
+    if (int rc = check_device(t)) return rc;
+    t->reg_n = n;
+    return hgmm_register_impl(t, reinterpret_cast<const float4*>(d_src), n, d_T_init, iters,
+                              lam_c, static_cast<cudaStream_t>(stream), d_T_out, d_T_hist);
+}
+
+int hgmm_sync(hgmm_tree* t, void* stream) {
+    if (!t) return HGMM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int st = 0;
+    if (!ok(cudaMemcpyAsync(&st, t->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy"))
+        return HGMM_ECUDA;
+    if (!ok(cudaStreamSynchronize(s), "cudaStreamSynchronize")) return HGMM_ECUDA;
+    if (st) {
+        const int zero = 0;
+        if (!ok(cudaMemcpy(t->status, &zero, sizeof(int), cudaMemcpyHostToDevice), "status reset"))
+            return HGMM_ECUDA;
+    }
+    if (st & ST_NONFINITE) return HGMM_ENONFINITE;
+    if (st & ST_TIMEOUT) return HGMM_ETIMEOUT;
+    if (st & ST_DEGENERATE) return HGMM_EDEGENERATE;
+    return HGMM_OK;
+}
+
+int hgmm_register_pair_host(hgmm_tree* t, const float* h_tgt, int64_t n_tgt, const float* h_src,
+                            int64_t n_src, int32_t depth, const hgmm_params* p,
+                            const double* h_T_init, int32_t iters, void* stream,
+                            double* h_T_out) {
+    if (!t || !h_tgt || !h_src || !h_T_out) return HGMM_EINVAL;
+    if (n_tgt > t->cap || n_src > t->cap) return HGMM_ECAPACITY;
+    if (n_tgt < 8 || n_src < 1) return HGMM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!ok(cudaMemcpyAsync(t->stage_tgt, h_tgt, size_t(n_tgt) * 16, cudaMemcpyHostToDevice, s), "H2D"))
+        return HGMM_ECUDA;
+    if (!ok(cudaMemcpyAsync(t->stage_src, h_src, size_t(n_src) * 16, cudaMemcpyHostToDevice, s), "H2D"))
+        return HGMM_ECUDA;
+    const double* dTi = nullptr;
+    if (h_T_init) {
+        if (!ok(cudaMemcpyAsync(t->stage_T, h_T_init, 16 * sizeof(double), cudaMemcpyHostToDevice, s), "H2D"))
+            return HGMM_ECUDA;
+        dTi = t->stage_T;
+    }
+    int rc = hgmm_build(t, reinterpret_cast<const float*>(t->stage_tgt), n_tgt, depth, HGMM_J, p, stream);
+    if (rc) return rc;
+    rc = hgmm_register(t, reinterpret_cast<const float*>(t->stage_src), n_src, dTi, iters, -1.f,
+                       stream, t->stage_T + 16, nullptr);
+    if (rc) return rc;
+    if (!ok(cudaMemcpyAsync(h_T_out, t->stage_T + 16, 16 * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"))
+        return HGMM_ECUDA;
+    return hgmm_sync(t, stream);
+}
+
+int hgmm_tree_export(hgmm_tree* t, int32_t level, double* h_nodes, int64_t cap) {
+    if (!t || !h_nodes || !t->built || level < 0 || level >= t->depth) return HGMM_EINVAL;
+    const int64_t m = level_size(level);
+    if (cap < m * HGMM_NODE_DOUBLES) return HGMM_ECAPACITY;
+    std::vector<NodeStat> st(m);
+    std::vector<int> cnt(m);
+    const int64_t off = level_offset(level);
+    if (!ok(cudaDeviceSynchronize(), "sync")) return HGMM_ECUDA;
+    if (!ok(cudaMemcpy(st.data(), t->stat + off, m * sizeof(NodeStat), cudaMemcpyDeviceToHost), "D2H"))
+        return HGMM_ECUDA;
+    if (!ok(cudaMemcpy(cnt.data(), t->seg_count + off, m * sizeof(int), cudaMemcpyDeviceToHost), "D2H"))
+        return HGMM_ECUDA;
+    for (int64_t i = 0; i < m; ++i) {
+        double* o = h_nodes + i * HGMM_NODE_DOUBLES;
+        const NodeStat& s = st[i];
+        o[0] = s.live ? s.pi : 0.0;
+        for (int a = 0; a < 3; ++a) o[1 + a] = s.mu[a];
+        for (int v = 0; v < 6; ++v) o[4 + v] = s.S[v];
+        o[10] = s.live ? 1.0 : 0.0;
+        o[11] = double(cnt[i]);
+        o[12] = s.complexity;
+        for (int a = 0; a < 3; ++a) o[13 + a] = s.lam[a];
+    }
+    return HGMM_OK;
+}
+
+int hgmm_debug_labels(hgmm_tree* t, int32_t level, int32_t* h_labels, int64_t cap) {
+    if (!t || !h_labels || !t->built || level < 0 || level >= t->depth) return HGMM_EINVAL;
+    if (cap < t->n) return HGMM_ECAPACITY;
+    // the hand-off codes are dead after the build: reuse them as the output
+    int* d = reinterpret_cast<int*>(t->codes);
+    int rc = hgmm_export_labels_impl(t, level, d, nullptr);
+    if (rc == HGMM_OK &&
+        !ok(cudaMemcpy(h_labels, d, size_t(t->n) * sizeof(int), cudaMemcpyDeviceToHost), "D2H"))
+        rc = HGMM_ECUDA;
+    return rc;
+}
+
+int hgmm_debug_root(hgmm_tree* t, double* h_root12) {
+    if (!t || !h_root12 || !t->built) return HGMM_EINVAL;
+    RootDev r;
+    if (!ok(cudaDeviceSynchronize(), "sync")) return HGMM_ECUDA;
+    if (!ok(cudaMemcpy(&r, t->root, sizeof(r), cudaMemcpyDeviceToHost), "D2H")) return HGMM_ECUDA;
+    h_root12[0] = r.n;
+    for (int a = 0; a < 3; ++a) h_root12[1 + a] = r.mu[a];
+    for (int v = 0; v < 6; ++v) h_root12[4 + v] = r.S[v];
+    h_root12[10] = r.extent;
+    h_root12[11] = r.eps;
+    return HGMM_OK;
+}
+
+int hgmm_debug_reg_moments(hgmm_tree* t, double* h_m, int64_t cap) {
+    if (!t || !h_m || !t->built) return HGMM_EINVAL;
+    const int64_t m = hgmm_node_count(t->depth);
+    if (cap < 4 * m) return HGMM_ECAPACITY;
+    if (!ok(cudaDeviceSynchronize(), "sync")) return HGMM_ECUDA;
+    if (!ok(cudaMemcpy(h_m, t->reg_dbg, size_t(4 * m) * sizeof(double), cudaMemcpyDeviceToHost), "D2H"))
+        return HGMM_ECUDA;
+    return HGMM_OK;
+}
+
+int hgmm_profile(hgmm_tree* t, int32_t enable) {
+    if (!t) return HGMM_EINVAL;
+    if (enable) {
+        if (!ok(cudaDeviceSynchronize(), "sync")) return HGMM_ECUDA;
+        clear_prof(t);
+    }
+    t->prof_on = enable != 0;
+    return HGMM_OK;
+}
+
+int hgmm_profile_read(hgmm_tree* t, int32_t kernel, const char** name, double* total_ms,
+                      int64_t* launches) {
+    static_assert(K_COUNT == HGMM_PROF_KERNELS, "kernel table");
+    if (!t || kernel < 0 || kernel >= HGMM_PROF_KERNELS) return HGMM_EINVAL;
+    if (!ok(cudaDeviceSynchronize(), "sync")) return HGMM_ECUDA;
+    double ms = 0.0;
+    int64_t cnt = 0;
+    for (const auto& r : t->prof) {
+        if (r.id != kernel) continue;
+        float x = 0.f;
+        if (!ok(cudaEventElapsedTime(&x, r.a, r.b), "cudaEventElapsedTime")) return HGMM_ECUDA;
+        ms += x;
+        ++cnt;
+    }
+    if (name) *name = kKernelNames[kernel];
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = cnt;
+    return HGMM_OK;
+}
+
+}  // extern "C"

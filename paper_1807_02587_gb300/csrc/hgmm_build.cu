@@ -1,0 +1,848 @@
+// GMM-tree build on the GPU (the model construction Sec. 3 takes from its
+// reference [33]; 8-component nodes, Sec. 4.1).
+//
+// Per level l (children = the 8^(l+1) nodes of level l, parents = level l-1
+// or the root):
+//   k_init_children   PCA-octant initial children of every parent (FP64 eigen)
+//   k_make_items      split each parent's contiguous point segment into work
+//                     items of <= TILE points, laid out parent by parent
+//   K x { k_estep     per point: Eq. 3 posteriors over the 8 children of its
+//                     parent (FP32, log2 domain, max-subtracted exp2) and the
+//                     gamma-weighted moments S0, S1, S2 of every child,
+//                     centred on the child's current mean; compensated sums;
+//                     one partial per (CTA, parent) run
+//         k_mstep }   per parent: reduce its runs, FP64 M-step, Cholesky, the
+//                     dead-child rule, new FP32 E-step constants
+//   k_assign          argmax hand-off (ties -> lowest index) with in-item ranks
+//   k_child_offsets   per parent: child segment starts and per-item offsets
+//   k_scatter         stable 8-way partition of every parent's segment
+//   k_finalize        FP64 eigen, complexity, precision matrix of level l
+#include <cstdio>
+
+#include "hgmm_internal.cuh"
+#include "hgmm_math.cuh"
+
+namespace hgmm {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int64_t d_level_offset(int l) {
+    return ((int64_t(1) << (3 * (l + 1))) - 8) / 7;
+}
+
+// ---------------------------------------------------------------- root stats
+// partial layout (32 floats): [0..17] 9 compensated pairs of sum (z - z0) and
+// sum (z - z0)(z - z0)^T, [18..20] min, [21..23] max, [24] non-finite count.
+__global__ void __launch_bounds__(256) k_root_partial(const float4* __restrict__ pts, int n,
+                                                       float* __restrict__ part) {
+    __shared__ float sm[8][32];
+    const float4 z0 = pts[0];
+    float in[9] = {}, s[9] = {}, c[9] = {};
+    float mn[3] = {CUDART_INF_F, CUDART_INF_F, CUDART_INF_F};
+    float mx[3] = {-CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F};
+    int bad = 0, cnt = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 z = pts[i];
+        if (!(isfinite(z.x) && isfinite(z.y) && isfinite(z.z))) {
+            ++bad;
+            continue;
+        }
+        const float dx = z.x - z0.x, dy = z.y - z0.y, dz = z.z - z0.z;
+        in[0] += dx; in[1] += dy; in[2] += dz;
+        in[3] = fmaf(dx, dx, in[3]); in[4] = fmaf(dx, dy, in[4]); in[5] = fmaf(dx, dz, in[5]);
+        in[6] = fmaf(dy, dy, in[6]); in[7] = fmaf(dy, dz, in[7]); in[8] = fmaf(dz, dz, in[8]);
+        mn[0] = fminf(mn[0], z.x); mn[1] = fminf(mn[1], z.y); mn[2] = fminf(mn[2], z.z);
+        mx[0] = fmaxf(mx[0], z.x); mx[1] = fmaxf(mx[1], z.y); mx[2] = fmaxf(mx[2], z.z);
+        if (++cnt == 16) {
+#pragma unroll
+            for (int v = 0; v < 9; ++v) { pair_add(s[v], c[v], in[v], 0.f); in[v] = 0.f; }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 9; ++v) pair_add(s[v], c[v], in[v], 0.f);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) {
+            const float s2 = __shfl_xor_sync(FULL, s[v], off);
+            const float c2 = __shfl_xor_sync(FULL, c[v], off);
+            pair_add(s[v], c[v], s2, c2);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(FULL, mn[a], off));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(FULL, mx[a], off));
+        }
+        bad += __shfl_xor_sync(FULL, bad, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int v = 0; v < 9; ++v) { sm[warp][2 * v] = s[v]; sm[warp][2 * v + 1] = c[v]; }
+        for (int a = 0; a < 3; ++a) { sm[warp][18 + a] = mn[a]; sm[warp][21 + a] = mx[a]; }
+        sm[warp][24] = __int_as_float(bad);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float S[9], C[9], MN[3], MX[3];
+        int B = 0;
+        for (int v = 0; v < 9; ++v) { S[v] = 0.f; C[v] = 0.f; }
+        for (int a = 0; a < 3; ++a) { MN[a] = CUDART_INF_F; MX[a] = -CUDART_INF_F; }
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            for (int v = 0; v < 9; ++v) pair_add(S[v], C[v], sm[w][2 * v], sm[w][2 * v + 1]);
+            for (int a = 0; a < 3; ++a) {
+                MN[a] = fminf(MN[a], sm[w][18 + a]);
+                MX[a] = fmaxf(MX[a], sm[w][21 + a]);
+            }
+            B += __float_as_int(sm[w][24]);
+        }
+        float* o = part + 32 * blockIdx.x;
+        for (int v = 0; v < 9; ++v) { o[2 * v] = S[v]; o[2 * v + 1] = C[v]; }
+        for (int a = 0; a < 3; ++a) { o[18 + a] = MN[a]; o[21 + a] = MX[a]; }
+        o[24] = __int_as_float(B);
+    }
+}
+
+__global__ void k_root_final(const float4* __restrict__ pts, const float* __restrict__ part,
+                             int nblocks, int n, float eps_rel, RootDev* __restrict__ root,
+                             int* __restrict__ status) {
+    if (threadIdx.x != 0) return;
+    float S[9], C[9], MN[3], MX[3];
+    int B = 0;
+    for (int v = 0; v < 9; ++v) { S[v] = 0.f; C[v] = 0.f; }
+    for (int a = 0; a < 3; ++a) { MN[a] = CUDART_INF_F; MX[a] = -CUDART_INF_F; }
+    for (int b = 0; b < nblocks; ++b) {
+        const float* o = part + 32 * b;
+        for (int v = 0; v < 9; ++v) pair_add(S[v], C[v], o[2 * v], o[2 * v + 1]);
+        for (int a = 0; a < 3; ++a) { MN[a] = fminf(MN[a], o[18 + a]); MX[a] = fmaxf(MX[a], o[21 + a]); }
+        B += __float_as_int(o[24]);
+    }
+    if (B > 0) atomicOr(status, ST_NONFINITE);
+    const float4 z0 = pts[0];
+    const double z0d[3] = {z0.x, z0.y, z0.z};
+    const double nn = double(n);
+    double m1[3], m2[6];
+    for (int a = 0; a < 3; ++a) m1[a] = (double(S[a]) + double(C[a])) / nn;
+    for (int v = 0; v < 6; ++v) m2[v] = (double(S[3 + v]) + double(C[3 + v])) / nn;
+    root->n = nn;
+    for (int a = 0; a < 3; ++a) root->mu[a] = z0d[a] + m1[a];
+    root->S[0] = m2[0] - m1[0] * m1[0];
+    root->S[1] = m2[1] - m1[0] * m1[1];
+    root->S[2] = m2[2] - m1[0] * m1[2];
+    root->S[3] = m2[3] - m1[1] * m1[1];
+    root->S[4] = m2[4] - m1[1] * m1[2];
+    root->S[5] = m2[5] - m1[2] * m1[2];
+    double e2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double d = double(MX[a]) - double(MN[a]);
+        e2 += d * d;
+    }
+    root->extent = sqrt(e2);
+    const double e = double(eps_rel) * root->extent;
+    root->eps = e * e;
+}
+
+// ---------------------------------------------------------------- init
+// One CTA per parent; threads 0..7 build child c.
+__global__ void k_init_children(int level, const RootDev* __restrict__ root,
+                                NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
+                                const int* __restrict__ seg_count, int* __restrict__ status) {
+    __shared__ double lam[3], V[9], mu_p[3], S_p[6];
+    __shared__ int alive;
+    const int p = blockIdx.x;
+    const int64_t child0 = d_level_offset(level) + 8 * int64_t(p);
+    if (threadIdx.x == 0) {
+        if (level == 0) {
+            for (int a = 0; a < 3; ++a) mu_p[a] = root->mu[a];
+            for (int v = 0; v < 6; ++v) S_p[v] = root->S[v];
+            alive = 1;
+        } else {
+            const int64_t g = d_level_offset(level - 1) + p;
+            const NodeStat& ps = stat[g];
+            for (int a = 0; a < 3; ++a) mu_p[a] = ps.mu[a];
+            for (int v = 0; v < 6; ++v) S_p[v] = ps.S[v];
+            alive = (ps.live && seg_count[g] > 0) ? 1 : 0;
+        }
+        if (alive) jacobi_eig3(S_p, lam, V);
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c >= 8) return;
+    NodeStat& cs = stat[child0 + c];
+    NodeEst& ce = est[child0 + c];
+    if (!alive) {
+        cs.live = 0;
+        cs.pi = 0.0;
+        for (int a = 0; a < 3; ++a) cs.mu[a] = mu_p[a];
+        for (int v = 0; v < 6; ++v) cs.S[v] = 0.0;
+        dead_est(mu_p, ce);
+        return;
+    }
+    const double eps = root->eps;
+    double mu[3];
+    for (int a = 0; a < 3; ++a) {
+        double acc = mu_p[a];
+        for (int b = 0; b < 3; ++b) {
+            const double sgn = ((c >> b) & 1) ? 1.0 : -1.0;
+            acc += sgn * 0.5 * sqrt(fmax(lam[b], 0.0)) * V[a * 3 + b];
+        }
+        mu[a] = acc;
+    }
+    double S[6];
+    for (int v = 0; v < 6; ++v) S[v] = S_p[v] * 0.25;
+    S[0] += eps; S[3] += eps; S[5] += eps;
+    cs.live = 1;
+    cs.pi = 0.125;
+    for (int a = 0; a < 3; ++a) cs.mu[a] = mu[a];
+    for (int v = 0; v < 6; ++v) cs.S[v] = S[v];
+    if (!pack_est(0.125, mu, S, eps, 0.f, ce)) atomicOr(status, ST_CHOL);
+}
+
+// ---------------------------------------------------------------- items
+// Single CTA of 1024 threads: exclusive scan over parents of their item counts.
+__global__ void __launch_bounds__(1024) k_make_items(int level, int n, int n_parents,
+                                                     const int* __restrict__ seg_start,
+                                                     const int* __restrict__ seg_count,
+                                                     const NodeStat* __restrict__ stat,
+                                                     Item* __restrict__ items,
+                                                     int* __restrict__ item_range,
+                                                     int* __restrict__ meta, int est_grid) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int64_t poff = level == 0 ? 0 : d_level_offset(level - 1);
+    for (int base = 0; base < n_parents; base += blockDim.x) {
+        const int p = base + threadIdx.x;
+        int count = 0;
+        if (p < n_parents) {
+            if (level == 0) {
+                count = n;
+            } else {
+                const int64_t g = poff + p;
+                count = stat[g].live ? seg_count[g] : 0;
+            }
+        }
+        const int k = (count + TILE - 1) / TILE;
+        // block exclusive scan of k
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int x = k;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(FULL, w, off);
+                if (lane >= off) w += y;
+            }
+            warp_tot[lane] = w;  // inclusive
+        }
+        __syncthreads();
+        const int excl = carry + (warp ? warp_tot[warp - 1] : 0) + x - k;
+        if (p < n_parents) {
+            item_range[2 * p] = excl;
+            item_range[2 * p + 1] = excl + k;
+            // the item list itself is written in parallel by k_fill_items
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        meta[0] = carry;
+        meta[1] = max(1, (carry + est_grid - 1) / est_grid);
+    }
+}
+
+// One thread per item: locate its parent (largest p with begin(p) <= j; an
+// empty parent shares its begin with the next one, which owns j) and write it.
+__global__ void k_fill_items(int level, int n, int n_parents, const int* __restrict__ seg_start,
+                             const int* __restrict__ seg_count,
+                             const int* __restrict__ item_range, const int* __restrict__ meta,
+                             Item* __restrict__ items) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= meta[0]) return;
+    int lo = 0, hi = n_parents - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_range[2 * mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    const int p = lo;
+    const int r = j - item_range[2 * p];
+    int start = 0, count = n;
+    if (level > 0) {
+        const int64_t g = d_level_offset(level - 1) + p;
+        start = seg_start[g];
+        count = seg_count[g];
+    }
+    Item it;
+    it.parent = p;
+    it.start = start + r * TILE;
+    it.count = min(TILE, count - r * TILE);
+    it.pad = 0;
+    items[j] = it;
+}
+
+// ---------------------------------------------------------------- E-step
+// Lane layout: a quad of 4 lanes handles one point, lane k of the quad owns
+// children 2k and 2k+1 (their constants live in registers); a warp handles 8
+// points per step, the CTA 64.  Each lane accumulates the 10 moments of its
+// two children: plain FP32 over up to 16 points, then folded into a
+// compensated (sum, error) pair.
+struct ChildRegs {
+    float mx, my, mz, C, w00, w10, w11, w20, w21, w22;
+};
+
+__device__ __forceinline__ void load_child(const NodeEst* __restrict__ e, ChildRegs& r) {
+    const float4 a = e->a, b = e->b, c = e->c;
+    r.mx = a.x; r.my = a.y; r.mz = a.z; r.C = a.w;
+    r.w00 = b.x; r.w10 = b.y; r.w11 = b.z; r.w20 = b.w;
+    r.w21 = c.x; r.w22 = c.y;
+}
+
+// log2(pi N(z | child)) and the centred offset e = z - mu.
+__device__ __forceinline__ float child_score(const ChildRegs& r, float zx, float zy, float zz,
+                                             float& ex, float& ey, float& ez) {
+    ex = zx - r.mx;
+    ey = zy - r.my;
+    ez = zz - r.mz;
+    const float d0 = r.w00 * ex;
+    const float d1 = fmaf(r.w11, ey, r.w10 * ex);
+    const float d2 = fmaf(r.w22, ez, fmaf(r.w21, ey, r.w20 * ex));
+    float s = fmaf(-d0, d0, r.C);
+    s = fmaf(-d1, d1, s);
+    s = fmaf(-d2, d2, s);
+    return s;
+}
+
+__device__ __forceinline__ void accum10(float* a, float g, float ex, float ey, float ez) {
+    const float gx = g * ex, gy = g * ey, gz = g * ez;
+    a[0] += g;
+    a[1] += gx;
+    a[2] += gy;
+    a[3] += gz;
+    a[4] = fmaf(gx, ex, a[4]);
+    a[5] = fmaf(gx, ey, a[5]);
+    a[6] = fmaf(gx, ez, a[6]);
+    a[7] = fmaf(gy, ey, a[7]);
+    a[8] = fmaf(gy, ez, a[8]);
+    a[9] = fmaf(gz, ez, a[9]);
+}
+
+template <bool COMP>
+__device__ __forceinline__ void fold20(float* in, float* s, float* c) {
+#pragma unroll
+    for (int v = 0; v < 20; ++v) {
+        if (COMP) {
+            float t, e;
+            two_sum(s[v], in[v], t, e);
+            s[v] = t;
+            c[v] += e;
+        } else {
+            s[v] += in[v];
+        }
+        in[v] = 0.f;
+    }
+}
+
+// Block-wide reduction of the (s, c) accumulators into partial slot `run`.
+template <bool COMP>
+__device__ __forceinline__ void flush_run(float* s, float* c, float2 (*red)[NPART],
+                                          float2* __restrict__ out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, k = lane & 3;
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+#pragma unroll
+        for (int v = 0; v < 20; ++v) {
+            const float s2 = __shfl_xor_sync(FULL, s[v], off);
+            const float c2 = __shfl_xor_sync(FULL, c[v], off);
+            if (COMP) pair_add(s[v], c[v], s2, c2);
+            else s[v] += s2;
+        }
+    }
+    if (lane < 4) {
+#pragma unroll
+        for (int v = 0; v < 20; ++v) red[warp][k * 20 + v] = make_float2(s[v], COMP ? c[v] : 0.f);
+    }
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        float S = 0.f, Cc = 0.f;
+        for (int w = 0; w < EST_THREADS / 32; ++w) {
+            const float2 x = red[w][threadIdx.x];
+            if (COMP) pair_add(S, Cc, x.x, x.y);
+            else S += x.x;
+        }
+        out[threadIdx.x] = make_float2(S, Cc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 20; ++v) { s[v] = 0.f; c[v] = 0.f; }
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(EST_THREADS, 2)
+k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
+        const int* __restrict__ meta, const NodeEst* __restrict__ est_lvl,
+        float2* __restrict__ partials) {
+    __shared__ float2 red[EST_THREADS / 32][NPART];
+    const int n_items = meta[0];
+    const int C = meta[1];
+    const int ib = blockIdx.x * C;
+    const int ie = min(ib + C, n_items);
+    if (ib >= ie) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 2, k = lane & 3;
+    float in[20], s[20], c[20];
+#pragma unroll
+    for (int v = 0; v < 20; ++v) { in[v] = 0.f; s[v] = 0.f; c[v] = 0.f; }
+    int nfold = 0;
+    int cur = -1, run = -1;
+    ChildRegs r0, r1;
+    for (int it = ib; it < ie; ++it) {
+        const Item w = items[it];
+        if (w.parent != cur) {
+            if (cur >= 0) {
+                fold20<COMP>(in, s, c);
+                nfold = 0;
+                flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+            }
+            cur = w.parent;
+            run = it;
+            load_child(est_lvl + 8 * cur + 2 * k, r0);
+            load_child(est_lvl + 8 * cur + 2 * k + 1, r1);
+        }
+        for (int base = 0; base < w.count; base += 64) {
+            const int idx = base + warp * 8 + q;
+            const bool valid = idx < w.count;
+            const float4 z = pts[w.start + (valid ? idx : 0)];
+            float e0x, e0y, e0z, e1x, e1y, e1z;
+            const float s0 = child_score(r0, z.x, z.y, z.z, e0x, e0y, e0z);
+            const float s1 = child_score(r1, z.x, z.y, z.z, e1x, e1y, e1z);
+            float m = fmaxf(s0, s1);
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
+            const float p0 = exp2f(s0 - m);
+            const float p1 = exp2f(s1 - m);
+            float tot = p0 + p1;
+            tot += __shfl_xor_sync(FULL, tot, 1);
+            tot += __shfl_xor_sync(FULL, tot, 2);
+            const float rinv = valid ? 1.0f / tot : 0.0f;
+            accum10(in, p0 * rinv, e0x, e0y, e0z);
+            accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
+            if (++nfold == 16) {
+                fold20<COMP>(in, s, c);
+                nfold = 0;
+            }
+        }
+    }
+    fold20<COMP>(in, s, c);
+    flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+}
+
+// ---------------------------------------------------------------- M-step
+template <bool COMP>
+__global__ void __launch_bounds__(128) k_mstep(int level, int n, const int* __restrict__ item_range,
+                                               const int* __restrict__ meta,
+                                               const float2* __restrict__ partials,
+                                               const int* __restrict__ seg_count,
+                                               const RootDev* __restrict__ root, float n_min,
+                                               NodeStat* __restrict__ stat,
+                                               NodeEst* __restrict__ est, int* __restrict__ status) {
+    __shared__ double mom[NPART];
+    __shared__ int heavy;
+    const int p = blockIdx.x;
+    const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
+    if (i0 >= i1) return;  // parent without points: children stay dead
+    const int C = meta[1];
+    if (threadIdx.x < NPART) {
+        float S = 0.f, Cc = 0.f;
+        for (int slot = i0; slot < i1; slot = (slot / C + 1) * C) {
+            const float2 x = partials[int64_t(slot) * NPART + threadIdx.x];
+            if (COMP) pair_add(S, Cc, x.x, x.y);
+            else S += x.x;
+        }
+        mom[threadIdx.x] = double(S) + double(Cc);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int h = 0;
+        for (int cc = 1; cc < 8; ++cc)
+            if (mom[cc * NMOM] > mom[h * NMOM]) h = cc;
+        heavy = h;
+    }
+    __syncthreads();
+    const int cidx = threadIdx.x;
+    if (cidx >= 8) return;
+    const int64_t g = d_level_offset(level) + 8 * int64_t(p) + cidx;
+    NodeStat& cs = stat[g];
+    NodeEst& ce = est[g];
+    const double* m = mom + cidx * NMOM;
+    const double S0 = m[0];
+    const double n_p = level == 0 ? double(n) : double(seg_count[d_level_offset(level - 1) + p]);
+    const bool live = cs.live && (S0 >= double(n_min) || cidx == heavy) && S0 > 0.0;
+    if (!live) {
+        cs.live = 0;
+        cs.pi = 0.0;
+        ce.a.w = -CUDART_INF_F;
+        ce.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        ce.c.x = 0.f;
+        ce.c.y = 0.f;
+        return;
+    }
+    const double eps = root->eps;
+    const double inv = 1.0 / S0;
+    const double d[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
+    // the E-step centred on the FP32 mean it used
+    const double mu[3] = {double(ce.a.x) + d[0], double(ce.a.y) + d[1], double(ce.a.z) + d[2]};
+    double S[6];
+    S[0] = m[4] * inv - d[0] * d[0] + eps;
+    S[1] = m[5] * inv - d[0] * d[1];
+    S[2] = m[6] * inv - d[0] * d[2];
+    S[3] = m[7] * inv - d[1] * d[1] + eps;
+    S[4] = m[8] * inv - d[1] * d[2];
+    S[5] = m[9] * inv - d[2] * d[2] + eps;
+    const double pi = S0 / n_p;
+    cs.pi = pi;
+    for (int a = 0; a < 3; ++a) cs.mu[a] = mu[a];
+    for (int v = 0; v < 6; ++v) cs.S[v] = S[v];
+    if (!pack_est(pi, mu, S, eps, 0.f, ce)) atomicOr(status, ST_CHOL);
+}
+
+// ---------------------------------------------------------------- hand-off
+__global__ void __launch_bounds__(EST_THREADS) k_assign(const float4* __restrict__ pts,
+                                                        const Item* __restrict__ items,
+                                                        const int* __restrict__ meta,
+                                                        const NodeEst* __restrict__ est_lvl,
+                                                        uint32_t* __restrict__ codes,
+                                                        int* __restrict__ item_cnt) {
+    __shared__ int cnt[EST_THREADS / 32][8];
+    __shared__ int base[8];
+    const int n_items = meta[0];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 2, k = lane & 3;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const Item w = items[it];
+        ChildRegs r0, r1;
+        load_child(est_lvl + 8 * w.parent + 2 * k, r0);
+        load_child(est_lvl + 8 * w.parent + 2 * k + 1, r1);
+        if (threadIdx.x < 8) base[threadIdx.x] = 0;
+        __syncthreads();
+        for (int b0 = 0; b0 < w.count; b0 += 64) {
+            const int idx = b0 + warp * 8 + q;
+            const bool valid = idx < w.count;
+            const float4 z = pts[w.start + (valid ? idx : 0)];
+            float ex, ey, ez;
+            const float s0 = child_score(r0, z.x, z.y, z.z, ex, ey, ez);
+            const float s1 = child_score(r1, z.x, z.y, z.z, ex, ey, ez);
+            float best = s0;
+            int lab = 2 * k;
+            if (s1 > best) { best = s1; lab = 2 * k + 1; }
+#pragma unroll
+            for (int off = 1; off <= 2; off <<= 1) {
+                const float ob = __shfl_xor_sync(FULL, best, off);
+                const int ol = __shfl_xor_sync(FULL, lab, off);
+                if (ob > best || (ob == best && ol < lab)) { best = ob; lab = ol; }
+            }
+            const bool lead = valid && k == 0;
+            int my_rank = 0;
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                const unsigned bal = __ballot_sync(FULL, lead && lab == cc);
+                if (lane == 0) cnt[warp][cc] = __popc(bal);
+                if (lab == cc) my_rank = __popc(bal & lt);
+            }
+            __syncthreads();
+            if (lead) {
+                int r = base[lab] + my_rank;
+                for (int w2 = 0; w2 < warp; ++w2) r += cnt[w2][lab];
+                codes[w.start + idx] = uint32_t(lab) | (uint32_t(r) << 3);
+            }
+            __syncthreads();
+            if (threadIdx.x < 8) {
+                int tsum = 0;
+                for (int w2 = 0; w2 < EST_THREADS / 32; ++w2) tsum += cnt[w2][threadIdx.x];
+                base[threadIdx.x] += tsum;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < 8) item_cnt[8 * it + threadIdx.x] = base[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// One CTA (256 threads) per parent: per child, exclusive scan over the
+// parent's items of the item counts -> absolute destination offsets.
+__global__ void __launch_bounds__(256) k_child_offsets(int level, int n,
+                                                       const int* __restrict__ item_range,
+                                                       const Item* __restrict__ items,
+                                                       const int* __restrict__ item_cnt,
+                                                       int* __restrict__ item_off,
+                                                       int* __restrict__ seg_start,
+                                                       int* __restrict__ seg_count) {
+    __shared__ int tot[8][8];       // [warp][child]
+    __shared__ int carry[8];
+    const int p = blockIdx.x;
+    const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t g0 = d_level_offset(level) + 8 * int64_t(p);
+    int pstart;
+    if (i0 < i1) {
+        pstart = items[i0].start;
+    } else {
+        // empty parent: its children get empty segments at the parent's start
+        pstart = level == 0 ? 0 : seg_start[d_level_offset(level - 1) + p];
+    }
+    // pass 1: totals per child
+    int t8[8] = {};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+        for (int cc = 0; cc < 8; ++cc) t8[cc] += item_cnt[8 * i + cc];
+    for (int cc = 0; cc < 8; ++cc) {
+        int x = t8[cc];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+        if (lane == 0) tot[warp][cc] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = pstart;
+        for (int cc = 0; cc < 8; ++cc) {
+            int s = 0;
+            for (int w = 0; w < 8; ++w) s += tot[w][cc];
+            carry[cc] = run;
+            seg_start[g0 + cc] = run;
+            seg_count[g0 + cc] = s;
+            run += s;
+        }
+    }
+    __syncthreads();
+    // pass 2: scan in chunks of 256 items
+    for (int b = i0; b < i1; b += blockDim.x) {
+        const int i = b + threadIdx.x;
+        int v8[8];
+        for (int cc = 0; cc < 8; ++cc) v8[cc] = i < i1 ? item_cnt[8 * i + cc] : 0;
+        int incl[8];
+        for (int cc = 0; cc < 8; ++cc) {
+            int x = v8[cc];
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, off);
+                if (lane >= off) x += y;
+            }
+            incl[cc] = x;
+            if (lane == 31) tot[warp][cc] = x;
+        }
+        __syncthreads();
+        for (int cc = 0; cc < 8; ++cc) {
+            int pre = carry[cc];
+            for (int w = 0; w < warp; ++w) pre += tot[w][cc];
+            if (i < i1) item_off[8 * i + cc] = pre + incl[cc] - v8[cc];
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            int s = 0;
+            for (int w = 0; w < 8; ++w) s += tot[w][threadIdx.x];
+            carry[threadIdx.x] += s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const float4* __restrict__ pts_in,
+                                                 const int* __restrict__ perm_in,
+                                                 const Item* __restrict__ items,
+                                                 const int* __restrict__ meta,
+                                                 const uint32_t* __restrict__ codes,
+                                                 const int* __restrict__ item_off,
+                                                 float4* __restrict__ pts_out,
+                                                 int* __restrict__ perm_out) {
+    const int n_items = meta[0];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const Item w = items[it];
+        for (int j = threadIdx.x; j < w.count; j += blockDim.x) {
+            const int pos = w.start + j;
+            const uint32_t code = codes[pos];
+            const int dst = item_off[8 * it + (code & 7u)] + int(code >> 3);
+            pts_out[dst] = pts_in[pos];
+            perm_out[dst] = perm_in ? perm_in[pos] : pos;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- finalize
+__global__ void k_finalize(int level, float lam_c, const RootDev* __restrict__ root,
+                           NodeStat* __restrict__ stat, NodeEst* __restrict__ est) {
+    const int64_t m = int64_t(1) << (3 * (level + 1));
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t g = d_level_offset(level) + i;
+    NodeStat& s = stat[g];
+    if (!s.live) {
+        for (int a = 0; a < 3; ++a) s.lam[a] = 1.0;
+        for (int v = 0; v < 9; ++v) s.V[v] = (v % 4 == 0) ? 1.0 : 0.0;
+        for (int v = 0; v < 6; ++v) s.P[v] = 0.0;
+        s.complexity = 1.0;
+        est[g].c.z = 0.f;
+        return;
+    }
+    double lam[3], V[9];
+    jacobi_eig3(s.S, lam, V);
+    const double eps = root->eps;
+    double il[3];
+    for (int a = 0; a < 3; ++a) {
+        s.lam[a] = lam[a];
+        il[a] = 1.0 / fmax(lam[a], eps);
+    }
+    for (int v = 0; v < 9; ++v) s.V[v] = V[v];
+    // P = V diag(1/lambda) V^T (Eq. 10)
+    const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int v = 0; v < 6; ++v) {
+        const int r = ij[v][0], c = ij[v][1];
+        double acc = 0.0;
+        for (int k = 0; k < 3; ++k) acc += V[r * 3 + k] * il[k] * V[c * 3 + k];
+        s.P[v] = acc;
+    }
+    s.complexity = lam[2] / (lam[0] + lam[1] + lam[2]);
+    est[g].c.z = (s.complexity <= double(lam_c)) ? 1.f : 0.f;
+}
+
+// ---------------------------------------------------------------- labels
+__global__ void k_labels(int level, int n, const int* __restrict__ perm,
+                         const int* __restrict__ seg_start, const int* __restrict__ seg_count,
+                         int* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t off = d_level_offset(level);
+    const int64_t m = int64_t(1) << (3 * (level + 1));
+    // largest node with seg_start <= i (segments are in node order)
+    int64_t lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (seg_start[off + mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    while (lo > 0 && seg_count[off + lo] == 0) --lo;  // never needed for a non-empty segment
+    out[perm[i]] = int(lo);
+}
+
+}  // namespace
+
+}  // namespace hgmm
+
+using namespace hgmm;
+
+#define HGMM_LAUNCH_CHECK()                                   \
+    do {                                                      \
+        cudaError_t e_ = cudaGetLastError();                  \
+        if (e_ != cudaSuccess) {                              \
+            fprintf(stderr, "hgmm: launch failed: %s (%s:%d)\n", cudaGetErrorString(e_), \
+                    __FILE__, __LINE__);                      \
+            return HGMM_ECUDA;                                \
+        }                                                     \
+    } while (0)
+
+int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
+                    const hgmm_params& p, cudaStream_t s) {
+    const int n = int(n64);
+    const int G = t->est_grid;
+    {
+        ProfScope ps_(t, K_ROOT_PARTIAL, s);
+        k_root_partial<<<G, 256, 0, s>>>(pts, n, t->root_part);
+    }
+    {
+        ProfScope ps_(t, K_ROOT_FINAL, s);
+        k_root_final<<<1, 32, 0, s>>>(pts, t->root_part, G, n, p.eps_rel, t->root, t->status);
+    }
+    HGMM_LAUNCH_CHECK();
+    const float4* cur = pts;
+    const int* perm_prev = nullptr;
+    const bool comp = p.precision == 0;
+    for (int l = 0; l < depth; ++l) {
+        const int n_par = l == 0 ? 1 : int(level_size(l - 1));
+        const int64_t off = level_offset(l);
+        NodeEst* est_lvl = t->est + off;
+        {
+            ProfScope ps_(t, K_INIT, s);
+            k_init_children<<<n_par, 32, 0, s>>>(l, t->root, t->stat, t->est, t->seg_count, t->status);
+        }
+        {
+            ProfScope ps_(t, K_MAKE_ITEMS, s);
+            k_make_items<<<1, 1024, 0, s>>>(l, n, n_par, t->seg_start, t->seg_count, t->stat,
+                                            t->items, t->item_range, t->meta, G);
+        }
+        {
+            ProfScope ps_(t, K_FILL_ITEMS, s);
+            k_fill_items<<<int((t->max_items + 255) / 256), 256, 0, s>>>(
+                l, n, n_par, t->seg_start, t->seg_count, t->item_range, t->meta, t->items);
+        }
+        HGMM_LAUNCH_CHECK();
+        for (int k = 0; k < p.em_iters; ++k) {
+            if (comp) {
+                {
+                    ProfScope ps_(t, K_ESTEP, s);
+                    k_estep<true><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials);
+                }
+                {
+                    ProfScope ps_(t, K_MSTEP, s);
+                    k_mstep<true><<<n_par, 128, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
+                                                        t->seg_count, t->root, p.n_min, t->stat,
+                                                        t->est, t->status);
+                }
+            } else {
+                {
+                    ProfScope ps_(t, K_ESTEP, s);
+                    k_estep<false><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials);
+                }
+                {
+                    ProfScope ps_(t, K_MSTEP, s);
+                    k_mstep<false><<<n_par, 128, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
+                                                         t->seg_count, t->root, p.n_min, t->stat,
+                                                         t->est, t->status);
+                }
+            }
+        }
+        HGMM_LAUNCH_CHECK();
+        {
+            ProfScope ps_(t, K_ASSIGN, s);
+            k_assign<<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->codes, t->item_cnt);
+        }
+        {
+            ProfScope ps_(t, K_OFFSETS, s);
+            k_child_offsets<<<n_par, 256, 0, s>>>(l, n, t->item_range, t->items, t->item_cnt,
+                                                  t->item_off, t->seg_start, t->seg_count);
+        }
+        float4* out = t->pts[l & 1];
+        {
+            ProfScope ps_(t, K_SCATTER, s);
+            k_scatter<<<G, 256, 0, s>>>(cur, perm_prev, t->items, t->meta, t->codes, t->item_off,
+                                        out, t->perm[l]);
+        }
+        const int m = int(level_size(l));
+        {
+            ProfScope ps_(t, K_FINALIZE, s);
+            k_finalize<<<(m + 127) / 128, 128, 0, s>>>(l, p.lam_c, t->root, t->stat, t->est);
+        }
+        HGMM_LAUNCH_CHECK();
+        cur = out;
+        perm_prev = t->perm[l];
+    }
+    return HGMM_OK;
+}
+
+int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s) {
+    const int n = int(t->n);
+    {
+        ProfScope ps_(t, K_LABELS, s);
+        k_labels<<<(n + 255) / 256, 256, 0, s>>>(level, n, t->perm[level], t->seg_start,
+                                                 t->seg_count, d_out);
+    }
+    HGMM_LAUNCH_CHECK();
+    return HGMM_OK;
+}

@@ -1,0 +1,167 @@
+// Internal declarations shared by the HGMM CUDA translation units.
+//
+// Device data layout (all arrays are per tree, indexed by global node id
+// g = level_offset(l) + i, level l holding 8^(l+1) nodes; the children of
+// node i of level l are nodes 8i .. 8i+7 of level l+1):
+//
+//   NodeEst  est[g]   48 B, FP32: what the E-step and the descent read.
+//                     a = (mu_x, mu_y, mu_z, C), b = (W00, W10, W11, W20),
+//                     c = (W21, W22, stop, -) with W = sqrt(log2(e)/2) L^-1
+//                     (Sigma = L L^T) and C = log2 pi - 3/2 log2(2 pi)
+//                     - sum_i log2 L_ii, so that
+//                     log2(pi N(z | mu, Sigma)) = C - |W (z - mu)|^2.
+//                     A dead node has C = -inf.
+//   NodeStat stat[g]  FP64 parameters (pi, mu, Sigma), eigen-decomposition,
+//                     precision matrix P = V diag(1/max(lambda, eps)) V^T and
+//                     complexity (Sec. 4.1).
+//   seg_start/count   hard segment of each node in the sorted point order.
+//
+// Points are float4 (x, y, z, pad), re-ordered level by level so that the
+// points of every parent are contiguous ("segments"); perm[l] maps sorted
+// positions after level l's hand-off back to input indices.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hgmm.h"
+
+namespace hgmm {
+
+constexpr int J = 8;
+constexpr int NMOM = 10;              // S0, S1 (3), S2 (6 upper)
+constexpr int NPART = J * NMOM;       // 80 moment values per parent run
+constexpr int TILE = 256;             // points per build work item
+constexpr int EST_THREADS = 256;      // build E-step CTA
+constexpr int REG_THREADS = 256;      // registration descent CTA
+constexpr int MSTEP_THREADS = 128;    // registration M-step CTA
+
+// status bits (device word, OR-ed)
+constexpr int ST_NONFINITE = 1;
+constexpr int ST_DEGENERATE = 2;
+constexpr int ST_CHOL = 4;            // a covariance needed extra regularisation
+constexpr int ST_TIMEOUT = 8;
+
+struct NodeEst {
+    float4 a, b, c;
+};
+
+struct NodeStat {
+    double pi;
+    double mu[3];
+    double S[6];      // xx xy xz yy yz zz
+    double lam[3];    // descending
+    double V[9];      // eigenvectors in columns, V[r*3+c]
+    double P[6];      // precision matrix, same packing as S
+    double complexity;
+    int live;
+    int pad;
+};
+
+struct Item {
+    int parent;   // parent index within its level (root = 0)
+    int start;    // first sorted position
+    int count;    // <= TILE
+    int pad;
+};
+
+struct RootDev {
+    double n;
+    double mu[3];
+    double S[6];
+    double extent;
+    double eps;
+};
+
+enum KernelId {
+    K_ROOT_PARTIAL, K_ROOT_FINAL, K_INIT, K_MAKE_ITEMS, K_FILL_ITEMS, K_ESTEP, K_MSTEP,
+    K_ASSIGN, K_OFFSETS, K_SCATTER, K_FINALIZE, K_REG_INIT, K_DESCEND, K_REG_MSTEP, K_COPY_T,
+    K_LABELS, K_COUNT
+};
+
+struct ProfRecord {
+    int id;
+    cudaEvent_t a, b;
+};
+
+inline int64_t level_size(int l) { return int64_t(1) << (3 * (l + 1)); }
+inline int64_t level_offset(int l) { return ((int64_t(1) << (3 * (l + 1))) - 8) / 7; }
+
+}  // namespace hgmm
+
+struct hgmm_tree {
+    int device = 0;
+    int n_sm = 0;
+    int64_t cap = 0;
+    int max_depth = 0;
+    int64_t max_items = 0;
+    int64_t max_nodes = 0;
+    int est_grid = 0;   // CTAs of the persistent build E-step
+    int reg_grid = 0;   // CTAs of the descent
+    // last build
+    int64_t n = 0;
+    int depth = 0;
+    hgmm_params prm{};
+    int64_t reg_n = 0;
+    bool built = false;
+    // device buffers
+    hgmm::NodeEst* est = nullptr;
+    hgmm::NodeStat* stat = nullptr;
+    int* seg_start = nullptr;
+    int* seg_count = nullptr;
+    float4* pts[2] = {nullptr, nullptr};
+    int* perm[HGMM_MAX_DEPTH] = {};
+    uint32_t* codes = nullptr;
+    hgmm::Item* items = nullptr;
+    int* item_range = nullptr;   // per parent: [begin, end) item indices
+    int* meta = nullptr;         // [0] n_items, [1] items per E-step CTA
+    float2* partials = nullptr;  // max_items x NPART (sum, compensation)
+    int* item_cnt = nullptr;     // max_items x 8
+    int* item_off = nullptr;     // max_items x 8
+    hgmm::RootDev* root = nullptr;
+    float* root_part = nullptr;  // est_grid x 32
+    int* status = nullptr;
+    // registration
+    unsigned long long* reg_acc = nullptr;  // nodes x 4 fixed point
+    double* reg_part = nullptr;             // blocks x 27
+    unsigned* reg_counter = nullptr;
+    double* reg_T = nullptr;                // 16 doubles current T
+    float* reg_Rt = nullptr;                // 12 floats (R row-major, t)
+    unsigned char* reg_stop = nullptr;      // per node stop flag
+    double* reg_dbg = nullptr;              // nodes x 4 (last round)
+    // per-kernel timing
+    bool prof_on = false;
+    std::vector<hgmm::ProfRecord> prof;
+    // host-API staging
+    float4* stage_tgt = nullptr;
+    float4* stage_src = nullptr;
+    double* stage_T = nullptr;              // 32 doubles: T_init, T_out
+};
+
+// Brackets one kernel launch with a CUDA event pair when profiling is on.
+struct ProfScope {
+    hgmm_tree* t;
+    int id;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(hgmm_tree* t_, int id_, cudaStream_t s_) : t(t_), id(id_), s(s_) {
+        if (t->prof_on && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, s);
+    }
+    ~ProfScope() {
+        if (a && b) {
+            cudaEventRecord(b, s);
+            t->prof.push_back({id, a, b});
+        }
+    }
+};
+
+// Host-side launchers (defined in the .cu files).
+int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n, int depth,
+                    const hgmm_params& p, cudaStream_t s);
+int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n,
+                       const double* T_init, int iters, float lam_c,
+                       cudaStream_t s, double* T_out, double* T_hist);
+int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s);

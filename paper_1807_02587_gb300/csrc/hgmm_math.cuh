@@ -1,0 +1,209 @@
+// Small device-side numerics used by the build and registration kernels.
+//
+//  * two_sum        Knuth's error-free transformation a + b = s + e, the
+//                   building block of the compensated (Kahan-style) moment
+//                   sums of the precision form.
+//  * jacobi_eig3    cyclic Jacobi eigen-decomposition of a symmetric 3x3
+//                   matrix in FP64 (Jacobi's method with Rutishauser's
+//                   rotation formulas), eigenvalues sorted descending
+//                   (lambda_1 >= lambda_2 >= lambda_3, Sec. 4.1), each
+//                   eigenvector signed so that its largest-magnitude entry is
+//                   positive.
+//  * chol3 / pack   FP64 Cholesky factor of a 3x3 covariance and the
+//                   E-step constants of Eq. 2 in log2 units.
+//  * chol_solve6    FP64 Cholesky (LL^T) solve of the 6x6 normal equations
+//                   of Eq. 16.
+//  * rodrigues      axis-angle to rotation matrix (FP64).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "hgmm_internal.cuh"
+
+namespace hgmm {
+
+// ---------------------------------------------------------------- FP32 sums
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// (s, c) += (s2, c2): compensated pair addition.
+__device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2) {
+    float t, e;
+    two_sum(s, s2, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, e));
+}
+
+// ---------------------------------------------------------------- FP64 3x3
+// S packed xx xy xz yy yz zz.
+__device__ inline void jacobi_eig3(const double S[6], double lam[3], double V[9]) {
+    double a[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
+    double v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (!(off > 1e-34 * dia)) break;  // also stops on NaN
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0;
+            const int q = pq == 0 ? 1 : 2;
+            const double apq = a[p][q];
+            if (apq == 0.0) continue;
+            const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+            double t;
+            if (fabs(theta) > 1e150) {
+                t = 0.5 / theta;  // theta^2 would overflow: t ~ 1/(2 theta)
+            } else {
+                t = 1.0 / (fabs(theta) + sqrt(theta * theta + 1.0));
+                if (theta < 0.0) t = -t;
+            }
+            const double c = 1.0 / sqrt(t * t + 1.0);
+            const double s = t * c;
+            a[p][p] -= t * apq;
+            a[q][q] += t * apq;
+            a[p][q] = a[q][p] = 0.0;
+            const int r = 3 - p - q;
+            const double arp = a[r][p], arq = a[r][q];
+            a[r][p] = a[p][r] = c * arp - s * arq;
+            a[r][q] = a[q][r] = s * arp + c * arq;
+            for (int k = 0; k < 3; ++k) {
+                const double vkp = v[k][p], vkq = v[k][q];
+                v[k][p] = c * vkp - s * vkq;
+                v[k][q] = s * vkp + c * vkq;
+            }
+        }
+    }
+    int idx[3] = {0, 1, 2};
+    double d[3] = {a[0][0], a[1][1], a[2][2]};
+    // sort descending (3 elements)
+    if (d[idx[0]] < d[idx[1]]) { int x = idx[0]; idx[0] = idx[1]; idx[1] = x; }
+    if (d[idx[1]] < d[idx[2]]) { int x = idx[1]; idx[1] = idx[2]; idx[2] = x; }
+    if (d[idx[0]] < d[idx[1]]) { int x = idx[0]; idx[0] = idx[1]; idx[1] = x; }
+    for (int c = 0; c < 3; ++c) {
+        const int k = idx[c];
+        lam[c] = d[k];
+        int best = 0;
+        for (int r = 1; r < 3; ++r)
+            if (fabs(v[r][k]) > fabs(v[best][k])) best = r;
+        const double sg = v[best][k] < 0.0 ? -1.0 : 1.0;
+        for (int r = 0; r < 3; ++r) V[r * 3 + c] = sg * v[r][k];
+    }
+}
+
+// Cholesky Sigma = L L^T, returns false if not positive definite.
+// L packed: L00 L10 L11 L20 L21 L22.
+__device__ inline bool chol3(const double S[6], double L[6]) {
+    const double d0 = S[0];
+    if (!(d0 > 0.0)) return false;
+    const double l00 = sqrt(d0);
+    const double l10 = S[1] / l00;
+    const double l20 = S[2] / l00;
+    const double d1 = S[3] - l10 * l10;
+    if (!(d1 > 0.0)) return false;
+    const double l11 = sqrt(d1);
+    const double l21 = (S[4] - l20 * l10) / l11;
+    const double d2 = S[5] - l20 * l20 - l21 * l21;
+    if (!(d2 > 0.0)) return false;
+    L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = sqrt(d2);
+    return true;
+}
+
+// E-step constants of a live node (see NodeEst): returns false when Sigma
+// needed extra diagonal loading to become positive definite.
+__device__ inline bool pack_est(double pi, const double mu[3], const double S_in[6],
+                                double eps, float stop, NodeEst& out) {
+    double S[6] = {S_in[0], S_in[1], S_in[2], S_in[3], S_in[4], S_in[5]};
+    double L[6];
+    bool clean = true;
+    double boost = eps > 0.0 ? eps : 1e-30;
+    for (int tries = 0; tries < 8 && !chol3(S, L); ++tries) {
+        clean = false;
+        S[0] += boost; S[3] += boost; S[5] += boost;
+        boost *= 10.0;
+    }
+    if (!chol3(S, L)) {  // hopeless (NaN input): make it an isotropic unit Gaussian
+        L[0] = 1; L[1] = 0; L[2] = 1; L[3] = 0; L[4] = 0; L[5] = 1;
+        clean = false;
+    }
+    // M = L^-1 (lower triangular)
+    const double m00 = 1.0 / L[0], m11 = 1.0 / L[2], m22 = 1.0 / L[5];
+    const double m10 = -L[1] * m00 * m11;
+    const double m21 = -L[4] * m11 * m22;
+    const double m20 = -(L[3] * m00 + L[4] * m10) * m22;
+    const double k = sqrt(0.5 * 1.4426950408889634);  // sqrt(log2(e) / 2)
+    const double C = log2(pi) - 1.5 * log2(2.0 * CUDART_PI) -
+                     (log2(L[0]) + log2(L[2]) + log2(L[5]));
+    out.a = make_float4(float(mu[0]), float(mu[1]), float(mu[2]), float(C));
+    out.b = make_float4(float(k * m00), float(k * m10), float(k * m11), float(k * m20));
+    out.c = make_float4(float(k * m21), float(k * m22), stop, 0.f);
+    return clean;
+}
+
+__device__ inline void dead_est(const double mu[3], NodeEst& out) {
+    out.a = make_float4(float(mu[0]), float(mu[1]), float(mu[2]), -CUDART_INF_F);
+    out.b = make_float4(0.f, 0.f, 0.f, 0.f);
+    out.c = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// ---------------------------------------------------------------- FP64 6x6
+// H packed upper row-major (21): (0,0..5),(1,1..5),...; solves H x = g.
+__device__ inline bool chol_solve6(const double Hu[21], const double g[6], double x[6]) {
+    double A[6][6];
+    int k = 0;
+    double dmax = 0.0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) {
+            A[i][j] = A[j][i] = Hu[k++];
+        }
+    for (int i = 0; i < 6; ++i) dmax = fmax(dmax, fabs(A[i][i]));
+    if (!(dmax > 0.0)) return false;
+    double L[6][6] = {};
+    for (int j = 0; j < 6; ++j) {
+        double d = A[j][j];
+        for (int p = 0; p < j; ++p) d -= L[j][p] * L[j][p];
+        if (!(d > 1e-15 * dmax)) return false;
+        L[j][j] = sqrt(d);
+        for (int i = j + 1; i < 6; ++i) {
+            double s = A[i][j];
+            for (int p = 0; p < j; ++p) s -= L[i][p] * L[j][p];
+            L[i][j] = s / L[j][j];
+        }
+    }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = g[i];
+        for (int p = 0; p < i; ++p) s -= L[i][p] * y[p];
+        y[i] = s / L[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+        for (int p = i + 1; p < 6; ++p) s -= L[p][i] * x[p];
+        x[i] = s / L[i][i];
+    }
+    return true;
+}
+
+__device__ inline void rodrigues(const double w[3], double R[9]) {
+    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const double th = sqrt(th2);
+    double a, b;  // R = I + a K + b K^2
+    if (th < 1e-8) {
+        a = 1.0 - th2 / 6.0;
+        b = 0.5 - th2 / 24.0;
+    } else {
+        a = sin(th) / th;
+        b = (1.0 - cos(th)) / th2;
+    }
+    const double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double kk = 0.0;
+            for (int m = 0; m < 3; ++m) kk += K[i * 3 + m] * K[m * 3 + j];
+            R[i * 3 + j] = (i == j ? 1.0 : 0.0) + a * K[i * 3 + j] + b * kk;
+        }
+}
+
+}  // namespace hgmm

@@ -1,0 +1,119 @@
+"""Edge cases and error behaviour of the C ABI on the GPU: smallest clouds,
+deep sparse trees, degenerate geometry, non-finite input, invalid arguments,
+capacity limits, the host-buffer entry point."""
+import numpy as np
+import pytest
+
+from paper_1807_02587_gb300 import synth
+from tests import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1807_02587_gb300 import binding
+    return binding
+
+
+def _consistent(tree, n, depth):
+    for l in range(depth):
+        g = tree.export(l)
+        lab = tree.labels(l)
+        assert lab.min() >= 0 and lab.max() < 8 ** (l + 1)
+        assert np.array_equal(np.bincount(lab, minlength=8 ** (l + 1)), g["count"])
+        assert g["count"].sum() == n
+        assert np.all(g["count"][~g["live"]] == 0)
+        assert np.all(np.isfinite(g["mu"][g["live"]]))
+        assert np.all(np.isfinite(g["Sigma"][g["live"]]))
+        if l:
+            assert np.array_equal(lab // 8, tree.labels(l - 1))
+
+
+@pytest.mark.parametrize("n,depth", [(8, 1), (8, 3), (9, 2), (300, 5), (30001, 5)])
+def test_small_and_deep_trees(B, n, depth):
+    P = synth.corner_scene(synth.make_rng(n), n)
+    dev, Z = PT.device_cloud(P)
+    tree = B.Tree(n, depth)
+    tree.build(dev, depth)
+    tree.sync()
+    _consistent(tree, n, depth)
+    if n >= 300:
+        res = PT.check_build(tree, Z, PT.oracle_params(B.params(), depth))
+        for r in res["levels"]:
+            assert r["live_mismatch"] == 0 and r["mu"] < PT.MEAN_TOL and r["S"] < PT.COV_TOL, r
+
+
+def test_coincident_points(B):
+    import torch
+    P = np.tile(np.array([[1.0, 2.0, 3.0]]), (1000, 1))
+    dev, Z = PT.device_cloud(P)
+    tree = B.Tree(1000, 3)
+    tree.build(dev, 3)
+    tree.sync()
+    _consistent(tree, 1000, 3)
+    T = tree.register(dev, iters=3)
+    try:
+        tree.sync()
+    except B.HgmmError as e:
+        assert e.code == B.HGMM_EDEGENERATE
+    assert np.all(np.isfinite(T.cpu().numpy()))
+
+
+def test_nonfinite_input_is_reported(B):
+    P = synth.corner_scene(synth.make_rng(1), 2000)
+    P[123, 1] = np.nan
+    dev, _ = PT.device_cloud(P)
+    tree = B.Tree(2000, 2)
+    tree.build(dev, 2)
+    with pytest.raises(B.HgmmError) as ei:
+        tree.sync()
+    assert ei.value.code == B.HGMM_ENONFINITE
+    # the tree stays usable
+    P[123, 1] = 0.5
+    dev, _ = PT.device_cloud(P)
+    tree.build(dev, 2)
+    tree.sync()
+
+
+def test_invalid_arguments(B):
+    import torch
+    P = synth.corner_scene(synth.make_rng(2), 1000)
+    dev, _ = PT.device_cloud(P)
+    tree = B.Tree(1000, 3)
+    with pytest.raises(B.HgmmError) as e:
+        B.hgmm_build(tree.handle, dev, 3, J=7)
+    assert e.value.code == B.HGMM_EINVAL
+    for d in (0, 6):
+        with pytest.raises(B.HgmmError):
+            B.hgmm_build(tree.handle, dev, d)
+    with pytest.raises(B.HgmmError) as e:
+        B.hgmm_build(tree.handle, dev, 4)  # deeper than the tree was created for
+    assert e.value.code == B.HGMM_ECAPACITY
+    big = torch.zeros((1001, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.HgmmError) as e:
+        B.hgmm_build(tree.handle, big, 2)
+    assert e.value.code == B.HGMM_ECAPACITY
+    flat = torch.zeros(4 * 100 + 1, dtype=torch.float32, device="cuda")
+    mis = flat[1:].view(100, 4)
+    with pytest.raises(B.HgmmError) as e:
+        B.hgmm_build(tree.handle, mis, 2)
+    assert e.value.code == B.HGMM_EINVAL
+    tiny = torch.zeros((7, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.HgmmError) as e:
+        B.hgmm_build(tree.handle, tiny, 1)
+    assert e.value.code == B.HGMM_EINVAL
+
+
+def test_host_entry_point_matches_device_path(B):
+    import torch
+    p = synth.corner_pair(11, n=6000, max_deg=3.0, max_t=0.02)
+    tree = B.Tree(6000, 3)
+    T_host = B.hgmm_register_pair_host(tree.handle, synth.to_float4(p["tgt"]),
+                                       synth.to_float4(p["src"]), 3, B.params(), None, 12)
+    tgt, _ = PT.device_cloud(p["tgt"])
+    src, _ = PT.device_cloud(p["src"])
+    tree.build(tgt, 3)
+    T_dev = tree.register(src, iters=12).cpu().numpy()
+    tree.sync()
+    assert np.array_equal(T_host, T_dev)
