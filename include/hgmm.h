@@ -66,14 +66,21 @@ typedef struct hgmm_tree hgmm_tree; /* opaque, device-resident, library-owned */
  *   eps_rel   : covariances get eps*I with eps = (eps_rel * extent)^2, extent
  *               = bounding-box diagonal of the modelled cloud (default 1e-3).
  *   precision : 0 = FP32 moment sums with compensated (Kahan/TwoSum)
- *               accumulation (default); 1 = plain FP32 sums (for comparison). */
+ *               accumulation (default); 1 = plain FP32 sums (for comparison).
+ *   debug_stop_level, debug_stop_iters : checking aid; 0 = off.  With
+ *               debug_stop_level = L + 1 the build finishes levels < L, then
+ *               runs only debug_stop_iters EM iterations of level L and stops
+ *               (no hand-off), so hgmm_tree_export(L) shows the parameters
+ *               after that many iterations (0 = the initial children). */
 typedef struct hgmm_params {
     int32_t em_iters;
     float n_min;
     float lam_c;
     float eps_rel;
     int32_t precision;
-    int32_t reserved[3];
+    int32_t debug_stop_level;
+    int32_t debug_stop_iters;
+    int32_t reserved;
 } hgmm_params;
 
 /* Per-node record written by hgmm_tree_export: 16 float64 per node,

@@ -15,7 +15,8 @@ Algorithm 1) and written to be read against the paper:
   nodes.  The paper defers the build to its reference [33]; the steps below
   are this project's stated reading (PCA-octant child init, K fixed EM
   iterations per level on the hard-assigned points of each parent, dead
-  children below ``n_min`` expected points, argmax hand-off).
+  children below ``n_min`` expected points, a parent whose children all die
+  stays a leaf, argmax hand-off).
 * Algorithm 1  E_STEP_ADAPTIVE: max-likelihood descent with the PCA
   complexity early stop (Sec. 4.1, lambda_c = 0.01), accumulation of the
   zeroth and first moments M0, M1 (and M2 for checking).
@@ -169,18 +170,25 @@ def child_scores(Z, parent, pi, mu, Sigma):
 
 def posteriors(S):
     """Eq. 3 evaluated as a log-sum-exp with the row maximum subtracted.
-    Returns the posteriors and the per-point log-likelihood log p(z_i)."""
+    Returns the posteriors and the per-point log-likelihood log p(z_i).  A
+    row without any live component (a leaf parent) gets zero posteriors."""
     m = S.max(axis=1, keepdims=True)
-    e = np.exp(S - m)
+    none = ~np.isfinite(m)
+    e = np.exp(S - np.where(none, 0.0, m))
+    e[none[:, 0]] = 0.0
     tot = e.sum(axis=1, keepdims=True)
-    return e / tot, (m + np.log(tot))[:, 0]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        g = np.where(none, 0.0, e / np.where(none, 1.0, tot))
+        ll = np.where(none, -np.inf, m + np.log(tot))
+    return g, ll[:, 0]
 
 
 def mstep_children(Z, parent, gamma, n_parents, n_points_parent, eps, n_min):
     """Maximisation step of every child GMM from the posteriors: expected
     counts S0_c, means, covariances (+ eps I) and weights pi_c = S0_c / n_p.
-    A child whose expected count is below n_min dies (pi = 0) unless it is the
-    parent's heaviest child; children of a parent without points die."""
+    A child whose expected count is below n_min dies (pi = 0); when all eight
+    die the parent is not split (it stays a leaf).  Children of a parent
+    without points are dead."""
     m = n_parents * J
     node = (parent[:, None] * J + np.arange(J)[None, :]).ravel()
     g = gamma.ravel()
@@ -201,20 +209,15 @@ def mstep_children(Z, parent, gamma, n_parents, n_points_parent, eps, n_min):
         pi = S0 / np.repeat(n_points_parent, J)
     S0p = S0.reshape(n_parents, J)
     dead = S0p < n_min
-    heaviest = np.argmax(S0p, axis=1)
-    dead[np.arange(n_parents), heaviest] = False
     dead[n_points_parent == 0, :] = True
     live = ~dead.ravel()
     pi = np.where(live, pi, 0.0)
     return pi, mu, Sigma, live, S0
 
 
-def build_level(Z, parent, n_parents, parent_mu, parent_Sigma, parent_count,
-                params, eps):
-    """One level of the top-down build.  ``parent`` gives each point's parent
-    node (index within the previous level, 0 for the root).  Runs K EM
-    iterations of every parent's 8-child GMM on that parent's points, then the
-    argmax hand-off (ties to the lowest index)."""
+def init_children(n_parents, parent_mu, parent_Sigma, parent_count, eps):
+    """Initial (pi, mu, Sigma, live) of all children: PCA octants of every
+    parent that holds points; children of empty parents are dead."""
     m = n_parents * J
     pi = np.zeros(m)
     mu = np.zeros((m, 3))
@@ -226,18 +229,38 @@ def build_level(Z, parent, n_parents, parent_mu, parent_Sigma, parent_count,
         cm, cS, cp = octant_children(parent_mu[p], parent_Sigma[p], eps)
         sl = slice(p * J, (p + 1) * J)
         mu[sl], Sigma[sl], pi[sl], live[sl] = cm, cS, cp, True
-    history = []
+    return pi, mu, Sigma, live
+
+
+def em_iteration(Z, parent, n_parents, parent_count, pi, mu, Sigma, eps, n_min):
+    """One EM iteration of every parent's 8-child GMM on its own points:
+    E-step (Eq. 3) with the current parameters, then the M-step.  Dead
+    children keep their last parameters (they are never used again).
+    Returns the new (pi, mu, Sigma, live), the expected counts S0 and the
+    per-parent log-likelihood under the parameters the E-step used."""
+    S = child_scores(Z, parent, pi, mu, Sigma)
+    gamma, ll = posteriors(S)
+    pi_n, mu_n, Sig_n, live_n, S0 = mstep_children(
+        Z, parent, gamma, n_parents, parent_count, eps, n_min)
+    mu = np.where(live_n[:, None], mu_n, mu)
+    Sigma = np.where(live_n[:, None, None], Sig_n, Sigma)
+    return pi_n, mu, Sigma, live_n, S0, np.bincount(parent, weights=ll, minlength=n_parents)
+
+
+def build_level(Z, parent, n_parents, parent_mu, parent_Sigma, parent_count,
+                params, eps):
+    """One level of the top-down build.  ``parent`` gives each point's parent
+    node (index within the previous level, 0 for the root).  Runs K EM
+    iterations of every parent's 8-child GMM on that parent's points, then the
+    argmax hand-off (ties to the lowest index)."""
+    m = n_parents * J
+    pi, mu, Sigma, live = init_children(n_parents, parent_mu, parent_Sigma, parent_count, eps)
+    history, s0_hist = [], []
     for _ in range(params.em_iters):
-        S = child_scores(Z, parent, pi, mu, Sigma)
-        gamma, ll = posteriors(S)
-        history.append(np.bincount(parent, weights=ll, minlength=n_parents))
-        pi_n, mu_n, Sig_n, live_n, _ = mstep_children(
-            Z, parent, gamma, n_parents, parent_count, eps, params.n_min)
-        keep = live_n
-        pi = pi_n
-        mu = np.where(keep[:, None], mu_n, mu)
-        Sigma = np.where(keep[:, None, None], Sig_n, Sigma)
-        live = live_n
+        pi, mu, Sigma, live, S0, ll = em_iteration(
+            Z, parent, n_parents, parent_count, pi, mu, Sigma, eps, params.n_min)
+        history.append(ll)
+        s0_hist.append(S0)
     S = child_scores(Z, parent, pi, mu, Sigma)
     _, ll = posteriors(S)
     history.append(np.bincount(parent, weights=ll, minlength=n_parents))
@@ -249,6 +272,7 @@ def build_level(Z, parent, n_parents, parent_mu, parent_Sigma, parent_count,
     lv = Level(pi=pi, mu=mu, Sigma=Sigma, live=live, labels=labels,
                count=count, lam=lam, vec=vec, complexity=complexity(lam),
                loglik=history)
+    lv.s0_hist = s0_hist
     return lv
 
 

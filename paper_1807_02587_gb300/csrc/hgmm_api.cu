@@ -45,8 +45,8 @@ void free_tree(hgmm_tree* t) {
     clear_prof(t);
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
                     t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
-                    t->item_off, t->root, t->root_part, t->status, t->reg_acc, t->reg_part,
-                    t->reg_counter, t->reg_T, t->reg_Rt, t->reg_dbg, t->stage_tgt,
+                    t->item_off, t->root, t->root_part, t->root_counter, t->status, t->reg_acc, t->reg_part,
+                    t->reg_counter, t->reg_T, t->reg_Rt, t->reg_dbg, t->rnode, t->stage_tgt,
                     t->stage_src, t->stage_T};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -137,9 +137,11 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->item_off, t->max_items * 8);
     good &= dalloc(&t->root, 1);
     good &= dalloc(&t->root_part, int64_t(t->est_grid) * 32);
+    good &= dalloc(&t->root_counter, 1);
     good &= dalloc(&t->status, 1);
     good &= dalloc(&t->reg_acc, 4 * t->max_nodes);
     good &= dalloc(&t->reg_part, 27 * nb);
+    good &= dalloc(&t->rnode, 3 * t->max_nodes);
     good &= dalloc(&t->reg_counter, 1);
     good &= dalloc(&t->reg_T, 16);
     good &= dalloc(&t->reg_Rt, 12);
@@ -153,6 +155,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     }
     good &= ok(cudaMemset(t->status, 0, sizeof(int)), "cudaMemset");
     good &= ok(cudaMemset(t->reg_counter, 0, sizeof(unsigned)), "cudaMemset");
+    good &= ok(cudaMemset(t->root_counter, 0, sizeof(unsigned)), "cudaMemset");
     good &= ok(cudaMemset(t->reg_acc, 0, 4 * t->max_nodes * sizeof(unsigned long long)), "cudaMemset");
     good &= ok(cudaMemset(t->stat, 0, t->max_nodes * sizeof(NodeStat)), "cudaMemset");
     good &= ok(cudaMemset(t->seg_count, 0, t->max_nodes * sizeof(int)), "cudaMemset");
@@ -179,7 +182,9 @@ int hgmm_build(hgmm_tree* t, const float* d_points, int64_t n, int32_t depth, in
     if (p) {
         prm = *p;
         if (prm.em_iters < 0 || prm.em_iters > 1000 || !(prm.eps_rel >= 0.f) ||
-            !(prm.n_min >= 0.f) || !(prm.lam_c >= 0.f))
+            !(prm.n_min >= 0.f) || !(prm.lam_c >= 0.f) || prm.debug_stop_level < 0 ||
+            prm.debug_stop_level > depth || prm.debug_stop_iters < 0 ||
+            prm.debug_stop_iters > prm.em_iters)
             return HGMM_EINVAL;
     } else {
         hgmm_params_default(&prm);

@@ -33,11 +33,37 @@ __device__ __forceinline__ int64_t d_level_offset(int l) {
 }
 
 // ---------------------------------------------------------------- root stats
-// partial layout (32 floats): [0..17] 9 compensated pairs of sum (z - z0) and
-// sum (z - z0)(z - z0)^T, [18..20] min, [21..23] max, [24] non-finite count.
-__global__ void __launch_bounds__(256) k_root_partial(const float4* __restrict__ pts, int n,
-                                                       float* __restrict__ part) {
-    __shared__ float sm[8][32];
+// Whole-cloud mean, covariance and bounding box (the root of the tree, whose
+// children are Children(-1) of Algorithm 1).  Sums of (z - z0) and
+// (z - z0)(z - z0)^T with z0 = the first point, FP32 with compensated
+// accumulation.  Each CTA writes a partial (32 floats: [0..17] 9 (sum, err)
+// pairs, [18..20] min, [21..23] max, [24] non-finite count); the last CTA to
+// finish reduces them in a fixed order and writes the FP64 root record.
+__device__ __forceinline__ void root_combine(float* f, const float* o) {
+#pragma unroll
+    for (int v = 0; v < 9; ++v) pair_add(f[2 * v], f[2 * v + 1], o[2 * v], o[2 * v + 1]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[18 + a] = fminf(f[18 + a], o[18 + a]);
+        f[21 + a] = fmaxf(f[21 + a], o[21 + a]);
+    }
+    f[24] = __int_as_float(__float_as_int(f[24]) + __float_as_int(o[24]));
+}
+
+__device__ __forceinline__ void root_identity(float* f) {
+#pragma unroll
+    for (int v = 0; v < 18; ++v) f[v] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { f[18 + a] = CUDART_INF_F; f[21 + a] = -CUDART_INF_F; }
+    f[24] = __int_as_float(0);
+}
+
+__global__ void __launch_bounds__(256) k_root(const float4* __restrict__ pts, int n,
+                                              float eps_rel, float* __restrict__ part,
+                                              unsigned* __restrict__ counter,
+                                              RootDev* __restrict__ root, int* __restrict__ status) {
+    __shared__ float sm[8][25];
+    __shared__ bool last;
     const float4 z0 = pts[0];
     float in[9] = {}, s[9] = {}, c[9] = {};
     float mn[3] = {CUDART_INF_F, CUDART_INF_F, CUDART_INF_F};
@@ -86,62 +112,72 @@ __global__ void __launch_bounds__(256) k_root_partial(const float4* __restrict__
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float S[9], C[9], MN[3], MX[3];
-        int B = 0;
-        for (int v = 0; v < 9; ++v) { S[v] = 0.f; C[v] = 0.f; }
-        for (int a = 0; a < 3; ++a) { MN[a] = CUDART_INF_F; MX[a] = -CUDART_INF_F; }
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            for (int v = 0; v < 9; ++v) pair_add(S[v], C[v], sm[w][2 * v], sm[w][2 * v + 1]);
-            for (int a = 0; a < 3; ++a) {
-                MN[a] = fminf(MN[a], sm[w][18 + a]);
-                MX[a] = fmaxf(MX[a], sm[w][21 + a]);
-            }
-            B += __float_as_int(sm[w][24]);
-        }
+        float f[25];
+        root_identity(f);
+        for (int w = 0; w < 8; ++w) root_combine(f, sm[w]);
         float* o = part + 32 * blockIdx.x;
-        for (int v = 0; v < 9; ++v) { o[2 * v] = S[v]; o[2 * v + 1] = C[v]; }
-        for (int a = 0; a < 3; ++a) { o[18 + a] = MN[a]; o[21 + a] = MX[a]; }
-        o[24] = __int_as_float(B);
+        for (int v = 0; v < 25; ++v) o[v] = f[v];
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
-}
-
-__global__ void k_root_final(const float4* __restrict__ pts, const float* __restrict__ part,
-                             int nblocks, int n, float eps_rel, RootDev* __restrict__ root,
-                             int* __restrict__ status) {
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // last CTA: 16 half-warp groups each reduce every 16th partial (lane i of
+    // a group owns item i: 9 (sum, err) pairs, 3 min, 3 max, count), then one
+    // thread combines the 16 group results in order
+    __shared__ float gs[16][25];
+    {
+        const int grp = threadIdx.x >> 4, it = threadIdx.x & 15;
+        float a = 0.f, b = 0.f;
+        if (it >= 9 && it < 12) a = CUDART_INF_F;
+        if (it >= 12 && it < 15) a = -CUDART_INF_F;
+        int cntb = 0;
+#pragma unroll 4
+        for (int blk = grp; blk < (int)gridDim.x; blk += 16) {
+            const float* o = part + 32 * blk;
+            if (it < 9) pair_add(a, b, __ldcg(o + 2 * it), __ldcg(o + 2 * it + 1));
+            else if (it < 12) a = fminf(a, __ldcg(o + 18 + it - 9));
+            else if (it < 15) a = fmaxf(a, __ldcg(o + 21 + it - 12));
+            else cntb += __float_as_int(__ldcg(o + 24));
+        }
+        if (it < 9) { gs[grp][2 * it] = a; gs[grp][2 * it + 1] = b; }
+        else if (it < 12) gs[grp][18 + it - 9] = a;
+        else if (it < 15) gs[grp][21 + it - 12] = a;
+        else gs[grp][24] = __int_as_float(cntb);
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
-    float S[9], C[9], MN[3], MX[3];
-    int B = 0;
-    for (int v = 0; v < 9; ++v) { S[v] = 0.f; C[v] = 0.f; }
-    for (int a = 0; a < 3; ++a) { MN[a] = CUDART_INF_F; MX[a] = -CUDART_INF_F; }
-    for (int b = 0; b < nblocks; ++b) {
-        const float* o = part + 32 * b;
-        for (int v = 0; v < 9; ++v) pair_add(S[v], C[v], o[2 * v], o[2 * v + 1]);
-        for (int a = 0; a < 3; ++a) { MN[a] = fminf(MN[a], o[18 + a]); MX[a] = fmaxf(MX[a], o[21 + a]); }
-        B += __float_as_int(o[24]);
-    }
-    if (B > 0) atomicOr(status, ST_NONFINITE);
-    const float4 z0 = pts[0];
-    const double z0d[3] = {z0.x, z0.y, z0.z};
+    float F[25];
+    root_identity(F);
+    for (int w = 0; w < 16; ++w) root_combine(F, gs[w]);
+    *counter = 0u;
+    if (__float_as_int(F[24]) > 0) atomicOr(status, ST_NONFINITE);
     const double nn = double(n);
     double m1[3], m2[6];
-    for (int a = 0; a < 3; ++a) m1[a] = (double(S[a]) + double(C[a])) / nn;
-    for (int v = 0; v < 6; ++v) m2[v] = (double(S[3 + v]) + double(C[3 + v])) / nn;
+    for (int a = 0; a < 3; ++a) m1[a] = (double(F[2 * a]) + double(F[2 * a + 1])) / nn;
+    for (int v = 0; v < 6; ++v) m2[v] = (double(F[6 + 2 * v]) + double(F[7 + 2 * v])) / nn;
     root->n = nn;
-    for (int a = 0; a < 3; ++a) root->mu[a] = z0d[a] + m1[a];
-    root->S[0] = m2[0] - m1[0] * m1[0];
-    root->S[1] = m2[1] - m1[0] * m1[1];
-    root->S[2] = m2[2] - m1[0] * m1[2];
-    root->S[3] = m2[3] - m1[1] * m1[1];
-    root->S[4] = m2[4] - m1[1] * m1[2];
-    root->S[5] = m2[5] - m1[2] * m1[2];
+    root->mu[0] = double(z0.x) + m1[0];
+    root->mu[1] = double(z0.y) + m1[1];
+    root->mu[2] = double(z0.z) + m1[2];
+    double S[6];
+    S[0] = m2[0] - m1[0] * m1[0];
+    S[1] = m2[1] - m1[0] * m1[1];
+    S[2] = m2[2] - m1[0] * m1[2];
+    S[3] = m2[3] - m1[1] * m1[1];
+    S[4] = m2[4] - m1[1] * m1[2];
+    S[5] = m2[5] - m1[2] * m1[2];
+    for (int v = 0; v < 6; ++v) root->S[v] = S[v];
     double e2 = 0.0;
     for (int a = 0; a < 3; ++a) {
-        const double d = double(MX[a]) - double(MN[a]);
+        const double d = double(F[21 + a]) - double(F[18 + a]);
         e2 += d * d;
     }
     root->extent = sqrt(e2);
     const double e = double(eps_rel) * root->extent;
     root->eps = e * e;
+    jacobi_eig3(S, root->lam, root->V);
 }
 
 // ---------------------------------------------------------------- init
@@ -154,18 +190,20 @@ __global__ void k_init_children(int level, const RootDev* __restrict__ root,
     const int p = blockIdx.x;
     const int64_t child0 = d_level_offset(level) + 8 * int64_t(p);
     if (threadIdx.x == 0) {
+        // the parent's eigen-decomposition was computed when it was finalised
         if (level == 0) {
-            for (int a = 0; a < 3; ++a) mu_p[a] = root->mu[a];
+            for (int a = 0; a < 3; ++a) { mu_p[a] = root->mu[a]; lam[a] = root->lam[a]; }
             for (int v = 0; v < 6; ++v) S_p[v] = root->S[v];
+            for (int v = 0; v < 9; ++v) V[v] = root->V[v];
             alive = 1;
         } else {
             const int64_t g = d_level_offset(level - 1) + p;
             const NodeStat& ps = stat[g];
-            for (int a = 0; a < 3; ++a) mu_p[a] = ps.mu[a];
+            for (int a = 0; a < 3; ++a) { mu_p[a] = ps.mu[a]; lam[a] = ps.lam[a]; }
             for (int v = 0; v < 6; ++v) S_p[v] = ps.S[v];
+            for (int v = 0; v < 9; ++v) V[v] = ps.V[v];
             alive = (ps.live && seg_count[g] > 0) ? 1 : 0;
         }
-        if (alive) jacobi_eig3(S_p, lam, V);
     }
     __syncthreads();
     const int c = threadIdx.x;
@@ -430,12 +468,13 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
             float m = fmaxf(s0, s1);
             m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
             m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
-            const float p0 = exp2f(s0 - m);
-            const float p1 = exp2f(s1 - m);
+            const bool any_live = m > -CUDART_INF_F;  // false for a leaf parent
+            const float p0 = any_live ? exp2f(s0 - m) : 0.f;
+            const float p1 = any_live ? exp2f(s1 - m) : 0.f;
             float tot = p0 + p1;
             tot += __shfl_xor_sync(FULL, tot, 1);
             tot += __shfl_xor_sync(FULL, tot, 2);
-            const float rinv = valid ? 1.0f / tot : 0.0f;
+            const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
             accum10(in, p0 * rinv, e0x, e0y, e0z);
             accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
             if (++nfold == 16) {
@@ -450,7 +489,7 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
 
 // ---------------------------------------------------------------- M-step
 template <bool COMP>
-__global__ void __launch_bounds__(128) k_mstep(int level, int n, const int* __restrict__ item_range,
+__global__ void __launch_bounds__(256) k_mstep(int level, int n, const int* __restrict__ item_range,
                                                const int* __restrict__ meta,
                                                const float2* __restrict__ partials,
                                                const int* __restrict__ seg_count,
@@ -458,26 +497,33 @@ __global__ void __launch_bounds__(128) k_mstep(int level, int n, const int* __re
                                                NodeStat* __restrict__ stat,
                                                NodeEst* __restrict__ est, int* __restrict__ status) {
     __shared__ double mom[NPART];
-    __shared__ int heavy;
+    __shared__ float2 grp[3][NPART];
     const int p = blockIdx.x;
     const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
     if (i0 >= i1) return;  // parent without points: children stay dead
+    // the parent's runs start at i0 and at every E-step chunk boundary in (i0, i1)
     const int C = meta[1];
-    if (threadIdx.x < NPART) {
+    const int nruns = (i1 - 1) / C - i0 / C + 1;
+    if (threadIdx.x < 3 * NPART) {
+        const int v = threadIdx.x % NPART, q = threadIdx.x / NPART;
         float S = 0.f, Cc = 0.f;
-        for (int slot = i0; slot < i1; slot = (slot / C + 1) * C) {
-            const float2 x = partials[int64_t(slot) * NPART + threadIdx.x];
+#pragma unroll 4
+        for (int r = q; r < nruns; r += 3) {
+            const int slot = r == 0 ? i0 : (i0 / C + r) * C;
+            const float2 x = partials[int64_t(slot) * NPART + v];
             if (COMP) pair_add(S, Cc, x.x, x.y);
             else S += x.x;
         }
-        mom[threadIdx.x] = double(S) + double(Cc);
+        grp[q][v] = make_float2(S, Cc);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int h = 0;
-        for (int cc = 1; cc < 8; ++cc)
-            if (mom[cc * NMOM] > mom[h * NMOM]) h = cc;
-        heavy = h;
+    if (threadIdx.x < NPART) {
+        float S = 0.f, Cc = 0.f;
+        for (int q = 0; q < 3; ++q) {
+            if (COMP) pair_add(S, Cc, grp[q][threadIdx.x].x, grp[q][threadIdx.x].y);
+            else S += grp[q][threadIdx.x].x;
+        }
+        mom[threadIdx.x] = double(S) + double(Cc);
     }
     __syncthreads();
     const int cidx = threadIdx.x;
@@ -488,7 +534,9 @@ __global__ void __launch_bounds__(128) k_mstep(int level, int n, const int* __re
     const double* m = mom + cidx * NMOM;
     const double S0 = m[0];
     const double n_p = level == 0 ? double(n) : double(seg_count[d_level_offset(level - 1) + p]);
-    const bool live = cs.live && (S0 >= double(n_min) || cidx == heavy) && S0 > 0.0;
+    // a child below n_min expected points dies; if all eight die the parent
+    // stays a leaf (its points keep zero posteriors from then on)
+    const bool live = cs.live && S0 >= double(n_min) && S0 > 0.0;
     if (!live) {
         cs.live = 0;
         cs.pi = 0.0;
@@ -678,7 +726,8 @@ __global__ void __launch_bounds__(256) k_scatter(const float4* __restrict__ pts_
 
 // ---------------------------------------------------------------- finalize
 __global__ void k_finalize(int level, float lam_c, const RootDev* __restrict__ root,
-                           NodeStat* __restrict__ stat, NodeEst* __restrict__ est) {
+                           NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
+                           float4* __restrict__ rnode) {
     const int64_t m = int64_t(1) << (3 * (level + 1));
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= m) return;
@@ -690,6 +739,9 @@ __global__ void k_finalize(int level, float lam_c, const RootDev* __restrict__ r
         for (int v = 0; v < 6; ++v) s.P[v] = 0.0;
         s.complexity = 1.0;
         est[g].c.z = 0.f;
+        rnode[3 * g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rnode[3 * g + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rnode[3 * g + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     double lam[3], V[9];
@@ -710,7 +762,14 @@ __global__ void k_finalize(int level, float lam_c, const RootDev* __restrict__ r
         s.P[v] = acc;
     }
     s.complexity = lam[2] / (lam[0] + lam[1] + lam[2]);
+    const float4 a = est[g].a;
     est[g].c.z = (s.complexity <= double(lam_c)) ? 1.f : 0.f;
+    // FP32 registration constants: P and the offset of the FP64 mean from the
+    // FP32 mean the descent measures against
+    rnode[3 * g] = make_float4(float(s.P[0]), float(s.P[1]), float(s.P[2]), float(s.P[3]));
+    rnode[3 * g + 1] = make_float4(float(s.P[4]), float(s.P[5]), 0.f, 0.f);
+    rnode[3 * g + 2] = make_float4(float(s.mu[0] - double(a.x)), float(s.mu[1] - double(a.y)),
+                                   float(s.mu[2] - double(a.z)), 0.f);
 }
 
 // ---------------------------------------------------------------- labels
@@ -754,11 +813,8 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
     const int G = t->est_grid;
     {
         ProfScope ps_(t, K_ROOT_PARTIAL, s);
-        k_root_partial<<<G, 256, 0, s>>>(pts, n, t->root_part);
-    }
-    {
-        ProfScope ps_(t, K_ROOT_FINAL, s);
-        k_root_final<<<1, 32, 0, s>>>(pts, t->root_part, G, n, p.eps_rel, t->root, t->status);
+        k_root<<<G, 256, 0, s>>>(pts, n, p.eps_rel, t->root_part, t->root_counter, t->root,
+                                 t->status);
     }
     HGMM_LAUNCH_CHECK();
     const float4* cur = pts;
@@ -783,7 +839,9 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                 l, n, n_par, t->seg_start, t->seg_count, t->item_range, t->meta, t->items);
         }
         HGMM_LAUNCH_CHECK();
-        for (int k = 0; k < p.em_iters; ++k) {
+        const bool stop_here = p.debug_stop_level == l + 1;
+        const int em_iters = stop_here ? p.debug_stop_iters : p.em_iters;
+        for (int k = 0; k < em_iters; ++k) {
             if (comp) {
                 {
                     ProfScope ps_(t, K_ESTEP, s);
@@ -791,7 +849,7 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                 }
                 {
                     ProfScope ps_(t, K_MSTEP, s);
-                    k_mstep<true><<<n_par, 128, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
+                    k_mstep<true><<<n_par, 256, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
                                                         t->seg_count, t->root, p.n_min, t->stat,
                                                         t->est, t->status);
                 }
@@ -802,13 +860,14 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                 }
                 {
                     ProfScope ps_(t, K_MSTEP, s);
-                    k_mstep<false><<<n_par, 128, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
+                    k_mstep<false><<<n_par, 256, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
                                                          t->seg_count, t->root, p.n_min, t->stat,
                                                          t->est, t->status);
                 }
             }
         }
         HGMM_LAUNCH_CHECK();
+        if (stop_here) return HGMM_OK;  // checking aid: parameters after em_iters
         {
             ProfScope ps_(t, K_ASSIGN, s);
             k_assign<<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->codes, t->item_cnt);
@@ -827,7 +886,8 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
         const int m = int(level_size(l));
         {
             ProfScope ps_(t, K_FINALIZE, s);
-            k_finalize<<<(m + 127) / 128, 128, 0, s>>>(l, p.lam_c, t->root, t->stat, t->est);
+            k_finalize<<<(m + 127) / 128, 128, 0, s>>>(l, p.lam_c, t->root, t->stat, t->est,
+                                                       t->rnode);
         }
         HGMM_LAUNCH_CHECK();
         cur = out;

@@ -73,6 +73,8 @@ struct RootDev {
     double S[6];
     double extent;
     double eps;
+    double lam[3];    // eigen-decomposition of S (descending)
+    double V[9];
 };
 
 enum KernelId {
@@ -122,14 +124,15 @@ struct hgmm_tree {
     int* item_off = nullptr;     // max_items x 8
     hgmm::RootDev* root = nullptr;
     float* root_part = nullptr;  // est_grid x 32
+    unsigned* root_counter = nullptr;
     int* status = nullptr;
     // registration
     unsigned long long* reg_acc = nullptr;  // nodes x 4 fixed point
-    double* reg_part = nullptr;             // blocks x 27
+    float2* reg_part = nullptr;             // blocks x 27 (sum, compensation)
+    float4* rnode = nullptr;                // nodes x 3: P (6), mu - mu32 (3), FP32
     unsigned* reg_counter = nullptr;
     double* reg_T = nullptr;                // 16 doubles current T
     float* reg_Rt = nullptr;                // 12 floats (R row-major, t)
-    unsigned char* reg_stop = nullptr;      // per node stop flag
     double* reg_dbg = nullptr;              // nodes x 4 (last round)
     // per-kernel timing
     bool prof_on = false;

@@ -134,9 +134,13 @@ __device__ inline bool pack_est(double pi, const double mu[3], const double S_in
     const double m21 = -L[4] * m11 * m22;
     const double m20 = -(L[3] * m00 + L[4] * m10) * m22;
     const double k = sqrt(0.5 * 1.4426950408889634);  // sqrt(log2(e) / 2)
-    const double C = log2(pi) - 1.5 * log2(2.0 * CUDART_PI) -
-                     (log2(L[0]) + log2(L[2]) + log2(L[5]));
-    out.a = make_float4(float(mu[0]), float(mu[1]), float(mu[2]), float(C));
+    // log-normaliser in FP32 (it is stored as FP32): log2 det(L) from the
+    // FP64 product split into exponent and mantissa
+    int ex = 0;
+    const double mant = frexp(L[0] * L[2] * L[5], &ex);
+    const float C = log2f(float(pi)) - 3.9547135f /* 1.5 log2(2 pi) */ -
+                    (float(ex) + log2f(float(mant)));
+    out.a = make_float4(float(mu[0]), float(mu[1]), float(mu[2]), C);
     out.b = make_float4(float(k * m00), float(k * m10), float(k * m11), float(k * m20));
     out.c = make_float4(float(k * m21), float(k * m22), stop, 0.f);
     return clean;

@@ -154,43 +154,104 @@ __global__ void __launch_bounds__(REG_THREADS) k_descend(const float4* __restric
     }
 }
 
-// Block-wide sum of 27 doubles into out[27] (fixed order).
-__device__ __forceinline__ void block_sum27(double* v, double (*sm)[27], double* out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Per-node contribution to the 6x6 normal equations in FP32; the sums over
+// nodes are compensated (TwoSum pairs), so the 27 totals that reach the FP64
+// solve carry ~2x FP32 precision.  Per node j with mass (M0 > 0):
+//   mu* = mu_j32 + o,  o = (M1 rel. to mu_j32) / M0,   d = mu_j - mu* = dmu_j - o
+//   H_j = pi* [[A [mu*]x^T, A], [A^T, P]],  A = [mu*]x P,   g_j = pi* [mu* x P d; P d]
+__device__ __forceinline__ void node_terms(const float4 p0, const float4 p1, const float4 dm,
+                                           const float4 cm, float M0, float o0, float o1,
+                                           float o2, float pis, float* v) {
+    const float P[3][3] = {{p0.x, p0.y, p0.z}, {p0.y, p0.w, p1.x}, {p0.z, p1.x, p1.y}};
+    const float m0 = cm.x + o0, m1 = cm.y + o1, m2 = cm.z + o2;
+    const float d0 = dm.x - o0, d1 = dm.y - o1, d2 = dm.z - o2;
+    float A[3][3], Bm[3][3];
 #pragma unroll
-    for (int k = 0; k < 27; ++k) {
-        double x = v[k];
+    for (int k = 0; k < 3; ++k) {
+        A[0][k] = m1 * P[2][k] - m2 * P[1][k];
+        A[1][k] = m2 * P[0][k] - m0 * P[2][k];
+        A[2][k] = m0 * P[1][k] - m1 * P[0][k];
+    }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
-        v[k] = x;
+    for (int i = 0; i < 3; ++i) {
+        Bm[i][0] = m1 * A[i][2] - m2 * A[i][1];
+        Bm[i][1] = m2 * A[i][0] - m0 * A[i][2];
+        Bm[i][2] = m0 * A[i][1] - m1 * A[i][0];
     }
-    if (lane == 0)
-        for (int k = 0; k < 27; ++k) sm[warp][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x < 27) {
-        double s = 0.0;
-        for (int w = 0; w < MSTEP_THREADS / 32; ++w) s += sm[w][threadIdx.x];
-        out[threadIdx.x] = s;
+    float Pd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Pd[i] = P[i][0] * d0 + P[i][1] * d1 + P[i][2] * d2;
+    const float top[3] = {m1 * Pd[2] - m2 * Pd[1], m2 * Pd[0] - m0 * Pd[2], m0 * Pd[1] - m1 * Pd[0]};
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) {
+            float h;
+            if (i < 3 && j < 3) h = Bm[i][j];
+            else if (i < 3) h = A[i][j - 3];
+            else h = P[i - 3][j - 3];
+            v[k++] = pis * h;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        v[21 + i] = pis * top[i];
+        v[24 + i] = pis * Pd[i];
     }
+    (void)M0;
+}
+
+// T <- dT T with dT = (Rodrigues(w), t); FP64.  sin(th)/th and
+// (1 - cos th)/th^2 by their Taylor series for th < 0.5 (truncation < 1e-15).
+__device__ inline void compose_update(const double x[6], double* T) {
+    const double th2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    double a, b;
+    if (th2 < 0.25) {
+        a = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880 +
+            th2 * (-1.0 / 39916800 + th2 * (1.0 / 6227020800.0))))));
+        b = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720 + th2 * (-1.0 / 40320 + th2 * (1.0 / 3628800 +
+            th2 * (-1.0 / 479001600 + th2 * (1.0 / 87178291200.0))))));
+    } else {
+        const double th = sqrt(th2);
+        a = sin(th) / th;
+        b = (1.0 - cos(th)) / th2;
+    }
+    const double K[9] = {0, -x[2], x[1], x[2], 0, -x[0], -x[1], x[0], 0};
+    double dR[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double kk = 0.0;
+            for (int m = 0; m < 3; ++m) kk += K[i * 3 + m] * K[m * 3 + j];
+            dR[i * 3 + j] = (i == j ? 1.0 : 0.0) + a * K[i * 3 + j] + b * kk;
+        }
+    double Tn[12];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 4; ++c)
+            Tn[r * 4 + c] = dR[r * 3 + 0] * T[c] + dR[r * 3 + 1] * T[4 + c] + dR[r * 3 + 2] * T[8 + c];
+        Tn[r * 4 + 3] += x[3 + r];
+    }
+    for (int k = 0; k < 12; ++k) T[k] = Tn[k];
 }
 
 __global__ void __launch_bounds__(MSTEP_THREADS) k_mstep(int n_nodes, int n_src, int iter,
-                                                        const NodeStat* __restrict__ stat,
+                                                        const float4* __restrict__ rnode,
                                                         const NodeEst* __restrict__ est,
                                                         const RootDev* __restrict__ root,
                                                         unsigned long long* __restrict__ acc,
-                                                        double* __restrict__ part,
+                                                        float2* __restrict__ part,
                                                         unsigned* __restrict__ counter,
                                                         double* __restrict__ T, float* __restrict__ Rt,
                                                         double* __restrict__ T_hist,
                                                         double* __restrict__ dbg,
                                                         int* __restrict__ status) {
-    __shared__ double sm[MSTEP_THREADS / 32][27];
+    __shared__ float2 sm[MSTEP_THREADS / 32][27];
+    __shared__ float2 fin[4][27];
     __shared__ bool last;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[27];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float v[27], c[27];
 #pragma unroll
-    for (int k = 0; k < 27; ++k) v[k] = 0.0;
+    for (int k = 0; k < 27; ++k) { v[k] = 0.f; c[k] = 0.f; }
     if (g < n_nodes) {
         const long long a0 = (long long)acc[4 * g + 0];
         const long long a1 = (long long)acc[4 * g + 1];
@@ -200,100 +261,82 @@ __global__ void __launch_bounds__(MSTEP_THREADS) k_mstep(int n_nodes, int n_src,
         acc[4 * g + 1] = 0ull;
         acc[4 * g + 2] = 0ull;
         acc[4 * g + 3] = 0ull;
-        const double M0 = double(a0) * INV_FIX;
-        double ms[3] = {0.0, 0.0, 0.0};
+        const float4 cm = est[g].a;
+        float M0 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
         if (a0 > 0) {
-            const float4 cm = est[g].a;
-            // decode with the same FP32 scale the descent used
+            M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
             const float qs = float(FIX / (root->extent > 0.0 ? root->extent : 1.0));
-            const double r = 1.0 / (double(qs) * M0);
-            ms[0] = double(cm.x) + double(a1) * r;
-            ms[1] = double(cm.y) + double(a2) * r;
-            ms[2] = double(cm.z) + double(a3) * r;
-            const double pis = M0 / double(n_src);
-            const NodeStat& st = stat[g];
-            const double* P = st.P;
-            const double Pm[3][3] = {{P[0], P[1], P[2]}, {P[1], P[3], P[4]}, {P[2], P[4], P[5]}};
-            const double d[3] = {st.mu[0] - ms[0], st.mu[1] - ms[1], st.mu[2] - ms[2]};
-            // A = [mu*]x P (column k = mu* x P[:,k]); B = A [mu*]x^T (row i = mu* x A[i,:])
-            double A[3][3], Bm[3][3];
-            for (int k = 0; k < 3; ++k) {
-                A[0][k] = ms[1] * Pm[2][k] - ms[2] * Pm[1][k];
-                A[1][k] = ms[2] * Pm[0][k] - ms[0] * Pm[2][k];
-                A[2][k] = ms[0] * Pm[1][k] - ms[1] * Pm[0][k];
-            }
-            for (int i = 0; i < 3; ++i) {
-                Bm[i][0] = ms[1] * A[i][2] - ms[2] * A[i][1];
-                Bm[i][1] = ms[2] * A[i][0] - ms[0] * A[i][2];
-                Bm[i][2] = ms[0] * A[i][1] - ms[1] * A[i][0];
-            }
-            double Pd[3];
-            for (int i = 0; i < 3; ++i) Pd[i] = Pm[i][0] * d[0] + Pm[i][1] * d[1] + Pm[i][2] * d[2];
-            const double top[3] = {ms[1] * Pd[2] - ms[2] * Pd[1], ms[2] * Pd[0] - ms[0] * Pd[2],
-                                   ms[0] * Pd[1] - ms[1] * Pd[0]};
-            // H (6x6, upper row-major): [[B, A], [A^T, P]]
-            double H[6][6];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    H[i][j] = Bm[i][j];
-                    H[i][3 + j] = A[i][j];
-                    H[3 + i][3 + j] = Pm[i][j];
-                }
-            int k = 0;
-            for (int i = 0; i < 6; ++i)
-                for (int j = i; j < 6; ++j) v[k++] = pis * H[i][j];
-            for (int i = 0; i < 3; ++i) {
-                v[21 + i] = pis * top[i];
-                v[24 + i] = pis * Pd[i];
-            }
+            const float inv = 1.0f / (qs * M0);
+            o0 = float(a1) * inv;
+            o1 = float(a2) * inv;
+            o2 = float(a3) * inv;
+            node_terms(rnode[3 * g], rnode[3 * g + 1], rnode[3 * g + 2], cm, M0, o0, o1, o2,
+                       M0 / float(n_src), v);
         }
         if (dbg) {
-            dbg[4 * g + 0] = M0;
-            dbg[4 * g + 1] = M0 * ms[0];
-            dbg[4 * g + 2] = M0 * ms[1];
-            dbg[4 * g + 3] = M0 * ms[2];
+            dbg[4 * g + 0] = double(a0) * INV_FIX;
+            dbg[4 * g + 1] = double(M0) * (double(cm.x) + double(o0));
+            dbg[4 * g + 2] = double(M0) * (double(cm.y) + double(o1));
+            dbg[4 * g + 3] = double(M0) * (double(cm.z) + double(o2));
         }
     }
-    block_sum27(v, sm, part + 27 * blockIdx.x);
+    // compensated warp + block reduction, fixed order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < 27; ++k) {
+            const float s2 = __shfl_xor_sync(FULL, v[k], off);
+            const float c2 = __shfl_xor_sync(FULL, c[k], off);
+            pair_add(v[k], c[k], s2, c2);
+        }
+    if (lane == 0)
+        for (int k = 0; k < 27; ++k) sm[warp][k] = make_float2(v[k], c[k]);
+    __syncthreads();
+    if (threadIdx.x < 27) {
+        float S = 0.f, C = 0.f;
+        for (int w = 0; w < MSTEP_THREADS / 32; ++w) pair_add(S, C, sm[w][threadIdx.x].x, sm[w][threadIdx.x].y);
+        part[27 * blockIdx.x + threadIdx.x] = make_float2(S, C);
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // the last CTA: fixed-order sum over CTAs, solve, update
-    __shared__ double tot[27];
-    if (threadIdx.x < 27) {
-        double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double*)part)[27 * b + threadIdx.x];
-        tot[threadIdx.x] = s;
+    // the last CTA: 4 groups of 27 threads sum the block partials (fixed order)
+    const int nb = gridDim.x;
+    if (threadIdx.x < 108) {
+        const int k = threadIdx.x % 27, q = threadIdx.x / 27;
+        float S = 0.f, C = 0.f;
+        for (int b = q; b < nb; b += 4) {
+            const float2 x = __ldcg(&part[27 * b + k]);
+            pair_add(S, C, x.x, x.y);
+        }
+        fin[q][k] = make_float2(S, C);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        double tot[27];
+        for (int k = 0; k < 27; ++k) {
+            float S = 0.f, C = 0.f;
+            for (int q = 0; q < 4; ++q) pair_add(S, C, fin[q][k].x, fin[q][k].y);
+            tot[k] = double(S) + double(C);
+        }
         double x[6];
-        const bool ok = chol_solve6(tot, tot + 21, x);
-        double Tn[16];
-        for (int k = 0; k < 16; ++k) Tn[k] = T[k];
-        if (ok) {
-            double dR[9];
-            rodrigues(x, dR);
-            for (int r = 0; r < 3; ++r) {
-                for (int c = 0; c < 3; ++c)
-                    Tn[r * 4 + c] = dR[r * 3 + 0] * T[0 * 4 + c] + dR[r * 3 + 1] * T[1 * 4 + c] +
-                                    dR[r * 3 + 2] * T[2 * 4 + c];
-                Tn[r * 4 + 3] = dR[r * 3 + 0] * T[3] + dR[r * 3 + 1] * T[7] + dR[r * 3 + 2] * T[11] +
-                                x[3 + r];
-            }
+        double Tl[16];
+        for (int k = 0; k < 16; ++k) Tl[k] = T[k];
+        if (chol_solve6(tot, tot + 21, x)) {
+            compose_update(x, Tl);
         } else {
             atomicOr(status, ST_DEGENERATE);
         }
-        for (int k = 0; k < 16; ++k) T[k] = Tn[k];
+        for (int k = 0; k < 16; ++k) T[k] = Tl[k];
         for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) Rt[r * 3 + c] = float(Tn[r * 4 + c]);
-            Rt[9 + r] = float(Tn[r * 4 + 3]);
+            for (int cc = 0; cc < 3; ++cc) Rt[r * 3 + cc] = float(Tl[r * 4 + cc]);
+            Rt[9 + r] = float(Tl[r * 4 + 3]);
         }
         if (T_hist)
-            for (int k = 0; k < 16; ++k) T_hist[16 * iter + k] = Tn[k];
+            for (int k = 0; k < 16; ++k) T_hist[16 * iter + k] = Tl[k];
         *counter = 0u;
     }
 }
@@ -327,7 +370,7 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         }
         {
             ProfScope ps_(t, K_REG_MSTEP, s);
-            k_mstep<<<nb, MSTEP_THREADS, 0, s>>>(n_nodes, n, it, t->stat, t->est, t->root, t->reg_acc,
+            k_mstep<<<nb, MSTEP_THREADS, 0, s>>>(n_nodes, n, it, t->rnode, t->est, t->root, t->reg_acc,
                                                  t->reg_part, t->reg_counter, t->reg_T, t->reg_Rt,
                                                  T_hist, t->reg_dbg, t->status);
         }

@@ -45,6 +45,23 @@ def test_build_matches_oracle_teacher_forced(B, case):
         assert r["pi"] < PT.PI_TOL, (l, r)
         assert r["label_disagree_not_tie"] == 0, (l, r)
         assert r["label_disagree"] <= max(3, 1e-3 * Z.shape[0]), (l, r)
+        # near-tie / ill-conditioned parents are few
+        assert r["excluded_parents"] <= max(2, 0.02 * r["parents_with_points"]), (l, r)
+
+
+@pytest.mark.parametrize("case", ["corner10k_d3", "lidar_d4"])
+def test_em_iteration_teacher_forced(B, case):
+    """One EM iteration at a time: GPU parameters after iteration k against
+    the oracle's iteration from the GPU's parameters after k-1 (every level;
+    first, middle and last iteration)."""
+    make, depth = _cases()[case]
+    dev, Z = PT.device_cloud(make())
+    steps = [(l, k) for l in range(depth) for k in (1, 4, 8)]
+    res = PT.check_em_steps(B, dev, Z, depth, steps)
+    for r in res:
+        print(case, r)
+        assert r["live_mismatch"] == 0, r
+        assert r["mu"] < 1e-5 and r["S"] < 1e-5 and r["pi"] < 1e-5, r
 
 
 def test_build_is_deterministic(B):

@@ -42,6 +42,7 @@ def test_small_and_deep_trees(B, n, depth):
         res = PT.check_build(tree, Z, PT.oracle_params(B.params(), depth))
         for r in res["levels"]:
             assert r["live_mismatch"] == 0 and r["mu"] < PT.MEAN_TOL and r["S"] < PT.COV_TOL, r
+            assert r["excluded_parents"] <= max(2, 0.02 * r["parents_with_points"]), r
 
 
 def test_coincident_points(B):

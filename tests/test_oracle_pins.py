@@ -113,8 +113,10 @@ def test_sibling_mass_equals_parent_count():
         g, _ = O.posteriors(Sx)
         *_, S0 = O.mstep_children(Z, prev, g, n_par,
                                   np.bincount(prev, minlength=n_par), tree.eps, 8)
+        split = lv.live.reshape(n_par, 8).any(1)  # leaf parents keep zero posteriors
         np.testing.assert_allclose(S0.reshape(n_par, 8).sum(1),
-                                   np.bincount(prev, minlength=n_par), rtol=1e-12)
+                                   np.where(split, np.bincount(prev, minlength=n_par), 0),
+                                   rtol=1e-12)
         assert lv.count.sum() == Z.shape[0]
         prev = lv.labels
 
@@ -159,18 +161,22 @@ def test_blob_mixture_recovery():
 
 def test_dead_children_and_terminal_nodes():
     """Children with fewer than n_min expected points get pi = 0 and never
-    receive points; a parent without points has no live children."""
+    receive points; a parent without points, or whose children all fall below
+    n_min, has no live children; a parent with >= 8 n_min points always has
+    one (pigeonhole)."""
     Z = S.corner_scene(S.make_rng(7), 600)
     tree = O.build_tree(Z, O.Params(depth=3, n_min=8))
     for l, lv in enumerate(tree.levels):
         assert np.all(lv.pi[~lv.live] == 0)
-        assert np.all(lv.count[~lv.live] == 0)
         n_par = lv.pi.shape[0] // 8
-        par_count = (np.bincount(tree.levels[l - 1].labels, minlength=n_par)
-                     if l else np.array([Z.shape[0]]))
         live_par = lv.live.reshape(n_par, 8).any(1)
-        assert np.array_equal(live_par, par_count > 0)
-        tot = lv.pi.reshape(n_par, 8).sum(1)[par_count > 0]
+        # points of a leaf parent stay on its (dead) first child's segment
+        assert np.all(lv.count[~lv.live & ~np.repeat(~live_par, 8)] == 0)
+        par_count = (np.where(tree.levels[l - 1].live, tree.levels[l - 1].count, 0)
+                     if l else np.array([Z.shape[0]]))
+        assert np.all(live_par[par_count >= 64])
+        assert not np.any(live_par[par_count == 0])
+        tot = lv.pi.reshape(n_par, 8).sum(1)[live_par]
         assert np.all(tot <= 1.0 + 1e-12) and np.all(tot > 0.5)
 
 
