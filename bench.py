@@ -50,7 +50,7 @@ KERNEL_WORK = {
     "estep": {"bytes": 16, "flops": 355, "unit": "target point"},
     "assign": {"bytes": 20, "flops": 160, "unit": "target point"},
     "scatter": {"bytes": 44, "flops": 0, "unit": "target point"},
-    "descend": {"bytes": 16, "flops": None, "unit": "source point"},
+    "register": {"bytes": 16, "flops": None, "unit": "source point"},
 }
 DESCEND_FLOPS_PER_LEVEL = 8 * 18 + 8 * 2 + 8  # 8 child scores, 8 exp2 + sum, rcp
 DESCEND_FLOPS_FIXED = 18 + 12  # transform, fixed-point conversion
@@ -218,10 +218,18 @@ def gpu_main(args, rank, world, local_rank):
     launches_per_step = sum(c for _, c in prof.values()) // 2
 
     graph = None
+    graph_note = "disabled"
     if not args.no_graph:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=s):
-            step()
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                step()
+            graph_note = "captured"
+        except Exception as e:  # capture unsupported: time eager launches
+            graph = None
+            graph_note = f"capture failed ({type(e).__name__}: {str(e)[:120]}), eager launches"
+            torch.cuda.synchronize()
+    if graph is not None:
         T_out.zero_()
         torch.cuda.synchronize()
         with torch.cuda.stream(s):
@@ -299,9 +307,11 @@ def gpu_main(args, rank, world, local_rank):
     roof = {"kernel": dom, "avg_launch_us": dom_ms * 1e3}
     work = KERNEL_WORK.get(dom)
     units = n_t if (work and work["unit"] == "target point") else n_s
-    if dom == "descend":
+    if dom == "register":
+        # one launch runs all ITERS rounds of Algorithm 1 + the M-step
         lv = _descend_levels(B, tree, src4, DEPTH)
         flops_pt = DESCEND_FLOPS_FIXED + DESCEND_FLOPS_PER_LEVEL * lv
+        units = n_s * ITERS
         roof.update(bound="alu", achieved=flops_pt * units / (dom_ms / 1e3) / 1e12,
                     peak=fp32_peak_tflops, unit="TFLOP/s",
                     note=f"FP32 flops/point {flops_pt:.0f} (avg {lv:.2f} levels visited); "
@@ -344,7 +354,7 @@ def gpu_main(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "n_target": n_t, "n_source": n_s, "depth": DEPTH,
                    "J": 8, "em_iters": prm.em_iters, "reg_iters": ITERS,
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
-                   "cuda_graph": graph is not None, "parallelism": f"replicas{world}"},
+                   "cuda_graph": graph_note, "parallelism": f"replicas{world}"},
         "pairs_per_s": world / (ms_max / 1e3),
         "e2e": {"value": pts_tot / (e2e_max / 1e3) / 1e6, "unit": "Mpts/s",
                 "h2d_bytes_per_step": int(16 * (n_t + n_s)), "d2h_bytes_per_step": 128,

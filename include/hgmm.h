@@ -32,7 +32,10 @@
  *   - The tree lives on the device that was current at hgmm_tree_create and
  *     every call must run with that device current.
  *   - No entry point except hgmm_tree_create / hgmm_tree_destroy allocates or
- *     frees device memory, so build + register can be captured in a CUDA graph.
+ *     frees device memory, so build + register can be captured in a CUDA graph
+ *     (the registration is one cooperative launch).
+ *   - Device-side waits are bounded: the registration's grid barriers give up
+ *     after about a second, record HGMM_ETIMEOUT and return.
  */
 #ifndef HGMM_H
 #define HGMM_H
@@ -150,6 +153,13 @@ int hgmm_debug_root(hgmm_tree* t, double* h_root12);
  * of every level (levels concatenated) [M0, M1_x, M1_y, M1_z] float64 with M1
  * = sum gamma z' in the model frame (Algorithm 1, Eq. 9). */
 int hgmm_debug_reg_moments(hgmm_tree* t, double* h_m, int64_t cap);
+
+/* Failure-detection check: runs the registration's bounded grid barrier with
+ * one of the two arrivals it expects, so the wait must give up after
+ * spin_limit polls (~1 us each).  The kernel then records the timeout and
+ * returns normally (no fault, no hang): the next hgmm_sync returns
+ * HGMM_ETIMEOUT and the tree stays usable.  Enqueued on `stream`. */
+int hgmm_debug_barrier_timeout(hgmm_tree* t, int64_t spin_limit, void* stream);
 
 /* ---- per-kernel timing (tracing) ----
  * hgmm_profile(t, 1) clears and starts recording a CUDA event pair around

@@ -65,6 +65,7 @@ def _load():
         "hgmm_debug_reg_moments": (ctypes.c_int, [vp, vp, i64]),
         "hgmm_node_count": (i64, [i32]),
         "hgmm_profile": (ctypes.c_int, [vp, i32]),
+        "hgmm_debug_barrier_timeout": (ctypes.c_int, [vp, i64, vp]),
         "hgmm_profile_read": (ctypes.c_int, [vp, i32, P(ctypes.c_char_p), P(ctypes.c_double),
                                              P(ctypes.c_int64)]),
         "hgmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -215,6 +216,11 @@ def hgmm_debug_reg_moments(h, n_nodes: int) -> np.ndarray:
 
 
 HGMM_PROF_KERNELS = 16
+
+
+def hgmm_debug_barrier_timeout(h, spin_limit: int, stream=None) -> None:
+    _check(_lib.hgmm_debug_barrier_timeout(h, int(spin_limit), _stream_ptr(stream)),
+           "hgmm_debug_barrier_timeout")
 
 
 def hgmm_profile(h, enable: bool) -> None:

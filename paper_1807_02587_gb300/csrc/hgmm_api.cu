@@ -34,7 +34,7 @@ void clear_prof(hgmm_tree* t) {
 
 const char* const kKernelNames[HGMM_PROF_KERNELS] = {
     "root_partial", "root_final", "init_children", "make_items", "fill_items", "estep",
-    "mstep", "assign", "child_offsets", "scatter", "finalize", "reg_init", "descend",
+    "mstep", "assign", "child_offsets", "scatter", "finalize", "reg_init", "register",
     "reg_mstep", "copy_T", "labels"};
 
 void free_tree(hgmm_tree* t) {
@@ -44,9 +44,9 @@ void free_tree(hgmm_tree* t) {
     cudaSetDevice(t->device);
     clear_prof(t);
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
-                    t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
+                    t->codes, t->items, t->item_range, t->pdone, t->meta, t->partials, t->item_cnt,
                     t->item_off, t->root, t->root_part, t->root_counter, t->status, t->reg_acc, t->reg_part,
-                    t->reg_counter, t->reg_T, t->reg_Rt, t->reg_dbg, t->rnode, t->stage_tgt,
+                    t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->rnode, t->stage_tgt,
                     t->stage_src, t->stage_T};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -118,8 +118,12 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     const int64_t parents = max_depth >= 2 ? level_size(max_depth - 2) : 1;
     t->max_items = (max_points + TILE - 1) / TILE + parents;
     t->est_grid = t->n_sm * 2;
-    t->reg_grid = t->n_sm * 4;
-    const int64_t nb = (t->max_nodes + MSTEP_THREADS - 1) / MSTEP_THREADS;
+    t->reg_grid = hgmm_register_grid(t->n_sm);
+    if (t->reg_grid < 1) {
+        delete t;
+        return HGMM_ECUDA;
+    }
+    const int64_t nb = t->reg_grid;  // one normal-equation partial per registration CTA
     bool good = true;
     good &= dalloc(&t->est, t->max_nodes);
     good &= dalloc(&t->stat, t->max_nodes);
@@ -131,6 +135,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->codes, max_points);
     good &= dalloc(&t->items, t->max_items);
     good &= dalloc(&t->item_range, 2 * std::max<int64_t>(parents, 1));
+    good &= dalloc(&t->pdone, std::max<int64_t>(parents, 1));
     good &= dalloc(&t->meta, 4);
     good &= dalloc(&t->partials, t->max_items * NPART);
     good &= dalloc(&t->item_cnt, t->max_items * 8);
@@ -142,7 +147,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->reg_acc, 4 * t->max_nodes);
     good &= dalloc(&t->reg_part, 27 * nb);
     good &= dalloc(&t->rnode, 3 * t->max_nodes);
-    good &= dalloc(&t->reg_counter, 1);
+    good &= dalloc(&t->reg_bar, 8);
     good &= dalloc(&t->reg_T, 16);
     good &= dalloc(&t->reg_Rt, 12);
     good &= dalloc(&t->reg_dbg, 4 * t->max_nodes);
@@ -154,8 +159,9 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
         return HGMM_ENOMEM;
     }
     good &= ok(cudaMemset(t->status, 0, sizeof(int)), "cudaMemset");
-    good &= ok(cudaMemset(t->reg_counter, 0, sizeof(unsigned)), "cudaMemset");
+    good &= ok(cudaMemset(t->reg_bar, 0, 8 * sizeof(unsigned)), "cudaMemset");
     good &= ok(cudaMemset(t->root_counter, 0, sizeof(unsigned)), "cudaMemset");
+    good &= ok(cudaMemset(t->pdone, 0, std::max<int64_t>(parents, 1) * sizeof(int)), "cudaMemset");
     good &= ok(cudaMemset(t->reg_acc, 0, 4 * t->max_nodes * sizeof(unsigned long long)), "cudaMemset");
     good &= ok(cudaMemset(t->stat, 0, t->max_nodes * sizeof(NodeStat)), "cudaMemset");
     good &= ok(cudaMemset(t->seg_count, 0, t->max_nodes * sizeof(int)), "cudaMemset");
@@ -313,6 +319,12 @@ int hgmm_debug_reg_moments(hgmm_tree* t, double* h_m, int64_t cap) {
     if (!ok(cudaMemcpy(h_m, t->reg_dbg, size_t(4 * m) * sizeof(double), cudaMemcpyDeviceToHost), "D2H"))
         return HGMM_ECUDA;
     return HGMM_OK;
+}
+
+int hgmm_debug_barrier_timeout(hgmm_tree* t, int64_t spin_limit, void* stream) {
+    if (!t || spin_limit < 1 || spin_limit > 100000000) return HGMM_EINVAL;
+    if (int rc = check_device(t)) return rc;
+    return hgmm_barrier_timeout_probe_impl(t, spin_limit, static_cast<cudaStream_t>(stream));
 }
 
 int hgmm_profile(hgmm_tree* t, int32_t enable) {

@@ -6,13 +6,14 @@
 //   k_init_children   PCA-octant initial children of every parent (FP64 eigen)
 //   k_make_items      split each parent's contiguous point segment into work
 //                     items of <= TILE points, laid out parent by parent
-//   K x { k_estep     per point: Eq. 3 posteriors over the 8 children of its
+//   K x k_estep       per point: Eq. 3 posteriors over the 8 children of its
 //                     parent (FP32, log2 domain, max-subtracted exp2) and the
 //                     gamma-weighted moments S0, S1, S2 of every child,
 //                     centred on the child's current mean; compensated sums;
-//                     one partial per (CTA, parent) run
-//         k_mstep }   per parent: reduce its runs, FP64 M-step, Cholesky, the
-//                     dead-child rule, new FP32 E-step constants
+//                     one partial per (CTA, parent) run.  The CTA that
+//                     completes a parent's last run also runs its M-step:
+//                     fixed-order reduction of the runs, FP64 M-step and
+//                     Cholesky, dead-child rule, new FP32 E-step constants
 //   k_assign          argmax hand-off (ties -> lowest index) with in-item ranks
 //   k_child_offsets   per parent: child segment starts and per-item offsets
 //   k_scatter         stable 8-way partition of every parent's segment
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(256) k_root(const float4* __restrict__ pts, in
     root->extent = sqrt(e2);
     const double e = double(eps_rel) * root->extent;
     root->eps = e * e;
-    jacobi_eig3(S, root->lam, root->V);
+    eig3(S, root->lam, root->V);
 }
 
 // ---------------------------------------------------------------- init
@@ -224,7 +225,8 @@ __global__ void k_init_children(int level, const RootDev* __restrict__ root,
         double acc = mu_p[a];
         for (int b = 0; b < 3; ++b) {
             const double sgn = ((c >> b) & 1) ? 1.0 : -1.0;
-            acc += sgn * 0.5 * sqrt(fmax(lam[b], 0.0)) * V[a * 3 + b];
+            const double lb = fmax(lam[b], 0.0);
+            acc += sgn * 0.5 * (lb > 0.0 ? lb * rsqrt_f64(lb) : 0.0) * V[a * 3 + b];
         }
         mu[a] = acc;
     }
@@ -256,12 +258,10 @@ __global__ void __launch_bounds__(1024) k_make_items(int level, int n, int n_par
         const int p = base + threadIdx.x;
         int count = 0;
         if (p < n_parents) {
-            if (level == 0) {
-                count = n;
-            } else {
-                const int64_t g = poff + p;
-                count = stat[g].live ? seg_count[g] : 0;
-            }
+            // every parent segment that holds points gets items, live or not:
+            // points under a leaf parent (no live children) are carried down on
+            // its first child's segment with zero posteriors
+            count = level == 0 ? n : seg_count[poff + p];
         }
         const int k = (count + TILE - 1) / TILE;
         // block exclusive scan of k
@@ -295,8 +295,13 @@ __global__ void __launch_bounds__(1024) k_make_items(int level, int n, int n_par
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        // items per E-step CTA: enough CTAs to cover the items, but at least
+        // ~sqrt(items)/4 items each so that the last CTA of a big parent has
+        // few run partials to reduce
         meta[0] = carry;
-        meta[1] = max(1, (carry + est_grid - 1) / est_grid);
+        int rt = 1;
+        while ((rt + 1) * (rt + 1) <= carry) ++rt;
+        meta[1] = max(max(1, (carry + est_grid - 1) / est_grid), rt / 4);
     }
 }
 
@@ -328,6 +333,85 @@ __global__ void k_fill_items(int level, int n, int n_parents, const int* __restr
     it.count = min(TILE, count - r * TILE);
     it.pad = 0;
     items[j] = it;
+}
+
+// ---------------------------------------------------------------- M-step
+// M-step of parent p (Sec. 3 EM on the parent's points): reduce the parent's
+// run partials in a fixed order (3 groups of 80 threads, then in order),
+// then threads 0..7 build child c in FP64: S0, mean shift d = S1/S0 from the
+// FP32 mean the E-step used, Sigma = S2/S0 - d d^T + eps I, pi = S0 / n_p;
+// a child below n_min expected points dies (a parent whose children all die
+// stays a leaf).  Needs >= 240 threads.
+struct MstepSmem {
+    double mom[NPART];
+    float2 grp[3][NPART];
+};
+
+template <bool COMP>
+__device__ void mstep_parent(int level, int n, int p, int i0, int i1, int C,
+                             const float2* __restrict__ partials,
+                             const int* __restrict__ seg_count, const RootDev* __restrict__ root,
+                             float n_min, NodeStat* __restrict__ stat,
+                             NodeEst* __restrict__ est, int* __restrict__ status, MstepSmem& sm) {
+    const int nruns = (i1 - 1) / C - i0 / C + 1;
+    if (threadIdx.x < 3 * NPART) {
+        const int v = threadIdx.x % NPART, q = threadIdx.x / NPART;
+        float S = 0.f, Cc = 0.f;
+#pragma unroll 4
+        for (int r = q; r < nruns; r += 3) {
+            const int slot = r == 0 ? i0 : (i0 / C + r) * C;
+            const float2 x = __ldcg(&partials[int64_t(slot) * NPART + v]);
+            if (COMP) pair_add(S, Cc, x.x, x.y);
+            else S += x.x;
+        }
+        sm.grp[q][v] = make_float2(S, Cc);
+    }
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        float S = 0.f, Cc = 0.f;
+        for (int q = 0; q < 3; ++q) {
+            if (COMP) pair_add(S, Cc, sm.grp[q][threadIdx.x].x, sm.grp[q][threadIdx.x].y);
+            else S += sm.grp[q][threadIdx.x].x;
+        }
+        sm.mom[threadIdx.x] = double(S) + double(Cc);
+    }
+    __syncthreads();
+    const int cidx = threadIdx.x;
+    if (cidx < 8) {
+        const int64_t g = d_level_offset(level) + 8 * int64_t(p) + cidx;
+        NodeStat& cs = stat[g];
+        NodeEst& ce = est[g];
+        const double* m = sm.mom + cidx * NMOM;
+        const double S0 = m[0];
+        const double n_p = level == 0 ? double(n) : double(seg_count[d_level_offset(level - 1) + p]);
+        const bool live = cs.live && S0 >= double(n_min) && S0 > 0.0;
+        if (!live) {
+            cs.live = 0;
+            cs.pi = 0.0;
+            ce.a.w = -CUDART_INF_F;
+            ce.b = make_float4(0.f, 0.f, 0.f, 0.f);
+            ce.c.x = 0.f;
+            ce.c.y = 0.f;
+        } else {
+            const double eps = root->eps;
+            const double inv = rcp_f64(S0);
+            const double d[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
+            const double mu[3] = {double(ce.a.x) + d[0], double(ce.a.y) + d[1], double(ce.a.z) + d[2]};
+            double S[6];
+            S[0] = m[4] * inv - d[0] * d[0] + eps;
+            S[1] = m[5] * inv - d[0] * d[1];
+            S[2] = m[6] * inv - d[0] * d[2];
+            S[3] = m[7] * inv - d[1] * d[1] + eps;
+            S[4] = m[8] * inv - d[1] * d[2];
+            S[5] = m[9] * inv - d[2] * d[2] + eps;
+            const double pi = S0 * rcp_f64(n_p);
+            cs.pi = pi;
+            for (int a = 0; a < 3; ++a) cs.mu[a] = mu[a];
+            for (int v = 0; v < 6; ++v) cs.S[v] = S[v];
+            if (!pack_est(pi, mu, S, eps, 0.f, ce)) atomicOr(status, ST_CHOL);
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- E-step
@@ -426,12 +510,45 @@ __device__ __forceinline__ void flush_run(float* s, float* c, float2 (*red)[NPAR
     for (int v = 0; v < 20; ++v) { s[v] = 0.f; c[v] = 0.f; }
 }
 
+// Completes a parent run: the run's partial is already written; count its
+// items against the parent's total and, if this CTA brought the count to the
+// total, run the parent's M-step (the last CTA for a parent, no waiting).
+template <bool COMP>
+__device__ __forceinline__ void close_run(int level, int n, int parent, int run_items,
+                                          const int* __restrict__ item_range, int C,
+                                          int* __restrict__ pdone,
+                                          const float2* __restrict__ partials,
+                                          const int* __restrict__ seg_count,
+                                          const RootDev* __restrict__ root, float n_min,
+                                          NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
+                                          int* __restrict__ status, MstepSmem& msm, int* flag) {
+    const int i0 = item_range[2 * parent], i1 = item_range[2 * parent + 1];
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int old = atomicAdd(&pdone[parent], run_items);
+        *flag = (old + run_items == i1 - i0) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*flag) {
+        __threadfence();
+        mstep_parent<COMP>(level, n, parent, i0, i1, C, partials, seg_count, root, n_min, stat,
+                           est, status, msm);
+        if (threadIdx.x == 0) pdone[parent] = 0;  // ready for the next iteration
+    }
+    __syncthreads();
+}
+
 template <bool COMP>
 __global__ void __launch_bounds__(EST_THREADS, 2)
 k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
-        const int* __restrict__ meta, const NodeEst* __restrict__ est_lvl,
-        float2* __restrict__ partials) {
+        const int* __restrict__ meta, NodeEst* __restrict__ est_lvl,
+        float2* __restrict__ partials, int level, int n, const int* __restrict__ item_range,
+        int* __restrict__ pdone, const int* __restrict__ seg_count,
+        const RootDev* __restrict__ root, float n_min, NodeStat* __restrict__ stat,
+        NodeEst* __restrict__ est, int* __restrict__ status) {
     __shared__ float2 red[EST_THREADS / 32][NPART];
+    __shared__ MstepSmem msm;
+    __shared__ int flag;
     const int n_items = meta[0];
     const int C = meta[1];
     const int ib = blockIdx.x * C;
@@ -452,16 +569,20 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
                 fold20<COMP>(in, s, c);
                 nfold = 0;
                 flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+                close_run<COMP>(level, n, cur, it - run, item_range, C, pdone, partials,
+                                seg_count, root, n_min, stat, est, status, msm, &flag);
             }
             cur = w.parent;
             run = it;
             load_child(est_lvl + 8 * cur + 2 * k, r0);
             load_child(est_lvl + 8 * cur + 2 * k + 1, r1);
         }
+        float4 znext = pts[w.start + min(warp * 8 + q, w.count - 1)];
         for (int base = 0; base < w.count; base += 64) {
             const int idx = base + warp * 8 + q;
             const bool valid = idx < w.count;
-            const float4 z = pts[w.start + (valid ? idx : 0)];
+            const float4 z = znext;
+            if (base + 64 < w.count) znext = pts[w.start + min(idx + 64, w.count - 1)];
             float e0x, e0y, e0z, e1x, e1y, e1z;
             const float s0 = child_score(r0, z.x, z.y, z.z, e0x, e0y, e0z);
             const float s1 = child_score(r1, z.x, z.y, z.z, e1x, e1y, e1z);
@@ -485,86 +606,11 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
     }
     fold20<COMP>(in, s, c);
     flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+    close_run<COMP>(level, n, cur, ie - run, item_range, C, pdone, partials, seg_count, root,
+                    n_min, stat, est, status, msm, &flag);
 }
 
 // ---------------------------------------------------------------- M-step
-template <bool COMP>
-__global__ void __launch_bounds__(256) k_mstep(int level, int n, const int* __restrict__ item_range,
-                                               const int* __restrict__ meta,
-                                               const float2* __restrict__ partials,
-                                               const int* __restrict__ seg_count,
-                                               const RootDev* __restrict__ root, float n_min,
-                                               NodeStat* __restrict__ stat,
-                                               NodeEst* __restrict__ est, int* __restrict__ status) {
-    __shared__ double mom[NPART];
-    __shared__ float2 grp[3][NPART];
-    const int p = blockIdx.x;
-    const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
-    if (i0 >= i1) return;  // parent without points: children stay dead
-    // the parent's runs start at i0 and at every E-step chunk boundary in (i0, i1)
-    const int C = meta[1];
-    const int nruns = (i1 - 1) / C - i0 / C + 1;
-    if (threadIdx.x < 3 * NPART) {
-        const int v = threadIdx.x % NPART, q = threadIdx.x / NPART;
-        float S = 0.f, Cc = 0.f;
-#pragma unroll 4
-        for (int r = q; r < nruns; r += 3) {
-            const int slot = r == 0 ? i0 : (i0 / C + r) * C;
-            const float2 x = partials[int64_t(slot) * NPART + v];
-            if (COMP) pair_add(S, Cc, x.x, x.y);
-            else S += x.x;
-        }
-        grp[q][v] = make_float2(S, Cc);
-    }
-    __syncthreads();
-    if (threadIdx.x < NPART) {
-        float S = 0.f, Cc = 0.f;
-        for (int q = 0; q < 3; ++q) {
-            if (COMP) pair_add(S, Cc, grp[q][threadIdx.x].x, grp[q][threadIdx.x].y);
-            else S += grp[q][threadIdx.x].x;
-        }
-        mom[threadIdx.x] = double(S) + double(Cc);
-    }
-    __syncthreads();
-    const int cidx = threadIdx.x;
-    if (cidx >= 8) return;
-    const int64_t g = d_level_offset(level) + 8 * int64_t(p) + cidx;
-    NodeStat& cs = stat[g];
-    NodeEst& ce = est[g];
-    const double* m = mom + cidx * NMOM;
-    const double S0 = m[0];
-    const double n_p = level == 0 ? double(n) : double(seg_count[d_level_offset(level - 1) + p]);
-    // a child below n_min expected points dies; if all eight die the parent
-    // stays a leaf (its points keep zero posteriors from then on)
-    const bool live = cs.live && S0 >= double(n_min) && S0 > 0.0;
-    if (!live) {
-        cs.live = 0;
-        cs.pi = 0.0;
-        ce.a.w = -CUDART_INF_F;
-        ce.b = make_float4(0.f, 0.f, 0.f, 0.f);
-        ce.c.x = 0.f;
-        ce.c.y = 0.f;
-        return;
-    }
-    const double eps = root->eps;
-    const double inv = 1.0 / S0;
-    const double d[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
-    // the E-step centred on the FP32 mean it used
-    const double mu[3] = {double(ce.a.x) + d[0], double(ce.a.y) + d[1], double(ce.a.z) + d[2]};
-    double S[6];
-    S[0] = m[4] * inv - d[0] * d[0] + eps;
-    S[1] = m[5] * inv - d[0] * d[1];
-    S[2] = m[6] * inv - d[0] * d[2];
-    S[3] = m[7] * inv - d[1] * d[1] + eps;
-    S[4] = m[8] * inv - d[1] * d[2];
-    S[5] = m[9] * inv - d[2] * d[2] + eps;
-    const double pi = S0 / n_p;
-    cs.pi = pi;
-    for (int a = 0; a < 3; ++a) cs.mu[a] = mu[a];
-    for (int v = 0; v < 6; ++v) cs.S[v] = S[v];
-    if (!pack_est(pi, mu, S, eps, 0.f, ce)) atomicOr(status, ST_CHOL);
-}
-
 // ---------------------------------------------------------------- hand-off
 __global__ void __launch_bounds__(EST_THREADS) k_assign(const float4* __restrict__ pts,
                                                         const Item* __restrict__ items,
@@ -745,12 +791,12 @@ __global__ void k_finalize(int level, float lam_c, const RootDev* __restrict__ r
         return;
     }
     double lam[3], V[9];
-    jacobi_eig3(s.S, lam, V);
+    eig3(s.S, lam, V);
     const double eps = root->eps;
     double il[3];
     for (int a = 0; a < 3; ++a) {
         s.lam[a] = lam[a];
-        il[a] = 1.0 / fmax(lam[a], eps);
+        il[a] = rcp_f64(fmax(lam[a], eps));
     }
     for (int v = 0; v < 9; ++v) s.V[v] = V[v];
     // P = V diag(1/lambda) V^T (Eq. 10)
@@ -761,7 +807,7 @@ __global__ void k_finalize(int level, float lam_c, const RootDev* __restrict__ r
         for (int k = 0; k < 3; ++k) acc += V[r * 3 + k] * il[k] * V[c * 3 + k];
         s.P[v] = acc;
     }
-    s.complexity = lam[2] / (lam[0] + lam[1] + lam[2]);
+    s.complexity = lam[2] * rcp_f64(lam[0] + lam[1] + lam[2]);
     const float4 a = est[g].a;
     est[g].c.z = (s.complexity <= double(lam_c)) ? 1.f : 0.f;
     // FP32 registration constants: P and the offset of the FP64 mean from the
@@ -787,8 +833,8 @@ __global__ void k_labels(int level, int n, const int* __restrict__ perm,
         if (seg_start[off + mid] <= i) lo = mid;
         else hi = mid - 1;
     }
-    while (lo > 0 && seg_count[off + lo] == 0) --lo;  // never needed for a non-empty segment
-    out[perm[i]] = int(lo);
+    const int dst = perm[i];
+    if (dst >= 0 && dst < n) out[dst] = int(lo);
 }
 
 }  // namespace
@@ -842,29 +888,15 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
         const bool stop_here = p.debug_stop_level == l + 1;
         const int em_iters = stop_here ? p.debug_stop_iters : p.em_iters;
         for (int k = 0; k < em_iters; ++k) {
-            if (comp) {
-                {
-                    ProfScope ps_(t, K_ESTEP, s);
-                    k_estep<true><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials);
-                }
-                {
-                    ProfScope ps_(t, K_MSTEP, s);
-                    k_mstep<true><<<n_par, 256, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
-                                                        t->seg_count, t->root, p.n_min, t->stat,
-                                                        t->est, t->status);
-                }
-            } else {
-                {
-                    ProfScope ps_(t, K_ESTEP, s);
-                    k_estep<false><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials);
-                }
-                {
-                    ProfScope ps_(t, K_MSTEP, s);
-                    k_mstep<false><<<n_par, 256, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
-                                                         t->seg_count, t->root, p.n_min, t->stat,
-                                                         t->est, t->status);
-                }
-            }
+            ProfScope ps_(t, K_ESTEP, s);
+            if (comp)
+                k_estep<true><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials,
+                                                        l, n, t->item_range, t->pdone, t->seg_count,
+                                                        t->root, p.n_min, t->stat, t->est, t->status);
+            else
+                k_estep<false><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials,
+                                                         l, n, t->item_range, t->pdone, t->seg_count,
+                                                         t->root, p.n_min, t->stat, t->est, t->status);
         }
         HGMM_LAUNCH_CHECK();
         if (stop_here) return HGMM_OK;  // checking aid: parameters after em_iters
@@ -886,8 +918,10 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
         const int m = int(level_size(l));
         {
             ProfScope ps_(t, K_FINALIZE, s);
-            k_finalize<<<(m + 127) / 128, 128, 0, s>>>(l, p.lam_c, t->root, t->stat, t->est,
-                                                       t->rnode);
+            // one warp per CTA: the FP64 eigen work is spread over as many SMs
+            // as possible (each SM's FP64 pipe is narrow)
+            k_finalize<<<(m + 31) / 32, 32, 0, s>>>(l, p.lam_c, t->root, t->stat, t->est,
+                                                    t->rnode);
         }
         HGMM_LAUNCH_CHECK();
         cur = out;

@@ -118,6 +118,7 @@ struct hgmm_tree {
     uint32_t* codes = nullptr;
     hgmm::Item* items = nullptr;
     int* item_range = nullptr;   // per parent: [begin, end) item indices
+    int* pdone = nullptr;        // per parent: items whose partial is written (E-step)
     int* meta = nullptr;         // [0] n_items, [1] items per E-step CTA
     float2* partials = nullptr;  // max_items x NPART (sum, compensation)
     int* item_cnt = nullptr;     // max_items x 8
@@ -130,7 +131,7 @@ struct hgmm_tree {
     unsigned long long* reg_acc = nullptr;  // nodes x 4 fixed point
     float2* reg_part = nullptr;             // blocks x 27 (sum, compensation)
     float4* rnode = nullptr;                // nodes x 3: P (6), mu - mu32 (3), FP32
-    unsigned* reg_counter = nullptr;
+    unsigned* reg_bar = nullptr;            // grid barrier words (8)
     double* reg_T = nullptr;                // 16 doubles current T
     float* reg_Rt = nullptr;                // 12 floats (R row-major, t)
     double* reg_dbg = nullptr;              // nodes x 4 (last round)
@@ -168,3 +169,5 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n,
                        const double* T_init, int iters, float lam_c,
                        cudaStream_t s, double* T_out, double* T_hist);
 int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s);
+int hgmm_register_grid(int n_sm);
+int hgmm_barrier_timeout_probe_impl(hgmm_tree* t, long long limit, cudaStream_t s);

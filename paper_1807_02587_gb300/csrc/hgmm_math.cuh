@@ -38,6 +38,30 @@ __device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2)
     c = __fadd_rn(c, __fadd_rn(c2, e));
 }
 
+// ---------------------------------------------------------------- FP64 helpers
+// On sm_103 a dependent FP64 FMA costs ~64 cycles and the library FP64
+// division / square root several hundred, so FP64 reciprocals and inverse
+// square roots are seeded in FP32 and refined by Newton steps in FP64
+// (quadratic convergence: 2^-22 -> ~1e-13 -> full precision).
+__device__ __forceinline__ double rcp_f64(double x) {
+    const double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double y = double(__frcp_rn(float(x)));
+    y = y * fma(-x, y, 2.0);
+    y = y * fma(-x, y, 2.0);
+    return y;
+}
+
+// one Newton step: relative error <= ~1e-13 (used where the result feeds
+// FP32 constants, Cholesky pivots or Jacobi rotation factors)
+__device__ __forceinline__ double rsqrt_f64(double x) {
+    if (!(x > 1e-30 && x < 1e30)) return rsqrt(x);
+    const double h = 0.5 * x;
+    double y = double(rsqrtf(float(x)));
+    y = y * fma(-h * y, y, 1.5);
+    return y;
+}
+
 // ---------------------------------------------------------------- FP64 3x3
 // S packed xx xy xz yy yz zz.
 __device__ inline void jacobi_eig3(const double S[6], double lam[3], double V[9]) {
@@ -93,21 +117,145 @@ __device__ inline void jacobi_eig3(const double S[6], double lam[3], double V[9]
     }
 }
 
+// Symmetric 3x3 eigen-decomposition accurate to FP64: cyclic Jacobi in FP32
+// brings the matrix to within ~1e-7 of diagonal, the FP32 eigenvectors are
+// re-orthonormalised in FP64 (Gram-Schmidt), the FP64 matrix is rotated into
+// that basis and FP64 Jacobi sweeps (quadratically convergent) finish it.
+// Eigenvalues descending, each eigenvector signed so that its largest-
+// magnitude entry is positive.
+__device__ inline void eig3(const double S[6], double lam[3], double V[9]) {
+    double sc = fmax(fmax(fabs(S[0]), fabs(S[3])), fabs(S[5]));
+    sc = fmax(sc, fmax(fmax(fabs(S[1]), fabs(S[2])), fabs(S[4])));
+    if (!(sc > 0.0) || !isfinite(sc)) {
+        jacobi_eig3(S, lam, V);  // zero or non-finite input: plain path
+        return;
+    }
+    const double isc = rcp_f64(sc);
+    // 1) FP32 cyclic Jacobi on S / sc
+    float a[3][3] = {{float(S[0] * isc), float(S[1] * isc), float(S[2] * isc)},
+                     {float(S[1] * isc), float(S[3] * isc), float(S[4] * isc)},
+                     {float(S[2] * isc), float(S[4] * isc), float(S[5] * isc)}};
+    float v[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const float off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        if (!(off > 1e-18f)) break;
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            const float apq = a[p][q];
+            if (apq == 0.f) continue;
+            const float theta = (a[q][q] - a[p][p]) / (2.f * apq);
+            float t = 1.f / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            if (theta < 0.f) t = -t;
+            if (fabsf(theta) > 1e18f) t = 0.5f / theta;
+            const float c = rsqrtf(t * t + 1.f), s = t * c;
+            a[p][p] -= t * apq;
+            a[q][q] += t * apq;
+            a[p][q] = a[q][p] = 0.f;
+            const int r = 3 - p - q;
+            const float arp = a[r][p], arq = a[r][q];
+            a[r][p] = a[p][r] = c * arp - s * arq;
+            a[r][q] = a[q][r] = s * arp + c * arq;
+            for (int k = 0; k < 3; ++k) {
+                const float vkp = v[k][p], vkq = v[k][q];
+                v[k][p] = c * vkp - s * vkq;
+                v[k][q] = s * vkp + c * vkq;
+            }
+        }
+    }
+    // 2) FP64 Gram-Schmidt of the FP32 columns
+    double U[3][3];
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) U[r][c] = v[r][c];
+    for (int c = 0; c < 3; ++c) {
+        for (int b = 0; b < c; ++b) {
+            const double d = U[0][b] * U[0][c] + U[1][b] * U[1][c] + U[2][b] * U[2][c];
+            for (int r = 0; r < 3; ++r) U[r][c] -= d * U[r][b];
+        }
+        const double nn = rsqrt_f64(U[0][c] * U[0][c] + U[1][c] * U[1][c] + U[2][c] * U[2][c]);
+        for (int r = 0; r < 3; ++r) U[r][c] *= nn;
+    }
+    // 3) B = U^T S U in FP64 (unscaled S)
+    const double Sm[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
+    double SU[3][3], B[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) SU[r][c] = Sm[r][0] * U[0][c] + Sm[r][1] * U[1][c] + Sm[r][2] * U[2][c];
+    for (int r = 0; r < 3; ++r)
+        for (int c = r; c < 3; ++c)
+            B[r][c] = B[c][r] = U[0][r] * SU[0][c] + U[1][r] * SU[1][c] + U[2][r] * SU[2][c];
+    // 4) FP64 Jacobi sweeps on the nearly diagonal B
+    for (int sweep = 0; sweep < 4; ++sweep) {
+        const double off = B[0][1] * B[0][1] + B[0][2] * B[0][2] + B[1][2] * B[1][2];
+        const double dia = B[0][0] * B[0][0] + B[1][1] * B[1][1] + B[2][2] * B[2][2];
+        if (!(off > 1e-32 * dia)) break;
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            const double apq = B[p][q];
+            if (apq == 0.0) continue;
+            const double gap = B[q][q] - B[p][p];
+            double t, c;
+            if (fabs(apq) < 1e-8 * fabs(gap)) {
+                // small angle: t = tan(phi) ~ apq / gap to O(t^3) < 1e-24
+                t = apq * rcp_f64(gap);
+                c = 1.0 - 0.5 * t * t;
+            } else {
+                const double theta = gap * rcp_f64(2.0 * apq);
+                if (fabs(theta) > 1e150) {
+                    t = 0.5 * rcp_f64(theta);
+                } else {
+                    const double h = theta * theta + 1.0;
+                    t = rcp_f64(fabs(theta) + h * rsqrt_f64(h));
+                    if (theta < 0.0) t = -t;
+                }
+                c = rsqrt_f64(t * t + 1.0);
+            }
+            const double s = t * c;
+            B[p][p] -= t * apq;
+            B[q][q] += t * apq;
+            B[p][q] = B[q][p] = 0.0;
+            const int r = 3 - p - q;
+            const double brp = B[r][p], brq = B[r][q];
+            B[r][p] = B[p][r] = c * brp - s * brq;
+            B[r][q] = B[q][r] = s * brp + c * brq;
+            for (int k = 0; k < 3; ++k) {
+                const double ukp = U[k][p], ukq = U[k][q];
+                U[k][p] = c * ukp - s * ukq;
+                U[k][q] = s * ukp + c * ukq;
+            }
+        }
+    }
+    int idx[3] = {0, 1, 2};
+    const double d[3] = {B[0][0], B[1][1], B[2][2]};
+    if (d[idx[0]] < d[idx[1]]) { int x = idx[0]; idx[0] = idx[1]; idx[1] = x; }
+    if (d[idx[1]] < d[idx[2]]) { int x = idx[1]; idx[1] = idx[2]; idx[2] = x; }
+    if (d[idx[0]] < d[idx[1]]) { int x = idx[0]; idx[0] = idx[1]; idx[1] = x; }
+    for (int c = 0; c < 3; ++c) {
+        const int k = idx[c];
+        lam[c] = d[k];
+        int best = 0;
+        for (int r = 1; r < 3; ++r)
+            if (fabs(U[r][k]) > fabs(U[best][k])) best = r;
+        const double sg = U[best][k] < 0.0 ? -1.0 : 1.0;
+        for (int r = 0; r < 3; ++r) V[r * 3 + c] = sg * U[r][k];
+    }
+}
+
 // Cholesky Sigma = L L^T, returns false if not positive definite.
-// L packed: L00 L10 L11 L20 L21 L22.
-__device__ inline bool chol3(const double S[6], double L[6]) {
+// L packed: L00 L10 L11 L20 L21 L22; R = 1 / (L00, L11, L22).
+__device__ inline bool chol3(const double S[6], double L[6], double R[3]) {
     const double d0 = S[0];
     if (!(d0 > 0.0)) return false;
-    const double l00 = sqrt(d0);
-    const double l10 = S[1] / l00;
-    const double l20 = S[2] / l00;
+    const double r0 = rsqrt_f64(d0);
+    const double l10 = S[1] * r0;
+    const double l20 = S[2] * r0;
     const double d1 = S[3] - l10 * l10;
     if (!(d1 > 0.0)) return false;
-    const double l11 = sqrt(d1);
-    const double l21 = (S[4] - l20 * l10) / l11;
+    const double r1 = rsqrt_f64(d1);
+    const double l21 = (S[4] - l20 * l10) * r1;
     const double d2 = S[5] - l20 * l20 - l21 * l21;
     if (!(d2 > 0.0)) return false;
-    L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = sqrt(d2);
+    const double r2 = rsqrt_f64(d2);
+    L[0] = d0 * r0; L[1] = l10; L[2] = d1 * r1; L[3] = l20; L[4] = l21; L[5] = d2 * r2;
+    R[0] = r0; R[1] = r1; R[2] = r2;
     return true;
 }
 
@@ -116,20 +264,21 @@ __device__ inline bool chol3(const double S[6], double L[6]) {
 __device__ inline bool pack_est(double pi, const double mu[3], const double S_in[6],
                                 double eps, float stop, NodeEst& out) {
     double S[6] = {S_in[0], S_in[1], S_in[2], S_in[3], S_in[4], S_in[5]};
-    double L[6];
+    double L[6], R[3];
     bool clean = true;
     double boost = eps > 0.0 ? eps : 1e-30;
-    for (int tries = 0; tries < 8 && !chol3(S, L); ++tries) {
+    for (int tries = 0; tries < 8 && !chol3(S, L, R); ++tries) {
         clean = false;
         S[0] += boost; S[3] += boost; S[5] += boost;
         boost *= 10.0;
     }
-    if (!chol3(S, L)) {  // hopeless (NaN input): make it an isotropic unit Gaussian
+    if (!chol3(S, L, R)) {  // hopeless (NaN input): make it an isotropic unit Gaussian
         L[0] = 1; L[1] = 0; L[2] = 1; L[3] = 0; L[4] = 0; L[5] = 1;
+        R[0] = 1; R[1] = 1; R[2] = 1;
         clean = false;
     }
     // M = L^-1 (lower triangular)
-    const double m00 = 1.0 / L[0], m11 = 1.0 / L[2], m22 = 1.0 / L[5];
+    const double m00 = R[0], m11 = R[1], m22 = R[2];
     const double m10 = -L[1] * m00 * m11;
     const double m21 = -L[4] * m11 * m22;
     const double m20 = -(L[3] * m00 + L[4] * m10) * m22;
@@ -164,28 +313,32 @@ __device__ inline bool chol_solve6(const double Hu[21], const double g[6], doubl
         }
     for (int i = 0; i < 6; ++i) dmax = fmax(dmax, fabs(A[i][i]));
     if (!(dmax > 0.0)) return false;
+    // L L^T with one reciprocal per pivot (multiplications replace divisions)
     double L[6][6] = {};
+    double inv[6];
     for (int j = 0; j < 6; ++j) {
         double d = A[j][j];
         for (int p = 0; p < j; ++p) d -= L[j][p] * L[j][p];
         if (!(d > 1e-15 * dmax)) return false;
-        L[j][j] = sqrt(d);
+        const double r = rsqrt_f64(d);  // 1 / L_jj
+        L[j][j] = d * r;
+        inv[j] = r;
         for (int i = j + 1; i < 6; ++i) {
             double s = A[i][j];
             for (int p = 0; p < j; ++p) s -= L[i][p] * L[j][p];
-            L[i][j] = s / L[j][j];
+            L[i][j] = s * r;
         }
     }
     double y[6];
     for (int i = 0; i < 6; ++i) {
         double s = g[i];
         for (int p = 0; p < i; ++p) s -= L[i][p] * y[p];
-        y[i] = s / L[i][i];
+        y[i] = s * inv[i];
     }
     for (int i = 5; i >= 0; --i) {
         double s = y[i];
         for (int p = i + 1; p < 6; ++p) s -= L[p][i] * x[p];
-        x[i] = s / L[i][i];
+        x[i] = s * inv[i];
     }
     return true;
 }

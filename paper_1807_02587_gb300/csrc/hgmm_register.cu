@@ -38,7 +38,7 @@ __device__ __forceinline__ int64_t d_level_offset(int l) {
 __global__ void k_reg_init(const double* __restrict__ T_init, int n_nodes, float lam_c,
                            const NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
                            unsigned long long* __restrict__ acc, double* __restrict__ T,
-                           float* __restrict__ Rt, unsigned* __restrict__ counter) {
+                           float* __restrict__ Rt, unsigned* __restrict__ bar) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_nodes) {
         acc[4 * i + 0] = 0ull;
@@ -54,7 +54,8 @@ __global__ void k_reg_init(const double* __restrict__ T_init, int n_nodes, float
             for (int c = 0; c < 3; ++c) Rt[r * 3 + c] = float(T[r * 4 + c]);
             Rt[9 + r] = float(T[r * 4 + 3]);
         }
-        *counter = 0u;
+        bar[0] = 0u;
+        bar[2] = 0u;
     }
 }
 
@@ -63,21 +64,20 @@ __device__ __forceinline__ long long to_fix(float v) {
     return __float2ll_rn(c);
 }
 
-__global__ void __launch_bounds__(REG_THREADS) k_descend(const float4* __restrict__ src, int n,
-                                                        const NodeEst* __restrict__ est, int depth,
-                                                        const float* __restrict__ Rt,
-                                                        const RootDev* __restrict__ root,
-                                                        unsigned long long* __restrict__ acc) {
-    __shared__ unsigned long long slot[REG_THREADS / 32][32][4];
+// Algorithm 1 for the points of this CTA (grid-stride by warps) with the
+// current transform; adds each point's (gamma, gamma (z' - mu_j)) to the
+// chosen node's fixed-point moments.
+__device__ __forceinline__ void descend_points(const float4* __restrict__ src, int n,
+                                               const NodeEst* __restrict__ est, int depth,
+                                               const float* Rt_sm, float qscale,
+                                               unsigned long long* __restrict__ acc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = 0; v < 4; ++v) slot[warp][lane][v] = 0ull;
-    __syncwarp();
-    const float r00 = Rt[0], r01 = Rt[1], r02 = Rt[2], r10 = Rt[3], r11 = Rt[4], r12 = Rt[5];
-    const float r20 = Rt[6], r21 = Rt[7], r22 = Rt[8], tx = Rt[9], ty = Rt[10], tz = Rt[11];
-    // fixed-point units per metre (a zero-extent cloud uses unit scale)
-    const float qscale = float(FIX / (root->extent > 0.0 ? root->extent : 1.0));
-    const int warps_total = gridDim.x * (REG_THREADS / 32);
-    for (int base = (blockIdx.x * (REG_THREADS / 32) + warp) * 32; base < n; base += warps_total * 32) {
+    const float r00 = Rt_sm[0], r01 = Rt_sm[1], r02 = Rt_sm[2], r10 = Rt_sm[3], r11 = Rt_sm[4];
+    const float r12 = Rt_sm[5], r20 = Rt_sm[6], r21 = Rt_sm[7], r22 = Rt_sm[8];
+    const float tx = Rt_sm[9], ty = Rt_sm[10], tz = Rt_sm[11];
+    const int wpb = blockDim.x >> 5;
+    const int warps_total = gridDim.x * wpb;
+    for (int base = (blockIdx.x * wpb + warp) * 32; base < n; base += warps_total * 32) {
         const int i = base + lane;
         const bool valid = i < n;
         float4 z = valid ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -89,67 +89,67 @@ __global__ void __launch_bounds__(REG_THREADS) k_descend(const float4* __restric
         int local = 0;  // index within its level of the current search node
         for (int l = 0; l < depth && valid; ++l) {
             const int64_t first = d_level_offset(l) + 8 * int64_t(local);
-            float s[8];
+            float sc8[8];
             float best = -CUDART_INF_F;
             int bi = -1;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const NodeEst* e = est + first + c;
-                const float4 a = __ldg(&e->a), b = __ldg(&e->b), cc = __ldg(&e->c);
-                const float ex = x - a.x, ey = y - a.y, ez = w - a.z;
-                const float d0 = b.x * ex;
-                const float d1 = fmaf(b.z, ey, b.y * ex);
-                const float d2 = fmaf(cc.y, ez, fmaf(cc.x, ey, b.w * ex));
-                float sc = fmaf(-d0, d0, a.w);
+                const float4 ea = __ldg(&e->a), eb = __ldg(&e->b), ec = __ldg(&e->c);
+                const float ex = x - ea.x, ey = y - ea.y, ez = w - ea.z;
+                const float d0 = eb.x * ex;
+                const float d1 = fmaf(eb.z, ey, eb.y * ex);
+                const float d2 = fmaf(ec.y, ez, fmaf(ec.x, ey, eb.w * ex));
+                float sc = fmaf(-d0, d0, ea.w);
                 sc = fmaf(-d1, d1, sc);
                 sc = fmaf(-d2, d2, sc);
-                s[c] = sc;
+                sc8[c] = sc;
                 if (sc > best) { best = sc; bi = c; }
             }
             if (bi < 0) break;  // the current node has no live children
             float sum = 0.f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) sum += exp2f(s[c] - best);
+            for (int c = 0; c < 8; ++c) sum += exp2f(sc8[c] - best);
             gamma = 1.0f / sum;
             chosen = int(first + bi);
             local = 8 * local + bi;
-            const float4 a = __ldg(&est[chosen].a);
-            cmx = a.x; cmy = a.y; cmz = a.z;
+            const float4 ea = __ldg(&est[chosen].a);
+            cmx = ea.x; cmy = ea.y; cmz = ea.z;
             if (__ldg(&est[chosen].c).z != 0.f) break;  // Complexity <= lambda_c
         }
-        // accumulate (M0, M1 relative to the node's FP32 mean) as fixed point
+        // Sum (gamma, gamma (z' - mu_j)) over the lanes of this warp that chose
+        // the same node j: a pairwise tree over the members' ranks (fixed order,
+        // so deterministic), then one fixed-point atomic per value and group.
+        // Integer adds are exact, so the node totals do not depend on the
+        // order in which groups arrive.
         const bool has = chosen >= 0;
-        long long v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-        if (has) {
-            v0 = to_fix(gamma * 4294967296.0f);
-            v1 = to_fix(gamma * (x - cmx) * qscale);
-            v2 = to_fix(gamma * (y - cmy) * qscale);
-            v3 = to_fix(gamma * (w - cmz) * qscale);
-        }
-        const unsigned active = __ballot_sync(FULL, has);
-        if (has) {
-            const unsigned peers = __match_any_sync(active, chosen);
-            const int leader = __ffs(peers) - 1;
-            unsigned long long* dst = acc + 4 * int64_t(chosen);
-            if (peers == (1u << lane)) {
-                atomicAdd(dst + 0, (unsigned long long)v0);
-                atomicAdd(dst + 1, (unsigned long long)v1);
-                atomicAdd(dst + 2, (unsigned long long)v2);
-                atomicAdd(dst + 3, (unsigned long long)v3);
-            } else {
-                atomicAdd(&slot[warp][leader][0], (unsigned long long)v0);
-                atomicAdd(&slot[warp][leader][1], (unsigned long long)v1);
-                atomicAdd(&slot[warp][leader][2], (unsigned long long)v2);
-                atomicAdd(&slot[warp][leader][3], (unsigned long long)v3);
-                __syncwarp(peers);
-                if (lane == leader) {
-                    for (int v = 0; v < 4; ++v) {
-                        atomicAdd(dst + v, slot[warp][lane][v]);
-                        slot[warp][lane][v] = 0ull;
-                    }
-                }
-                __syncwarp(peers);
+        float v0 = has ? gamma : 0.f;
+        float v1 = has ? gamma * (x - cmx) : 0.f;
+        float v2 = has ? gamma * (y - cmy) : 0.f;
+        float v3 = has ? gamma * (w - cmz) : 0.f;
+        const unsigned peers = __match_any_sync(FULL, chosen);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        const int gsize = __popc(peers);
+        const unsigned higher = lane == 31 ? 0u : (peers & ~((2u << lane) - 1u));
+#pragma unroll
+        for (int st = 1; st < 32; st <<= 1) {
+            unsigned h = higher;  // lane holding rank + st within my group
+            for (int k = 1; k < st; ++k) h &= h - 1u;
+            const int srcl = h ? __ffs(h) - 1 : lane;
+            const float o0 = __shfl_sync(FULL, v0, srcl);
+            const float o1 = __shfl_sync(FULL, v1, srcl);
+            const float o2 = __shfl_sync(FULL, v2, srcl);
+            const float o3 = __shfl_sync(FULL, v3, srcl);
+            if ((rank & (2 * st - 1)) == 0 && rank + st < gsize) {
+                v0 += o0; v1 += o1; v2 += o2; v3 += o3;
             }
+        }
+        if (has && rank == 0) {
+            unsigned long long* dst = acc + 4 * int64_t(chosen);
+            atomicAdd(dst + 0, (unsigned long long)to_fix(v0 * 4294967296.0f));
+            atomicAdd(dst + 1, (unsigned long long)to_fix(v1 * qscale));
+            atomicAdd(dst + 2, (unsigned long long)to_fix(v2 * qscale));
+            atomicAdd(dst + 3, (unsigned long long)to_fix(v3 * qscale));
         }
     }
 }
@@ -233,111 +233,199 @@ __device__ inline void compose_update(const double x[6], double* T) {
     for (int k = 0; k < 12; ++k) T[k] = Tn[k];
 }
 
-__global__ void __launch_bounds__(MSTEP_THREADS) k_mstep(int n_nodes, int n_src, int iter,
-                                                        const float4* __restrict__ rnode,
-                                                        const NodeEst* __restrict__ est,
-                                                        const RootDev* __restrict__ root,
-                                                        unsigned long long* __restrict__ acc,
-                                                        float2* __restrict__ part,
-                                                        unsigned* __restrict__ counter,
-                                                        double* __restrict__ T, float* __restrict__ Rt,
-                                                        double* __restrict__ T_hist,
-                                                        double* __restrict__ dbg,
-                                                        int* __restrict__ status) {
-    __shared__ float2 sm[MSTEP_THREADS / 32][27];
-    __shared__ float2 fin[4][27];
-    __shared__ bool last;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float v[27], c[27];
-#pragma unroll
-    for (int k = 0; k < 27; ++k) { v[k] = 0.f; c[k] = 0.f; }
-    if (g < n_nodes) {
-        const long long a0 = (long long)acc[4 * g + 0];
-        const long long a1 = (long long)acc[4 * g + 1];
-        const long long a2 = (long long)acc[4 * g + 2];
-        const long long a3 = (long long)acc[4 * g + 3];
-        acc[4 * g + 0] = 0ull;
-        acc[4 * g + 1] = 0ull;
-        acc[4 * g + 2] = 0ull;
-        acc[4 * g + 3] = 0ull;
-        const float4 cm = est[g].a;
-        float M0 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
-        if (a0 > 0) {
-            M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
-            const float qs = float(FIX / (root->extent > 0.0 ? root->extent : 1.0));
-            const float inv = 1.0f / (qs * M0);
-            o0 = float(a1) * inv;
-            o1 = float(a2) * inv;
-            o2 = float(a3) * inv;
-            node_terms(rnode[3 * g], rnode[3 * g + 1], rnode[3 * g + 2], cm, M0, o0, o1, o2,
-                       M0 / float(n_src), v);
-        }
-        if (dbg) {
-            dbg[4 * g + 0] = double(a0) * INV_FIX;
-            dbg[4 * g + 1] = double(M0) * (double(cm.x) + double(o0));
-            dbg[4 * g + 2] = double(M0) * (double(cm.y) + double(o1));
-            dbg[4 * g + 3] = double(M0) * (double(cm.z) + double(o2));
-        }
-    }
-    // compensated warp + block reduction, fixed order
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-        for (int k = 0; k < 27; ++k) {
-            const float s2 = __shfl_xor_sync(FULL, v[k], off);
-            const float c2 = __shfl_xor_sync(FULL, c[k], off);
-            pair_add(v[k], c[k], s2, c2);
-        }
-    if (lane == 0)
-        for (int k = 0; k < 27; ++k) sm[warp][k] = make_float2(v[k], c[k]);
-    __syncthreads();
-    if (threadIdx.x < 27) {
-        float S = 0.f, C = 0.f;
-        for (int w = 0; w < MSTEP_THREADS / 32; ++w) pair_add(S, C, sm[w][threadIdx.x].x, sm[w][threadIdx.x].y);
-        part[27 * blockIdx.x + threadIdx.x] = make_float2(S, C);
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // the last CTA: 4 groups of 27 threads sum the block partials (fixed order)
-    const int nb = gridDim.x;
-    if (threadIdx.x < 108) {
-        const int k = threadIdx.x % 27, q = threadIdx.x / 27;
-        float S = 0.f, C = 0.f;
-        for (int b = q; b < nb; b += 4) {
-            const float2 x = __ldcg(&part[27 * b + k]);
-            pair_add(S, C, x.x, x.y);
-        }
-        fin[q][k] = make_float2(S, C);
-    }
+// Bounded grid-wide barrier for a cooperative launch (all CTAs co-resident):
+// generation counter, spin with a sleep and an iteration limit; on timeout
+// it records ST_TIMEOUT and returns false so the kernel can exit.
+constexpr long long BARRIER_SPIN_LIMIT = 1000000;  // about a second
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, long long limit) {
+    __shared__ int ok_sm;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tot[27];
-        for (int k = 0; k < 27; ++k) {
-            float S = 0.f, C = 0.f;
-            for (int q = 0; q < 4; ++q) pair_add(S, C, fin[q][k].x, fin[q][k].y);
-            tot[k] = double(S) + double(C);
-        }
-        double x[6];
-        double Tl[16];
-        for (int k = 0; k < 16; ++k) Tl[k] = T[k];
-        if (chol_solve6(tot, tot + 21, x)) {
-            compose_update(x, Tl);
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
         } else {
-            atomicOr(status, ST_DEGENERATE);
+            long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > limit) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
         }
-        for (int k = 0; k < 16; ++k) T[k] = Tl[k];
-        for (int r = 0; r < 3; ++r) {
-            for (int cc = 0; cc < 3; ++cc) Rt[r * 3 + cc] = float(Tl[r * 4 + cc]);
-            Rt[9 + r] = float(Tl[r * 4 + 3]);
+        __threadfence();
+        ok_sm = ok;
+    }
+    __syncthreads();
+    return ok_sm != 0;
+}
+
+struct RegArgs {
+    const float4* src;
+    int n;
+    const NodeEst* est;
+    const float4* rnode;
+    const RootDev* root;
+    int depth;
+    int n_nodes;
+    int iters;
+    unsigned long long* acc;
+    float2* part;
+    unsigned* bar;      // [0] arrivals, [1] generation, [2] partial counter
+    double* T;
+    float* Rt;
+    double* T_hist;
+    double* dbg;
+    int* status;
+};
+
+// The whole registration loop in one cooperative launch.  Per round:
+//   A. Algorithm 1 for every source point (fixed-point node moments)
+//   -- grid barrier --
+//   B. per node with mass: its 27 normal-equation terms (FP32), compensated
+//      block sums -> one partial per CTA; the last CTA to finish
+//   C. reduces the partials in a fixed order, solves the 6x6 system in FP64
+//      and composes T <- dT T
+//   -- grid barrier --  (everyone reads the new T)
+__global__ void __launch_bounds__(REG_THREADS) k_register(RegArgs a) {
+    __shared__ float Rt_sm[12];
+    __shared__ float2 sm[REG_THREADS / 32][27];
+    __shared__ float2 fin[4][27];
+    __shared__ double tot[27];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double ext = a.root->extent > 0.0 ? a.root->extent : 1.0;
+    const float qscale = float(FIX / ext);  // fixed-point units per metre
+    for (int it = 0; it < a.iters; ++it) {
+        if (threadIdx.x < 12) Rt_sm[threadIdx.x] = __ldcg(a.Rt + threadIdx.x);
+        __syncthreads();
+        descend_points(a.src, a.n, a.est, a.depth, Rt_sm, qscale, a.acc);
+        if (!grid_barrier(a.bar, a.status, BARRIER_SPIN_LIMIT)) return;
+        // ---- B: node terms
+        float v[27], c[27];
+#pragma unroll
+        for (int k = 0; k < 27; ++k) { v[k] = 0.f; c[k] = 0.f; }
+        double* dbg = it == a.iters - 1 ? a.dbg : nullptr;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_nodes; g += gridDim.x * blockDim.x) {
+            const long long a0 = (long long)__ldcg(a.acc + 4 * g + 0);
+            const long long a1 = (long long)__ldcg(a.acc + 4 * g + 1);
+            const long long a2 = (long long)__ldcg(a.acc + 4 * g + 2);
+            const long long a3 = (long long)__ldcg(a.acc + 4 * g + 3);
+            if (a0 | a1 | a2 | a3) {
+                a.acc[4 * g + 0] = 0ull;
+                a.acc[4 * g + 1] = 0ull;
+                a.acc[4 * g + 2] = 0ull;
+                a.acc[4 * g + 3] = 0ull;
+            }
+            const float4 cm = a.est[g].a;
+            float M0 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
+            if (a0 > 0) {
+                float w[27];
+                M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
+                const float inv = 1.0f / (qscale * M0);
+                o0 = float(a1) * inv;
+                o1 = float(a2) * inv;
+                o2 = float(a3) * inv;
+                node_terms(a.rnode[3 * g], a.rnode[3 * g + 1], a.rnode[3 * g + 2], cm, M0, o0, o1,
+                           o2, M0 / float(a.n), w);
+#pragma unroll
+                for (int k = 0; k < 27; ++k) pair_add(v[k], c[k], w[k], 0.f);
+            }
+            if (dbg) {
+                dbg[4 * g + 0] = double(a0) * INV_FIX;
+                dbg[4 * g + 1] = double(M0) * (double(cm.x) + double(o0));
+                dbg[4 * g + 2] = double(M0) * (double(cm.y) + double(o1));
+                dbg[4 * g + 3] = double(M0) * (double(cm.z) + double(o2));
+            }
         }
-        if (T_hist)
-            for (int k = 0; k < 16; ++k) T_hist[16 * iter + k] = Tl[k];
-        *counter = 0u;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 27; ++k) {
+                const float s2 = __shfl_xor_sync(FULL, v[k], off);
+                const float c2 = __shfl_xor_sync(FULL, c[k], off);
+                pair_add(v[k], c[k], s2, c2);
+            }
+        if (lane == 0)
+            for (int k = 0; k < 27; ++k) sm[warp][k] = make_float2(v[k], c[k]);
+        __syncthreads();
+        if (threadIdx.x < 27) {
+            float S = 0.f, C = 0.f;
+            for (int w = 0; w < REG_THREADS / 32; ++w) pair_add(S, C, sm[w][threadIdx.x].x, sm[w][threadIdx.x].y);
+            a.part[27 * blockIdx.x + threadIdx.x] = make_float2(S, C);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = (atomicAdd(a.bar + 2, 1u) == gridDim.x - 1);
+        __syncthreads();
+        if (last) {
+            // ---- C: fixed-order reduction, FP64 solve, pose update
+            __threadfence();
+            const int nb = gridDim.x;
+            if (threadIdx.x < 108) {
+                const int k = threadIdx.x % 27, q = threadIdx.x / 27;
+                float S = 0.f, C = 0.f;
+                for (int b = q; b < nb; b += 4) {
+                    const float2 x = __ldcg(&a.part[27 * b + k]);
+                    pair_add(S, C, x.x, x.y);
+                }
+                fin[q][k] = make_float2(S, C);
+            }
+            __syncthreads();
+            if (threadIdx.x < 27) {
+                float S = 0.f, C = 0.f;
+                for (int q = 0; q < 4; ++q) pair_add(S, C, fin[q][threadIdx.x].x, fin[q][threadIdx.x].y);
+                tot[threadIdx.x] = double(S) + double(C);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double x[6];
+                double Tl[16];
+                for (int k = 0; k < 16; ++k) Tl[k] = __ldcg(a.T + k);
+                if (chol_solve6(tot, tot + 21, x)) {
+                    compose_update(x, Tl);
+                } else {
+                    atomicOr(a.status, ST_DEGENERATE);
+                }
+                for (int k = 0; k < 16; ++k) a.T[k] = Tl[k];
+                for (int r = 0; r < 3; ++r) {
+                    for (int cc = 0; cc < 3; ++cc) a.Rt[r * 3 + cc] = float(Tl[r * 4 + cc]);
+                    a.Rt[9 + r] = float(Tl[r * 4 + 3]);
+                }
+                if (a.T_hist)
+                    for (int k = 0; k < 16; ++k) a.T_hist[16 * it + k] = Tl[k];
+                a.bar[2] = 0u;
+                __threadfence();
+            }
+        }
+        if (!grid_barrier(a.bar, a.status, BARRIER_SPIN_LIMIT)) return;
+    }
+}
+
+// A wait that nothing ends: the bounded barrier's timeout path, for tests of
+// failure detection.  One CTA arrives at a barrier that expects two.
+__global__ void k_barrier_timeout_probe(unsigned* bar, int* status, long long limit) {
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        atomicAdd(bar, 1u);  // expects 2 arrivals; the second never comes
+        long long spins = 0;
+        while (*vgen == gen) {
+            if (++spins > limit) {
+                atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+        }
+        bar[0] = 0u;
     }
 }
 
@@ -355,29 +443,42 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
                        int iters, float lam_c, cudaStream_t s, double* T_out, double* T_hist) {
     const int n = int(n64);
     const int n_nodes = int(hgmm_node_count(t->depth));
-    const int nb = (n_nodes + MSTEP_THREADS - 1) / MSTEP_THREADS;
     {
         ProfScope ps_(t, K_REG_INIT, s);
         k_reg_init<<<(n_nodes + 255) / 256, 256, 0, s>>>(T_init, n_nodes, lam_c, t->stat, t->est,
                                                           t->reg_acc, t->reg_T, t->reg_Rt,
-                                                          t->reg_counter);
+                                                          t->reg_bar);
     }
-    for (int it = 0; it < iters; ++it) {
-        {
-            ProfScope ps_(t, K_DESCEND, s);
-            k_descend<<<t->reg_grid, REG_THREADS, 0, s>>>(src, n, t->est, t->depth, t->reg_Rt, t->root,
-                                                         t->reg_acc);
-        }
-        {
-            ProfScope ps_(t, K_REG_MSTEP, s);
-            k_mstep<<<nb, MSTEP_THREADS, 0, s>>>(n_nodes, n, it, t->rnode, t->est, t->root, t->reg_acc,
-                                                 t->reg_part, t->reg_counter, t->reg_T, t->reg_Rt,
-                                                 T_hist, t->reg_dbg, t->status);
+    if (iters > 0) {
+        RegArgs a;
+        a.src = src;
+        a.n = n;
+        a.est = t->est;
+        a.rnode = t->rnode;
+        a.root = t->root;
+        a.depth = t->depth;
+        a.n_nodes = n_nodes;
+        a.iters = iters;
+        a.acc = t->reg_acc;
+        a.part = t->reg_part;
+        a.bar = t->reg_bar;
+        a.T = t->reg_T;
+        a.Rt = t->reg_Rt;
+        a.T_hist = T_hist;
+        a.dbg = t->reg_dbg;
+        a.status = t->status;
+        void* args[] = {&a};
+        ProfScope ps_(t, K_DESCEND, s);
+        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_register, dim3(t->reg_grid),
+                                                          dim3(REG_THREADS), args, 0, s);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "hgmm: cooperative launch failed: %s\n", cudaGetErrorString(e));
+            return HGMM_ECUDA;
         }
     }
-    {
+    if (T_out) {
         ProfScope ps_(t, K_COPY_T, s);
-        if (T_out) k_copy_T<<<1, 32, 0, s>>>(t->reg_T, T_out);
+        k_copy_T<<<1, 32, 0, s>>>(t->reg_T, T_out);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -385,4 +486,17 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         return HGMM_ECUDA;
     }
     return HGMM_OK;
+}
+
+int hgmm_register_grid(int n_sm) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_register, REG_THREADS, 0) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    return n_sm * (per_sm < 2 ? per_sm : 2);
+}
+
+int hgmm_barrier_timeout_probe_impl(hgmm_tree* t, long long limit, cudaStream_t s) {
+    k_barrier_timeout_probe<<<1, 32, 0, s>>>(t->reg_bar + 4, t->status, limit);
+    return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
 }

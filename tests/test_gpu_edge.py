@@ -23,7 +23,12 @@ def _consistent(tree, n, depth):
         assert lab.min() >= 0 and lab.max() < 8 ** (l + 1)
         assert np.array_equal(np.bincount(lab, minlength=8 ** (l + 1)), g["count"])
         assert g["count"].sum() == n
-        assert np.all(g["count"][~g["live"]] == 0)
+        # a dead node holds points only as child 0 of a parent without live
+        # children (a leaf parent's points are carried down there)
+        split = g["live"].reshape(-1, 8).any(axis=1)
+        carrier = np.zeros(g["live"].shape[0], bool)
+        carrier[0::8] = ~split
+        assert np.all(g["count"][~g["live"] & ~carrier] == 0)
         assert np.all(np.isfinite(g["mu"][g["live"]]))
         assert np.all(np.isfinite(g["Sigma"][g["live"]]))
         if l:
@@ -118,3 +123,19 @@ def test_host_entry_point_matches_device_path(B):
     T_dev = tree.register(src, iters=12).cpu().numpy()
     tree.sync()
     assert np.array_equal(T_host, T_dev)
+
+
+def test_bounded_wait_times_out_without_fault(B):
+    """Failure detection on the GPU: a grid-barrier wait that nothing ends
+    gives up after its spin limit, records HGMM_ETIMEOUT and returns; the
+    context and the tree stay usable."""
+    tree = B.Tree(2000, 2)
+    B.hgmm_debug_barrier_timeout(tree.handle, 20000)
+    with pytest.raises(B.HgmmError) as e:
+        tree.sync()
+    assert e.value.code == B.HGMM_ETIMEOUT
+    P = synth.corner_scene(synth.make_rng(3), 2000)
+    dev, _ = PT.device_cloud(P)
+    tree.build(dev, 2)
+    tree.register(dev, iters=2)
+    tree.sync()
