@@ -173,6 +173,17 @@ int hgmm_profile(hgmm_tree* t, int32_t enable);
 int hgmm_profile_read(hgmm_tree* t, int32_t kernel, const char** name, double* total_ms,
                       int64_t* launches);
 
+/* Registration phase trace: with hgmm_trace(t, 1) the next hgmm_register
+ * (up to 64 rounds) records, per round and per CTA of its cooperative launch,
+ * 6 %globaltimer stamps in ns: round start, descent done, first grid barrier
+ * passed, node terms done, solve done (only the CTA that solved; 0
+ * elsewhere), second grid barrier passed.  hgmm_trace_read synchronises and
+ * copies iters x ctas x 6 int64 (cap = capacity in int64) and reports the
+ * dimensions.  Tracing only adds the stamps; results are unchanged. */
+int hgmm_trace(hgmm_tree* t, int32_t enable);
+int hgmm_trace_read(hgmm_tree* t, int64_t* h_events, int64_t cap, int32_t* iters,
+                    int32_t* ctas);
+
 /* Total node count of a tree of `depth` levels (8 + 64 + ... + 8^depth). */
 int64_t hgmm_node_count(int32_t depth);
 

@@ -66,6 +66,8 @@ def _load():
         "hgmm_node_count": (i64, [i32]),
         "hgmm_profile": (ctypes.c_int, [vp, i32]),
         "hgmm_debug_barrier_timeout": (ctypes.c_int, [vp, i64, vp]),
+        "hgmm_trace": (ctypes.c_int, [vp, i32]),
+        "hgmm_trace_read": (ctypes.c_int, [vp, vp, i64, P(i32), P(i32)]),
         "hgmm_profile_read": (ctypes.c_int, [vp, i32, P(ctypes.c_char_p), P(ctypes.c_double),
                                              P(ctypes.c_int64)]),
         "hgmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -221,6 +223,20 @@ HGMM_PROF_KERNELS = 16
 def hgmm_debug_barrier_timeout(h, spin_limit: int, stream=None) -> None:
     _check(_lib.hgmm_debug_barrier_timeout(h, int(spin_limit), _stream_ptr(stream)),
            "hgmm_debug_barrier_timeout")
+
+
+def hgmm_trace(h, enable: bool) -> None:
+    _check(_lib.hgmm_trace(h, 1 if enable else 0), "hgmm_trace")
+
+
+def hgmm_trace_read(h, max_iters: int = 64, max_ctas: int = 4096) -> np.ndarray:
+    """(iters, ctas, 6) int64 globaltimer stamps of the last traced registration."""
+    buf = np.zeros(max_iters * max_ctas * 6, dtype=np.int64)
+    it = ctypes.c_int32()
+    nc = ctypes.c_int32()
+    _check(_lib.hgmm_trace_read(h, ctypes.c_void_p(buf.ctypes.data), buf.size,
+                                ctypes.byref(it), ctypes.byref(nc)), "hgmm_trace_read")
+    return buf[: it.value * nc.value * 6].reshape(it.value, nc.value, 6)
 
 
 def hgmm_profile(h, enable: bool) -> None:

@@ -44,9 +44,9 @@ void free_tree(hgmm_tree* t) {
     cudaSetDevice(t->device);
     clear_prof(t);
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
-                    t->codes, t->items, t->item_range, t->pdone, t->meta, t->partials, t->item_cnt,
+                    t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
                     t->item_off, t->root, t->root_part, t->root_counter, t->status, t->reg_acc, t->reg_part,
-                    t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->rnode, t->stage_tgt,
+                    t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->rnode, t->trace, t->stage_tgt,
                     t->stage_src, t->stage_T};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -135,7 +135,6 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->codes, max_points);
     good &= dalloc(&t->items, t->max_items);
     good &= dalloc(&t->item_range, 2 * std::max<int64_t>(parents, 1));
-    good &= dalloc(&t->pdone, std::max<int64_t>(parents, 1));
     good &= dalloc(&t->meta, 4);
     good &= dalloc(&t->partials, t->max_items * NPART);
     good &= dalloc(&t->item_cnt, t->max_items * 8);
@@ -144,9 +143,10 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->root_part, int64_t(t->est_grid) * 32);
     good &= dalloc(&t->root_counter, 1);
     good &= dalloc(&t->status, 1);
-    good &= dalloc(&t->reg_acc, 4 * t->max_nodes);
+    good &= dalloc(&t->reg_acc, 4 * ACC_REPLICAS * t->max_nodes);
     good &= dalloc(&t->reg_part, 27 * nb);
     good &= dalloc(&t->rnode, 3 * t->max_nodes);
+    good &= dalloc(&t->trace, int64_t(TRACE_MAX_ITERS) * t->reg_grid * 6);
     good &= dalloc(&t->reg_bar, 8);
     good &= dalloc(&t->reg_T, 16);
     good &= dalloc(&t->reg_Rt, 12);
@@ -161,8 +161,8 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= ok(cudaMemset(t->status, 0, sizeof(int)), "cudaMemset");
     good &= ok(cudaMemset(t->reg_bar, 0, 8 * sizeof(unsigned)), "cudaMemset");
     good &= ok(cudaMemset(t->root_counter, 0, sizeof(unsigned)), "cudaMemset");
-    good &= ok(cudaMemset(t->pdone, 0, std::max<int64_t>(parents, 1) * sizeof(int)), "cudaMemset");
-    good &= ok(cudaMemset(t->reg_acc, 0, 4 * t->max_nodes * sizeof(unsigned long long)), "cudaMemset");
+    good &= ok(cudaMemset(t->reg_acc, 0, 4 * ACC_REPLICAS * t->max_nodes * sizeof(unsigned long long)),
+               "cudaMemset");
     good &= ok(cudaMemset(t->stat, 0, t->max_nodes * sizeof(NodeStat)), "cudaMemset");
     good &= ok(cudaMemset(t->seg_count, 0, t->max_nodes * sizeof(int)), "cudaMemset");
     good &= ok(cudaMemset(t->seg_start, 0, t->max_nodes * sizeof(int)), "cudaMemset");
@@ -325,6 +325,20 @@ int hgmm_debug_barrier_timeout(hgmm_tree* t, int64_t spin_limit, void* stream) {
     if (!t || spin_limit < 1 || spin_limit > 100000000) return HGMM_EINVAL;
     if (int rc = check_device(t)) return rc;
     return hgmm_barrier_timeout_probe_impl(t, spin_limit, static_cast<cudaStream_t>(stream));
+}
+
+int hgmm_trace(hgmm_tree* t, int32_t enable) {
+    if (!t) return HGMM_EINVAL;
+    t->trace_on = enable != 0;
+    return HGMM_OK;
+}
+
+int hgmm_trace_read(hgmm_tree* t, int64_t* h_events, int64_t cap, int32_t* iters,
+                    int32_t* ctas) {
+    if (!t || !h_events) return HGMM_EINVAL;
+    if (iters) *iters = t->trace_iters;
+    if (ctas) *ctas = t->reg_grid;
+    return hgmm_trace_read_impl(t, reinterpret_cast<unsigned long long*>(h_events), cap);
 }
 
 int hgmm_profile(hgmm_tree* t, int32_t enable) {

@@ -6,14 +6,14 @@
 //   k_init_children   PCA-octant initial children of every parent (FP64 eigen)
 //   k_make_items      split each parent's contiguous point segment into work
 //                     items of <= TILE points, laid out parent by parent
-//   K x k_estep       per point: Eq. 3 posteriors over the 8 children of its
+//   K x ( k_estep     per point: Eq. 3 posteriors over the 8 children of its
 //                     parent (FP32, log2 domain, max-subtracted exp2) and the
 //                     gamma-weighted moments S0, S1, S2 of every child,
 //                     centred on the child's current mean; compensated sums;
-//                     one partial per (CTA, parent) run.  The CTA that
-//                     completes a parent's last run also runs its M-step:
-//                     fixed-order reduction of the runs, FP64 M-step and
-//                     Cholesky, dead-child rule, new FP32 E-step constants
+//                     one partial per (CTA, parent) run
+//    + k_mstep        per parent: fixed-order reduction of its runs, FP64
+//                     M-step and Cholesky, dead-child rule, new FP32 E-step
+//                     constants )
 //   k_assign          argmax hand-off (ties -> lowest index) with in-item ranks
 //   k_child_offsets   per parent: child segment starts and per-item offsets
 //   k_scatter         stable 8-way partition of every parent's segment
@@ -295,13 +295,9 @@ __global__ void __launch_bounds__(1024) k_make_items(int level, int n, int n_par
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        // items per E-step CTA: enough CTAs to cover the items, but at least
-        // ~sqrt(items)/4 items each so that the last CTA of a big parent has
-        // few run partials to reduce
+        // items per E-step CTA (contiguous chunks, so a parent's runs are few)
         meta[0] = carry;
-        int rt = 1;
-        while ((rt + 1) * (rt + 1) <= carry) ++rt;
-        meta[1] = max(max(1, (carry + est_grid - 1) / est_grid), rt / 4);
+        meta[1] = max(1, (carry + est_grid - 1) / est_grid);
     }
 }
 
@@ -337,14 +333,14 @@ __global__ void k_fill_items(int level, int n, int n_parents, const int* __restr
 
 // ---------------------------------------------------------------- M-step
 // M-step of parent p (Sec. 3 EM on the parent's points): reduce the parent's
-// run partials in a fixed order (3 groups of 80 threads, then in order),
+// run partials in a fixed order (8 warps over the runs, then in order),
 // then threads 0..7 build child c in FP64: S0, mean shift d = S1/S0 from the
 // FP32 mean the E-step used, Sigma = S2/S0 - d d^T + eps I, pi = S0 / n_p;
 // a child below n_min expected points dies (a parent whose children all die
-// stays a leaf).  Needs >= 240 threads.
+// stays a leaf).  Runs with 256 threads.
 struct MstepSmem {
     double mom[NPART];
-    float2 grp[3][NPART];
+    float2 grp[8][NPART];
 };
 
 template <bool COMP>
@@ -354,22 +350,43 @@ __device__ void mstep_parent(int level, int n, int p, int i0, int i1, int C,
                              float n_min, NodeStat* __restrict__ stat,
                              NodeEst* __restrict__ est, int* __restrict__ status, MstepSmem& sm) {
     const int nruns = (i1 - 1) / C - i0 / C + 1;
-    if (threadIdx.x < 3 * NPART) {
-        const int v = threadIdx.x % NPART, q = threadIdx.x / NPART;
-        float S = 0.f, Cc = 0.f;
-#pragma unroll 4
-        for (int r = q; r < nruns; r += 3) {
-            const int slot = r == 0 ? i0 : (i0 / C + r) * C;
-            const float2 x = __ldcg(&partials[int64_t(slot) * NPART + v]);
-            if (COMP) pair_add(S, Cc, x.x, x.y);
-            else S += x.x;
+    {
+        // warp w sums runs w, w+8, ...; lane l owns values l, l+32, l+64
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int nw = blockDim.x >> 5;
+        float S[3] = {0.f, 0.f, 0.f}, Cc[3] = {0.f, 0.f, 0.f};
+        for (int r0 = warp; r0 < nruns; r0 += 4 * nw) {
+            float2 x[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = r0 + u * nw;
+                const int slot = r == 0 ? i0 : (i0 / C + r) * C;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int v = lane + 32 * j;
+                    x[u][j] = (r < nruns && v < NPART)
+                                  ? __ldcg(&partials[int64_t(slot) * NPART + v])
+                                  : make_float2(0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (COMP) pair_add(S[j], Cc[j], x[u][j].x, x[u][j].y);
+                    else S[j] += x[u][j].x;
+                }
         }
-        sm.grp[q][v] = make_float2(S, Cc);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int v = lane + 32 * j;
+            if (v < NPART) sm.grp[warp][v] = make_float2(S[j], Cc[j]);
+        }
     }
     __syncthreads();
     if (threadIdx.x < NPART) {
         float S = 0.f, Cc = 0.f;
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < int(blockDim.x >> 5); ++q) {
             if (COMP) pair_add(S, Cc, sm.grp[q][threadIdx.x].x, sm.grp[q][threadIdx.x].y);
             else S += sm.grp[q][threadIdx.x].x;
         }
@@ -510,45 +527,12 @@ __device__ __forceinline__ void flush_run(float* s, float* c, float2 (*red)[NPAR
     for (int v = 0; v < 20; ++v) { s[v] = 0.f; c[v] = 0.f; }
 }
 
-// Completes a parent run: the run's partial is already written; count its
-// items against the parent's total and, if this CTA brought the count to the
-// total, run the parent's M-step (the last CTA for a parent, no waiting).
-template <bool COMP>
-__device__ __forceinline__ void close_run(int level, int n, int parent, int run_items,
-                                          const int* __restrict__ item_range, int C,
-                                          int* __restrict__ pdone,
-                                          const float2* __restrict__ partials,
-                                          const int* __restrict__ seg_count,
-                                          const RootDev* __restrict__ root, float n_min,
-                                          NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
-                                          int* __restrict__ status, MstepSmem& msm, int* flag) {
-    const int i0 = item_range[2 * parent], i1 = item_range[2 * parent + 1];
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const int old = atomicAdd(&pdone[parent], run_items);
-        *flag = (old + run_items == i1 - i0) ? 1 : 0;
-    }
-    __syncthreads();
-    if (*flag) {
-        __threadfence();
-        mstep_parent<COMP>(level, n, parent, i0, i1, C, partials, seg_count, root, n_min, stat,
-                           est, status, msm);
-        if (threadIdx.x == 0) pdone[parent] = 0;  // ready for the next iteration
-    }
-    __syncthreads();
-}
-
 template <bool COMP>
 __global__ void __launch_bounds__(EST_THREADS, 2)
 k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
-        const int* __restrict__ meta, NodeEst* __restrict__ est_lvl,
-        float2* __restrict__ partials, int level, int n, const int* __restrict__ item_range,
-        int* __restrict__ pdone, const int* __restrict__ seg_count,
-        const RootDev* __restrict__ root, float n_min, NodeStat* __restrict__ stat,
-        NodeEst* __restrict__ est, int* __restrict__ status) {
+        const int* __restrict__ meta, const NodeEst* __restrict__ est_lvl,
+        float2* __restrict__ partials) {
     __shared__ float2 red[EST_THREADS / 32][NPART];
-    __shared__ MstepSmem msm;
-    __shared__ int flag;
     const int n_items = meta[0];
     const int C = meta[1];
     const int ib = blockIdx.x * C;
@@ -569,8 +553,6 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
                 fold20<COMP>(in, s, c);
                 nfold = 0;
                 flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
-                close_run<COMP>(level, n, cur, it - run, item_range, C, pdone, partials,
-                                seg_count, root, n_min, stat, est, status, msm, &flag);
             }
             cur = w.parent;
             run = it;
@@ -606,8 +588,22 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
     }
     fold20<COMP>(in, s, c);
     flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
-    close_run<COMP>(level, n, cur, ie - run, item_range, C, pdone, partials, seg_count, root,
-                    n_min, stat, est, status, msm, &flag);
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(256) k_mstep(int level, int n, const int* __restrict__ item_range,
+                                               const int* __restrict__ meta,
+                                               const float2* __restrict__ partials,
+                                               const int* __restrict__ seg_count,
+                                               const RootDev* __restrict__ root, float n_min,
+                                               NodeStat* __restrict__ stat,
+                                               NodeEst* __restrict__ est, int* __restrict__ status) {
+    __shared__ MstepSmem msm;
+    const int p = blockIdx.x;
+    const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
+    if (i0 >= i1) return;  // parent without points: children stay dead
+    mstep_parent<COMP>(level, n, p, i0, i1, meta[1], partials, seg_count, root, n_min, stat, est,
+                       status, msm);
 }
 
 // ---------------------------------------------------------------- M-step
@@ -888,15 +884,24 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
         const bool stop_here = p.debug_stop_level == l + 1;
         const int em_iters = stop_here ? p.debug_stop_iters : p.em_iters;
         for (int k = 0; k < em_iters; ++k) {
-            ProfScope ps_(t, K_ESTEP, s);
-            if (comp)
-                k_estep<true><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials,
-                                                        l, n, t->item_range, t->pdone, t->seg_count,
-                                                        t->root, p.n_min, t->stat, t->est, t->status);
-            else
-                k_estep<false><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials,
-                                                         l, n, t->item_range, t->pdone, t->seg_count,
-                                                         t->root, p.n_min, t->stat, t->est, t->status);
+            {
+                ProfScope ps_(t, K_ESTEP, s);
+                if (comp)
+                    k_estep<true><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials);
+                else
+                    k_estep<false><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials);
+            }
+            {
+                ProfScope ps_(t, K_MSTEP, s);
+                if (comp)
+                    k_mstep<true><<<n_par, 256, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
+                                                        t->seg_count, t->root, p.n_min, t->stat,
+                                                        t->est, t->status);
+                else
+                    k_mstep<false><<<n_par, 256, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
+                                                         t->seg_count, t->root, p.n_min, t->stat,
+                                                         t->est, t->status);
+            }
         }
         HGMM_LAUNCH_CHECK();
         if (stop_here) return HGMM_OK;  // checking aid: parameters after em_iters

@@ -37,6 +37,8 @@ constexpr int TILE = 256;             // points per build work item
 constexpr int EST_THREADS = 256;      // build E-step CTA
 constexpr int REG_THREADS = 256;      // registration descent CTA
 constexpr int MSTEP_THREADS = 128;    // registration M-step CTA
+constexpr int TRACE_MAX_ITERS = 64;   // rounds the registration trace can hold
+constexpr int ACC_REPLICAS = 1;       // copies of each node's registration moments
 
 // status bits (device word, OR-ed)
 constexpr int ST_NONFINITE = 1;
@@ -118,7 +120,6 @@ struct hgmm_tree {
     uint32_t* codes = nullptr;
     hgmm::Item* items = nullptr;
     int* item_range = nullptr;   // per parent: [begin, end) item indices
-    int* pdone = nullptr;        // per parent: items whose partial is written (E-step)
     int* meta = nullptr;         // [0] n_items, [1] items per E-step CTA
     float2* partials = nullptr;  // max_items x NPART (sum, compensation)
     int* item_cnt = nullptr;     // max_items x 8
@@ -128,15 +129,18 @@ struct hgmm_tree {
     unsigned* root_counter = nullptr;
     int* status = nullptr;
     // registration
-    unsigned long long* reg_acc = nullptr;  // nodes x 4 fixed point
+    unsigned long long* reg_acc = nullptr;  // nodes x ACC_REPLICAS x 4 fixed point
     float2* reg_part = nullptr;             // blocks x 27 (sum, compensation)
     float4* rnode = nullptr;                // nodes x 3: P (6), mu - mu32 (3), FP32
     unsigned* reg_bar = nullptr;            // grid barrier words (8)
     double* reg_T = nullptr;                // 16 doubles current T
     float* reg_Rt = nullptr;                // 12 floats (R row-major, t)
     double* reg_dbg = nullptr;              // nodes x 4 (last round)
-    // per-kernel timing
+    // per-kernel timing and the registration's phase trace
     bool prof_on = false;
+    bool trace_on = false;
+    int trace_iters = 0;
+    unsigned long long* trace = nullptr;  // TRACE_MAX_ITERS x reg_grid x 6
     std::vector<hgmm::ProfRecord> prof;
     // host-API staging
     float4* stage_tgt = nullptr;
@@ -171,3 +175,4 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n,
 int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s);
 int hgmm_register_grid(int n_sm);
 int hgmm_barrier_timeout_probe_impl(hgmm_tree* t, long long limit, cudaStream_t s);
+int hgmm_trace_read_impl(hgmm_tree* t, unsigned long long* h, int64_t cap);

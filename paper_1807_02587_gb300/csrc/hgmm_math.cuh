@@ -183,10 +183,10 @@ __device__ inline void eig3(const double S[6], double lam[3], double V[9]) {
         for (int c = r; c < 3; ++c)
             B[r][c] = B[c][r] = U[0][r] * SU[0][c] + U[1][r] * SU[1][c] + U[2][r] * SU[2][c];
     // 4) FP64 Jacobi sweeps on the nearly diagonal B
-    for (int sweep = 0; sweep < 4; ++sweep) {
+    for (int sweep = 0; sweep < 3; ++sweep) {
         const double off = B[0][1] * B[0][1] + B[0][2] * B[0][2] + B[1][2] * B[1][2];
         const double dia = B[0][0] * B[0][0] + B[1][1] * B[1][1] + B[2][2] * B[2][2];
-        if (!(off > 1e-32 * dia)) break;
+        if (!(off > 1e-30 * dia)) break;
         for (int pq = 0; pq < 3; ++pq) {
             const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
             const double apq = B[p][q];

@@ -41,10 +41,7 @@ __global__ void k_reg_init(const double* __restrict__ T_init, int n_nodes, float
                            float* __restrict__ Rt, unsigned* __restrict__ bar) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_nodes) {
-        acc[4 * i + 0] = 0ull;
-        acc[4 * i + 1] = 0ull;
-        acc[4 * i + 2] = 0ull;
-        acc[4 * i + 3] = 0ull;
+        for (int k = 0; k < 4 * ACC_REPLICAS; ++k) acc[4 * ACC_REPLICAS * int64_t(i) + k] = 0ull;
         if (lam_c >= 0.f)
             est[i].c.z = (stat[i].live && stat[i].complexity <= double(lam_c)) ? 1.f : 0.f;
     }
@@ -67,9 +64,25 @@ __device__ __forceinline__ long long to_fix(float v) {
 // Algorithm 1 for the points of this CTA (grid-stride by warps) with the
 // current transform; adds each point's (gamma, gamma (z' - mu_j)) to the
 // chosen node's fixed-point moments.
+constexpr int STAGED_NODES = 584;  // levels 0..2 (8 + 64 + 512 nodes) live in shared memory
+
+__device__ __forceinline__ void load_node(const NodeEst* __restrict__ est, const float4* sm_est,
+                                          int64_t g, float4& ea, float4& eb, float4& ec) {
+    if (g < STAGED_NODES) {
+        ea = sm_est[3 * g];
+        eb = sm_est[3 * g + 1];
+        ec = sm_est[3 * g + 2];
+    } else {
+        const NodeEst* e = est + g;
+        ea = __ldg(&e->a);
+        eb = __ldg(&e->b);
+        ec = __ldg(&e->c);
+    }
+}
+
 __device__ __forceinline__ void descend_points(const float4* __restrict__ src, int n,
-                                               const NodeEst* __restrict__ est, int depth,
-                                               const float* Rt_sm, float qscale,
+                                               const NodeEst* __restrict__ est, const float4* sm_est,
+                                               int depth, const float* Rt_sm, float qscale,
                                                unsigned long long* __restrict__ acc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float r00 = Rt_sm[0], r01 = Rt_sm[1], r02 = Rt_sm[2], r10 = Rt_sm[3], r11 = Rt_sm[4];
@@ -94,8 +107,8 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             int bi = -1;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const NodeEst* e = est + first + c;
-                const float4 ea = __ldg(&e->a), eb = __ldg(&e->b), ec = __ldg(&e->c);
+                float4 ea, eb, ec;
+                load_node(est, sm_est, first + c, ea, eb, ec);
                 const float ex = x - ea.x, ey = y - ea.y, ez = w - ea.z;
                 const float d0 = eb.x * ex;
                 const float d1 = fmaf(eb.z, ey, eb.y * ex);
@@ -113,9 +126,10 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             gamma = 1.0f / sum;
             chosen = int(first + bi);
             local = 8 * local + bi;
-            const float4 ea = __ldg(&est[chosen].a);
+            float4 ea, eb, ec;
+            load_node(est, sm_est, chosen, ea, eb, ec);
             cmx = ea.x; cmy = ea.y; cmz = ea.z;
-            if (__ldg(&est[chosen].c).z != 0.f) break;  // Complexity <= lambda_c
+            if (ec.z != 0.f) break;  // Complexity <= lambda_c
         }
         // Sum (gamma, gamma (z' - mu_j)) over the lanes of this warp that chose
         // the same node j: a pairwise tree over the members' ranks (fixed order,
@@ -145,7 +159,10 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             }
         }
         if (has && rank == 0) {
-            unsigned long long* dst = acc + 4 * int64_t(chosen);
+            // one of ACC_REPLICAS copies per CTA spreads the atomics on hot
+            // nodes (a ground plane collects a large share of the points)
+            unsigned long long* dst =
+                acc + 4 * (int64_t(chosen) * ACC_REPLICAS + (blockIdx.x & (ACC_REPLICAS - 1)));
             atomicAdd(dst + 0, (unsigned long long)to_fix(v0 * 4294967296.0f));
             atomicAdd(dst + 1, (unsigned long long)to_fix(v1 * qscale));
             atomicAdd(dst + 2, (unsigned long long)to_fix(v2 * qscale));
@@ -233,6 +250,92 @@ __device__ inline void compose_update(const double x[6], double* T) {
     for (int k = 0; k < 12; ++k) T[k] = Tn[k];
 }
 
+// FP64 solve of the 6x6 normal equations and the pose update by one warp.
+// Lane i < 6 owns row i; the right-looking Cholesky updates all rows with
+// one instruction per column, so the FP64 instruction count of the critical
+// path (~70 cycles each on this part) is about a third of a one-thread
+// solve.  L is kept in shared memory for the back substitution.  Returns
+// false (uniformly) for a non-positive pivot.
+__device__ bool warp_solve_update(const double* tot, double (*Lsm)[6], double* T,
+                                  float* Rt, double* T_hist, int iter) {
+    const int lane = threadIdx.x & 31;
+    const int row = lane < 6 ? lane : 5;
+    auto H = [&](int i, int j) {  // upper-packed 21 entries
+        if (i > j) { const int t = i; i = j; j = t; }
+        return tot[i * 6 - (i * (i - 1)) / 2 + (j - i)];
+    };
+    double a[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a[j] = H(row, j);
+    double g = tot[21 + row];
+    double dmax = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) dmax = fmax(dmax, H(j, j));
+    double r[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double dk = __shfl_sync(FULL, a[k], k);
+        if (!(dk > 1e-15 * dmax)) return false;
+        r[k] = rsqrt_f64(dk);
+        const double lik = a[k] * r[k];  // L_ik for rows i >= k
+        if (lane < 6) Lsm[k][lane] = lik;
+#pragma unroll
+        for (int j = k + 1; j < 6; ++j) {
+            const double ljk = __shfl_sync(FULL, lik, j);
+            a[j] = fma(-lik, ljk, a[j]);
+        }
+    }
+    __syncwarp();
+    // forward: L y = g (column k: y_k = g_k r_k, then rows i > k lose L_ik y_k)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double yk = __shfl_sync(FULL, g, k) * r[k];
+        if (lane == k) g = yk;
+        else if (lane > k) g = fma(-Lsm[k][row], yk, g);
+    }
+    // backward: L^T x = y (x_k = y_k r_k, then rows j < k lose L_kj x_k)
+    double x[6];
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+        const double xk = __shfl_sync(FULL, g, k) * r[k];
+        x[k] = xk;
+        if (lane < k) g = fma(-Lsm[lane][k], xk, g);
+    }
+    // dT = (Rodrigues(w), t); lane e < 12 computes entry e of the new [R|t]
+    const double th2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    double ca, cb;
+    if (th2 < 0.25) {
+        ca = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880 +
+             th2 * (-1.0 / 39916800 + th2 * (1.0 / 6227020800.0))))));
+        cb = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720 + th2 * (-1.0 / 40320 + th2 * (1.0 / 3628800 +
+             th2 * (-1.0 / 479001600 + th2 * (1.0 / 87178291200.0))))));
+    } else {
+        const double th = sqrt(th2);
+        ca = sin(th) / th;
+        cb = (1.0 - cos(th)) / th2;
+    }
+    const int e = lane < 12 ? lane : 11;
+    const int rr = e >> 2, cc = e & 3;
+    // row rr of dR = I + a K + b K^2, K = [w]x, (K^2)_{rm} = w_r w_m - |w|^2 delta_rm
+    const double kr[3] = {rr == 0 ? 0.0 : (rr == 1 ? x[2] : -x[1]),
+                          rr == 0 ? -x[2] : (rr == 1 ? 0.0 : x[0]),
+                          rr == 0 ? x[1] : (rr == 1 ? -x[0] : 0.0)};
+    double acc = cc == 3 ? x[3 + rr] : 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const double drm = (m == rr ? 1.0 - cb * th2 : 0.0) + ca * kr[m] + cb * x[rr] * x[m];
+        acc = fma(drm, __ldcg(T + m * 4 + cc), acc);
+    }
+    __syncwarp();
+    if (lane < 12) {
+        T[e] = acc;
+        Rt[cc == 3 ? 9 + rr : rr * 3 + cc] = float(acc);
+        if (T_hist) T_hist[16 * iter + e] = acc;
+    }
+    if (T_hist && lane >= 12 && lane < 16) T_hist[16 * iter + lane] = lane == 15 ? 1.0 : 0.0;
+    return true;
+}
+
 // Bounded grid-wide barrier for a cooperative launch (all CTAs co-resident):
 // generation counter, spin with a sleep and an iteration limit; on timeout
 // it records ST_TIMEOUT and returns false so the kernel can exit.
@@ -285,7 +388,20 @@ struct RegArgs {
     double* T_hist;
     double* dbg;
     int* status;
+    unsigned long long* trace;  // optional: [iter][cta][TRACE_EVENTS] globaltimer ns
 };
+
+constexpr int TRACE_EVENTS = 6;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void trace_mark(unsigned long long* tr, int it, int ev) {
+    if (tr && threadIdx.x == 0) tr[(int64_t(it) * gridDim.x + blockIdx.x) * TRACE_EVENTS + ev] = gtimer();
+}
 
 // The whole registration loop in one cooperative launch.  Per round:
 //   A. Algorithm 1 for every source point (fixed-point node moments)
@@ -295,35 +411,63 @@ struct RegArgs {
 //   C. reduces the partials in a fixed order, solves the 6x6 system in FP64
 //      and composes T <- dT T
 //   -- grid barrier --  (everyone reads the new T)
-__global__ void __launch_bounds__(REG_THREADS) k_register(RegArgs a) {
+__global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     __shared__ float Rt_sm[12];
     __shared__ float2 sm[REG_THREADS / 32][27];
-    __shared__ float2 fin[4][27];
+    __shared__ float2 fin[8][27];
     __shared__ double tot[27];
+    __shared__ double Lsm[6][6];
     __shared__ bool last;
+    __shared__ float4 sm_est[3 * STAGED_NODES];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the top levels of the tree are read by every point: stage them once
+    // for all rounds (the stop flags were set by k_reg_init before launch)
+    {
+        const int ns = a.n_nodes < STAGED_NODES ? a.n_nodes : STAGED_NODES;
+        const float4* gsrc = reinterpret_cast<const float4*>(a.est);
+        for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) sm_est[i] = gsrc[i];
+        __syncthreads();
+    }
     const double ext = a.root->extent > 0.0 ? a.root->extent : 1.0;
     const float qscale = float(FIX / ext);  // fixed-point units per metre
     for (int it = 0; it < a.iters; ++it) {
+        trace_mark(a.trace, it, 0);
         if (threadIdx.x < 12) Rt_sm[threadIdx.x] = __ldcg(a.Rt + threadIdx.x);
         __syncthreads();
-        descend_points(a.src, a.n, a.est, a.depth, Rt_sm, qscale, a.acc);
+        descend_points(a.src, a.n, a.est, sm_est, a.depth, Rt_sm, qscale, a.acc);
+        trace_mark(a.trace, it, 1);
         if (!grid_barrier(a.bar, a.status, BARRIER_SPIN_LIMIT)) return;
-        // ---- B: node terms
+        trace_mark(a.trace, it, 2);
+        // ---- B: node terms (only the CTAs that own nodes take part)
+        const int nb_nodes = (a.n_nodes + blockDim.x - 1) / blockDim.x;
+        if (blockIdx.x < nb_nodes) {
         float v[27], c[27];
 #pragma unroll
         for (int k = 0; k < 27; ++k) { v[k] = 0.f; c[k] = 0.f; }
         double* dbg = it == a.iters - 1 ? a.dbg : nullptr;
-        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_nodes; g += gridDim.x * blockDim.x) {
-            const long long a0 = (long long)__ldcg(a.acc + 4 * g + 0);
-            const long long a1 = (long long)__ldcg(a.acc + 4 * g + 1);
-            const long long a2 = (long long)__ldcg(a.acc + 4 * g + 2);
-            const long long a3 = (long long)__ldcg(a.acc + 4 * g + 3);
-            if (a0 | a1 | a2 | a3) {
-                a.acc[4 * g + 0] = 0ull;
-                a.acc[4 * g + 1] = 0ull;
-                a.acc[4 * g + 2] = 0ull;
-                a.acc[4 * g + 3] = 0ull;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_nodes; g += nb_nodes * blockDim.x) {
+            long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            {
+                // integer sums of the replicas: exact, order-free
+                const ulonglong2* rp = reinterpret_cast<const ulonglong2*>(
+                    a.acc + 4 * int64_t(g) * ACC_REPLICAS);
+                ulonglong2 q[2 * ACC_REPLICAS];
+#pragma unroll
+                for (int r = 0; r < 2 * ACC_REPLICAS; ++r) q[r] = __ldcg(rp + r);
+                unsigned long long any = 0ull;
+#pragma unroll
+                for (int r = 0; r < ACC_REPLICAS; ++r) {
+                    a0 += (long long)q[2 * r].x;
+                    a1 += (long long)q[2 * r].y;
+                    a2 += (long long)q[2 * r + 1].x;
+                    a3 += (long long)q[2 * r + 1].y;
+                    any |= q[2 * r].x | q[2 * r].y | q[2 * r + 1].x | q[2 * r + 1].y;
+                }
+                if (any) {
+                    ulonglong2* wp = reinterpret_cast<ulonglong2*>(a.acc + 4 * int64_t(g) * ACC_REPLICAS);
+#pragma unroll
+                    for (int r = 0; r < 2 * ACC_REPLICAS; ++r) wp[r] = make_ulonglong2(0ull, 0ull);
+                }
             }
             const float4 cm = a.est[g].a;
             float M0 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
@@ -364,16 +508,27 @@ __global__ void __launch_bounds__(REG_THREADS) k_register(RegArgs a) {
         }
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) last = (atomicAdd(a.bar + 2, 1u) == gridDim.x - 1);
+        if (threadIdx.x == 0) last = (atomicAdd(a.bar + 2, 1u) == unsigned(nb_nodes) - 1);
         __syncthreads();
+        trace_mark(a.trace, it, 3);
         if (last) {
             // ---- C: fixed-order reduction, FP64 solve, pose update
             __threadfence();
-            const int nb = gridDim.x;
-            if (threadIdx.x < 108) {
+            const int nb = nb_nodes;
+            // all partial loads in flight at once (8 groups of 27 threads),
+            // then a fixed-order combine
+            if (threadIdx.x < 216) {
                 const int k = threadIdx.x % 27, q = threadIdx.x / 27;
                 float S = 0.f, C = 0.f;
-                for (int b = q; b < nb; b += 4) {
+                float2 xs[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int b = q + 8 * j;
+                    xs[j] = b < nb ? __ldcg(&a.part[27 * b + k]) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) pair_add(S, C, xs[j].x, xs[j].y);
+                for (int b = q + 64; b < nb; b += 8) {
                     const float2 x = __ldcg(&a.part[27 * b + k]);
                     pair_add(S, C, x.x, x.y);
                 }
@@ -382,31 +537,25 @@ __global__ void __launch_bounds__(REG_THREADS) k_register(RegArgs a) {
             __syncthreads();
             if (threadIdx.x < 27) {
                 float S = 0.f, C = 0.f;
-                for (int q = 0; q < 4; ++q) pair_add(S, C, fin[q][threadIdx.x].x, fin[q][threadIdx.x].y);
+                for (int q = 0; q < 8; ++q) pair_add(S, C, fin[q][threadIdx.x].x, fin[q][threadIdx.x].y);
                 tot[threadIdx.x] = double(S) + double(C);
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                double x[6];
-                double Tl[16];
-                for (int k = 0; k < 16; ++k) Tl[k] = __ldcg(a.T + k);
-                if (chol_solve6(tot, tot + 21, x)) {
-                    compose_update(x, Tl);
-                } else {
-                    atomicOr(a.status, ST_DEGENERATE);
+            if (warp == 0) {
+                const bool solved = warp_solve_update(tot, Lsm, a.T, a.Rt, a.T_hist, it);
+                if (!solved && lane == 0) {
+                    atomicOr(a.status, ST_DEGENERATE);  // T kept for this round
+                    if (a.T_hist)
+                        for (int k = 0; k < 16; ++k) a.T_hist[16 * it + k] = __ldcg(a.T + k);
                 }
-                for (int k = 0; k < 16; ++k) a.T[k] = Tl[k];
-                for (int r = 0; r < 3; ++r) {
-                    for (int cc = 0; cc < 3; ++cc) a.Rt[r * 3 + cc] = float(Tl[r * 4 + cc]);
-                    a.Rt[9 + r] = float(Tl[r * 4 + 3]);
-                }
-                if (a.T_hist)
-                    for (int k = 0; k < 16; ++k) a.T_hist[16 * it + k] = Tl[k];
-                a.bar[2] = 0u;
+                if (lane == 0) a.bar[2] = 0u;
                 __threadfence();
             }
+            trace_mark(a.trace, it, 4);
         }
+        }  // node-owning CTAs
         if (!grid_barrier(a.bar, a.status, BARRIER_SPIN_LIMIT)) return;
+        trace_mark(a.trace, it, 5);
     }
 }
 
@@ -467,6 +616,9 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         a.T_hist = T_hist;
         a.dbg = t->reg_dbg;
         a.status = t->status;
+        a.trace = (t->trace_on && iters <= TRACE_MAX_ITERS) ? t->trace : nullptr;
+        if (a.trace) cudaMemsetAsync(t->trace, 0, size_t(iters) * t->reg_grid * TRACE_EVENTS * 8, s);
+        t->trace_iters = a.trace ? iters : 0;
         void* args[] = {&a};
         ProfScope ps_(t, K_DESCEND, s);
         const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_register, dim3(t->reg_grid),
@@ -493,7 +645,16 @@ int hgmm_register_grid(int n_sm) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_register, REG_THREADS, 0) != cudaSuccess ||
         per_sm < 1)
         return 0;
-    return n_sm * (per_sm < 2 ? per_sm : 2);
+    return n_sm * (per_sm < 2 ? per_sm : 2);  // <= co-resident CTAs (cooperative launch)
+}
+
+int hgmm_trace_read_impl(hgmm_tree* t, unsigned long long* h, int64_t cap) {
+    const int64_t need = int64_t(t->trace_iters) * t->reg_grid * TRACE_EVENTS;
+    if (cap < need) return HGMM_ECAPACITY;
+    if (need == 0) return HGMM_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return HGMM_ECUDA;
+    return cudaMemcpy(h, t->trace, need * 8, cudaMemcpyDeviceToHost) == cudaSuccess ? HGMM_OK
+                                                                                     : HGMM_ECUDA;
 }
 
 int hgmm_barrier_timeout_probe_impl(hgmm_tree* t, long long limit, cudaStream_t s) {

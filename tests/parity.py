@@ -162,8 +162,14 @@ def check_em_steps(B, dev, Z, depth, steps, prm=None):
     eps = (prm_o.eps_rel * extent) ** 2
     tree = B.Tree(N, depth)
     res = []
+    def stop_at(level, iters):
+        q = B.params(em_iters=prm.em_iters, n_min=prm.n_min, lam_c=prm.lam_c,
+                     eps_rel=prm.eps_rel, precision=prm.precision,
+                     debug_stop_level=level, debug_stop_iters=iters)
+        return q
+
     for (l, k) in steps:
-        pa = B.params(debug_stop_level=l + 1, debug_stop_iters=k - 1)
+        pa = stop_at(l + 1, k - 1)
         tree.build(dev, depth, pa)
         tree.sync()
         A = tree.export(l)
@@ -173,7 +179,7 @@ def check_em_steps(B, dev, Z, depth, steps, prm=None):
         else:
             parent = tree.labels(l - 1).astype(np.int64)
             p_cnt = np.bincount(parent, minlength=8 ** l)
-        pb = B.params(debug_stop_level=l + 1, debug_stop_iters=k)
+        pb = stop_at(l + 1, k)
         tree.build(dev, depth, pb)
         tree.sync()
         G = tree.export(l)
