@@ -184,6 +184,28 @@ int hgmm_trace(hgmm_tree* t, int32_t enable);
 int hgmm_trace_read(hgmm_tree* t, int64_t* h_events, int64_t cap, int32_t* iters,
                     int32_t* ctas);
 
+/* Allocation-free fit of one 8-component GMM to a whole cloud: the level-0
+ * part of hgmm_build (root statistics, PCA-octant initial children, em_iters
+ * EM iterations, FP64 finalize) for callers that cannot allocate device
+ * memory at all - code running while someone else captures a CUDA graph on
+ * the stream, real-time loops with a memory budget fixed at start-up, or
+ * plug-ins whose host owns every allocation.  The paper has no counterpart:
+ * this is a deployment variant of the build's first level.
+ *   d_points : n x 4 float32, device, 16-byte aligned; 8 <= n <= 1048576
+ *              (the capacity of the fixed scratch; larger n -> HGMM_ECAPACITY)
+ *   p        : build parameters (NULL = defaults); debug fields ignored
+ *   d_out    : 129 float64, device, caller-owned: 8 node records laid out as
+ *              in hgmm_tree_export (hard count = -1, no hand-off is run),
+ *              then a status word (0, or HGMM_ENONFINITE for NaN/Inf input)
+ * Allocates nothing: its scratch is one static device array (~2.8 MB) that
+ * every GPU loading this library holds until exit.  The first call on a
+ * device resolves that array's address, so make it before any stream
+ * capture.  All calls in the process share the array, so calls that overlap
+ * on the GPU (other streams, other threads) race; serialise them.
+ * Asynchronous on `stream`.  Errors: HGMM_EINVAL, HGMM_ECAPACITY, HGMM_ECUDA. */
+int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const hgmm_params* p,
+                            void* stream, double* d_out);
+
 /* Total node count of a tree of `depth` levels (8 + 64 + ... + 8^depth). */
 int64_t hgmm_node_count(int32_t depth);
 

@@ -67,6 +67,7 @@ def _load():
         "hgmm_profile": (ctypes.c_int, [vp, i32]),
         "hgmm_debug_barrier_timeout": (ctypes.c_int, [vp, i64, vp]),
         "hgmm_trace": (ctypes.c_int, [vp, i32]),
+        "hgmm_fit_level0_noalloc": (ctypes.c_int, [vp, i64, P(hgmm_params), vp, vp]),
         "hgmm_trace_read": (ctypes.c_int, [vp, vp, i64, P(i32), P(i32)]),
         "hgmm_profile_read": (ctypes.c_int, [vp, i32, P(ctypes.c_char_p), P(ctypes.c_double),
                                              P(ctypes.c_int64)]),
@@ -223,6 +224,21 @@ HGMM_PROF_KERNELS = 16
 def hgmm_debug_barrier_timeout(h, spin_limit: int, stream=None) -> None:
     _check(_lib.hgmm_debug_barrier_timeout(h, int(spin_limit), _stream_ptr(stream)),
            "hgmm_debug_barrier_timeout")
+
+
+def hgmm_fit_level0_noalloc(points, prm: hgmm_params | None = None, stream=None, out=None):
+    """Allocation-free level-0 GMM fit; `out` is a caller-owned (129,) float64
+    CUDA tensor (8 node records of 16 + a status word), returned."""
+    import torch
+    if out is None:
+        raise ValueError("out: a (129,) float64 CUDA tensor owned by the caller is required")
+    if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous() or out.numel() < 129:
+        raise ValueError("out: expected a contiguous float64 CUDA tensor of 129 elements")
+    _check(_lib.hgmm_fit_level0_noalloc(_dev_points(points, "points"), points.shape[0],
+                                        None if prm is None else ctypes.byref(prm),
+                                        _stream_ptr(stream), ctypes.c_void_p(out.data_ptr())),
+           "hgmm_fit_level0_noalloc")
+    return out
 
 
 def hgmm_trace(h, enable: bool) -> None:

@@ -18,7 +18,9 @@
 //   k_child_offsets   per parent: child segment starts and per-item offsets
 //   k_scatter         stable 8-way partition of every parent's segment
 //   k_finalize        FP64 eigen, complexity, precision matrix of level l
+#include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "hgmm_internal.cuh"
 #include "hgmm_math.cuh"
@@ -943,5 +945,158 @@ int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s)
                                                  t->seg_count, d_out);
     }
     HGMM_LAUNCH_CHECK();
+    return HGMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the level-0 fit.
+//
+// Some callers cannot call cudaMalloc at all: code running while another
+// component is capturing a CUDA graph on the same stream, real-time loops
+// whose memory budget is fixed at start-up, or plug-ins whose host owns every
+// device allocation.  For them, hgmm_fit_level0_noalloc runs the same level-0
+// pipeline as hgmm_build (root statistics, PCA-octant initial children, K EM
+// iterations of the 8-component GMM, FP64 finalize) with all of its scratch in
+// the fixed array below instead of a tree's buffers.  The array lives in every
+// GPU that loads this library until the process exits.
+// ---------------------------------------------------------------------------
+namespace hgmm {
+namespace {
+
+constexpr int NA_MAX_POINTS = 1 << 20;              // largest cloud the scratch holds
+constexpr int NA_MAX_ITEMS = NA_MAX_POINTS / TILE + 1;
+constexpr int NA_MAX_GRID = 1024;                   // E-step / root CTAs
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t NA_OFF_EST = 0;
+constexpr size_t NA_OFF_STAT = na_align(NA_OFF_EST + 8 * sizeof(NodeEst));
+constexpr size_t NA_OFF_RNODE = na_align(NA_OFF_STAT + 8 * sizeof(NodeStat));
+constexpr size_t NA_OFF_ROOT = na_align(NA_OFF_RNODE + 24 * sizeof(float4));
+constexpr size_t NA_OFF_RPART = na_align(NA_OFF_ROOT + sizeof(RootDev));
+constexpr size_t NA_OFF_WORDS = na_align(NA_OFF_RPART + size_t(NA_MAX_GRID) * 32 * sizeof(float));
+constexpr size_t NA_OFF_ITEMS = na_align(NA_OFF_WORDS + 16 * sizeof(int));
+constexpr size_t NA_OFF_PART = na_align(NA_OFF_ITEMS + size_t(NA_MAX_ITEMS) * sizeof(Item));
+constexpr size_t NA_BYTES = na_align(NA_OFF_PART + size_t(NA_MAX_ITEMS) * NPART * sizeof(float2));
+
+// ~2.8 MB of device memory shared by every call in the process.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+__global__ void k_noalloc_out(const NodeStat* __restrict__ stat, const int* __restrict__ status,
+                              double* __restrict__ out) {
+    const int c = threadIdx.x;
+    if (c < 8) {
+        const NodeStat& s = stat[c];
+        double* o = out + 16 * c;
+        o[0] = s.live ? s.pi : 0.0;
+        for (int a = 0; a < 3; ++a) o[1 + a] = s.mu[a];
+        for (int v = 0; v < 6; ++v) o[4 + v] = s.S[v];
+        o[10] = s.live ? 1.0 : 0.0;
+        o[11] = -1.0;  // hard counts need the hand-off, which this fit does not run
+        o[12] = s.complexity;
+        for (int a = 0; a < 3; ++a) o[13 + a] = s.lam[a];
+    }
+    if (c == 8) {
+        const int st = *status;
+        out[128] = (st & ST_NONFINITE) ? double(HGMM_ENONFINITE) : 0.0;
+    }
+}
+
+struct NoAllocDevice {
+    unsigned char* base = nullptr;  // device address of g_noalloc_scratch
+    int grid = 0;
+};
+
+}  // namespace
+}  // namespace hgmm
+
+extern "C" int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const hgmm_params* p,
+                                       void* stream, double* d_out) {
+    using namespace hgmm;
+    if (!d_points || !d_out || n < 8) return HGMM_EINVAL;
+    if (n > NA_MAX_POINTS) {
+        fprintf(stderr,
+                "hgmm_fit_level0_noalloc: %lld points exceed the fixed scratch capacity of %d\n",
+                (long long)n, NA_MAX_POINTS);
+        return HGMM_ECAPACITY;
+    }
+    if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0) return HGMM_EINVAL;
+    hgmm_params prm;
+    if (p) {
+        prm = *p;
+        if (prm.em_iters < 0 || prm.em_iters > 1000 || !(prm.eps_rel >= 0.f) ||
+            !(prm.n_min >= 0.f) || !(prm.lam_c >= 0.f))
+            return HGMM_EINVAL;
+    } else {
+        hgmm_params_default(&prm);
+    }
+    // one-time set-up per device, with that device current: resolve the
+    // scratch array's device address (host code cannot use the symbol itself)
+    constexpr int MAX_DEV = 64;
+    static NoAllocDevice devs[MAX_DEV];
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return HGMM_ECUDA;
+    NoAllocDevice d;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!devs[dev].base) {
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+                fprintf(stderr, "hgmm_fit_level0_noalloc: cudaGetSymbolAddress failed\n");
+                return HGMM_ECUDA;
+            }
+            int n_sm = 0;
+            if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return HGMM_ECUDA;
+            devs[dev].grid = std::min(2 * n_sm, NA_MAX_GRID);
+            devs[dev].base = static_cast<unsigned char*>(ptr);
+        }
+        d = devs[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* b = d.base;
+    NodeEst* est = reinterpret_cast<NodeEst*>(b + NA_OFF_EST);
+    NodeStat* stat = reinterpret_cast<NodeStat*>(b + NA_OFF_STAT);
+    float4* rnode = reinterpret_cast<float4*>(b + NA_OFF_RNODE);
+    RootDev* root = reinterpret_cast<RootDev*>(b + NA_OFF_ROOT);
+    float* rpart = reinterpret_cast<float*>(b + NA_OFF_RPART);
+    int* words = reinterpret_cast<int*>(b + NA_OFF_WORDS);
+    unsigned* root_counter = reinterpret_cast<unsigned*>(words + 0);
+    int* status = words + 1;
+    int* item_range = words + 2;  // [2]
+    int* meta = words + 4;        // [2]
+    int* seg = words + 6;         // [2] (unused at level 0)
+    Item* items = reinterpret_cast<Item*>(b + NA_OFF_ITEMS);
+    float2* partials = reinterpret_cast<float2*>(b + NA_OFF_PART);
+    const int G = d.grid;
+    const int ni = int(n);
+    // the array keeps the previous call's contents: clear the words that
+    // must start at zero (counter, status)
+    if (cudaMemsetAsync(words, 0, 16 * sizeof(int), s) != cudaSuccess) return HGMM_ECUDA;
+    k_root<<<G, 256, 0, s>>>(reinterpret_cast<const float4*>(d_points), ni, prm.eps_rel, rpart,
+                             root_counter, root, status);
+    k_init_children<<<1, 32, 0, s>>>(0, root, stat, est, seg, status);
+    k_make_items<<<1, 1024, 0, s>>>(0, ni, 1, seg, seg, stat, items, item_range, meta, G);
+    k_fill_items<<<(NA_MAX_ITEMS + 255) / 256, 256, 0, s>>>(0, ni, 1, seg, seg, item_range, meta,
+                                                            items);
+    for (int k = 0; k < prm.em_iters; ++k) {
+        if (prm.precision == 0) {
+            k_estep<true><<<G, EST_THREADS, 0, s>>>(reinterpret_cast<const float4*>(d_points), items,
+                                                    meta, est, partials);
+            k_mstep<true><<<1, 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
+                                            prm.n_min, stat, est, status);
+        } else {
+            k_estep<false><<<G, EST_THREADS, 0, s>>>(reinterpret_cast<const float4*>(d_points), items,
+                                                     meta, est, partials);
+            k_mstep<false><<<1, 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
+                                             prm.n_min, stat, est, status);
+        }
+    }
+    k_finalize<<<1, 32, 0, s>>>(0, prm.lam_c, root, stat, est, rnode);
+    k_noalloc_out<<<1, 32, 0, s>>>(stat, status, d_out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "hgmm_fit_level0_noalloc: launch failed: %s\n", cudaGetErrorString(e));
+        return HGMM_ECUDA;
+    }
     return HGMM_OK;
 }
