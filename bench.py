@@ -18,6 +18,8 @@ e2e     = the same metric through hgmm_register_pair_host with pinned host
 roofline: the kernel with the largest share of device time, its average
           CUDA-event duration (library event profiler, same stream) against
           its algorithmic work per launch
+batched: 256 independent pairs (2k-200k points, depth 3/4) in one persistent
+          cluster launch, pairs/s against the plain path looped over a subset
 cpu_baseline / --impl reference: the FP64 numpy oracle on a bounded sample
           of the same workload (1/8 of each cloud, depth 3 so the points per
           leaf match, 30 rounds), single-threaded, on this machine's host.
@@ -336,6 +338,10 @@ def gpu_main(args, rank, world, local_rank):
         hbm_equiv = KERNEL_WORK[dom]["bytes"] * units / (dom_ms / 1e3) / 1e9
     roof["hbm_gbs_equivalent"] = hbm_equiv
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_section(args, B, synth, torch, prm)
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         res = run_oracle(ORACLE_REPS, seed=args.seed)
@@ -363,6 +369,7 @@ def gpu_main(args, rank, world, local_rank):
         "launches_per_step": int(launches_per_step),
         "roofline": roof,
         "kernels": kernels,
+        "batched": batched,
         "cpu_baseline": cpu,
         "clocks": clk,
         "accuracy": {"rot_err_deg_vs_truth": rot_err,
@@ -373,6 +380,96 @@ def gpu_main(args, rank, world, local_rank):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def batched_section(args, B, synth, torch, prm):
+    """Batched form on 256 plane/box/sphere pairs (2k-200k points, depth 3
+    or 4, rotations <= 30 deg): pairs/s of the single persistent cluster
+    launch against looping the plain single-pair path over a subset."""
+    pairs = synth.batched_pairs(args.seed + 100, count=args.batch_pairs)
+    tb = [synth.to_float4(p["tgt"]) for p in pairs]
+    sb = [synth.to_float4(p["src"]) for p in pairs]
+    t_off = np.concatenate([[0], np.cumsum([x.shape[0] for x in tb])]).astype(np.int64)
+    s_off = (np.concatenate([[0], np.cumsum([x.shape[0] for x in sb])]) + t_off[-1]).astype(np.int64)
+    depths = [p["depth"] for p in pairs]
+    n = len(pairs)
+    pts = torch.from_numpy(np.concatenate(tb + sb)).cuda()
+    maxn = int(max(np.diff(t_off).max(), np.diff(s_off).max()))
+    bat = B.Batch(maxn, 4, n)
+    B.hgmm_batch_plan(bat.handle, t_off, s_off, depths)
+    s = torch.cuda.Stream()
+    T = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
+    st = torch.zeros(n, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(s):
+        tune_ms = B.hgmm_batch_autotune(bat.handle, pts, T, prm, None, ITERS, stream=s)
+    shape, clusters = B.hgmm_batch_get_shape(bat.handle)
+
+    def run():
+        B.hgmm_batch_register(bat.handle, pts, T, prm, None, ITERS, stream=s, pair_status=st)
+
+    graph = torch.cuda.CUDAGraph()
+    note = "captured"
+    try:
+        with torch.cuda.graph(graph, stream=s):
+            run()
+    except Exception as e:
+        graph, note = None, f"capture failed ({type(e).__name__}), eager"
+        torch.cuda.synchronize()
+    for _ in range(2):
+        with torch.cuda.stream(s):
+            graph.replay() if graph is not None else run()
+    torch.cuda.synchronize()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
+    for k in range(args.batch_steps):
+        e0[k].record(s)
+        with torch.cuda.stream(s):
+            graph.replay() if graph is not None else run()
+        e1[k].record(s)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
+    Tb = T.cpu().numpy().reshape(n, 4, 4)
+    status = st.cpu().numpy()
+
+    def rot_err(Ta, Tb_):
+        c = (np.trace(Ta[:3, :3].T @ Tb_[:3, :3]) - 1.0) / 2.0
+        return float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
+
+    ok_b = [rot_err(Tb[i], p["T_gt"]) <= 0.1 for i, p in enumerate(pairs)]
+    # the plain path, one pair after another on one stream, over a subset
+    sub = list(range(0, n, max(1, n // args.plain_pairs)))[: args.plain_pairs]
+    tree = B.Tree(maxn, 4)
+    outs = [torch.zeros((4, 4), dtype=torch.float64, device="cuda") for _ in sub]
+
+    def plain():
+        for j, i in enumerate(sub):
+            tree.build(pts[t_off[i]:t_off[i + 1]], depths[i], prm, stream=s)
+            tree.register(pts[s_off[i]:s_off[i + 1]], None, ITERS, stream=s, T_out=outs[j])
+
+    with torch.cuda.stream(s):
+        plain()
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(s)
+    with torch.cuda.stream(s):
+        plain()
+    a1.record(s)
+    torch.cuda.synchronize()
+    plain_ms = a0.elapsed_time(a1)
+    agree = [rot_err(outs[j].cpu().numpy(), Tb[i]) for j, i in enumerate(sub)]
+    ok_p = [rot_err(outs[j].cpu().numpy(), pairs[i]["T_gt"]) <= 0.1 for j, i in enumerate(sub)]
+    return {
+        "pairs": n, "points_per_side": int(t_off[-1]), "pairs_per_s": n / (ms / 1e3),
+        "ms_per_batch": ms, "cluster_ctas": shape, "clusters": clusters,
+        "autotune_ms_by_cluster_ctas_1_2_4_8": tune_ms, "graph": note,
+        "plain_pairs_per_s": len(sub) / (plain_ms / 1e3), "plain_subset": len(sub),
+        "speedup_vs_plain": (n / (ms / 1e3)) / (len(sub) / (plain_ms / 1e3)),
+        "success_rate_le_0p1deg": float(np.mean(ok_b)),
+        "plain_success_rate_le_0p1deg_subset": float(np.mean(ok_p)),
+        "max_rot_diff_batch_vs_plain_deg": float(np.max(agree)),
+        "pair_status_nonzero": int(np.sum(status != 0)),
+    }
 
 
 def _descend_levels(B, tree, src4, depth):
@@ -396,6 +493,10 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--plain-pairs", type=int, default=32)
     ap.add_argument("--ncu", action="store_true",
                     help="only run warm-up + eager steps (for an ncu launch list)")
     args = ap.parse_args()

@@ -206,6 +206,53 @@ int hgmm_trace_read(hgmm_tree* t, int64_t* h_events, int64_t cap, int32_t* iters
 int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const hgmm_params* p,
                             void* stream, double* d_out);
 
+/* ---- batched form: many independent pairs in one persistent launch ----
+ * Every pair (target cloud Z1, source cloud Z2, depth) is built and
+ * registered exactly as hgmm_build + hgmm_register do (Sec. 3-4), but all
+ * pairs run in one launch: each thread-block cluster takes the next pair
+ * from a device queue (largest pairs first) and runs every phase with
+ * hardware cluster barriers between them, in its own workspace.  The
+ * E-step sums are grouped by how many CTAs share a level, so results match
+ * the single-pair path up to FP32 summation order. */
+typedef struct hgmm_batch hgmm_batch;
+
+/* Workspaces for clouds of up to max_points points, trees of up to
+ * max_depth levels (1..4) and up to max_pairs pairs; one workspace per
+ * cluster that can be resident.  Errors: HGMM_EINVAL, HGMM_ENOMEM, HGMM_ECUDA. */
+int hgmm_batch_create(int64_t max_points, int32_t max_depth, int32_t max_pairs,
+                      hgmm_batch** out);
+void hgmm_batch_destroy(hgmm_batch* b);
+
+/* Describe the pairs (host arrays): target of pair i = points
+ * [h_tgt_off[i], h_tgt_off[i+1]) of the concatenated cloud buffer, source
+ * likewise, tree depth h_depth[i].  Computes the longest-first schedule and
+ * uploads it (synchronous).  Errors: HGMM_EINVAL (n_tgt < 8, n_src < 1, bad
+ * depth), HGMM_ECAPACITY, HGMM_ECUDA. */
+int hgmm_batch_plan(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_off,
+                    const int64_t* h_src_off, const int32_t* h_depth);
+
+/* Cluster shape: CTAs (of 256 threads) per pair, 1, 2, 4 or 8 (default 2). */
+int hgmm_batch_set_shape(hgmm_batch* b, int32_t cluster_ctas);
+int hgmm_batch_get_shape(const hgmm_batch* b, int32_t* cluster_ctas, int32_t* clusters);
+
+/* Autotuner: runs the planned batch (arguments as hgmm_batch_register) once
+ * untimed and once timed with CUDA events for every cluster shape, keeps
+ * the fastest and writes the four times (ms; -1 if a shape cannot be
+ * resident) to h_ms4.  Synchronous. */
+int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params* p,
+                        const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
+                        float* h_ms4);
+
+/* Run the planned batch: d_points = all clouds (float4, device), p = build
+ * parameters (NULL = defaults), d_T_init = n_pairs x 16 float64 initial
+ * transforms (device; NULL = identity), iters registration rounds.  Writes
+ * d_T_out (n_pairs x 16 float64, device) and, if not NULL, d_pair_status
+ * (n_pairs int32: 0, HGMM_ENONFINITE or HGMM_EDEGENERATE).  One launch on
+ * `stream`, graph-capturable.  Errors: HGMM_EINVAL, HGMM_ECUDA. */
+int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params* p,
+                        const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
+                        int32_t* d_pair_status);
+
 /* Total node count of a tree of `depth` levels (8 + 64 + ... + 8^depth). */
 int64_t hgmm_node_count(int32_t depth);
 

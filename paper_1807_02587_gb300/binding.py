@@ -68,6 +68,13 @@ def _load():
         "hgmm_debug_barrier_timeout": (ctypes.c_int, [vp, i64, vp]),
         "hgmm_trace": (ctypes.c_int, [vp, i32]),
         "hgmm_fit_level0_noalloc": (ctypes.c_int, [vp, i64, P(hgmm_params), vp, vp]),
+        "hgmm_batch_create": (ctypes.c_int, [i64, i32, i32, P(vp)]),
+        "hgmm_batch_destroy": (None, [vp]),
+        "hgmm_batch_plan": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+        "hgmm_batch_set_shape": (ctypes.c_int, [vp, i32]),
+        "hgmm_batch_get_shape": (ctypes.c_int, [vp, P(i32), P(i32)]),
+        "hgmm_batch_register": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp]),
+        "hgmm_batch_autotune": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp]),
         "hgmm_trace_read": (ctypes.c_int, [vp, vp, i64, P(i32), P(i32)]),
         "hgmm_profile_read": (ctypes.c_int, [vp, i32, P(ctypes.c_char_p), P(ctypes.c_double),
                                              P(ctypes.c_int64)]),
@@ -239,6 +246,74 @@ def hgmm_fit_level0_noalloc(points, prm: hgmm_params | None = None, stream=None,
                                         _stream_ptr(stream), ctypes.c_void_p(out.data_ptr())),
            "hgmm_fit_level0_noalloc")
     return out
+
+
+def hgmm_batch_create(max_points: int, max_depth: int, max_pairs: int):
+    h = ctypes.c_void_p()
+    _check(_lib.hgmm_batch_create(int(max_points), int(max_depth), int(max_pairs), ctypes.byref(h)),
+           "hgmm_batch_create")
+    return h
+
+
+def hgmm_batch_destroy(h) -> None:
+    _lib.hgmm_batch_destroy(h)
+
+
+def hgmm_batch_plan(h, tgt_off, src_off, depth) -> None:
+    t = np.ascontiguousarray(tgt_off, dtype=np.int64)
+    s_ = np.ascontiguousarray(src_off, dtype=np.int64)
+    d = np.ascontiguousarray(depth, dtype=np.int32)
+    _check(_lib.hgmm_batch_plan(h, d.shape[0], ctypes.c_void_p(t.ctypes.data),
+                                ctypes.c_void_p(s_.ctypes.data), ctypes.c_void_p(d.ctypes.data)),
+           "hgmm_batch_plan")
+
+
+def hgmm_batch_set_shape(h, cluster_ctas: int) -> None:
+    _check(_lib.hgmm_batch_set_shape(h, int(cluster_ctas)), "hgmm_batch_set_shape")
+
+
+def hgmm_batch_get_shape(h):
+    c = ctypes.c_int32()
+    n = ctypes.c_int32()
+    _check(_lib.hgmm_batch_get_shape(h, ctypes.byref(c), ctypes.byref(n)), "hgmm_batch_get_shape")
+    return c.value, n.value
+
+
+def hgmm_batch_register(h, points, T_out, prm: hgmm_params | None = None, T_init=None,
+                        iters: int = 30, stream=None, pair_status=None):
+    _check(_lib.hgmm_batch_register(h, _dev_points(points, "points"),
+                                    None if prm is None else ctypes.byref(prm), _dptr(T_init),
+                                    int(iters), _stream_ptr(stream), _dptr(T_out),
+                                    _dptr(pair_status)), "hgmm_batch_register")
+    return T_out
+
+
+def hgmm_batch_autotune(h, points, T_out, prm: hgmm_params | None = None, T_init=None,
+                        iters: int = 30, stream=None) -> list:
+    ms = (ctypes.c_float * 4)()
+    _check(_lib.hgmm_batch_autotune(h, _dev_points(points, "points"),
+                                    None if prm is None else ctypes.byref(prm), _dptr(T_init),
+                                    int(iters), _stream_ptr(stream), _dptr(T_out), ms),
+           "hgmm_batch_autotune")
+    return list(ms)
+
+
+class Batch:
+    """Owns one hgmm_batch: planned pairs over one concatenated point buffer."""
+
+    def __init__(self, max_points: int, max_depth: int, max_pairs: int):
+        self.handle = hgmm_batch_create(max_points, max_depth, max_pairs)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hgmm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hgmm_trace(h, enable: bool) -> None:

@@ -1,0 +1,532 @@
+// Batched form: many independent (target, source) pairs of uneven sizes in
+// one persistent launch.  Each thread-block cluster takes the next pair from
+// a device queue (pairs ordered largest first), builds the target's GMM tree
+// and registers the source, with hardware cluster barriers between phases
+// (no spin waits) and its own workspace in HBM; the pair index is broadcast
+// to the cluster's CTAs through distributed shared memory.  The phases are
+// the shared device functions of hgmm_dev.cuh, so every pair computes what
+// hgmm_build + hgmm_register compute (up to the summation order of the
+// E-step runs, which depends on how many CTAs share a level).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hgmm_dev.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hgmm {
+
+// Device pointers of one cluster's workspace.
+struct BatchWs {
+    NodeEst* est;
+    NodeStat* stat;
+    float4* rnode;
+    int* seg_start;
+    int* seg_count;
+    RootDev* root;
+    float4* pts[2];
+    uint32_t* codes;
+    int* item_range;
+    int* meta;
+    float2* partials;
+    int* item_cnt;
+    int* item_off;
+    float* root_part;
+    unsigned long long* acc;
+    float2* reg_part;
+    double* T;
+    float* Rt;
+    int* status;
+};
+
+struct BatchArgs {
+    const float4* points;       // all clouds, concatenated
+    const int64_t* tgt_off;     // [n_pairs + 1]
+    const int64_t* src_off;     // [n_pairs + 1]
+    const int* depth;           // [n_pairs]
+    const int* order;           // [n_pairs] pair to run k-th
+    const double* T_init;       // [n_pairs x 16] or null (identity)
+    double* T_out;              // [n_pairs x 16]
+    int* pair_status;           // [n_pairs] HGMM error code per pair
+    const BatchWs* ws;          // [clusters]
+    int* queue;                 // next pair to take
+    int n_pairs;
+    int em_iters;
+    float n_min;
+    float lam_c;
+    float eps_rel;
+    int iters;
+};
+
+namespace {
+
+static_assert(ACC_REPLICAS == 1, "the batched node terms read one accumulator copy per node");
+
+struct BuildSmem {
+    union {
+        float2 red[EST_THREADS / 32][NPART];
+        MstepSmem msm;
+        double wmom[EST_THREADS / 32][NPART];
+        AssignSmem as;
+        RootSmem rs;
+        int warp_tot[33];
+    };
+};
+
+struct RegSmem {
+    float Rt[12];
+    float2 sm[EST_THREADS / 32][27];
+    double tot[27];
+    double Lsm[6][6];
+    float4 est[3 * STAGED_NODES];
+};
+
+// One pair, run by all CTAs of this cluster.
+template <bool COMP>
+__device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::cluster_group& cl,
+                         BuildSmem& bs, RegSmem& rgs) {
+    const int cs = int(cl.num_blocks());
+    const int rank = int(cl.block_rank());
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int gw = rank * wpb + warp, nwt = cs * wpb;
+    const float4* tgt = a.points + a.tgt_off[pair];
+    const int n_t = int(a.tgt_off[pair + 1] - a.tgt_off[pair]);
+    const float4* src = a.points + a.src_off[pair];
+    const int n_s = int(a.src_off[pair + 1] - a.src_off[pair]);
+    const int depth = a.depth[pair];
+    if (rank == 0 && threadIdx.x == 0) *w.status = 0;
+
+    // ---- root statistics
+    root_partial_cta(tgt, n_t, rank, cs, w.root_part + 32 * rank, bs.rs);
+    cl.sync();
+    if (rank == 0) root_final_cta(w.root_part, cs, tgt, n_t, a.eps_rel, w.root, w.status, bs.rs);
+    cl.sync();
+
+    // ---- levels
+    const float4* cur = tgt;
+    for (int l = 0; l < depth; ++l) {
+        const int n_par = l == 0 ? 1 : int(level_size(l - 1));
+        for (int p = gw; p < n_par; p += nwt)
+            if (lane < 8) init_child(l, p, lane, w.root, w.stat, w.est, w.seg_count, w.status);
+        if (rank == 0)
+            make_items_cta(l, n_t, n_par, w.seg_count, w.item_range, w.meta, cs, bs.warp_tot);
+        cl.sync();
+        const int n_items = __ldcg(w.meta);
+        const int C = __ldcg(w.meta + 1);
+        const ItemCalc items{l, n_t, n_par, w.item_range, w.seg_start, w.seg_count};
+        NodeEst* est_lvl = w.est + level_offset(l);
+        for (int k = 0; k < a.em_iters; ++k) {
+            estep_range<COMP>(cur, items, rank * C, min(rank * C + C, n_items), est_lvl, w.partials,
+                              bs.red);
+            cl.sync();
+            // parents with many runs: a whole CTA; the others: one warp each
+            for (int p = rank; p < n_par; p += cs) {
+                const int i0 = __ldcg(w.item_range + 2 * p), i1 = __ldcg(w.item_range + 2 * p + 1);
+                if (i0 < i1 && (i1 - 1) / C - i0 / C + 1 >= 8)
+                    mstep_parent<COMP>(l, n_t, p, i0, i1, C, w.partials, w.seg_count, w.root,
+                                       a.n_min, w.stat, w.est, w.status, bs.msm);
+            }
+            __syncthreads();
+            for (int p = gw; p < n_par; p += nwt) {
+                const int i0 = __ldcg(w.item_range + 2 * p), i1 = __ldcg(w.item_range + 2 * p + 1);
+                if (i0 < i1 && (i1 - 1) / C - i0 / C + 1 < 8)
+                    mstep_parent_warp<COMP>(l, n_t, p, i0, i1, C, w.partials, w.seg_count, w.root,
+                                            a.n_min, w.stat, w.est, w.status, bs.wmom[warp]);
+            }
+            cl.sync();
+        }
+        // hand-off: argmax, per-parent child offsets, stable partition
+        for (int it = rank; it < n_items; it += cs)
+            assign_item(cur, items(it), it, est_lvl, w.codes, w.item_cnt, bs.as);
+        cl.sync();
+        for (int p = gw; p < n_par; p += nwt) {
+            const int i0 = __ldcg(w.item_range + 2 * p), i1 = __ldcg(w.item_range + 2 * p + 1);
+            const int pstart = i0 < i1 ? items(i0).start
+                                       : (l == 0 ? 0 : __ldcg(w.seg_start + level_offset(l - 1) + p));
+            child_offsets_warp(l, p, i0, i1, pstart, w.item_cnt, w.item_off, w.seg_start,
+                               w.seg_count);
+        }
+        cl.sync();
+        float4* out = w.pts[l & 1];
+        for (int it = rank; it < n_items; it += cs)
+            scatter_item(cur, nullptr, items(it), it, w.codes, w.item_off, out, nullptr,
+                         threadIdx.x, blockDim.x);
+        const int64_t m = level_size(l);
+        for (int64_t i = int64_t(rank) * blockDim.x + threadIdx.x; i < m; i += int64_t(cs) * blockDim.x)
+            finalize_node(l, i, a.lam_c, w.root, w.stat, w.est, w.rnode);
+        cl.sync();
+        cur = out;
+    }
+
+    // ---- registration (Algorithm 1 + Eq. 9-16)
+    const int n_nodes = int(level_offset(depth));
+    for (int i = rank * blockDim.x + threadIdx.x; i < n_nodes; i += cs * blockDim.x) {
+        for (int k = 0; k < 4 * ACC_REPLICAS; ++k) w.acc[4 * ACC_REPLICAS * int64_t(i) + k] = 0ull;
+    }
+    if (rank == 0 && threadIdx.x < 16) {
+        const double v = a.T_init ? a.T_init[16 * pair + threadIdx.x] : ((threadIdx.x % 5 == 0) ? 1.0 : 0.0);
+        w.T[threadIdx.x] = v;
+        const int r = threadIdx.x >> 2, c = threadIdx.x & 3;
+        if (r < 3) w.Rt[c == 3 ? 9 + r : r * 3 + c] = float(v);
+    }
+    {
+        const int ns = n_nodes < STAGED_NODES ? n_nodes : STAGED_NODES;
+        const float4* gsrc = reinterpret_cast<const float4*>(w.est);
+        for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) rgs.est[i] = __ldcg(gsrc + i);
+    }
+    cl.sync();
+    const double ext = __ldcg(&w.root->extent) > 0.0 ? __ldcg(&w.root->extent) : 1.0;
+    const float qscale = float(FIX / ext);
+    for (int it = 0; it < a.iters; ++it) {
+        if (threadIdx.x < 12) rgs.Rt[threadIdx.x] = __ldcg(w.Rt + threadIdx.x);
+        __syncthreads();
+        descend_points(src, n_s, w.est, rgs.est, depth, rgs.Rt, qscale, w.acc, rank, cs);
+        cl.sync();
+        float v[27], c[27];
+#pragma unroll
+        for (int k = 0; k < 27; ++k) { v[k] = 0.f; c[k] = 0.f; }
+        for (int g = rank * blockDim.x + threadIdx.x; g < n_nodes; g += cs * blockDim.x) {
+            const long long a0 = (long long)__ldcg(w.acc + 4 * g + 0);
+            if (a0 == 0) continue;
+            const long long a1 = (long long)__ldcg(w.acc + 4 * g + 1);
+            const long long a2 = (long long)__ldcg(w.acc + 4 * g + 2);
+            const long long a3 = (long long)__ldcg(w.acc + 4 * g + 3);
+            w.acc[4 * g + 0] = 0ull;
+            w.acc[4 * g + 1] = 0ull;
+            w.acc[4 * g + 2] = 0ull;
+            w.acc[4 * g + 3] = 0ull;
+            if (a0 < 0) continue;
+            const float M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
+            const float inv = 1.0f / (qscale * M0);
+            float t27[27];
+            node_terms(w.rnode[3 * g], w.rnode[3 * g + 1], w.rnode[3 * g + 2], w.est[g].a, M0,
+                       float(a1) * inv, float(a2) * inv, float(a3) * inv, M0 / float(n_s), t27);
+#pragma unroll
+            for (int k = 0; k < 27; ++k) pair_add(v[k], c[k], t27[k], 0.f);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 27; ++k) {
+                const float s2 = __shfl_xor_sync(FULL, v[k], off);
+                const float c2 = __shfl_xor_sync(FULL, c[k], off);
+                pair_add(v[k], c[k], s2, c2);
+            }
+        if (lane == 0)
+            for (int k = 0; k < 27; ++k) rgs.sm[warp][k] = make_float2(v[k], c[k]);
+        __syncthreads();
+        if (threadIdx.x < 27) {
+            float S = 0.f, C = 0.f;
+            for (int w2 = 0; w2 < wpb; ++w2) pair_add(S, C, rgs.sm[w2][threadIdx.x].x, rgs.sm[w2][threadIdx.x].y);
+            w.reg_part[27 * rank + threadIdx.x] = make_float2(S, C);
+        }
+        cl.sync();
+        if (rank == 0) {
+            if (threadIdx.x < 27) {
+                float S = 0.f, C = 0.f;
+                for (int b = 0; b < cs; ++b) {
+                    const float2 x = __ldcg(&w.reg_part[27 * b + threadIdx.x]);
+                    pair_add(S, C, x.x, x.y);
+                }
+                rgs.tot[threadIdx.x] = double(S) + double(C);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const bool solved = warp_solve_update(rgs.tot, rgs.Lsm, w.T, w.Rt, nullptr, it);
+                if (!solved && lane == 0) atomicOr(w.status, ST_DEGENERATE);
+            }
+        }
+        cl.sync();
+    }
+    if (rank == 0 && threadIdx.x < 16) {
+        a.T_out[16 * pair + threadIdx.x] = __ldcg(w.T + threadIdx.x);
+        if (threadIdx.x == 0) {
+            const int st = __ldcg(w.status);
+            a.pair_status[pair] = (st & ST_NONFINITE) ? HGMM_ENONFINITE
+                                  : (st & ST_DEGENERATE) ? HGMM_EDEGENERATE : HGMM_OK;
+        }
+    }
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(EST_THREADS, 2) k_batch(BatchArgs a) {
+    __shared__ BuildSmem bs;
+    __shared__ RegSmem rgs;
+    __shared__ int next_pair;
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = int(cl.num_blocks());
+    const int cid = blockIdx.x / cs;
+    const BatchWs w = a.ws[cid];
+    for (;;) {
+        if (cl.block_rank() == 0 && threadIdx.x == 0) next_pair = atomicAdd(a.queue, 1);
+        cl.sync();
+        // the pair index from the cluster's first CTA (distributed shared memory)
+        const int k = *cl.map_shared_rank(&next_pair, 0);
+        cl.sync();
+        if (k >= a.n_pairs) break;
+        run_pair<COMP>(a, w, a.order[k], cl, bs, rgs);
+    }
+}
+
+}  // namespace
+
+}  // namespace hgmm
+
+using namespace hgmm;
+
+struct hgmm_batch {
+    int device = 0;
+    int n_sm = 0;
+    int64_t max_points = 0;
+    int max_depth = 0;
+    int max_pairs = 0;
+    int max_clusters = 0;      // workspaces allocated
+    int cluster_ctas = 2;      // current cluster shape
+    int n_pairs = 0;
+    std::vector<void*> allocs;
+    BatchWs* d_ws = nullptr;
+    int64_t* d_tgt_off = nullptr;
+    int64_t* d_src_off = nullptr;
+    int* d_depth = nullptr;
+    int* d_order = nullptr;
+    int* d_queue = nullptr;
+    int* d_pair_status = nullptr;
+    std::vector<int64_t> h_tgt_off, h_src_off;
+};
+
+namespace {
+
+template <typename T>
+bool balloc(hgmm_batch* b, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) return false;
+    b->allocs.push_back(*p);
+    return true;
+}
+
+int clusters_for(int cs, bool comp) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * 64);
+    cfg.blockDim = dim3(EST_THREADS);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = cs;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t e = comp ? cudaOccupancyMaxActiveClusters(&n, (void*)k_batch<true>, &cfg)
+                               : cudaOccupancyMaxActiveClusters(&n, (void*)k_batch<false>, &cfg);
+    return e == cudaSuccess ? n : 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hgmm_batch_create(int64_t max_points, int32_t max_depth, int32_t max_pairs, hgmm_batch** out) {
+    if (!out) return HGMM_EINVAL;
+    *out = nullptr;
+    if (max_points < 8 || max_points > (int64_t(1) << 28) || max_depth < 1 || max_depth > 4 ||
+        max_pairs < 1 || max_pairs > (1 << 20))
+        return HGMM_EINVAL;
+    hgmm_batch* b = new hgmm_batch();
+    if (cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+        delete b;
+        return HGMM_ECUDA;
+    }
+    b->max_points = max_points;
+    b->max_depth = max_depth;
+    b->max_pairs = max_pairs;
+    // one workspace per cluster that can be resident at the smallest shape
+    int mc = 0;
+    for (int cs : {1, 2, 4, 8}) mc = std::max(mc, clusters_for(cs, true));
+    if (mc < 1) {
+        delete b;
+        return HGMM_ECUDA;
+    }
+    b->max_clusters = mc;
+    const int64_t nodes = level_offset(max_depth);
+    const int64_t parents = max_depth >= 2 ? level_size(max_depth - 2) : 1;
+    const int64_t items = (max_points + TILE - 1) / TILE + parents;
+    std::vector<BatchWs> ws(mc);
+    bool good = true;
+    for (int c = 0; c < mc && good; ++c) {
+        BatchWs& w = ws[c];
+        good &= balloc(b, &w.est, nodes) && balloc(b, &w.stat, nodes) && balloc(b, &w.rnode, 3 * nodes);
+        good &= balloc(b, &w.seg_start, nodes) && balloc(b, &w.seg_count, nodes);
+        good &= balloc(b, &w.root, 1) && balloc(b, &w.pts[0], max_points) && balloc(b, &w.pts[1], max_points);
+        good &= balloc(b, &w.codes, max_points) && balloc(b, &w.item_range, 2 * parents);
+        good &= balloc(b, &w.meta, 4) && balloc(b, &w.partials, items * NPART);
+        good &= balloc(b, &w.item_cnt, items * 8) && balloc(b, &w.item_off, items * 8);
+        good &= balloc(b, &w.root_part, 32 * 16) && balloc(b, &w.acc, 4 * ACC_REPLICAS * nodes);
+        good &= balloc(b, &w.reg_part, 27 * 16) && balloc(b, &w.T, 16) && balloc(b, &w.Rt, 12);
+        good &= balloc(b, &w.status, 1);
+        if (good) good &= cudaMemset(w.seg_count, 0, nodes * sizeof(int)) == cudaSuccess &&
+                          cudaMemset(w.stat, 0, nodes * sizeof(NodeStat)) == cudaSuccess;
+    }
+    good = good && balloc(b, &b->d_ws, mc) && balloc(b, &b->d_tgt_off, max_pairs + 1) &&
+           balloc(b, &b->d_src_off, max_pairs + 1) && balloc(b, &b->d_depth, max_pairs) &&
+           balloc(b, &b->d_order, max_pairs) && balloc(b, &b->d_queue, 1) &&
+           balloc(b, &b->d_pair_status, max_pairs);
+    if (good)
+        good = cudaMemcpy(b->d_ws, ws.data(), mc * sizeof(BatchWs), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!good) {
+        hgmm_batch_destroy(b);
+        return HGMM_ENOMEM;
+    }
+    *out = b;
+    return HGMM_OK;
+}
+
+void hgmm_batch_destroy(hgmm_batch* b) {
+    if (!b) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(b->device);
+    for (void* p : b->allocs) cudaFree(p);
+    cudaSetDevice(cur);
+    delete b;
+}
+
+int hgmm_batch_plan(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_off,
+                    const int64_t* h_src_off, const int32_t* h_depth) {
+    if (!b || !h_tgt_off || !h_src_off || !h_depth || n_pairs < 1 || n_pairs > b->max_pairs)
+        return HGMM_EINVAL;
+    std::vector<int> order(n_pairs);
+    for (int i = 0; i < n_pairs; ++i) {
+        const int64_t nt = h_tgt_off[i + 1] - h_tgt_off[i];
+        const int64_t ns = h_src_off[i + 1] - h_src_off[i];
+        if (nt < 8 || ns < 1 || h_depth[i] < 1 || h_depth[i] > b->max_depth) return HGMM_EINVAL;
+        if (nt > b->max_points || ns > b->max_points) return HGMM_ECAPACITY;
+        if (h_tgt_off[i] < 0 || h_src_off[i] < 0) return HGMM_EINVAL;
+        order[i] = i;
+    }
+    // longest pairs first (LPT): the queue hands the biggest work out early
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const int64_t wx = (h_tgt_off[x + 1] - h_tgt_off[x]) + (h_src_off[x + 1] - h_src_off[x]);
+        const int64_t wy = (h_tgt_off[y + 1] - h_tgt_off[y]) + (h_src_off[y + 1] - h_src_off[y]);
+        return wx > wy;
+    });
+    bool good = cudaMemcpy(b->d_tgt_off, h_tgt_off, (n_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess;
+    good &= cudaMemcpy(b->d_src_off, h_src_off, (n_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess;
+    good &= cudaMemcpy(b->d_depth, h_depth, n_pairs * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    good &= cudaMemcpy(b->d_order, order.data(), n_pairs * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!good) return HGMM_ECUDA;
+    b->n_pairs = n_pairs;
+    return HGMM_OK;
+}
+
+int hgmm_batch_set_shape(hgmm_batch* b, int32_t cluster_ctas) {
+    if (!b || (cluster_ctas != 1 && cluster_ctas != 2 && cluster_ctas != 4 && cluster_ctas != 8))
+        return HGMM_EINVAL;
+    b->cluster_ctas = cluster_ctas;
+    return HGMM_OK;
+}
+
+int hgmm_batch_get_shape(const hgmm_batch* b, int32_t* cluster_ctas, int32_t* clusters) {
+    if (!b) return HGMM_EINVAL;
+    if (cluster_ctas) *cluster_ctas = b->cluster_ctas;
+    if (clusters) *clusters = std::min(b->max_clusters, clusters_for(b->cluster_ctas, true));
+    return HGMM_OK;
+}
+
+int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params* p,
+                        const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
+                        int32_t* d_pair_status) {
+    if (!b || !d_points || !d_T_out || b->n_pairs < 1 || iters < 0) return HGMM_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0) return HGMM_EINVAL;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device) return HGMM_EINVAL;
+    hgmm_params prm;
+    if (p) prm = *p;
+    else hgmm_params_default(&prm);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int cs = b->cluster_ctas;
+    const bool comp = prm.precision == 0;
+    const int nclu = std::min(std::min(b->max_clusters, clusters_for(cs, comp)), b->n_pairs);
+    if (nclu < 1) return HGMM_ECUDA;
+    BatchArgs a;
+    a.points = reinterpret_cast<const float4*>(d_points);
+    a.tgt_off = b->d_tgt_off;
+    a.src_off = b->d_src_off;
+    a.depth = b->d_depth;
+    a.order = b->d_order;
+    a.T_init = d_T_init;
+    a.T_out = d_T_out;
+    a.pair_status = d_pair_status ? d_pair_status : b->d_pair_status;
+    a.ws = b->d_ws;
+    a.queue = b->d_queue;
+    a.n_pairs = b->n_pairs;
+    a.em_iters = prm.em_iters;
+    a.n_min = prm.n_min;
+    a.lam_c = prm.lam_c;
+    a.eps_rel = prm.eps_rel;
+    a.iters = iters;
+    if (cudaMemsetAsync(b->d_queue, 0, sizeof(int), s) != cudaSuccess) return HGMM_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nclu * cs);
+    cfg.blockDim = dim3(EST_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = cs;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = comp ? cudaLaunchKernelEx(&cfg, k_batch<true>, a)
+                               : cudaLaunchKernelEx(&cfg, k_batch<false>, a);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "hgmm_batch_register: launch failed: %s\n", cudaGetErrorString(e));
+        return HGMM_ECUDA;
+    }
+    return HGMM_OK;
+}
+
+int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params* p,
+                        const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
+                        float* h_ms4) {
+    if (!b || b->n_pairs < 1) return HGMM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int shapes[4] = {1, 2, 4, 8};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HGMM_ECUDA;
+    float best = 1e30f;
+    int best_cs = b->cluster_ctas;
+    int rc = HGMM_OK;
+    for (int k = 0; k < 4 && rc == HGMM_OK; ++k) {
+        b->cluster_ctas = shapes[k];
+        float ms = -1.f;
+        if (clusters_for(shapes[k], true) > 0) {
+            // one untimed run, then one timed run of the whole batch
+            rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr);
+            if (rc == HGMM_OK) {
+                cudaEventRecord(e0, s);
+                rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = HGMM_ECUDA;
+                else cudaEventElapsedTime(&ms, e0, e1);
+            }
+        }
+        if (h_ms4) h_ms4[k] = ms;
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            best_cs = shapes[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cluster_ctas = best_cs;
+    return rc;
+}
+
+}  // extern "C"

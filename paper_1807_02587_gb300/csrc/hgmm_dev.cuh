@@ -1,0 +1,1157 @@
+// Device-side building blocks of the HGMM path, shared by the single-cloud
+// kernels (one launch per phase, or one cooperative launch), the batched
+// engine (one thread-block cluster per pair) and the allocation-free fit.
+// Every phase takes the index and count of the CTAs that share it, so the
+// same arithmetic runs under any of those schedules.
+#pragma once
+
+#include "hgmm_internal.cuh"
+#include "hgmm_math.cuh"
+
+namespace hgmm {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr double FIX = 4294967296.0;      // 2^32
+constexpr double INV_FIX = 1.0 / 4294967296.0;
+constexpr float FIX_CLAMP = 1.0995116e12f;  // 2^40
+
+__device__ __forceinline__ int64_t d_level_offset(int l) {
+    return ((int64_t(1) << (3 * (l + 1))) - 8) / 7;
+}
+
+// ===================================================================== root
+// Whole-cloud mean, covariance and bounding box (the root of the tree, whose
+// children are Children(-1) of Algorithm 1).  Sums of (z - z0) and
+// (z - z0)(z - z0)^T with z0 = the first point, FP32 with compensated
+// accumulation.  A CTA partial is 25 floats: [0..17] 9 (sum, err) pairs,
+// [18..20] min, [21..23] max, [24] non-finite count.
+__device__ __forceinline__ void root_combine(float* f, const float* o) {
+#pragma unroll
+    for (int v = 0; v < 9; ++v) pair_add(f[2 * v], f[2 * v + 1], o[2 * v], o[2 * v + 1]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[18 + a] = fminf(f[18 + a], o[18 + a]);
+        f[21 + a] = fmaxf(f[21 + a], o[21 + a]);
+    }
+    f[24] = __int_as_float(__float_as_int(f[24]) + __float_as_int(o[24]));
+}
+
+__device__ __forceinline__ void root_identity(float* f) {
+#pragma unroll
+    for (int v = 0; v < 18; ++v) f[v] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { f[18 + a] = CUDART_INF_F; f[21 + a] = -CUDART_INF_F; }
+    f[24] = __int_as_float(0);
+}
+
+
+struct RootSmem {
+    float sm[8][25];
+    float gs[16][25];
+};
+
+// CTA `cta` of `ncta` sums its share of the points into out[0..24].
+__device__ __forceinline__ void root_partial_cta(const float4* __restrict__ pts, int n, int cta,
+                                                 int ncta, float* __restrict__ out, RootSmem& rs) {
+    const float4 z0 = pts[0];
+    float in[9] = {}, s[9] = {}, c[9] = {};
+    float mn[3] = {CUDART_INF_F, CUDART_INF_F, CUDART_INF_F};
+    float mx[3] = {-CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F};
+    int bad = 0, cnt = 0;
+    for (int i = cta * blockDim.x + threadIdx.x; i < n; i += ncta * blockDim.x) {
+        const float4 z = pts[i];
+        if (!(isfinite(z.x) && isfinite(z.y) && isfinite(z.z))) {
+            ++bad;
+            continue;
+        }
+        const float dx = z.x - z0.x, dy = z.y - z0.y, dz = z.z - z0.z;
+        in[0] += dx; in[1] += dy; in[2] += dz;
+        in[3] = fmaf(dx, dx, in[3]); in[4] = fmaf(dx, dy, in[4]); in[5] = fmaf(dx, dz, in[5]);
+        in[6] = fmaf(dy, dy, in[6]); in[7] = fmaf(dy, dz, in[7]); in[8] = fmaf(dz, dz, in[8]);
+        mn[0] = fminf(mn[0], z.x); mn[1] = fminf(mn[1], z.y); mn[2] = fminf(mn[2], z.z);
+        mx[0] = fmaxf(mx[0], z.x); mx[1] = fmaxf(mx[1], z.y); mx[2] = fmaxf(mx[2], z.z);
+        if (++cnt == 16) {
+#pragma unroll
+            for (int v = 0; v < 9; ++v) { pair_add(s[v], c[v], in[v], 0.f); in[v] = 0.f; }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 9; ++v) pair_add(s[v], c[v], in[v], 0.f);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) {
+            const float s2 = __shfl_xor_sync(FULL, s[v], off);
+            const float c2 = __shfl_xor_sync(FULL, c[v], off);
+            pair_add(s[v], c[v], s2, c2);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(FULL, mn[a], off));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(FULL, mx[a], off));
+        }
+        bad += __shfl_xor_sync(FULL, bad, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int v = 0; v < 9; ++v) { rs.sm[warp][2 * v] = s[v]; rs.sm[warp][2 * v + 1] = c[v]; }
+        for (int a = 0; a < 3; ++a) { rs.sm[warp][18 + a] = mn[a]; rs.sm[warp][21 + a] = mx[a]; }
+        rs.sm[warp][24] = __int_as_float(bad);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float f[25];
+        root_identity(f);
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) root_combine(f, rs.sm[w]);
+        for (int v = 0; v < 25; ++v) out[v] = f[v];
+    }
+    __syncthreads();
+}
+
+// One CTA (>= 256 threads) reduces the `nparts` partials (stride 32 floats)
+// in a fixed order -- 16 half-warp groups, then one thread -- and writes the
+// FP64 root record with its eigen-decomposition.
+__device__ __forceinline__ void root_final_cta(const float* __restrict__ part, int nparts,
+                                               const float4* __restrict__ pts, int n, float eps_rel,
+                                               RootDev* __restrict__ root, int* __restrict__ status,
+                                               RootSmem& rs) {
+    if (threadIdx.x < 256) {
+        const int grp = threadIdx.x >> 4, it = threadIdx.x & 15;
+        float a = 0.f, b = 0.f;
+        if (it >= 9 && it < 12) a = CUDART_INF_F;
+        if (it >= 12 && it < 15) a = -CUDART_INF_F;
+        int cntb = 0;
+#pragma unroll 4
+        for (int blk = grp; blk < nparts; blk += 16) {
+            const float* o = part + 32 * blk;
+            if (it < 9) pair_add(a, b, __ldcg(o + 2 * it), __ldcg(o + 2 * it + 1));
+            else if (it < 12) a = fminf(a, __ldcg(o + 18 + it - 9));
+            else if (it < 15) a = fmaxf(a, __ldcg(o + 21 + it - 12));
+            else cntb += __float_as_int(__ldcg(o + 24));
+        }
+        if (it < 9) { rs.gs[grp][2 * it] = a; rs.gs[grp][2 * it + 1] = b; }
+        else if (it < 12) rs.gs[grp][18 + it - 9] = a;
+        else if (it < 15) rs.gs[grp][21 + it - 12] = a;
+        else rs.gs[grp][24] = __int_as_float(cntb);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float F[25];
+        root_identity(F);
+        for (int w = 0; w < 16; ++w) root_combine(F, rs.gs[w]);
+        if (__float_as_int(F[24]) > 0) atomicOr(status, ST_NONFINITE);
+        const float4 z0 = pts[0];
+        const double nn = double(n);
+        double m1[3], m2[6];
+        for (int a = 0; a < 3; ++a) m1[a] = (double(F[2 * a]) + double(F[2 * a + 1])) / nn;
+        for (int v = 0; v < 6; ++v) m2[v] = (double(F[6 + 2 * v]) + double(F[7 + 2 * v])) / nn;
+        root->n = nn;
+        root->mu[0] = double(z0.x) + m1[0];
+        root->mu[1] = double(z0.y) + m1[1];
+        root->mu[2] = double(z0.z) + m1[2];
+        double S[6];
+        S[0] = m2[0] - m1[0] * m1[0];
+        S[1] = m2[1] - m1[0] * m1[1];
+        S[2] = m2[2] - m1[0] * m1[2];
+        S[3] = m2[3] - m1[1] * m1[1];
+        S[4] = m2[4] - m1[1] * m1[2];
+        S[5] = m2[5] - m1[2] * m1[2];
+        for (int v = 0; v < 6; ++v) root->S[v] = S[v];
+        double e2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double d = double(F[21 + a]) - double(F[18 + a]);
+            e2 += d * d;
+        }
+        root->extent = sqrt(e2);
+        const double e = double(eps_rel) * root->extent;
+        root->eps = e * e;
+        eig3(S, root->lam, root->V);
+    }
+    __syncthreads();
+}
+
+// ===================================================================== init
+// PCA-octant initial child c of parent p (level-0 parent = the root): mean
+// mu_p + 1/2 sum_a s_a sqrt(lambda_a) v_a (s_a = +1 iff bit a of c), covariance
+// Sigma_p / 4 + eps I, weight 1/8.  Children of a parent that is dead or
+// holds no points are dead.  The parent's eigen-decomposition was computed
+// when it was finalised.
+__device__ __forceinline__ void init_child(int level, int p, int c, const RootDev* __restrict__ root,
+                                           NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
+                                           const int* __restrict__ seg_count,
+                                           int* __restrict__ status) {
+    double lam[3], V[9], mu_p[3], S_p[6];
+    bool alive;
+    if (level == 0) {
+        for (int a = 0; a < 3; ++a) { mu_p[a] = root->mu[a]; lam[a] = root->lam[a]; }
+        for (int v = 0; v < 6; ++v) S_p[v] = root->S[v];
+        for (int v = 0; v < 9; ++v) V[v] = root->V[v];
+        alive = true;
+    } else {
+        const int64_t g = d_level_offset(level - 1) + p;
+        const NodeStat& ps = stat[g];
+        for (int a = 0; a < 3; ++a) { mu_p[a] = ps.mu[a]; lam[a] = ps.lam[a]; }
+        for (int v = 0; v < 6; ++v) S_p[v] = ps.S[v];
+        for (int v = 0; v < 9; ++v) V[v] = ps.V[v];
+        alive = ps.live && seg_count[g] > 0;
+    }
+    const int64_t gc = d_level_offset(level) + 8 * int64_t(p) + c;
+    NodeStat& cs = stat[gc];
+    NodeEst& ce = est[gc];
+    if (!alive) {
+        cs.live = 0;
+        cs.pi = 0.0;
+        for (int a = 0; a < 3; ++a) cs.mu[a] = mu_p[a];
+        for (int v = 0; v < 6; ++v) cs.S[v] = 0.0;
+        dead_est(mu_p, ce);
+        return;
+    }
+    const double eps = root->eps;
+    double mu[3];
+    for (int a = 0; a < 3; ++a) {
+        double acc = mu_p[a];
+        for (int b = 0; b < 3; ++b) {
+            const double sgn = ((c >> b) & 1) ? 1.0 : -1.0;
+            const double lb = fmax(lam[b], 0.0);
+            acc += sgn * 0.5 * (lb > 0.0 ? lb * rsqrt_f64(lb) : 0.0) * V[a * 3 + b];
+        }
+        mu[a] = acc;
+    }
+    double S[6];
+    for (int v = 0; v < 6; ++v) S[v] = S_p[v] * 0.25;
+    S[0] += eps; S[3] += eps; S[5] += eps;
+    cs.live = 1;
+    cs.pi = 0.125;
+    for (int a = 0; a < 3; ++a) cs.mu[a] = mu[a];
+    for (int v = 0; v < 6; ++v) cs.S[v] = S[v];
+    if (!pack_est(0.125, mu, S, eps, 0.f, ce)) atomicOr(status, ST_CHOL);
+}
+
+// ==================================================================== items
+// One CTA: exclusive scan over the level's parents of ceil(count / TILE);
+// item_range[2p..2p+1] = [begin, end) item indices of parent p, meta[0] =
+// item count, meta[1] = items per CTA for `nchunks` contiguous chunks.
+// Every parent segment that holds points gets items, live or not: points
+// under a leaf parent are carried down on its first child's segment with
+// zero posteriors.
+__device__ __forceinline__ void make_items_cta(int level, int n, int n_parents,
+                                               const int* __restrict__ seg_count,
+                                               int* __restrict__ item_range, int* __restrict__ meta,
+                                               int nchunks, int* warp_tot /* smem[33] */) {
+    int& carry = warp_tot[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int64_t poff = level == 0 ? 0 : d_level_offset(level - 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int base = 0; base < n_parents; base += blockDim.x) {
+        const int p = base + threadIdx.x;
+        int count = 0;
+        if (p < n_parents) count = level == 0 ? n : seg_count[poff + p];
+        const int k = (count + TILE - 1) / TILE;
+        int x = k;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(FULL, w, off);
+                if (lane >= off) w += y;
+            }
+            warp_tot[lane] = w;  // inclusive
+        }
+        __syncthreads();
+        const int excl = carry + (warp ? warp_tot[warp - 1] : 0) + x - k;
+        if (p < n_parents) {
+            item_range[2 * p] = excl;
+            item_range[2 * p + 1] = excl + k;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // items per CTA (contiguous chunks, so a parent's runs are few)
+        meta[0] = carry;
+        meta[1] = max(1, (carry + nchunks - 1) / nchunks);
+    }
+    __syncthreads();
+}
+
+// Item j of a level: its parent is the largest p with begin(p) <= j (an
+// empty parent shares its begin with the next one, which owns j).
+__device__ __forceinline__ Item item_at(int j, int level, int n, int n_parents,
+                                        const int* __restrict__ item_range,
+                                        const int* __restrict__ seg_start,
+                                        const int* __restrict__ seg_count) {
+    int lo = 0, hi = n_parents - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_range[2 * mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    const int p = lo;
+    const int r = j - item_range[2 * p];
+    int start = 0, count = n;
+    if (level > 0) {
+        const int64_t g = d_level_offset(level - 1) + p;
+        start = seg_start[g];
+        count = seg_count[g];
+    }
+    Item it;
+    it.parent = p;
+    it.start = start + r * TILE;
+    it.count = min(TILE, count - r * TILE);
+    it.pad = 0;
+    return it;
+}
+
+// Item sources for the phases below: a materialised list, or computed on
+// the fly from the per-parent ranges.
+struct ItemList {
+    const Item* items;
+    __device__ __forceinline__ Item operator()(int j) const { return items[j]; }
+};
+
+struct ItemCalc {
+    int level, n, n_parents;
+    const int* item_range;
+    const int* seg_start;
+    const int* seg_count;
+    __device__ __forceinline__ Item operator()(int j) const {
+        return item_at(j, level, n, n_parents, item_range, seg_start, seg_count);
+    }
+};
+
+// =================================================================== E-step
+// Lane layout: a quad of 4 lanes handles one point, lane k of the quad owns
+// children 2k and 2k+1 (their constants live in registers); a warp handles 8
+// points per step, the CTA (EST_THREADS) 64.  Each lane accumulates the 10
+// moments of its two children: plain FP32 over up to 16 points, then
+// folded into a compensated (sum, error) pair.
+struct ChildRegs {
+    float mx, my, mz, C, w00, w10, w11, w20, w21, w22;
+};
+
+__device__ __forceinline__ void load_child(const NodeEst* __restrict__ e, ChildRegs& r) {
+    const float4 a = e->a, b = e->b, c = e->c;
+    r.mx = a.x; r.my = a.y; r.mz = a.z; r.C = a.w;
+    r.w00 = b.x; r.w10 = b.y; r.w11 = b.z; r.w20 = b.w;
+    r.w21 = c.x; r.w22 = c.y;
+}
+
+// log2(pi N(z | child)) and the centred offset e = z - mu.
+__device__ __forceinline__ float child_score(const ChildRegs& r, float zx, float zy, float zz,
+                                             float& ex, float& ey, float& ez) {
+    ex = zx - r.mx;
+    ey = zy - r.my;
+    ez = zz - r.mz;
+    const float d0 = r.w00 * ex;
+    const float d1 = fmaf(r.w11, ey, r.w10 * ex);
+    const float d2 = fmaf(r.w22, ez, fmaf(r.w21, ey, r.w20 * ex));
+    float s = fmaf(-d0, d0, r.C);
+    s = fmaf(-d1, d1, s);
+    s = fmaf(-d2, d2, s);
+    return s;
+}
+
+__device__ __forceinline__ void accum10(float* a, float g, float ex, float ey, float ez) {
+    const float gx = g * ex, gy = g * ey, gz = g * ez;
+    a[0] += g;
+    a[1] += gx;
+    a[2] += gy;
+    a[3] += gz;
+    a[4] = fmaf(gx, ex, a[4]);
+    a[5] = fmaf(gx, ey, a[5]);
+    a[6] = fmaf(gx, ez, a[6]);
+    a[7] = fmaf(gy, ey, a[7]);
+    a[8] = fmaf(gy, ez, a[8]);
+    a[9] = fmaf(gz, ez, a[9]);
+}
+
+template <bool COMP>
+__device__ __forceinline__ void fold20(float* in, float* s, float* c) {
+#pragma unroll
+    for (int v = 0; v < 20; ++v) {
+        if (COMP) {
+            float t, e;
+            two_sum(s[v], in[v], t, e);
+            s[v] = t;
+            c[v] += e;
+        } else {
+            s[v] += in[v];
+        }
+        in[v] = 0.f;
+    }
+}
+
+// Block-wide reduction of the (s, c) accumulators into partial slot `run`.
+template <bool COMP>
+__device__ __forceinline__ void flush_run(float* s, float* c, float2 (*red)[NPART],
+                                          float2* __restrict__ out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, k = lane & 3;
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+#pragma unroll
+        for (int v = 0; v < 20; ++v) {
+            const float s2 = __shfl_xor_sync(FULL, s[v], off);
+            const float c2 = __shfl_xor_sync(FULL, c[v], off);
+            if (COMP) pair_add(s[v], c[v], s2, c2);
+            else s[v] += s2;
+        }
+    }
+    if (lane < 4) {
+#pragma unroll
+        for (int v = 0; v < 20; ++v) red[warp][k * 20 + v] = make_float2(s[v], COMP ? c[v] : 0.f);
+    }
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        float S = 0.f, Cc = 0.f;
+        for (int w = 0; w < EST_THREADS / 32; ++w) {
+            const float2 x = red[w][threadIdx.x];
+            if (COMP) pair_add(S, Cc, x.x, x.y);
+            else S += x.x;
+        }
+        out[threadIdx.x] = make_float2(S, Cc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 20; ++v) { s[v] = 0.f; c[v] = 0.f; }
+}
+
+
+// E-step of items [ib, ie) by one CTA: Eq. 3 posteriors of every point over
+// the 8 children of its parent (log2 domain, max subtracted), gamma-weighted
+// moments of each child centred on the child's current FP32 mean, one
+// partial per run of consecutive items with the same parent, stored at the
+// run's first item.
+template <bool COMP, class Items>
+__device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Items items, int ib,
+                                            int ie, const NodeEst* __restrict__ est_lvl,
+                                            float2* __restrict__ partials,
+                                            float2 (*red)[NPART]) {
+    if (ib >= ie) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 2, k = lane & 3;
+    float in[20], s[20], c[20];
+#pragma unroll
+    for (int v = 0; v < 20; ++v) { in[v] = 0.f; s[v] = 0.f; c[v] = 0.f; }
+    int nfold = 0;
+    int cur = -1, run = -1;
+    ChildRegs r0, r1;
+    for (int it = ib; it < ie; ++it) {
+        const Item w = items(it);
+        if (w.parent != cur) {
+            if (cur >= 0) {
+                fold20<COMP>(in, s, c);
+                nfold = 0;
+                flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+            }
+            cur = w.parent;
+            run = it;
+            load_child(est_lvl + 8 * cur + 2 * k, r0);
+            load_child(est_lvl + 8 * cur + 2 * k + 1, r1);
+        }
+        float4 znext = pts[w.start + min(warp * 8 + q, w.count - 1)];
+        for (int base = 0; base < w.count; base += 64) {
+            const int idx = base + warp * 8 + q;
+            const bool valid = idx < w.count;
+            const float4 z = znext;
+            if (base + 64 < w.count) znext = pts[w.start + min(idx + 64, w.count - 1)];
+            float e0x, e0y, e0z, e1x, e1y, e1z;
+            const float s0 = child_score(r0, z.x, z.y, z.z, e0x, e0y, e0z);
+            const float s1 = child_score(r1, z.x, z.y, z.z, e1x, e1y, e1z);
+            float m = fmaxf(s0, s1);
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
+            const bool any_live = m > -CUDART_INF_F;  // false for a leaf parent
+            const float p0 = any_live ? exp2f(s0 - m) : 0.f;
+            const float p1 = any_live ? exp2f(s1 - m) : 0.f;
+            float tot = p0 + p1;
+            tot += __shfl_xor_sync(FULL, tot, 1);
+            tot += __shfl_xor_sync(FULL, tot, 2);
+            const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
+            accum10(in, p0 * rinv, e0x, e0y, e0z);
+            accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
+            if (++nfold == 16) {
+                fold20<COMP>(in, s, c);
+                nfold = 0;
+            }
+        }
+    }
+    fold20<COMP>(in, s, c);
+    flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+}
+
+// =================================================================== M-step
+// M-step of child c of parent p from its 10 reduced moments m (FP64): S0,
+// mean shift d = S1/S0 from the FP32 mean the E-step used, Sigma = S2/S0 -
+// d d^T + eps I, pi = S0 / n_p; a child below n_min expected points dies (a
+// parent whose children all die stays a leaf); FP64 Cholesky -> new FP32
+// E-step constants.
+__device__ __forceinline__ void child_mstep(int level, int n, int p, int c, const double* m,
+                                            const int* __restrict__ seg_count,
+                                            const RootDev* __restrict__ root, float n_min,
+                                            NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
+                                            int* __restrict__ status) {
+    const int64_t g = d_level_offset(level) + 8 * int64_t(p) + c;
+    NodeStat& cs = stat[g];
+    NodeEst& ce = est[g];
+    const double S0 = m[0];
+    const double n_p = level == 0 ? double(n) : double(seg_count[d_level_offset(level - 1) + p]);
+    // a child below n_min expected points dies; if all eight die the parent
+    // stays a leaf (its points keep zero posteriors from then on)
+    const bool live = cs.live && S0 >= double(n_min) && S0 > 0.0;
+    if (!live) {
+        cs.live = 0;
+        cs.pi = 0.0;
+        ce.a.w = -CUDART_INF_F;
+        ce.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        ce.c.x = 0.f;
+        ce.c.y = 0.f;
+        return;
+    }
+    const double eps = root->eps;
+    const double inv = rcp_f64(S0);
+    const double d[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
+    const double mu[3] = {double(ce.a.x) + d[0], double(ce.a.y) + d[1], double(ce.a.z) + d[2]};
+    double S[6];
+    S[0] = m[4] * inv - d[0] * d[0] + eps;
+    S[1] = m[5] * inv - d[0] * d[1];
+    S[2] = m[6] * inv - d[0] * d[2];
+    S[3] = m[7] * inv - d[1] * d[1] + eps;
+    S[4] = m[8] * inv - d[1] * d[2];
+    S[5] = m[9] * inv - d[2] * d[2] + eps;
+    const double pi = S0 * rcp_f64(n_p);
+    cs.pi = pi;
+    for (int a = 0; a < 3; ++a) cs.mu[a] = mu[a];
+    for (int v = 0; v < 6; ++v) cs.S[v] = S[v];
+    if (!pack_est(pi, mu, S, eps, 0.f, ce)) atomicOr(status, ST_CHOL);
+}
+
+struct MstepSmem {
+    double mom[NPART];
+    float2 grp[8][NPART];
+};
+
+template <bool COMP>
+__device__ void mstep_parent(int level, int n, int p, int i0, int i1, int C,
+                             const float2* __restrict__ partials,
+                             const int* __restrict__ seg_count, const RootDev* __restrict__ root,
+                             float n_min, NodeStat* __restrict__ stat,
+                             NodeEst* __restrict__ est, int* __restrict__ status, MstepSmem& sm) {
+    const int nruns = (i1 - 1) / C - i0 / C + 1;
+    {
+        // warp w sums runs w, w+8, ...; lane l owns values l, l+32, l+64
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int nw = blockDim.x >> 5;
+        float S[3] = {0.f, 0.f, 0.f}, Cc[3] = {0.f, 0.f, 0.f};
+        for (int r0 = warp; r0 < nruns; r0 += 4 * nw) {
+            float2 x[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = r0 + u * nw;
+                const int slot = r == 0 ? i0 : (i0 / C + r) * C;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int v = lane + 32 * j;
+                    x[u][j] = (r < nruns && v < NPART)
+                                  ? __ldcg(&partials[int64_t(slot) * NPART + v])
+                                  : make_float2(0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (COMP) pair_add(S[j], Cc[j], x[u][j].x, x[u][j].y);
+                    else S[j] += x[u][j].x;
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int v = lane + 32 * j;
+            if (v < NPART) sm.grp[warp][v] = make_float2(S[j], Cc[j]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        float S = 0.f, Cc = 0.f;
+        for (int q = 0; q < int(blockDim.x >> 5); ++q) {
+            if (COMP) pair_add(S, Cc, sm.grp[q][threadIdx.x].x, sm.grp[q][threadIdx.x].y);
+            else S += sm.grp[q][threadIdx.x].x;
+        }
+        sm.mom[threadIdx.x] = double(S) + double(Cc);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8)
+        child_mstep(level, n, p, threadIdx.x, sm.mom + threadIdx.x * NMOM, seg_count, root, n_min, stat,
+                    est, status);
+    __syncthreads();
+}
+
+// The same M-step for a parent with few runs, by one warp (no block
+// barriers): lane l sums values l, l+32, l+64 over the runs in order; lanes
+// 0..7 then build the children.  mom = 80 doubles of shared memory per warp.
+template <bool COMP>
+__device__ void mstep_parent_warp(int level, int n, int p, int i0, int i1, int C,
+                                  const float2* __restrict__ partials,
+                                  const int* __restrict__ seg_count, const RootDev* __restrict__ root,
+                                  float n_min, NodeStat* __restrict__ stat,
+                                  NodeEst* __restrict__ est, int* __restrict__ status, double* mom) {
+    const int lane = threadIdx.x & 31;
+    const int nruns = (i1 - 1) / C - i0 / C + 1;
+    float S[3] = {0.f, 0.f, 0.f}, Cc[3] = {0.f, 0.f, 0.f};
+    for (int r = 0; r < nruns; ++r) {
+        const int slot = r == 0 ? i0 : (i0 / C + r) * C;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int v = lane + 32 * j;
+            if (v < NPART) {
+                const float2 x = __ldcg(&partials[int64_t(slot) * NPART + v]);
+                if (COMP) pair_add(S[j], Cc[j], x.x, x.y);
+                else S[j] += x.x;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int v = lane + 32 * j;
+        if (v < NPART) mom[v] = double(S[j]) + double(Cc[j]);
+    }
+    __syncwarp();
+    if (lane < 8)
+        child_mstep(level, n, p, lane, mom + lane * NMOM, seg_count, root, n_min, stat, est, status);
+    __syncwarp();
+}
+
+
+// ================================================================= hand-off
+struct AssignSmem {
+    int cnt[EST_THREADS / 32][8];
+    int base[8];
+};
+
+// Argmax hand-off (ties -> lowest index) of one item's points by one CTA,
+// with each point's rank among the item's points that chose the same child
+// (ballots, so deterministic and stable): codes[pos] = child | rank << 3 and
+// item_cnt[8 it + c] = the item's count per child.
+__device__ __forceinline__ void assign_item(const float4* __restrict__ pts, const Item w, int it,
+                                            const NodeEst* __restrict__ est_lvl,
+                                            uint32_t* __restrict__ codes,
+                                            int* __restrict__ item_cnt, AssignSmem& as) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 2, k = lane & 3;
+    const unsigned lt = (1u << lane) - 1u;
+    ChildRegs r0, r1;
+    load_child(est_lvl + 8 * w.parent + 2 * k, r0);
+    load_child(est_lvl + 8 * w.parent + 2 * k + 1, r1);
+    if (threadIdx.x < 8) as.base[threadIdx.x] = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < w.count; b0 += 64) {
+        const int idx = b0 + warp * 8 + q;
+        const bool valid = idx < w.count;
+        const float4 z = pts[w.start + (valid ? idx : 0)];
+        float ex, ey, ez;
+        const float s0 = child_score(r0, z.x, z.y, z.z, ex, ey, ez);
+        const float s1 = child_score(r1, z.x, z.y, z.z, ex, ey, ez);
+        float best = s0;
+        int lab = 2 * k;
+        if (s1 > best) { best = s1; lab = 2 * k + 1; }
+#pragma unroll
+        for (int off = 1; off <= 2; off <<= 1) {
+            const float ob = __shfl_xor_sync(FULL, best, off);
+            const int ol = __shfl_xor_sync(FULL, lab, off);
+            if (ob > best || (ob == best && ol < lab)) { best = ob; lab = ol; }
+        }
+        const bool lead = valid && k == 0;
+        int my_rank = 0;
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+            const unsigned bal = __ballot_sync(FULL, lead && lab == cc);
+            if (lane == 0) as.cnt[warp][cc] = __popc(bal);
+            if (lab == cc) my_rank = __popc(bal & lt);
+        }
+        __syncthreads();
+        if (lead) {
+            int r = as.base[lab] + my_rank;
+            for (int w2 = 0; w2 < warp; ++w2) r += as.cnt[w2][lab];
+            codes[w.start + idx] = uint32_t(lab) | (uint32_t(r) << 3);
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            int tsum = 0;
+            for (int w2 = 0; w2 < EST_THREADS / 32; ++w2) tsum += as.cnt[w2][threadIdx.x];
+            as.base[threadIdx.x] += tsum;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) item_cnt[8 * it + threadIdx.x] = as.base[threadIdx.x];
+    __syncthreads();
+}
+
+struct OffsetSmem {
+    int tot[8][8];  // [warp][child]
+    int carry[8];
+};
+
+// Child segments of parent p (items [i0, i1), segment start pstart) by one
+// CTA of 256 threads: per child, an exclusive scan over the parent's items
+// of the item counts -> absolute destination offsets; children's seg_start /
+// seg_count.
+__device__ __forceinline__ void child_offsets_cta(int level, int p, int i0, int i1, int pstart,
+                                                  const int* __restrict__ item_cnt,
+                                                  int* __restrict__ item_off,
+                                                  int* __restrict__ seg_start,
+                                                  int* __restrict__ seg_count, OffsetSmem& os) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t g0 = d_level_offset(level) + 8 * int64_t(p);
+    int t8[8] = {};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+        for (int cc = 0; cc < 8; ++cc) t8[cc] += item_cnt[8 * i + cc];
+    for (int cc = 0; cc < 8; ++cc) {
+        int x = t8[cc];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+        if (lane == 0) os.tot[warp][cc] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = pstart;
+        for (int cc = 0; cc < 8; ++cc) {
+            int s = 0;
+            for (int w = 0; w < 8; ++w) s += os.tot[w][cc];
+            os.carry[cc] = run;
+            seg_start[g0 + cc] = run;
+            seg_count[g0 + cc] = s;
+            run += s;
+        }
+    }
+    __syncthreads();
+    for (int b = i0; b < i1; b += blockDim.x) {
+        const int i = b + threadIdx.x;
+        int v8[8];
+        for (int cc = 0; cc < 8; ++cc) v8[cc] = i < i1 ? item_cnt[8 * i + cc] : 0;
+        int incl[8];
+        for (int cc = 0; cc < 8; ++cc) {
+            int x = v8[cc];
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, off);
+                if (lane >= off) x += y;
+            }
+            incl[cc] = x;
+            if (lane == 31) os.tot[warp][cc] = x;
+        }
+        __syncthreads();
+        for (int cc = 0; cc < 8; ++cc) {
+            int pre = os.carry[cc];
+            for (int w = 0; w < warp; ++w) pre += os.tot[w][cc];
+            if (i < i1) item_off[8 * i + cc] = pre + incl[cc] - v8[cc];
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            int s = 0;
+            for (int w = 0; w < 8; ++w) s += os.tot[w][threadIdx.x];
+            os.carry[threadIdx.x] += s;
+        }
+        __syncthreads();
+    }
+}
+
+// The same by one warp (for parents with few items): lanes scan 32 items at
+// a time per child in a fixed order.
+__device__ __forceinline__ void child_offsets_warp(int level, int p, int i0, int i1, int pstart,
+                                                   const int* __restrict__ item_cnt,
+                                                   int* __restrict__ item_off,
+                                                   int* __restrict__ seg_start,
+                                                   int* __restrict__ seg_count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t g0 = d_level_offset(level) + 8 * int64_t(p);
+    int tot8[8] = {};
+    for (int i = i0 + lane; i < i1; i += 32)
+        for (int cc = 0; cc < 8; ++cc) tot8[cc] += item_cnt[8 * i + cc];
+    int carry8[8];
+    int run = pstart;
+    for (int cc = 0; cc < 8; ++cc) {
+        int x = tot8[cc];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+        carry8[cc] = run;
+        if (lane == 0) {
+            seg_start[g0 + cc] = run;
+            seg_count[g0 + cc] = x;
+        }
+        run += x;
+    }
+    for (int b = i0; b < i1; b += 32) {
+        const int i = b + lane;
+        for (int cc = 0; cc < 8; ++cc) {
+            const int v = i < i1 ? item_cnt[8 * i + cc] : 0;
+            int x = v;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, off);
+                if (lane >= off) x += y;
+            }
+            if (i < i1) item_off[8 * i + cc] = carry8[cc] + x - v;
+            carry8[cc] += __shfl_sync(FULL, x, 31);
+        }
+    }
+}
+
+// Stable 8-way partition of one item's points by one CTA (or any group of
+// threads striding by `stride` from `first`).
+__device__ __forceinline__ void scatter_item(const float4* __restrict__ pts_in,
+                                             const int* __restrict__ perm_in, const Item w, int it,
+                                             const uint32_t* __restrict__ codes,
+                                             const int* __restrict__ item_off,
+                                             float4* __restrict__ pts_out,
+                                             int* __restrict__ perm_out, int first, int stride) {
+    for (int j = first; j < w.count; j += stride) {
+        const int pos = w.start + j;
+        const uint32_t code = codes[pos];
+        const int dst = item_off[8 * it + (code & 7u)] + int(code >> 3);
+        pts_out[dst] = pts_in[pos];
+        if (perm_out) perm_out[dst] = perm_in ? perm_in[pos] : pos;
+    }
+}
+
+// =================================================================== finalize
+// Node i of a level: FP64 eigen-decomposition of its covariance,
+// complexity lambda_3 / (lambda_1 + lambda_2 + lambda_3) and the stop flag
+// (<= lambda_c, Sec. 4.1), precision P = V diag(1/max(lambda, eps)) V^T
+// (Eq. 10) and the FP32 registration constants.
+__device__ __forceinline__ void finalize_node(int level, int64_t i, float lam_c,
+                                              const RootDev* __restrict__ root,
+                                              NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
+                                              float4* __restrict__ rnode) {
+    const int64_t g = d_level_offset(level) + i;
+    NodeStat& s = stat[g];
+    if (!s.live) {
+        for (int a = 0; a < 3; ++a) s.lam[a] = 1.0;
+        for (int v = 0; v < 9; ++v) s.V[v] = (v % 4 == 0) ? 1.0 : 0.0;
+        for (int v = 0; v < 6; ++v) s.P[v] = 0.0;
+        s.complexity = 1.0;
+        est[g].c.z = 0.f;
+        rnode[3 * g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rnode[3 * g + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rnode[3 * g + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    double lam[3], V[9];
+    eig3(s.S, lam, V);
+    const double eps = root->eps;
+    double il[3];
+    for (int a = 0; a < 3; ++a) {
+        s.lam[a] = lam[a];
+        il[a] = rcp_f64(fmax(lam[a], eps));
+    }
+    for (int v = 0; v < 9; ++v) s.V[v] = V[v];
+    const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int v = 0; v < 6; ++v) {
+        const int r = ij[v][0], c = ij[v][1];
+        double acc = 0.0;
+        for (int k = 0; k < 3; ++k) acc += V[r * 3 + k] * il[k] * V[c * 3 + k];
+        s.P[v] = acc;
+    }
+    s.complexity = lam[2] * rcp_f64(lam[0] + lam[1] + lam[2]);
+    const float4 a = est[g].a;
+    est[g].c.z = (s.complexity <= double(lam_c)) ? 1.f : 0.f;
+    // FP32 registration constants: P and the offset of the FP64 mean from the
+    // FP32 mean the descent measures against
+    rnode[3 * g] = make_float4(float(s.P[0]), float(s.P[1]), float(s.P[2]), float(s.P[3]));
+    rnode[3 * g + 1] = make_float4(float(s.P[4]), float(s.P[5]), 0.f, 0.f);
+    rnode[3 * g + 2] = make_float4(float(s.mu[0] - double(a.x)), float(s.mu[1] - double(a.y)),
+                                   float(s.mu[2] - double(a.z)), 0.f);
+}
+
+// ============================================================ registration
+__device__ __forceinline__ long long to_fix(float v) {
+    const float c = fminf(fmaxf(v, -FIX_CLAMP), FIX_CLAMP);
+    return __float2ll_rn(c);
+}
+
+// Algorithm 1 for the points of this CTA (grid-stride by warps) with the
+// current transform; adds each point's (gamma, gamma (z' - mu_j)) to the
+// chosen node's fixed-point moments.
+constexpr int STAGED_NODES = 584;  // levels 0..2 (8 + 64 + 512 nodes) live in shared memory
+
+__device__ __forceinline__ void load_node(const NodeEst* __restrict__ est, const float4* sm_est,
+                                          int64_t g, float4& ea, float4& eb, float4& ec) {
+    if (g < STAGED_NODES) {
+        ea = sm_est[3 * g];
+        eb = sm_est[3 * g + 1];
+        ec = sm_est[3 * g + 2];
+    } else {
+        const NodeEst* e = est + g;
+        ea = __ldg(&e->a);
+        eb = __ldg(&e->b);
+        ec = __ldg(&e->c);
+    }
+}
+
+__device__ __forceinline__ void descend_points(const float4* __restrict__ src, int n,
+                                               const NodeEst* __restrict__ est, const float4* sm_est,
+                                               int depth, const float* Rt_sm, float qscale,
+                                               unsigned long long* __restrict__ acc, int cta, int ncta) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float r00 = Rt_sm[0], r01 = Rt_sm[1], r02 = Rt_sm[2], r10 = Rt_sm[3], r11 = Rt_sm[4];
+    const float r12 = Rt_sm[5], r20 = Rt_sm[6], r21 = Rt_sm[7], r22 = Rt_sm[8];
+    const float tx = Rt_sm[9], ty = Rt_sm[10], tz = Rt_sm[11];
+    const int wpb = blockDim.x >> 5;
+    const int warps_total = ncta * wpb;
+    for (int base = (cta * wpb + warp) * 32; base < n; base += warps_total * 32) {
+        const int i = base + lane;
+        const bool valid = i < n;
+        float4 z = valid ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float x = fmaf(r00, z.x, fmaf(r01, z.y, fmaf(r02, z.z, tx)));
+        const float y = fmaf(r10, z.x, fmaf(r11, z.y, fmaf(r12, z.z, ty)));
+        const float w = fmaf(r20, z.x, fmaf(r21, z.y, fmaf(r22, z.z, tz)));
+        int chosen = -1;
+        float gamma = 0.f, cmx = 0.f, cmy = 0.f, cmz = 0.f;
+        int local = 0;  // index within its level of the current search node
+        for (int l = 0; l < depth && valid; ++l) {
+            const int64_t first = d_level_offset(l) + 8 * int64_t(local);
+            float sc8[8];
+            float best = -CUDART_INF_F;
+            int bi = -1;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float4 ea, eb, ec;
+                load_node(est, sm_est, first + c, ea, eb, ec);
+                const float ex = x - ea.x, ey = y - ea.y, ez = w - ea.z;
+                const float d0 = eb.x * ex;
+                const float d1 = fmaf(eb.z, ey, eb.y * ex);
+                const float d2 = fmaf(ec.y, ez, fmaf(ec.x, ey, eb.w * ex));
+                float sc = fmaf(-d0, d0, ea.w);
+                sc = fmaf(-d1, d1, sc);
+                sc = fmaf(-d2, d2, sc);
+                sc8[c] = sc;
+                if (sc > best) { best = sc; bi = c; }
+            }
+            if (bi < 0) break;  // the current node has no live children
+            float sum = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) sum += exp2f(sc8[c] - best);
+            gamma = 1.0f / sum;
+            chosen = int(first + bi);
+            local = 8 * local + bi;
+            float4 ea, eb, ec;
+            load_node(est, sm_est, chosen, ea, eb, ec);
+            cmx = ea.x; cmy = ea.y; cmz = ea.z;
+            if (ec.z != 0.f) break;  // Complexity <= lambda_c
+        }
+        // Sum (gamma, gamma (z' - mu_j)) over the lanes of this warp that chose
+        // the same node j: a pairwise tree over the members' ranks (fixed order,
+        // so deterministic), then one fixed-point atomic per value and group.
+        // Integer adds are exact, so the node totals do not depend on the
+        // order in which groups arrive.
+        const bool has = chosen >= 0;
+        float v0 = has ? gamma : 0.f;
+        float v1 = has ? gamma * (x - cmx) : 0.f;
+        float v2 = has ? gamma * (y - cmy) : 0.f;
+        float v3 = has ? gamma * (w - cmz) : 0.f;
+        const unsigned peers = __match_any_sync(FULL, chosen);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        const int gsize = __popc(peers);
+        const unsigned higher = lane == 31 ? 0u : (peers & ~((2u << lane) - 1u));
+#pragma unroll
+        for (int st = 1; st < 32; st <<= 1) {
+            unsigned h = higher;  // lane holding rank + st within my group
+            for (int k = 1; k < st; ++k) h &= h - 1u;
+            const int srcl = h ? __ffs(h) - 1 : lane;
+            const float o0 = __shfl_sync(FULL, v0, srcl);
+            const float o1 = __shfl_sync(FULL, v1, srcl);
+            const float o2 = __shfl_sync(FULL, v2, srcl);
+            const float o3 = __shfl_sync(FULL, v3, srcl);
+            if ((rank & (2 * st - 1)) == 0 && rank + st < gsize) {
+                v0 += o0; v1 += o1; v2 += o2; v3 += o3;
+            }
+        }
+        if (has && rank == 0) {
+            // one of ACC_REPLICAS copies per CTA spreads the atomics on hot
+            // nodes (a ground plane collects a large share of the points)
+            unsigned long long* dst =
+                acc + 4 * (int64_t(chosen) * ACC_REPLICAS + (cta & (ACC_REPLICAS - 1)));
+            atomicAdd(dst + 0, (unsigned long long)to_fix(v0 * 4294967296.0f));
+            atomicAdd(dst + 1, (unsigned long long)to_fix(v1 * qscale));
+            atomicAdd(dst + 2, (unsigned long long)to_fix(v2 * qscale));
+            atomicAdd(dst + 3, (unsigned long long)to_fix(v3 * qscale));
+        }
+    }
+}
+
+// Per-node contribution to the 6x6 normal equations in FP32; the sums over
+// nodes are compensated (TwoSum pairs), so the 27 totals that reach the FP64
+// solve carry ~2x FP32 precision.  Per node j with mass (M0 > 0):
+//   mu* = mu_j32 + o,  o = (M1 rel. to mu_j32) / M0,   d = mu_j - mu* = dmu_j - o
+//   H_j = pi* [[A [mu*]x^T, A], [A^T, P]],  A = [mu*]x P,   g_j = pi* [mu* x P d; P d]
+__device__ __forceinline__ void node_terms(const float4 p0, const float4 p1, const float4 dm,
+                                           const float4 cm, float M0, float o0, float o1,
+                                           float o2, float pis, float* v) {
+    const float P[3][3] = {{p0.x, p0.y, p0.z}, {p0.y, p0.w, p1.x}, {p0.z, p1.x, p1.y}};
+    const float m0 = cm.x + o0, m1 = cm.y + o1, m2 = cm.z + o2;
+    const float d0 = dm.x - o0, d1 = dm.y - o1, d2 = dm.z - o2;
+    float A[3][3], Bm[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        A[0][k] = m1 * P[2][k] - m2 * P[1][k];
+        A[1][k] = m2 * P[0][k] - m0 * P[2][k];
+        A[2][k] = m0 * P[1][k] - m1 * P[0][k];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Bm[i][0] = m1 * A[i][2] - m2 * A[i][1];
+        Bm[i][1] = m2 * A[i][0] - m0 * A[i][2];
+        Bm[i][2] = m0 * A[i][1] - m1 * A[i][0];
+    }
+    float Pd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Pd[i] = P[i][0] * d0 + P[i][1] * d1 + P[i][2] * d2;
+    const float top[3] = {m1 * Pd[2] - m2 * Pd[1], m2 * Pd[0] - m0 * Pd[2], m0 * Pd[1] - m1 * Pd[0]};
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) {
+            float h;
+            if (i < 3 && j < 3) h = Bm[i][j];
+            else if (i < 3) h = A[i][j - 3];
+            else h = P[i - 3][j - 3];
+            v[k++] = pis * h;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        v[21 + i] = pis * top[i];
+        v[24 + i] = pis * Pd[i];
+    }
+    (void)M0;
+}
+
+// FP64 solve of the 6x6 normal equations and the pose update by one warp.
+// Lane i < 6 owns row i; the right-looking Cholesky updates all rows with
+// one instruction per column, so the FP64 instruction count of the critical
+// path (~70 cycles each on this part) is about a third of a one-thread
+// solve.  L is kept in shared memory for the back substitution.  Returns
+// false (uniformly) for a non-positive pivot.
+__device__ inline bool warp_solve_update(const double* tot, double (*Lsm)[6], double* T,
+                                  float* Rt, double* T_hist, int iter) {
+    const int lane = threadIdx.x & 31;
+    const int row = lane < 6 ? lane : 5;
+    auto H = [&](int i, int j) {  // upper-packed 21 entries
+        if (i > j) { const int t = i; i = j; j = t; }
+        return tot[i * 6 - (i * (i - 1)) / 2 + (j - i)];
+    };
+    double a[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a[j] = H(row, j);
+    double g = tot[21 + row];
+    double dmax = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) dmax = fmax(dmax, H(j, j));
+    double r[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double dk = __shfl_sync(FULL, a[k], k);
+        if (!(dk > 1e-15 * dmax)) return false;
+        r[k] = rsqrt_f64(dk);
+        const double lik = a[k] * r[k];  // L_ik for rows i >= k
+        if (lane < 6) Lsm[k][lane] = lik;
+#pragma unroll
+        for (int j = k + 1; j < 6; ++j) {
+            const double ljk = __shfl_sync(FULL, lik, j);
+            a[j] = fma(-lik, ljk, a[j]);
+        }
+    }
+    __syncwarp();
+    // forward: L y = g (column k: y_k = g_k r_k, then rows i > k lose L_ik y_k)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double yk = __shfl_sync(FULL, g, k) * r[k];
+        if (lane == k) g = yk;
+        else if (lane > k) g = fma(-Lsm[k][row], yk, g);
+    }
+    // backward: L^T x = y (x_k = y_k r_k, then rows j < k lose L_kj x_k)
+    double x[6];
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+        const double xk = __shfl_sync(FULL, g, k) * r[k];
+        x[k] = xk;
+        if (lane < k) g = fma(-Lsm[lane][k], xk, g);
+    }
+    // dT = (Rodrigues(w), t); lane e < 12 computes entry e of the new [R|t]
+    const double th2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    double ca, cb;
+    if (th2 < 0.25) {
+        ca = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880 +
+             th2 * (-1.0 / 39916800 + th2 * (1.0 / 6227020800.0))))));
+        cb = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720 + th2 * (-1.0 / 40320 + th2 * (1.0 / 3628800 +
+             th2 * (-1.0 / 479001600 + th2 * (1.0 / 87178291200.0))))));
+    } else {
+        const double th = sqrt(th2);
+        ca = sin(th) / th;
+        cb = (1.0 - cos(th)) / th2;
+    }
+    const int e = lane < 12 ? lane : 11;
+    const int rr = e >> 2, cc = e & 3;
+    // row rr of dR = I + a K + b K^2, K = [w]x, (K^2)_{rm} = w_r w_m - |w|^2 delta_rm
+    const double kr[3] = {rr == 0 ? 0.0 : (rr == 1 ? x[2] : -x[1]),
+                          rr == 0 ? -x[2] : (rr == 1 ? 0.0 : x[0]),
+                          rr == 0 ? x[1] : (rr == 1 ? -x[0] : 0.0)};
+    double acc = cc == 3 ? x[3 + rr] : 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const double drm = (m == rr ? 1.0 - cb * th2 : 0.0) + ca * kr[m] + cb * x[rr] * x[m];
+        acc = fma(drm, __ldcg(T + m * 4 + cc), acc);
+    }
+    __syncwarp();
+    if (lane < 12) {
+        T[e] = acc;
+        Rt[cc == 3 ? 9 + rr : rr * 3 + cc] = float(acc);
+        if (T_hist) T_hist[16 * iter + e] = acc;
+    }
+    if (T_hist && lane >= 12 && lane < 16) T_hist[16 * iter + lane] = lane == 15 ? 1.0 : 0.0;
+    return true;
+}
+
+// Bounded grid-wide barrier for a cooperative launch (all CTAs co-resident):
+// generation counter, spin with a sleep and an iteration limit; on timeout
+// it records ST_TIMEOUT and returns false so the kernel can exit.
+constexpr long long BARRIER_SPIN_LIMIT = 1000000;  // about a second
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, long long limit) {
+    __shared__ int ok_sm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > limit) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_sm = ok;
+    }
+    __syncthreads();
+    return ok_sm != 0;
+}
+
+
+}  // namespace hgmm

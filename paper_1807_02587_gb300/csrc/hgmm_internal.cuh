@@ -90,8 +90,10 @@ struct ProfRecord {
     cudaEvent_t a, b;
 };
 
-inline int64_t level_size(int l) { return int64_t(1) << (3 * (l + 1)); }
-inline int64_t level_offset(int l) { return ((int64_t(1) << (3 * (l + 1))) - 8) / 7; }
+__host__ __device__ inline int64_t level_size(int l) { return int64_t(1) << (3 * (l + 1)); }
+__host__ __device__ inline int64_t level_offset(int l) {
+    return ((int64_t(1) << (3 * (l + 1))) - 8) / 7;
+}
 
 }  // namespace hgmm
 

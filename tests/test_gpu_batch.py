@@ -1,0 +1,105 @@
+"""Batched form: many uneven pairs in one persistent cluster launch must give
+the same registrations as the single-pair path (hgmm_build + hgmm_register,
+itself checked against the oracle), for every cluster shape."""
+import numpy as np
+import pytest
+
+from paper_1807_02587_gb300 import synth
+from tests import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1807_02587_gb300 import binding
+    return binding
+
+
+def _pairs(seed, count, lo, hi, max_deg=3.0):
+    rng = synth.make_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(int)
+    out = []
+    for i, n in enumerate(sizes):
+        p = synth.primitive_pair(int(rng.integers(1 << 30)), int(n), max_deg=max_deg, max_t=0.02)
+        p["depth"] = 3 + (i % 2)
+        out.append(p)
+    return out
+
+
+def _layout(pairs):
+    """All targets first, then all sources, as one float4 buffer; per-side
+    offsets with pair i at [off[i], off[i + 1])."""
+    tb = [synth.to_float4(p["tgt"]) for p in pairs]
+    sb = [synth.to_float4(p["src"]) for p in pairs]
+    t_off = np.concatenate([[0], np.cumsum([x.shape[0] for x in tb])]).astype(np.int64)
+    s_off = (np.concatenate([[0], np.cumsum([x.shape[0] for x in sb])]) + t_off[-1]).astype(np.int64)
+    return np.concatenate(tb + sb), t_off, s_off
+
+
+def test_batch_matches_single_pair_path(B):
+    import torch
+    pairs = _pairs(1, 10, 2000, 40000)
+    buf, t_off, s_off = _layout(pairs)
+    n = len(pairs)
+    pts = torch.from_numpy(buf).cuda()
+    single = []
+    for i, p in enumerate(pairs):
+        tgt = pts[t_off[i]:t_off[i + 1]]
+        src = pts[s_off[i]:s_off[i + 1]]
+        tree = B.Tree(max(tgt.shape[0], src.shape[0]), p["depth"])
+        tree.build(tgt, p["depth"])
+        single.append(tree.register(src, iters=20).cpu().numpy())
+        tree.sync()
+    bat = B.Batch(int(max(np.diff(t_off).max(), np.diff(s_off).max())), 4, n)
+    B.hgmm_batch_plan(bat.handle, t_off, s_off, [p["depth"] for p in pairs])
+    for shape in (1, 2, 4, 8):
+        B.hgmm_batch_set_shape(bat.handle, shape)
+        T = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
+        st = torch.full((n,), 99, dtype=torch.int32, device="cuda")
+        B.hgmm_batch_register(bat.handle, pts, T, iters=20, pair_status=st)
+        torch.cuda.synchronize()
+        assert np.all(st.cpu().numpy() == 0)
+        Tb = T.cpu().numpy().reshape(n, 4, 4)
+        for i, p in enumerate(pairs):
+            ext = np.linalg.norm(p["tgt"].max(0) - p["tgt"].min(0))
+            r, t = PT.pose_errors(Tb[i], single[i], ext)
+            assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (shape, i, r, t)
+
+
+def test_batch_autotune_and_nonfinite_pair(B):
+    import torch
+    pairs = _pairs(2, 6, 2000, 20000)
+    pairs[3]["tgt"] = pairs[3]["tgt"].copy()
+    pairs[3]["tgt"][5, 0] = np.nan
+    buf, t_off, s_off = _layout(pairs)
+    both = torch.from_numpy(buf).cuda()
+    bat = B.Batch(20000, 4, 6)
+    B.hgmm_batch_plan(bat.handle, t_off, s_off, [p["depth"] for p in pairs])
+    T = torch.zeros((6, 16), dtype=torch.float64, device="cuda")
+    ms = B.hgmm_batch_autotune(bat.handle, both, T, iters=5)
+    assert any(m > 0 for m in ms)
+    shape, clusters = B.hgmm_batch_get_shape(bat.handle)
+    assert shape in (1, 2, 4, 8) and clusters >= 1
+    st = torch.zeros(6, dtype=torch.int32, device="cuda")
+    B.hgmm_batch_register(bat.handle, both, T, iters=5, pair_status=st)
+    torch.cuda.synchronize()
+    s = st.cpu().numpy()
+    assert s[3] == B.HGMM_ENONFINITE
+    assert np.all(s[[0, 1, 2, 4, 5]] == 0)
+    assert np.all(np.isfinite(T.cpu().numpy()[[0, 1, 2, 4, 5]]))
+
+
+def test_batch_plan_rejects_bad_pairs(B):
+    bat = B.Batch(1000, 3, 4)
+    with pytest.raises(B.HgmmError) as e:
+        B.hgmm_batch_plan(bat.handle, np.array([0, 5], np.int64), np.array([5, 100], np.int64), [3])
+    assert e.value.code == B.HGMM_EINVAL  # 5 target points < 8
+    with pytest.raises(B.HgmmError) as e:
+        B.hgmm_batch_plan(bat.handle, np.array([0, 2000], np.int64),
+                          np.array([2000, 2100], np.int64), [3])
+    assert e.value.code == B.HGMM_ECAPACITY
+    with pytest.raises(B.HgmmError) as e:
+        B.hgmm_batch_plan(bat.handle, np.array([0, 100], np.int64),
+                          np.array([100, 200], np.int64), [5])
+    assert e.value.code == B.HGMM_EINVAL
