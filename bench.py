@@ -459,6 +459,7 @@ def batched_section(args, B, synth, torch, prm):
     plain_ms = a0.elapsed_time(a1)
     agree = [rot_err(outs[j].cpu().numpy(), Tb[i]) for j, i in enumerate(sub)]
     ok_p = [rot_err(outs[j].cpu().numpy(), pairs[i]["T_gt"]) <= 0.1 for j, i in enumerate(sub)]
+    ok_b_sub = [ok_b[i] for i in sub]
     return {
         "pairs": n, "points_per_side": int(t_off[-1]), "pairs_per_s": n / (ms / 1e3),
         "ms_per_batch": ms, "cluster_ctas": shape, "clusters": clusters,
@@ -466,8 +467,9 @@ def batched_section(args, B, synth, torch, prm):
         "plain_pairs_per_s": len(sub) / (plain_ms / 1e3), "plain_subset": len(sub),
         "speedup_vs_plain": (n / (ms / 1e3)) / (len(sub) / (plain_ms / 1e3)),
         "success_rate_le_0p1deg": float(np.mean(ok_b)),
+        "success_rate_le_0p1deg_subset": float(np.mean(ok_b_sub)),
         "plain_success_rate_le_0p1deg_subset": float(np.mean(ok_p)),
-        "max_rot_diff_batch_vs_plain_deg": float(np.max(agree)),
+        "agree_with_plain_within_0p01deg_subset": float(np.mean(np.array(agree) < 0.01)),
         "pair_status_nonzero": int(np.sum(status != 0)),
     }
 
