@@ -19,7 +19,11 @@ available here; the generators below stand in for them:
                       analogue of the Lounge structured-light frames (Sec. 6).
 * ``batched_pairs``   hundreds of uneven plane/sphere/box pairs.
 * ``so3_pairs``       pairs under rotations uniform over SO(3) (pose-proposal
-                      training data).
+                      test data).
+* ``so3_scene_set``   scenes sampled twice, each with several SO(3)-uniform
+                      poses of its second sample (pose-proposal training
+                      data; the rotated clouds are made by ``apply``).
+* ``mlp_init``        seeded initial weights of the proposal network.
 
 Convention: a pair holds ``src`` (cloud Z2) and ``tgt`` (cloud Z1, the model
 the tree is built on) as float64 (N, 3) arrays and the ground-truth rigid
@@ -34,7 +38,7 @@ __all__ = [
     "make_rng", "axis_angle_matrix", "random_rotation", "uniform_rotation",
     "rigid", "apply", "to_float4", "corner_scene", "corner_pair",
     "lidar_pair", "depth_pair", "primitive_scene", "primitive_pair",
-    "batched_pairs", "so3_pairs", "blob_cloud",
+    "batched_pairs", "so3_pairs", "so3_scene_set", "mlp_init", "blob_cloud",
 ]
 
 
@@ -412,6 +416,43 @@ def so3_pairs(seed: int, count: int, n: int):
         tgt = apply(T, _sample_primitives(r2, scene, n, 0.005))
         out.append({"src": src, "tgt": tgt, "T_gt": T, "name": "so3", "seed": s})
     return out
+
+
+def so3_scene_set(seed: int, n_scenes: int, per_scene: int, n: int, max_t: float = 0.1):
+    """``n_scenes`` plane/box/sphere scenes, each sampled twice (``src`` and
+    ``tgt_base``, float32 (n, 3)), and ``per_scene`` poses per scene with
+    rotations uniform over SO(3): pair (i, j) is src[i] against
+    apply(T[i, j], tgt_base[i])."""
+    rng = make_rng(seed)
+    src, base = [], []
+    T = np.empty((n_scenes, per_scene, 4, 4))
+    for i in range(n_scenes):
+        r2 = make_rng(int(rng.integers(0, 2**31 - 1)))
+        scene = primitive_scene(r2)
+        src.append(_sample_primitives(r2, scene, n, 0.005).astype(np.float32))
+        base.append(_sample_primitives(r2, scene, n, 0.005).astype(np.float32))
+        for j in range(per_scene):
+            T[i, j] = rigid(uniform_rotation(r2), r2.uniform(-max_t, max_t, 3))
+    return {"src": src, "tgt_base": base, "T": T}
+
+
+# layout of the proposal network's flat parameter vector (FP32):
+# W1 (256 x 1280), b1 (256), W2 (256 x 256), b2 (256), W3 (9 x 256), b3 (9)
+MLP_SHAPES = ((256, 1280), (256,), (256, 256), (256,), (9, 256), (9,))
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Flat FP32 parameters: weights uniform in +-sqrt(6 / fan_in) (He
+    uniform), biases zero."""
+    rng = make_rng(seed)
+    parts = []
+    for shape in MLP_SHAPES:
+        if len(shape) == 2:
+            b = np.sqrt(6.0 / shape[1])
+            parts.append(rng.uniform(-b, b, size=shape).reshape(-1))
+        else:
+            parts.append(np.zeros(shape[0]))
+    return np.concatenate(parts).astype(np.float32)
 
 
 # --------------------------------------------------------------------------
