@@ -121,6 +121,12 @@ int hgmm_register(hgmm_tree* t, const float* d_src, int64_t n,
                   const double* d_T_init, int32_t iters, float lam_c,
                   void* stream, double* d_T_out, double* d_T_hist);
 
+/* Eq. 11 objective of the last round of the last hgmm_register, evaluated
+ * at the pose that round started from: sum over nodes j with mass of
+ * pi*_j sum_l (n_jl^T (mu_j - mu*_j))^2 / lambda_jl (1 float64 to d_obj,
+ * device).  0 after a call with iters = 0. */
+int hgmm_register_objective(const hgmm_tree* t, double* d_obj, void* stream);
+
 /* Synchronise `stream` and return the first error the device recorded for
  * this tree since the last hgmm_sync (HGMM_OK if none); clears it. */
 int hgmm_sync(hgmm_tree* t, void* stream);
@@ -252,6 +258,10 @@ int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params*
 int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params* p,
                         const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
                         int32_t* d_pair_status);
+
+/* Per pair of the last hgmm_batch_register: the Eq. 11 objective of its
+ * last round (as hgmm_register_objective), n_pairs float64 to d_obj. */
+int hgmm_batch_objective(const hgmm_batch* b, double* d_obj, void* stream);
 
 /* Total node count of a tree of `depth` levels (8 + 64 + ... + 8^depth). */
 int64_t hgmm_node_count(int32_t depth);

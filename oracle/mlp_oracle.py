@@ -26,7 +26,11 @@ the definition written out in float64:
   are zeros.
 * Input x = [features(source), features(target)] (1280), rounded to BF16.
 * Network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3 with
-  BF16 weights (FP32 master copies) and 1280 -> 256 -> 256 -> 9.
+  BF16 weights (FP32 master copies) and 1280 -> 256 -> 256 -> 9.  The
+  default is FP64 throughout; ``act_bf16`` models the stated storage
+  precision of the tensor-core path (BF16 hidden activations and BF16
+  backward signals into every product) so that the arithmetic of the
+  kernels can be checked apart from the effect of that precision.
 * Output: y[0:3], y[3:6] are the 6-D rotation representation (Gram-Schmidt
   of two column vectors), y[6:9] the translation, both in canonical
   coordinates: x~_t = R' x~_s + t' with x~ = V^T (x - c) / s per cloud, so
@@ -89,16 +93,19 @@ def pack(d):
 # --------------------------------------------------------------------------
 # Network
 # --------------------------------------------------------------------------
-def forward(params, X, round_weights=True):
+def forward(params, X, round_weights=True, act_bf16=False):
     """y (B, 9) for inputs X (B, 1280).  With round_weights the weight
-    matrices take their BF16 values (biases stay FP32)."""
+    matrices take their BF16 values (biases stay FP32).  With act_bf16 the
+    hidden activations are stored in BF16 before the next product, as the
+    tensor-core path stores them."""
     P = unpack(params)
     W = {k: (bf16(P[k]) if round_weights else P[k]) for k in ("W1", "W2", "W3")}
+    r = bf16 if act_bf16 else (lambda a: a)
     X = np.asarray(X, np.float64)
     z1 = X @ W["W1"].T + P["b1"]
-    h1 = np.maximum(z1, 0.0)
+    h1 = r(np.maximum(z1, 0.0))
     z2 = h1 @ W["W2"].T + P["b2"]
-    h2 = np.maximum(z2, 0.0)
+    h2 = r(np.maximum(z2, 0.0))
     y = h2 @ W["W3"].T + P["b3"]
     return y, {"X": X, "z1": z1, "h1": h1, "z2": z2, "h2": h2, "W": W}
 
@@ -156,16 +163,21 @@ def loss_grad(y, labels, w_t):
     return np.concatenate([ga1, ga2, gt], axis=1) / B
 
 
-def backward(params, X, labels, w_t, round_weights=True):
+def backward(params, X, labels, w_t, round_weights=True, act_bf16=False):
     """Loss and its gradient with respect to the FP32 master parameters (the
-    BF16 rounding of the weights passes gradients through unchanged)."""
-    y, c = forward(params, X, round_weights)
+    BF16 rounding of the weights passes gradients through unchanged).  With
+    act_bf16 the forward stores hidden activations in BF16 and the backward
+    signals dL/dy, dL/dz2, dL/dz1 that enter a product are stored in BF16 too
+    (the bias gradient of the last layer sums the unrounded dL/dy)."""
+    y, c = forward(params, X, round_weights, act_bf16)
+    r = bf16 if act_bf16 else (lambda a: a)
     dy = loss_grad(y, labels, w_t)
+    dyr = r(dy)
     W = c["W"]
-    g = {"W3": dy.T @ c["h2"], "b3": dy.sum(axis=0)}
-    dz2 = (dy @ W["W3"]) * (c["z2"] > 0)
+    g = {"W3": dyr.T @ c["h2"], "b3": dy.sum(axis=0)}
+    dz2 = r((dyr @ W["W3"]) * (c["z2"] > 0))
     g["W2"], g["b2"] = dz2.T @ c["h1"], dz2.sum(axis=0)
-    dz1 = (dz2 @ W["W2"]) * (c["z1"] > 0)
+    dz1 = r((dz2 @ W["W2"]) * (c["z1"] > 0))
     g["W1"], g["b1"] = dz1.T @ c["X"], dz1.sum(axis=0)
     return loss(y, labels, w_t), pack(g), y
 

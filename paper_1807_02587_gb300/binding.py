@@ -27,6 +27,13 @@ HGMM_ECAPACITY = -7
 HGMM_J = 8
 HGMM_MAX_DEPTH = 5
 HGMM_NODE_DOUBLES = 16
+HGMM_MLP_IN = 1280
+HGMM_MLP_HIDDEN = 256
+HGMM_MLP_OUT = 9
+HGMM_MLP_PARAMS = 396041
+HGMM_FEAT_PER_CLOUD = 640
+HGMM_FRAME_DOUBLES = 16
+HGMM_LABEL_FLOATS = 12
 
 
 class HgmmError(RuntimeError):
@@ -79,6 +86,24 @@ def _load():
         "hgmm_profile_read": (ctypes.c_int, [vp, i32, P(ctypes.c_char_p), P(ctypes.c_double),
                                              P(ctypes.c_int64)]),
         "hgmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "hgmm_register_objective": (ctypes.c_int, [vp, vp, vp]),
+        "hgmm_batch_objective": (ctypes.c_int, [vp, vp, vp]),
+        "hgmm_batch_features": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, vp, vp]),
+        "hgmm_mlp_create": (ctypes.c_int, [i32, P(vp)]),
+        "hgmm_mlp_destroy": (None, [vp]),
+        "hgmm_mlp_set_params": (ctypes.c_int, [vp, vp, i64]),
+        "hgmm_mlp_get_params": (ctypes.c_int, [vp, vp, i64]),
+        "hgmm_mlp_read_grads": (ctypes.c_int, [vp, vp, i64]),
+        "hgmm_mlp_forward": (ctypes.c_int, [vp, vp, i32, vp, vp]),
+        "hgmm_mlp_gradients": (ctypes.c_int, [vp, vp, vp, vp, i32, i32, f32, vp, vp]),
+        "hgmm_mlp_adam": (ctypes.c_int, [vp, f32, vp]),
+        "hgmm_mlp_train_step": (ctypes.c_int, [vp, vp, vp, vp, i32, i32, f32, f32, vp, vp]),
+        "hgmm_mlp_sync": (ctypes.c_int, [vp, vp]),
+        "hgmm_tree_features": (ctypes.c_int, [vp, vp, vp, vp]),
+        "hgmm_pose_decode": (ctypes.c_int, [vp, vp, i32, vp, vp]),
+        "hgmm_pose_encode": (ctypes.c_int, [vp, vp, i32, vp, vp]),
+        "hgmm_pose_select": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, vp, vp]),
+        "hgmm_debug_gemm": (ctypes.c_int, [vp, i64, i64, vp, i64, i64, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -298,6 +323,22 @@ def hgmm_batch_autotune(h, points, T_out, prm: hgmm_params | None = None, T_init
     return list(ms)
 
 
+def hgmm_batch_objective(h, out, stream=None):
+    """Per pair of the last hgmm_batch_register: Eq. 11 objective of its last
+    round into ``out`` (n_pairs float64, CUDA)."""
+    _check(_lib.hgmm_batch_objective(h, _dptr(out), _stream_ptr(stream)), "hgmm_batch_objective")
+    return out
+
+
+def hgmm_batch_features(h, points, feat, frame, prm: hgmm_params | None = None, stream=None):
+    """Features (n_pairs x 640 bfloat16) and frames (n_pairs x 16 float64) of
+    every planned pair's target cloud."""
+    _check(_lib.hgmm_batch_features(h, _dev_points(points, "points"),
+                                    None if prm is None else ctypes.byref(prm), _dptr(feat),
+                                    _dptr(frame), _stream_ptr(stream)), "hgmm_batch_features")
+    return feat, frame
+
+
 class Batch:
     """Owns one hgmm_batch: planned pairs over one concatenated point buffer."""
 
@@ -346,6 +387,157 @@ def hgmm_profile_read(h) -> dict:
                                       ctypes.byref(cnt)), "hgmm_profile_read")
         out[name.value.decode()] = (ms.value, cnt.value)
     return out
+
+
+def hgmm_register_objective(h, out, stream=None):
+    _check(_lib.hgmm_register_objective(h, _dptr(out), _stream_ptr(stream)),
+           "hgmm_register_objective")
+    return out
+
+
+# ---------------------------------------------------------------- proposal
+def _need(x, dtype, numel, name):
+    import torch
+    if x is None or x.dtype != dtype or not x.is_cuda or not x.is_contiguous() or x.numel() < numel:
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor of >= {numel} elements")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def hgmm_mlp_create(max_batch: int):
+    h = ctypes.c_void_p()
+    _check(_lib.hgmm_mlp_create(int(max_batch), ctypes.byref(h)), "hgmm_mlp_create")
+    return h
+
+
+def hgmm_mlp_destroy(h) -> None:
+    _lib.hgmm_mlp_destroy(h)
+
+
+def hgmm_mlp_set_params(h, params) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib.hgmm_mlp_set_params(h, ctypes.c_void_p(p.ctypes.data), p.size), "hgmm_mlp_set_params")
+
+
+def hgmm_mlp_get_params(h) -> np.ndarray:
+    p = np.empty(HGMM_MLP_PARAMS, dtype=np.float32)
+    _check(_lib.hgmm_mlp_get_params(h, ctypes.c_void_p(p.ctypes.data), p.size), "hgmm_mlp_get_params")
+    return p
+
+
+def hgmm_mlp_read_grads(h) -> np.ndarray:
+    g = np.empty(HGMM_MLP_PARAMS, dtype=np.float32)
+    _check(_lib.hgmm_mlp_read_grads(h, ctypes.c_void_p(g.ctypes.data), g.size), "hgmm_mlp_read_grads")
+    return g
+
+
+def hgmm_mlp_forward(h, x, y, stream=None):
+    """x: (B, 1280) bfloat16 CUDA tensor; y: (B, 9) float32 CUDA tensor."""
+    import torch
+    B = int(x.shape[0])
+    _check(_lib.hgmm_mlp_forward(h, _need(x, torch.bfloat16, B * HGMM_MLP_IN, "x"), B,
+                                 _need(y, torch.float32, B * HGMM_MLP_OUT, "y"), _stream_ptr(stream)),
+           "hgmm_mlp_forward")
+    return y
+
+
+def hgmm_mlp_gradients(h, x, labels, batch: int, index=None, w_t: float = 1.0, loss=None,
+                       stream=None):
+    import torch
+    n_rows = int(x.shape[0])
+    _check(_lib.hgmm_mlp_gradients(h, _need(x, torch.bfloat16, HGMM_MLP_IN, "x"),
+                                   _need(labels, torch.float32, HGMM_LABEL_FLOATS, "labels"),
+                                   None if index is None else _need(index, torch.int32, batch, "index"),
+                                   int(batch), n_rows, float(w_t), _dptr(loss), _stream_ptr(stream)),
+           "hgmm_mlp_gradients")
+
+
+def hgmm_mlp_adam(h, lr: float, stream=None) -> None:
+    _check(_lib.hgmm_mlp_adam(h, float(lr), _stream_ptr(stream)), "hgmm_mlp_adam")
+
+
+def hgmm_mlp_train_step(h, x, labels, batch: int, index=None, w_t: float = 1.0, lr: float = 1e-3,
+                        loss=None, stream=None):
+    import torch
+    n_rows = int(x.shape[0])
+    _check(_lib.hgmm_mlp_train_step(h, _need(x, torch.bfloat16, HGMM_MLP_IN, "x"),
+                                    _need(labels, torch.float32, HGMM_LABEL_FLOATS, "labels"),
+                                    None if index is None else _need(index, torch.int32, batch, "index"),
+                                    int(batch), n_rows, float(w_t), float(lr), _dptr(loss),
+                                    _stream_ptr(stream)), "hgmm_mlp_train_step")
+
+
+def hgmm_mlp_sync(h, stream=None) -> None:
+    _check(_lib.hgmm_mlp_sync(h, _stream_ptr(stream)), "hgmm_mlp_sync")
+
+
+def hgmm_tree_features(h, feat, frame, stream=None):
+    import torch
+    _check(_lib.hgmm_tree_features(h, _need(feat, torch.bfloat16, HGMM_FEAT_PER_CLOUD, "feat"),
+                                   _need(frame, torch.float64, HGMM_FRAME_DOUBLES, "frame"),
+                                   _stream_ptr(stream)), "hgmm_tree_features")
+    return feat, frame
+
+
+def hgmm_pose_decode(y, frames, T, stream=None):
+    import torch
+    n = int(y.shape[0])
+    _check(_lib.hgmm_pose_decode(_need(y, torch.float32, 9 * n, "y"), _need(frames, torch.float64, 32 * n, "frames"),
+                                 n, _need(T, torch.float64, 16 * n, "T"), _stream_ptr(stream)),
+           "hgmm_pose_decode")
+    return T
+
+
+def hgmm_pose_encode(T, frames, labels, stream=None):
+    import torch
+    n = int(T.shape[0])
+    _check(_lib.hgmm_pose_encode(_need(T, torch.float64, 16 * n, "T"), _need(frames, torch.float64, 32 * n, "frames"),
+                                 n, _need(labels, torch.float32, 12 * n, "labels"), _stream_ptr(stream)),
+           "hgmm_pose_encode")
+    return labels
+
+
+def hgmm_pose_select(T_a, obj_a, T_b, obj_b, T_out, choice=None, stream=None):
+    import torch
+    n = int(T_a.shape[0])
+    _check(_lib.hgmm_pose_select(n, _need(T_a, torch.float64, 16 * n, "T_a"),
+                                 _need(obj_a, torch.float64, n, "obj_a"),
+                                 _need(T_b, torch.float64, 16 * n, "T_b"),
+                                 _need(obj_b, torch.float64, n, "obj_b"),
+                                 _need(T_out, torch.float64, 16 * n, "T_out"),
+                                 None if choice is None else _need(choice, torch.int32, n, "choice"),
+                                 _stream_ptr(stream)), "hgmm_pose_select")
+    return T_out
+
+
+def hgmm_debug_gemm(A, a_m: int, a_k: int, B, b_n: int, b_k: int, M: int, N: int, K: int, out,
+                    stream=None):
+    """out[m, n] = sum_k A[m][k] B[n][k] on the tensor cores; A and B are
+    bfloat16 CUDA tensors addressed by element strides."""
+    import torch
+    _check(_lib.hgmm_debug_gemm(_need(A, torch.bfloat16, 1, "A"), int(a_m), int(a_k),
+                                _need(B, torch.bfloat16, 1, "B"), int(b_n), int(b_k), int(M), int(N),
+                                int(K), _need(out, torch.float32, M * N, "out"), _stream_ptr(stream)),
+           "hgmm_debug_gemm")
+    return out
+
+
+class Mlp:
+    """Owns one hgmm_mlp (the proposal network and its training state)."""
+
+    def __init__(self, max_batch: int):
+        self.handle = hgmm_mlp_create(max_batch)
+        self.max_batch = max_batch
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hgmm_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience

@@ -46,7 +46,7 @@ void free_tree(hgmm_tree* t) {
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
                     t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
                     t->item_off, t->root, t->root_part, t->root_counter, t->status, t->reg_acc, t->reg_part,
-                    t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->rnode, t->trace, t->stage_tgt,
+                    t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->reg_obj, t->rnode, t->trace, t->stage_tgt,
                     t->stage_src, t->stage_T};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -144,13 +144,14 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->root_counter, 1);
     good &= dalloc(&t->status, 1);
     good &= dalloc(&t->reg_acc, 4 * ACC_REPLICAS * t->max_nodes);
-    good &= dalloc(&t->reg_part, 27 * nb);
+    good &= dalloc(&t->reg_part, NTERM * nb);
     good &= dalloc(&t->rnode, 3 * t->max_nodes);
     good &= dalloc(&t->trace, int64_t(TRACE_MAX_ITERS) * t->reg_grid * 6);
     good &= dalloc(&t->reg_bar, 8);
     good &= dalloc(&t->reg_T, 16);
     good &= dalloc(&t->reg_Rt, 12);
     good &= dalloc(&t->reg_dbg, 4 * t->max_nodes);
+    good &= dalloc(&t->reg_obj, 1);
     good &= dalloc(&t->stage_tgt, max_points);
     good &= dalloc(&t->stage_src, max_points);
     good &= dalloc(&t->stage_T, 32);
@@ -317,6 +318,14 @@ int hgmm_debug_reg_moments(hgmm_tree* t, double* h_m, int64_t cap) {
     if (cap < 4 * m) return HGMM_ECAPACITY;
     if (!ok(cudaDeviceSynchronize(), "sync")) return HGMM_ECUDA;
     if (!ok(cudaMemcpy(h_m, t->reg_dbg, size_t(4 * m) * sizeof(double), cudaMemcpyDeviceToHost), "D2H"))
+        return HGMM_ECUDA;
+    return HGMM_OK;
+}
+
+int hgmm_register_objective(const hgmm_tree* t, double* d_obj, void* stream) {
+    if (!t || !d_obj || !t->built) return HGMM_EINVAL;
+    if (!ok(cudaMemcpyAsync(d_obj, t->reg_obj, sizeof(double), cudaMemcpyDeviceToDevice,
+                            static_cast<cudaStream_t>(stream)), "D2D"))
         return HGMM_ECUDA;
     return HGMM_OK;
 }

@@ -14,7 +14,9 @@
 #include <cstring>
 #include <vector>
 
+#include "../../include/hgmm_proposal.h"
 #include "hgmm_dev.cuh"
+#include "hgmm_feat.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -52,6 +54,9 @@ struct BatchArgs {
     const double* T_init;       // [n_pairs x 16] or null (identity)
     double* T_out;              // [n_pairs x 16]
     int* pair_status;           // [n_pairs] HGMM error code per pair
+    double* obj;                // [n_pairs] Eq. 11 objective of the last round, or null
+    __nv_bfloat16* feat;        // [n_pairs x 640] target-cloud features, or null
+    double* frame;              // [n_pairs x 16] target-cloud frames (with feat)
     const BatchWs* ws;          // [clusters]
     int* queue;                 // next pair to take
     int n_pairs;
@@ -79,9 +84,10 @@ struct BuildSmem {
 
 struct RegSmem {
     float Rt[12];
-    float2 sm[EST_THREADS / 32][27];
-    double tot[27];
+    float2 sm[EST_THREADS / 32][NTERM];
+    double tot[NTERM];
     double Lsm[6][6];
+    double fsm[FRAME_DOUBLES];
     float4 est[3 * STAGED_NODES];
 };
 
@@ -163,6 +169,11 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
         cur = out;
     }
 
+    // ---- proposal features of the target (levels 0 and 1)
+    if (a.feat && rank == 0 && warp == 0 && depth >= 2)
+        tree_features_warp(w.root, w.stat, a.feat + int64_t(FEAT_PER_CLOUD) * pair,
+                           a.frame + int64_t(FRAME_DOUBLES) * pair, rgs.fsm);
+
     // ---- registration (Algorithm 1 + Eq. 9-16)
     const int n_nodes = int(level_offset(depth));
     for (int i = rank * blockDim.x + threadIdx.x; i < n_nodes; i += cs * blockDim.x) {
@@ -187,9 +198,9 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
         __syncthreads();
         descend_points(src, n_s, w.est, rgs.est, depth, rgs.Rt, qscale, w.acc, rank, cs);
         cl.sync();
-        float v[27], c[27];
+        float v[NTERM], c[NTERM];
 #pragma unroll
-        for (int k = 0; k < 27; ++k) { v[k] = 0.f; c[k] = 0.f; }
+        for (int k = 0; k < NTERM; ++k) { v[k] = 0.f; c[k] = 0.f; }
         for (int g = rank * blockDim.x + threadIdx.x; g < n_nodes; g += cs * blockDim.x) {
             const long long a0 = (long long)__ldcg(w.acc + 4 * g + 0);
             if (a0 == 0) continue;
@@ -203,39 +214,40 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
             if (a0 < 0) continue;
             const float M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
             const float inv = 1.0f / (qscale * M0);
-            float t27[27];
+            float tn[NTERM];
             node_terms(w.rnode[3 * g], w.rnode[3 * g + 1], w.rnode[3 * g + 2], w.est[g].a, M0,
-                       float(a1) * inv, float(a2) * inv, float(a3) * inv, M0 / float(n_s), t27);
+                       float(a1) * inv, float(a2) * inv, float(a3) * inv, M0 / float(n_s), tn);
 #pragma unroll
-            for (int k = 0; k < 27; ++k) pair_add(v[k], c[k], t27[k], 0.f);
+            for (int k = 0; k < NTERM; ++k) pair_add(v[k], c[k], tn[k], 0.f);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int k = 0; k < 27; ++k) {
+            for (int k = 0; k < NTERM; ++k) {
                 const float s2 = __shfl_xor_sync(FULL, v[k], off);
                 const float c2 = __shfl_xor_sync(FULL, c[k], off);
                 pair_add(v[k], c[k], s2, c2);
             }
         if (lane == 0)
-            for (int k = 0; k < 27; ++k) rgs.sm[warp][k] = make_float2(v[k], c[k]);
+            for (int k = 0; k < NTERM; ++k) rgs.sm[warp][k] = make_float2(v[k], c[k]);
         __syncthreads();
-        if (threadIdx.x < 27) {
+        if (threadIdx.x < NTERM) {
             float S = 0.f, C = 0.f;
             for (int w2 = 0; w2 < wpb; ++w2) pair_add(S, C, rgs.sm[w2][threadIdx.x].x, rgs.sm[w2][threadIdx.x].y);
-            w.reg_part[27 * rank + threadIdx.x] = make_float2(S, C);
+            w.reg_part[NTERM * rank + threadIdx.x] = make_float2(S, C);
         }
         cl.sync();
         if (rank == 0) {
-            if (threadIdx.x < 27) {
+            if (threadIdx.x < NTERM) {
                 float S = 0.f, C = 0.f;
                 for (int b = 0; b < cs; ++b) {
-                    const float2 x = __ldcg(&w.reg_part[27 * b + threadIdx.x]);
+                    const float2 x = __ldcg(&w.reg_part[NTERM * b + threadIdx.x]);
                     pair_add(S, C, x.x, x.y);
                 }
                 rgs.tot[threadIdx.x] = double(S) + double(C);
             }
             __syncthreads();
+            if (threadIdx.x == 32 && a.obj && it == a.iters - 1) a.obj[pair] = rgs.tot[NTERM - 1];
             if (warp == 0) {
                 const bool solved = warp_solve_update(rgs.tot, rgs.Lsm, w.T, w.Rt, nullptr, it);
                 if (!solved && lane == 0) atomicOr(w.status, ST_DEGENERATE);
@@ -296,6 +308,9 @@ struct hgmm_batch {
     int* d_order = nullptr;
     int* d_queue = nullptr;
     int* d_pair_status = nullptr;
+    double* d_obj = nullptr;        // per pair, last registration's objective
+    double* d_T_scratch = nullptr;  // poses of a features-only run
+    int min_depth = 0;              // of the current plan
     std::vector<int64_t> h_tgt_off, h_src_off;
 };
 
@@ -368,7 +383,7 @@ int hgmm_batch_create(int64_t max_points, int32_t max_depth, int32_t max_pairs, 
         good &= balloc(b, &w.meta, 4) && balloc(b, &w.partials, items * NPART);
         good &= balloc(b, &w.item_cnt, items * 8) && balloc(b, &w.item_off, items * 8);
         good &= balloc(b, &w.root_part, 32 * 16) && balloc(b, &w.acc, 4 * ACC_REPLICAS * nodes);
-        good &= balloc(b, &w.reg_part, 27 * 16) && balloc(b, &w.T, 16) && balloc(b, &w.Rt, 12);
+        good &= balloc(b, &w.reg_part, NTERM * 16) && balloc(b, &w.T, 16) && balloc(b, &w.Rt, 12);
         good &= balloc(b, &w.status, 1);
         if (good) good &= cudaMemset(w.seg_count, 0, nodes * sizeof(int)) == cudaSuccess &&
                           cudaMemset(w.stat, 0, nodes * sizeof(NodeStat)) == cudaSuccess;
@@ -376,7 +391,8 @@ int hgmm_batch_create(int64_t max_points, int32_t max_depth, int32_t max_pairs, 
     good = good && balloc(b, &b->d_ws, mc) && balloc(b, &b->d_tgt_off, max_pairs + 1) &&
            balloc(b, &b->d_src_off, max_pairs + 1) && balloc(b, &b->d_depth, max_pairs) &&
            balloc(b, &b->d_order, max_pairs) && balloc(b, &b->d_queue, 1) &&
-           balloc(b, &b->d_pair_status, max_pairs);
+           balloc(b, &b->d_pair_status, max_pairs) && balloc(b, &b->d_obj, max_pairs) &&
+           balloc(b, &b->d_T_scratch, 16 * int64_t(max_pairs));
     if (good)
         good = cudaMemcpy(b->d_ws, ws.data(), mc * sizeof(BatchWs), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!good) {
@@ -402,7 +418,9 @@ int hgmm_batch_plan(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_off,
     if (!b || !h_tgt_off || !h_src_off || !h_depth || n_pairs < 1 || n_pairs > b->max_pairs)
         return HGMM_EINVAL;
     std::vector<int> order(n_pairs);
+    int min_depth = 1 << 30;
     for (int i = 0; i < n_pairs; ++i) {
+        min_depth = std::min(min_depth, int(h_depth[i]));
         const int64_t nt = h_tgt_off[i + 1] - h_tgt_off[i];
         const int64_t ns = h_src_off[i + 1] - h_src_off[i];
         if (nt < 8 || ns < 1 || h_depth[i] < 1 || h_depth[i] > b->max_depth) return HGMM_EINVAL;
@@ -422,6 +440,7 @@ int hgmm_batch_plan(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_off,
     good &= cudaMemcpy(b->d_order, order.data(), n_pairs * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!good) return HGMM_ECUDA;
     b->n_pairs = n_pairs;
+    b->min_depth = min_depth;
     return HGMM_OK;
 }
 
@@ -439,9 +458,13 @@ int hgmm_batch_get_shape(const hgmm_batch* b, int32_t* cluster_ctas, int32_t* cl
     return HGMM_OK;
 }
 
-int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params* p,
-                        const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
-                        int32_t* d_pair_status) {
+}  // extern "C"
+
+namespace {
+
+int launch_batch(hgmm_batch* b, const float* d_points, const hgmm_params* p, const double* d_T_init,
+                 int32_t iters, void* stream, double* d_T_out, int32_t* d_pair_status,
+                 __nv_bfloat16* d_feat, double* d_frame) {
     if (!b || !d_points || !d_T_out || b->n_pairs < 1 || iters < 0) return HGMM_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0) return HGMM_EINVAL;
     int cur = -1;
@@ -463,6 +486,9 @@ int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params*
     a.T_init = d_T_init;
     a.T_out = d_T_out;
     a.pair_status = d_pair_status ? d_pair_status : b->d_pair_status;
+    a.obj = b->d_obj;
+    a.feat = d_feat;
+    a.frame = d_frame;
     a.ws = b->d_ws;
     a.queue = b->d_queue;
     a.n_pairs = b->n_pairs;
@@ -490,6 +516,34 @@ int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params*
         return HGMM_ECUDA;
     }
     return HGMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params* p,
+                        const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
+                        int32_t* d_pair_status) {
+    return launch_batch(b, d_points, p, d_T_init, iters, stream, d_T_out, d_pair_status, nullptr,
+                        nullptr);
+}
+
+int hgmm_batch_objective(const hgmm_batch* b, double* d_obj, void* stream) {
+    if (!b || !d_obj || b->n_pairs < 1) return HGMM_EINVAL;
+    return cudaMemcpyAsync(d_obj, b->d_obj, size_t(b->n_pairs) * sizeof(double),
+                           cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? HGMM_OK
+               : HGMM_ECUDA;
+}
+
+int hgmm_batch_features(hgmm_batch* b, const float* d_points, const hgmm_params* p,
+                        uint16_t* d_feat, double* d_frame, void* stream) {
+    if (!b || !d_feat || !d_frame || b->n_pairs < 1 || b->min_depth < 2) return HGMM_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_feat) & 15u) != 0 || (reinterpret_cast<uintptr_t>(d_frame) & 7u) != 0)
+        return HGMM_EINVAL;
+    return launch_batch(b, d_points, p, nullptr, 0, stream, b->d_T_scratch, nullptr,
+                        reinterpret_cast<__nv_bfloat16*>(d_feat), d_frame);
 }
 
 int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params* p,

@@ -986,10 +986,14 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
 }
 
 // Per-node contribution to the 6x6 normal equations in FP32; the sums over
-// nodes are compensated (TwoSum pairs), so the 27 totals that reach the FP64
+// nodes are compensated (TwoSum pairs), so the totals that reach the FP64
 // solve carry ~2x FP32 precision.  Per node j with mass (M0 > 0):
 //   mu* = mu_j32 + o,  o = (M1 rel. to mu_j32) / M0,   d = mu_j - mu* = dmu_j - o
 //   H_j = pi* [[A [mu*]x^T, A], [A^T, P]],  A = [mu*]x P,   g_j = pi* [mu* x P d; P d]
+// and the node's share of the Eq. 11 objective at the current pose,
+//   pi* d^T P d = pi* sum_l (n_l^T d)^2 / lambda_l.
+// Layout of v (NTERM floats): 21 upper-packed H entries, 6 of g, the objective.
+
 __device__ __forceinline__ void node_terms(const float4 p0, const float4 p1, const float4 dm,
                                            const float4 cm, float M0, float o0, float o1,
                                            float o2, float pis, float* v) {
@@ -1029,6 +1033,7 @@ __device__ __forceinline__ void node_terms(const float4 p0, const float4 p1, con
         v[21 + i] = pis * top[i];
         v[24 + i] = pis * Pd[i];
     }
+    v[27] = pis * (d0 * Pd[0] + d1 * Pd[1] + d2 * Pd[2]);
     (void)M0;
 }
 

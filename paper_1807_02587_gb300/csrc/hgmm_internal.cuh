@@ -37,6 +37,7 @@ constexpr int TILE = 256;             // points per build work item
 constexpr int EST_THREADS = 256;      // build E-step CTA
 constexpr int REG_THREADS = 256;      // registration descent CTA
 constexpr int MSTEP_THREADS = 128;    // registration M-step CTA
+constexpr int NTERM = 28;             // per-round sums: 21 of H, 6 of g, the objective
 constexpr int TRACE_MAX_ITERS = 64;   // rounds the registration trace can hold
 constexpr int ACC_REPLICAS = 1;       // copies of each node's registration moments
 
@@ -138,6 +139,7 @@ struct hgmm_tree {
     double* reg_T = nullptr;                // 16 doubles current T
     float* reg_Rt = nullptr;                // 12 floats (R row-major, t)
     double* reg_dbg = nullptr;              // nodes x 4 (last round)
+    double* reg_obj = nullptr;              // Eq. 11 objective of the last round
     // per-kernel timing and the registration's phase trace
     bool prof_on = false;
     bool trace_on = false;

@@ -28,7 +28,8 @@ namespace {
 __global__ void k_reg_init(const double* __restrict__ T_init, int n_nodes, float lam_c,
                            const NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
                            unsigned long long* __restrict__ acc, double* __restrict__ T,
-                           float* __restrict__ Rt, unsigned* __restrict__ bar) {
+                           float* __restrict__ Rt, unsigned* __restrict__ bar,
+                           double* __restrict__ obj) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_nodes) {
         for (int k = 0; k < 4 * ACC_REPLICAS; ++k) acc[4 * ACC_REPLICAS * int64_t(i) + k] = 0ull;
@@ -43,6 +44,7 @@ __global__ void k_reg_init(const double* __restrict__ T_init, int n_nodes, float
         }
         bar[0] = 0u;
         bar[2] = 0u;
+        *obj = 0.0;
     }
 }
 
@@ -61,6 +63,7 @@ struct RegArgs {
     double* T;
     float* Rt;
     double* T_hist;
+    double* obj;        // Eq. 11 objective of the latest round (pose before its update)
     double* dbg;
     int* status;
     unsigned long long* trace;  // optional: [iter][cta][TRACE_EVENTS] globaltimer ns
@@ -81,16 +84,16 @@ __device__ __forceinline__ void trace_mark(unsigned long long* tr, int it, int e
 // The whole registration loop in one cooperative launch.  Per round:
 //   A. Algorithm 1 for every source point (fixed-point node moments)
 //   -- grid barrier --
-//   B. per node with mass: its 27 normal-equation terms (FP32), compensated
+//   B. per node with mass: its normal-equation and objective terms (FP32), compensated
 //      block sums -> one partial per CTA; the last CTA to finish
 //   C. reduces the partials in a fixed order, solves the 6x6 system in FP64
 //      and composes T <- dT T
 //   -- grid barrier --  (everyone reads the new T)
 __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     __shared__ float Rt_sm[12];
-    __shared__ float2 sm[REG_THREADS / 32][27];
-    __shared__ float2 fin[8][27];
-    __shared__ double tot[27];
+    __shared__ float2 sm[REG_THREADS / 32][NTERM];
+    __shared__ float2 fin[8][NTERM];
+    __shared__ double tot[NTERM];
     __shared__ double Lsm[6][6];
     __shared__ bool last;
     __shared__ float4 sm_est[3 * STAGED_NODES];
@@ -116,9 +119,9 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
         // ---- B: node terms (only the CTAs that own nodes take part)
         const int nb_nodes = (a.n_nodes + blockDim.x - 1) / blockDim.x;
         if (blockIdx.x < nb_nodes) {
-        float v[27], c[27];
+        float v[NTERM], c[NTERM];
 #pragma unroll
-        for (int k = 0; k < 27; ++k) { v[k] = 0.f; c[k] = 0.f; }
+        for (int k = 0; k < NTERM; ++k) { v[k] = 0.f; c[k] = 0.f; }
         double* dbg = it == a.iters - 1 ? a.dbg : nullptr;
         for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_nodes; g += nb_nodes * blockDim.x) {
             long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
             const float4 cm = a.est[g].a;
             float M0 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
             if (a0 > 0) {
-                float w[27];
+                float w[NTERM];
                 M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
                 const float inv = 1.0f / (qscale * M0);
                 o0 = float(a1) * inv;
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
                 node_terms(a.rnode[3 * g], a.rnode[3 * g + 1], a.rnode[3 * g + 2], cm, M0, o0, o1,
                            o2, M0 / float(a.n), w);
 #pragma unroll
-                for (int k = 0; k < 27; ++k) pair_add(v[k], c[k], w[k], 0.f);
+                for (int k = 0; k < NTERM; ++k) pair_add(v[k], c[k], w[k], 0.f);
             }
             if (dbg) {
                 dbg[4 * g + 0] = double(a0) * INV_FIX;
@@ -168,18 +171,18 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int k = 0; k < 27; ++k) {
+            for (int k = 0; k < NTERM; ++k) {
                 const float s2 = __shfl_xor_sync(FULL, v[k], off);
                 const float c2 = __shfl_xor_sync(FULL, c[k], off);
                 pair_add(v[k], c[k], s2, c2);
             }
         if (lane == 0)
-            for (int k = 0; k < 27; ++k) sm[warp][k] = make_float2(v[k], c[k]);
+            for (int k = 0; k < NTERM; ++k) sm[warp][k] = make_float2(v[k], c[k]);
         __syncthreads();
-        if (threadIdx.x < 27) {
+        if (threadIdx.x < NTERM) {
             float S = 0.f, C = 0.f;
             for (int w = 0; w < REG_THREADS / 32; ++w) pair_add(S, C, sm[w][threadIdx.x].x, sm[w][threadIdx.x].y);
-            a.part[27 * blockIdx.x + threadIdx.x] = make_float2(S, C);
+            a.part[NTERM * blockIdx.x + threadIdx.x] = make_float2(S, C);
         }
         __threadfence();
         __syncthreads();
@@ -190,32 +193,33 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
             // ---- C: fixed-order reduction, FP64 solve, pose update
             __threadfence();
             const int nb = nb_nodes;
-            // all partial loads in flight at once (8 groups of 27 threads),
+            // all partial loads in flight at once (8 groups of NTERM threads),
             // then a fixed-order combine
-            if (threadIdx.x < 216) {
-                const int k = threadIdx.x % 27, q = threadIdx.x / 27;
+            if (threadIdx.x < 8 * NTERM) {
+                const int k = threadIdx.x % NTERM, q = threadIdx.x / NTERM;
                 float S = 0.f, C = 0.f;
                 float2 xs[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int b = q + 8 * j;
-                    xs[j] = b < nb ? __ldcg(&a.part[27 * b + k]) : make_float2(0.f, 0.f);
+                    xs[j] = b < nb ? __ldcg(&a.part[NTERM * b + k]) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) pair_add(S, C, xs[j].x, xs[j].y);
                 for (int b = q + 64; b < nb; b += 8) {
-                    const float2 x = __ldcg(&a.part[27 * b + k]);
+                    const float2 x = __ldcg(&a.part[NTERM * b + k]);
                     pair_add(S, C, x.x, x.y);
                 }
                 fin[q][k] = make_float2(S, C);
             }
             __syncthreads();
-            if (threadIdx.x < 27) {
+            if (threadIdx.x < NTERM) {
                 float S = 0.f, C = 0.f;
                 for (int q = 0; q < 8; ++q) pair_add(S, C, fin[q][threadIdx.x].x, fin[q][threadIdx.x].y);
                 tot[threadIdx.x] = double(S) + double(C);
             }
             __syncthreads();
+            if (threadIdx.x == 32 && a.obj) *a.obj = tot[NTERM - 1];
             if (warp == 0) {
                 const bool solved = warp_solve_update(tot, Lsm, a.T, a.Rt, a.T_hist, it);
                 if (!solved && lane == 0) {
@@ -271,7 +275,7 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         ProfScope ps_(t, K_REG_INIT, s);
         k_reg_init<<<(n_nodes + 255) / 256, 256, 0, s>>>(T_init, n_nodes, lam_c, t->stat, t->est,
                                                           t->reg_acc, t->reg_T, t->reg_Rt,
-                                                          t->reg_bar);
+                                                          t->reg_bar, t->reg_obj);
     }
     if (iters > 0) {
         RegArgs a;
@@ -290,6 +294,7 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         a.Rt = t->reg_Rt;
         a.T_hist = T_hist;
         a.dbg = t->reg_dbg;
+        a.obj = t->reg_obj;
         a.status = t->status;
         a.trace = (t->trace_on && iters <= TRACE_MAX_ITERS) ? t->trace : nullptr;
         if (a.trace) cudaMemsetAsync(t->trace, 0, size_t(iters) * t->reg_grid * TRACE_EVENTS * 8, s);

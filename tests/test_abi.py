@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point
-declared in include/hgmm.h (no GPU needed: nothing here launches a kernel)."""
+declared in include/*.h (no GPU needed: nothing here launches a kernel)."""
 import ctypes
 import os
 import re
@@ -12,7 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared_functions():
-    txt = open(os.path.join(ROOT, "include", "hgmm.h")).read()
+    inc = os.path.join(ROOT, "include")
+    txt = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s+(hgmm_[a-z_0-9]+)\s*\(", txt, flags=re.M)
     return sorted(set(names))
@@ -28,7 +29,10 @@ def test_header_declares_the_boundary():
     names = _declared_functions()
     for must in ["hgmm_build", "hgmm_register", "hgmm_tree_create", "hgmm_tree_destroy",
                  "hgmm_tree_export", "hgmm_debug_labels", "hgmm_debug_reg_moments",
-                 "hgmm_register_pair_host", "hgmm_sync", "hgmm_strerror"]:
+                 "hgmm_register_pair_host", "hgmm_sync", "hgmm_strerror",
+                 "hgmm_batch_register", "hgmm_batch_features", "hgmm_mlp_forward",
+                 "hgmm_mlp_train_step", "hgmm_pose_decode", "hgmm_pose_select",
+                 "hgmm_register_objective"]:
         assert must in names
 
 
@@ -56,6 +60,18 @@ def test_host_side_argument_checks(lib):
     assert B._lib.hgmm_register(None, None, 100, None, 3, -1.0, None, None, None) == B.HGMM_EINVAL
     for code in range(0, -8, -1):
         assert B.strerror(code) != "unknown error"
+    # proposal entry points: rejected before any CUDA call
+    assert B._lib.hgmm_mlp_create(0, ctypes.byref(h)) == B.HGMM_EINVAL
+    assert B._lib.hgmm_mlp_create(1 << 20, ctypes.byref(h)) == B.HGMM_EINVAL
+    assert B._lib.hgmm_mlp_forward(None, None, 4, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_mlp_gradients(None, None, None, None, 4, 4, 1.0, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_pose_decode(None, None, 4, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_pose_encode(None, None, 4, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_pose_select(0, None, None, None, None, None, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_tree_features(None, None, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_batch_features(None, None, None, None, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_register_objective(None, None, None) == B.HGMM_EINVAL
+    assert B.HGMM_MLP_PARAMS == 256 * 1280 + 256 + 256 * 256 + 256 + 9 * 256 + 9
 
 
 def test_build_is_sm103a_only():
