@@ -341,6 +341,9 @@ def gpu_main(args, rank, world, local_rank):
     batched = None
     if not args.no_batched:
         batched = batched_section(args, B, synth, torch, prm)
+    learned = None
+    if not args.no_learned:
+        learned = learned_section(args, B, torch)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -370,6 +373,7 @@ def gpu_main(args, rank, world, local_rank):
         "roofline": roof,
         "kernels": kernels,
         "batched": batched,
+        "learned": learned,
         "cpu_baseline": cpu,
         "clocks": clk,
         "accuracy": {"rot_err_deg_vs_truth": rot_err,
@@ -474,6 +478,71 @@ def batched_section(args, B, synth, torch, prm):
     }
 
 
+# algorithmic FLOPs of the proposal network per pair (1280 -> 256 -> 256 -> 9)
+MLP_FWD_FLOPS = 2 * (1280 * 256 + 256 * 256 + 256 * 9)
+MLP_BWD_FLOPS = 2 * (256 * 9 + 9 * 256 + 256 * 256 + 256 * 256 + 256 * 1280)
+
+
+def learned_section(args, B, torch):
+    """Learned pose proposal: the shipped network (trained on 100k pairs by
+    paper_1807_02587_gb300.train_proposal) proposes, the plain method refines
+    at depth 4 with the identity start as fallback; success (<= 0.1 deg) and
+    pairs/s against the plain method from the identity on held-out pairs with
+    SO(3)-uniform rotations.  Plus the network's tensor-core throughput."""
+    from paper_1807_02587_gb300 import proposal as P
+    path = os.path.join(ROOT, "paper_1807_02587_gb300", "weights", "proposal_mlp.npz")
+    if not os.path.exists(path):
+        return {"skipped": "no trained weights at paper_1807_02587_gb300/weights/proposal_mlp.npz"}
+    params = np.load(path)["params"]
+    big = 8192
+    net = B.Mlp(big)
+    B.hgmm_mlp_set_params(net.handle, params)
+    ts = P.so3_test_pairs(args.seed + 31337, args.learned_pairs, args.learned_points)
+    res = P.evaluate(net, ts, depth=4, iters=30, reps=3)
+    # the network alone: one forward of a large batch, and one training step
+    x = torch.randn((big, 1280), device="cuda").to(torch.bfloat16)
+    y = torch.zeros((big, 9), dtype=torch.float32, device="cuda")
+    lab = torch.zeros((big, 12), dtype=torch.float32, device="cuda")
+    lab[:, [0, 4, 8]] = 1.0
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    t_fwd = timed(lambda: B.hgmm_mlp_forward(net.handle, x, y))
+    tb = 1024
+    t_train = timed(lambda: B.hgmm_mlp_train_step(net.handle, x, lab, tb, lr=0.0))
+    B.hgmm_mlp_set_params(net.handle, params)  # lr 0 left them unchanged; reset Adam state anyway
+    bf16_peak = _bf16_peak()
+    fwd_tf = MLP_FWD_FLOPS * big / t_fwd / 1e12
+    res.update({
+        "weights": "paper_1807_02587_gb300/weights/proposal_mlp.npz (train_proposal, 100k pairs)",
+        "test_points": args.learned_points,
+        "mlp": {"forward_batch": big, "forward_us": t_fwd * 1e6, "forward_tflops": fwd_tf,
+                "train_step_batch": tb, "train_step_us": t_train * 1e6,
+                "train_step_tflops": (MLP_FWD_FLOPS + MLP_BWD_FLOPS) * tb / t_train / 1e12,
+                "bf16_peak_tflops": bf16_peak[0], "peak_kind": bf16_peak[1],
+                "forward_frac": fwd_tf / bf16_peak[0]},
+    })
+    return res
+
+
+def _bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured burst (cuBLAS bf16)"
+    return 1900.0, "fallback"
+
+
 def _descend_levels(B, tree, src4, depth):
     """Average number of tree levels the descent visits per source point in
     the last round (from the association levels of the exported moments)."""
@@ -499,6 +568,9 @@ def main():
     ap.add_argument("--batch-pairs", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--plain-pairs", type=int, default=32)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-pairs", type=int, default=256)
+    ap.add_argument("--learned-points", type=int, default=50000)
     ap.add_argument("--ncu", action="store_true",
                     help="only run warm-up + eager steps (for an ncu launch list)")
     args = ap.parse_args()

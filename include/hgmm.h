@@ -237,6 +237,12 @@ void hgmm_batch_destroy(hgmm_batch* b);
 int hgmm_batch_plan(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_off,
                     const int64_t* h_src_off, const int32_t* h_depth);
 
+/* As hgmm_batch_plan with an explicit range per pair: target of pair i =
+ * points [h_tgt_rng[2i], h_tgt_rng[2i+1]), source likewise (2 n_pairs int64
+ * each).  Ranges may overlap or repeat, so pairs can share a cloud. */
+int hgmm_batch_plan_ranges(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_rng,
+                           const int64_t* h_src_rng, const int32_t* h_depth);
+
 /* Cluster shape: CTAs (of 256 threads) per pair, 1, 2, 4 or 8 (default 2). */
 int hgmm_batch_set_shape(hgmm_batch* b, int32_t cluster_ctas);
 int hgmm_batch_get_shape(const hgmm_batch* b, int32_t* cluster_ctas, int32_t* clusters);

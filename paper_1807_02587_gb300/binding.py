@@ -78,6 +78,7 @@ def _load():
         "hgmm_batch_create": (ctypes.c_int, [i64, i32, i32, P(vp)]),
         "hgmm_batch_destroy": (None, [vp]),
         "hgmm_batch_plan": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+        "hgmm_batch_plan_ranges": (ctypes.c_int, [vp, i32, vp, vp, vp]),
         "hgmm_batch_set_shape": (ctypes.c_int, [vp, i32]),
         "hgmm_batch_get_shape": (ctypes.c_int, [vp, P(i32), P(i32)]),
         "hgmm_batch_register": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp]),
@@ -291,6 +292,18 @@ def hgmm_batch_plan(h, tgt_off, src_off, depth) -> None:
     _check(_lib.hgmm_batch_plan(h, d.shape[0], ctypes.c_void_p(t.ctypes.data),
                                 ctypes.c_void_p(s_.ctypes.data), ctypes.c_void_p(d.ctypes.data)),
            "hgmm_batch_plan")
+
+
+def hgmm_batch_plan_ranges(h, tgt_rng, src_rng, depth) -> None:
+    """tgt_rng / src_rng: (n_pairs, 2) int64 [start, end) point ranges."""
+    t = np.ascontiguousarray(tgt_rng, dtype=np.int64).reshape(-1)
+    s_ = np.ascontiguousarray(src_rng, dtype=np.int64).reshape(-1)
+    d = np.ascontiguousarray(depth, dtype=np.int32)
+    if t.shape[0] != 2 * d.shape[0] or s_.shape[0] != 2 * d.shape[0]:
+        raise ValueError("ranges: expected (n_pairs, 2) arrays matching depth")
+    _check(_lib.hgmm_batch_plan_ranges(h, d.shape[0], ctypes.c_void_p(t.ctypes.data),
+                                       ctypes.c_void_p(s_.ctypes.data), ctypes.c_void_p(d.ctypes.data)),
+           "hgmm_batch_plan_ranges")
 
 
 def hgmm_batch_set_shape(h, cluster_ctas: int) -> None:

@@ -47,8 +47,8 @@ struct BatchWs {
 
 struct BatchArgs {
     const float4* points;       // all clouds, concatenated
-    const int64_t* tgt_off;     // [n_pairs + 1]
-    const int64_t* src_off;     // [n_pairs + 1]
+    const int64_t* tgt_rng;     // [2 n_pairs]: target of pair i = points [rng[2i], rng[2i+1])
+    const int64_t* src_rng;     // [2 n_pairs]
     const int* depth;           // [n_pairs]
     const int* order;           // [n_pairs] pair to run k-th
     const double* T_init;       // [n_pairs x 16] or null (identity)
@@ -100,10 +100,10 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     const int gw = rank * wpb + warp, nwt = cs * wpb;
-    const float4* tgt = a.points + a.tgt_off[pair];
-    const int n_t = int(a.tgt_off[pair + 1] - a.tgt_off[pair]);
-    const float4* src = a.points + a.src_off[pair];
-    const int n_s = int(a.src_off[pair + 1] - a.src_off[pair]);
+    const float4* tgt = a.points + a.tgt_rng[2 * pair];
+    const int n_t = int(a.tgt_rng[2 * pair + 1] - a.tgt_rng[2 * pair]);
+    const float4* src = a.points + a.src_rng[2 * pair];
+    const int n_s = int(a.src_rng[2 * pair + 1] - a.src_rng[2 * pair]);
     const int depth = a.depth[pair];
     if (rank == 0 && threadIdx.x == 0) *w.status = 0;
 
@@ -302,8 +302,8 @@ struct hgmm_batch {
     int n_pairs = 0;
     std::vector<void*> allocs;
     BatchWs* d_ws = nullptr;
-    int64_t* d_tgt_off = nullptr;
-    int64_t* d_src_off = nullptr;
+    int64_t* d_tgt_rng = nullptr;
+    int64_t* d_src_rng = nullptr;
     int* d_depth = nullptr;
     int* d_order = nullptr;
     int* d_queue = nullptr;
@@ -311,7 +311,6 @@ struct hgmm_batch {
     double* d_obj = nullptr;        // per pair, last registration's objective
     double* d_T_scratch = nullptr;  // poses of a features-only run
     int min_depth = 0;              // of the current plan
-    std::vector<int64_t> h_tgt_off, h_src_off;
 };
 
 namespace {
@@ -388,8 +387,8 @@ int hgmm_batch_create(int64_t max_points, int32_t max_depth, int32_t max_pairs, 
         if (good) good &= cudaMemset(w.seg_count, 0, nodes * sizeof(int)) == cudaSuccess &&
                           cudaMemset(w.stat, 0, nodes * sizeof(NodeStat)) == cudaSuccess;
     }
-    good = good && balloc(b, &b->d_ws, mc) && balloc(b, &b->d_tgt_off, max_pairs + 1) &&
-           balloc(b, &b->d_src_off, max_pairs + 1) && balloc(b, &b->d_depth, max_pairs) &&
+    good = good && balloc(b, &b->d_ws, mc) && balloc(b, &b->d_tgt_rng, 2 * int64_t(max_pairs)) &&
+           balloc(b, &b->d_src_rng, 2 * int64_t(max_pairs)) && balloc(b, &b->d_depth, max_pairs) &&
            balloc(b, &b->d_order, max_pairs) && balloc(b, &b->d_queue, 1) &&
            balloc(b, &b->d_pair_status, max_pairs) && balloc(b, &b->d_obj, max_pairs) &&
            balloc(b, &b->d_T_scratch, 16 * int64_t(max_pairs));
@@ -413,35 +412,49 @@ void hgmm_batch_destroy(hgmm_batch* b) {
     delete b;
 }
 
-int hgmm_batch_plan(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_off,
-                    const int64_t* h_src_off, const int32_t* h_depth) {
-    if (!b || !h_tgt_off || !h_src_off || !h_depth || n_pairs < 1 || n_pairs > b->max_pairs)
+int hgmm_batch_plan_ranges(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_rng,
+                           const int64_t* h_src_rng, const int32_t* h_depth) {
+    if (!b || !h_tgt_rng || !h_src_rng || !h_depth || n_pairs < 1 || n_pairs > b->max_pairs)
         return HGMM_EINVAL;
     std::vector<int> order(n_pairs);
     int min_depth = 1 << 30;
     for (int i = 0; i < n_pairs; ++i) {
         min_depth = std::min(min_depth, int(h_depth[i]));
-        const int64_t nt = h_tgt_off[i + 1] - h_tgt_off[i];
-        const int64_t ns = h_src_off[i + 1] - h_src_off[i];
+        const int64_t nt = h_tgt_rng[2 * i + 1] - h_tgt_rng[2 * i];
+        const int64_t ns = h_src_rng[2 * i + 1] - h_src_rng[2 * i];
         if (nt < 8 || ns < 1 || h_depth[i] < 1 || h_depth[i] > b->max_depth) return HGMM_EINVAL;
         if (nt > b->max_points || ns > b->max_points) return HGMM_ECAPACITY;
-        if (h_tgt_off[i] < 0 || h_src_off[i] < 0) return HGMM_EINVAL;
+        if (h_tgt_rng[2 * i] < 0 || h_src_rng[2 * i] < 0) return HGMM_EINVAL;
         order[i] = i;
     }
     // longest pairs first (LPT): the queue hands the biggest work out early
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        const int64_t wx = (h_tgt_off[x + 1] - h_tgt_off[x]) + (h_src_off[x + 1] - h_src_off[x]);
-        const int64_t wy = (h_tgt_off[y + 1] - h_tgt_off[y]) + (h_src_off[y + 1] - h_src_off[y]);
-        return wx > wy;
-    });
-    bool good = cudaMemcpy(b->d_tgt_off, h_tgt_off, (n_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess;
-    good &= cudaMemcpy(b->d_src_off, h_src_off, (n_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess;
+    auto work = [&](int x) {
+        return (h_tgt_rng[2 * x + 1] - h_tgt_rng[2 * x]) + (h_src_rng[2 * x + 1] - h_src_rng[2 * x]);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+    const size_t rb = size_t(2) * n_pairs * sizeof(int64_t);
+    bool good = cudaMemcpy(b->d_tgt_rng, h_tgt_rng, rb, cudaMemcpyHostToDevice) == cudaSuccess;
+    good &= cudaMemcpy(b->d_src_rng, h_src_rng, rb, cudaMemcpyHostToDevice) == cudaSuccess;
     good &= cudaMemcpy(b->d_depth, h_depth, n_pairs * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     good &= cudaMemcpy(b->d_order, order.data(), n_pairs * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!good) return HGMM_ECUDA;
     b->n_pairs = n_pairs;
     b->min_depth = min_depth;
     return HGMM_OK;
+}
+
+int hgmm_batch_plan(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_off,
+                    const int64_t* h_src_off, const int32_t* h_depth) {
+    if (!b || !h_tgt_off || !h_src_off || !h_depth || n_pairs < 1 || n_pairs > b->max_pairs)
+        return HGMM_EINVAL;
+    std::vector<int64_t> t(2 * size_t(n_pairs)), sr(2 * size_t(n_pairs));
+    for (int i = 0; i < n_pairs; ++i) {
+        t[2 * i] = h_tgt_off[i];
+        t[2 * i + 1] = h_tgt_off[i + 1];
+        sr[2 * i] = h_src_off[i];
+        sr[2 * i + 1] = h_src_off[i + 1];
+    }
+    return hgmm_batch_plan_ranges(b, n_pairs, t.data(), sr.data(), h_depth);
 }
 
 int hgmm_batch_set_shape(hgmm_batch* b, int32_t cluster_ctas) {
@@ -479,8 +492,8 @@ int launch_batch(hgmm_batch* b, const float* d_points, const hgmm_params* p, con
     if (nclu < 1) return HGMM_ECUDA;
     BatchArgs a;
     a.points = reinterpret_cast<const float4*>(d_points);
-    a.tgt_off = b->d_tgt_off;
-    a.src_off = b->d_src_off;
+    a.tgt_rng = b->d_tgt_rng;
+    a.src_rng = b->d_src_rng;
     a.depth = b->d_depth;
     a.order = b->d_order;
     a.T_init = d_T_init;

@@ -85,9 +85,10 @@ def _rel(a, b):
 
 def test_forward_matches_oracle(B):
     """Against the oracle with the same BF16 storage points: FP32 against
-    FP64 accumulation only (~1e-5).  Against the plain FP64 oracle: each
-    layer input rounded to BF16 moves its output by ~2^-9 relative, so the
-    outputs agree to ~1e-2 (norm-wise) and no worse."""
+    FP64 accumulation, plus the hidden values whose two sums straddle a BF16
+    rounding tie and so land one BF16 step apart (~2e-4 norm-wise here).
+    Against the plain FP64 oracle: each layer input rounded to BF16 moves its
+    output by ~2^-9 relative, so the outputs agree to ~1e-2 and no worse."""
     import torch
     p = _params(1)
     X, _ = _batch(2, 300)
@@ -101,7 +102,7 @@ def test_forward_matches_oracle(B):
     emu, _ = M.forward(p.astype(np.float64), X, act_bf16=True)
     got = y.cpu().numpy()
     print("vs bf16-storage oracle", _rel(got, emu), "vs fp64 oracle", _rel(got, ref))
-    assert _rel(got, emu) < 1e-4, _rel(got, emu)
+    assert _rel(got, emu) < 1e-3, _rel(got, emu)
     assert _rel(got, ref) < 1e-2, _rel(got, ref)
     assert np.max(np.abs(got - ref)) < 5e-2 * np.sqrt(np.mean(ref ** 2))
 
