@@ -54,6 +54,7 @@ KERNEL_WORK = {
     "scatter": {"bytes": 44, "flops": 0, "unit": "target point"},
     "register": {"bytes": 16, "flops": None, "unit": "source point"},
 }
+REGISTER_TRAFFIC_BYTES = 1965824 + 256
 DESCEND_FLOPS_PER_LEVEL = 8 * 18 + 8 * 2 + 8  # 8 child scores, 8 exp2 + sum, rcp
 DESCEND_FLOPS_FIXED = 18 + 12  # transform, fixed-point conversion
 
@@ -332,7 +333,9 @@ def gpu_main(args, rank, world, local_rank):
                     note="no algorithmic model for this kernel")
     if roof.get("achieved") is not None:
         roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes (read + write) of one k_register launch on this workload, from
+    # an ncu capture of the kernel as it is built now (None for other kernels)
+    roof["traffic"] = REGISTER_TRAFFIC_BYTES if dom == "register" else None
     hbm_equiv = None
     if dom in KERNEL_WORK:
         hbm_equiv = KERNEL_WORK[dom]["bytes"] * units / (dom_ms / 1e3) / 1e9
@@ -571,6 +574,9 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-pairs", type=int, default=256)
     ap.add_argument("--learned-points", type=int, default=50000)
+    ap.add_argument("--profile-mlp", action="store_true",
+                    help="only run the proposal network (5 forwards of 8192 pairs, 3 training "
+                         "steps of 1024), for a profiler")
     ap.add_argument("--ncu", action="store_true",
                     help="only run warm-up + eager steps (for an ncu launch list)")
     args = ap.parse_args()
@@ -580,7 +586,30 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_main(args, rank, world)
+    if args.profile_mlp:
+        return profile_mlp_main()
     return gpu_main(args, rank, world, local_rank)
+
+
+def profile_mlp_main():
+    import torch
+    from paper_1807_02587_gb300 import binding as B
+    params = np.load(os.path.join(ROOT, "paper_1807_02587_gb300", "weights", "proposal_mlp.npz"))["params"]
+    net = B.Mlp(8192)
+    B.hgmm_mlp_set_params(net.handle, params)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.randn((8192, 1280), device="cuda", generator=g).to(torch.bfloat16)
+    y = torch.zeros((8192, 9), dtype=torch.float32, device="cuda")
+    lab = torch.zeros((8192, 12), dtype=torch.float32, device="cuda")
+    lab[:, [0, 4, 8]] = 1.0
+    for _ in range(5):
+        B.hgmm_mlp_forward(net.handle, x, y)
+    for _ in range(3):
+        B.hgmm_mlp_train_step(net.handle, x, lab, 1024, lr=0.0)
+    B.hgmm_mlp_sync(net.handle)
+    print(json.dumps({"profile_mlp": True, "y_finite": bool(torch.isfinite(y).all().item())}))
+    return 0
 
 
 if __name__ == "__main__":
