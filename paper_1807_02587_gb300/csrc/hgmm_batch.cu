@@ -86,7 +86,6 @@ struct RegSmem {
     float Rt[12];
     float2 sm[EST_THREADS / 32][NTERM];
     double tot[NTERM];
-    double Lsm[6][6];
     double fsm[FRAME_DOUBLES];
     float4 est[3 * STAGED_NODES];
 };
@@ -198,9 +197,9 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
         __syncthreads();
         descend_points(src, n_s, w.est, rgs.est, depth, rgs.Rt, qscale, w.acc, rank, cs);
         cl.sync();
-        float v[NTERM], c[NTERM];
+        float v[32], c[32];  // NTERM terms, padded to a warp's width
 #pragma unroll
-        for (int k = 0; k < NTERM; ++k) { v[k] = 0.f; c[k] = 0.f; }
+        for (int k = 0; k < 32; ++k) { v[k] = 0.f; c[k] = 0.f; }
         for (int g = rank * blockDim.x + threadIdx.x; g < n_nodes; g += cs * blockDim.x) {
             const long long a0 = (long long)__ldcg(w.acc + 4 * g + 0);
             if (a0 == 0) continue;
@@ -220,16 +219,11 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
 #pragma unroll
             for (int k = 0; k < NTERM; ++k) pair_add(v[k], c[k], tn[k], 0.f);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int k = 0; k < NTERM; ++k) {
-                const float s2 = __shfl_xor_sync(FULL, v[k], off);
-                const float c2 = __shfl_xor_sync(FULL, c[k], off);
-                pair_add(v[k], c[k], s2, c2);
-            }
-        if (lane == 0)
-            for (int k = 0; k < NTERM; ++k) rgs.sm[warp][k] = make_float2(v[k], c[k]);
+        {
+            float ws, we;
+            warp_reduce_scatter32(v, c, ws, we);
+            if (lane < NTERM) rgs.sm[warp][lane] = make_float2(ws, we);
+        }
         __syncthreads();
         if (threadIdx.x < NTERM) {
             float S = 0.f, C = 0.f;
@@ -249,7 +243,7 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
             __syncthreads();
             if (threadIdx.x == 32 && a.obj && it == a.iters - 1) a.obj[pair] = rgs.tot[NTERM - 1];
             if (warp == 0) {
-                const bool solved = warp_solve_update(rgs.tot, rgs.Lsm, w.T, w.Rt, nullptr, it);
+                const bool solved = warp_solve_update(rgs.tot, w.T, w.Rt, nullptr, it);
                 if (!solved && lane == 0) atomicOr(w.status, ST_DEGENERATE);
             }
         }

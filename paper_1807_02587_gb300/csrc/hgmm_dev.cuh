@@ -894,10 +894,17 @@ __device__ __forceinline__ void load_node(const NodeEst* __restrict__ est, const
     }
 }
 
+// hist (shared memory, 4 x STAGED_NODES fixed-point words, zero on entry, or
+// null): the groups whose node is one of the staged top levels add into the
+// CTA's own histogram instead of global memory; flush_node_hist then moves it
+// to the global accumulators with one atomic per touched word.  The top
+// levels are where most points stop on large planar structures, so this
+// keeps thousands of warps from serialising on a few hot addresses.
 __device__ __forceinline__ void descend_points(const float4* __restrict__ src, int n,
                                                const NodeEst* __restrict__ est, const float4* sm_est,
                                                int depth, const float* Rt_sm, float qscale,
-                                               unsigned long long* __restrict__ acc, int cta, int ncta) {
+                                               unsigned long long* __restrict__ acc, int cta, int ncta,
+                                               unsigned long long* hist = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float r00 = Rt_sm[0], r01 = Rt_sm[1], r02 = Rt_sm[2], r10 = Rt_sm[3], r11 = Rt_sm[4];
     const float r12 = Rt_sm[5], r20 = Rt_sm[6], r21 = Rt_sm[7], r22 = Rt_sm[8];
@@ -920,6 +927,7 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             float best = -CUDART_INF_F;
             int bi = -1;
 #pragma unroll
+            float bx = 0.f, by = 0.f, bz = 0.f, bstop = 0.f;  // the best child's mean, stop flag
             for (int c = 0; c < 8; ++c) {
                 float4 ea, eb, ec;
                 load_node(est, sm_est, first + c, ea, eb, ec);
@@ -931,7 +939,14 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
                 sc = fmaf(-d1, d1, sc);
                 sc = fmaf(-d2, d2, sc);
                 sc8[c] = sc;
-                if (sc > best) { best = sc; bi = c; }
+                if (sc > best) {
+                    best = sc;
+                    bi = c;
+                    bx = ea.x;
+                    by = ea.y;
+                    bz = ea.z;
+                    bstop = ec.z;
+                }
             }
             if (bi < 0) break;  // the current node has no live children
             float sum = 0.f;
@@ -940,10 +955,8 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             gamma = 1.0f / sum;
             chosen = int(first + bi);
             local = 8 * local + bi;
-            float4 ea, eb, ec;
-            load_node(est, sm_est, chosen, ea, eb, ec);
-            cmx = ea.x; cmy = ea.y; cmz = ea.z;
-            if (ec.z != 0.f) break;  // Complexity <= lambda_c
+            cmx = bx; cmy = by; cmz = bz;
+            if (bstop != 0.f) break;  // Complexity <= lambda_c
         }
         // Sum (gamma, gamma (z' - mu_j)) over the lanes of this warp that chose
         // the same node j: a pairwise tree over the members' ranks (fixed order,
@@ -973,14 +986,29 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             }
         }
         if (has && rank == 0) {
-            // one of ACC_REPLICAS copies per CTA spreads the atomics on hot
-            // nodes (a ground plane collects a large share of the points)
             unsigned long long* dst =
-                acc + 4 * (int64_t(chosen) * ACC_REPLICAS + (cta & (ACC_REPLICAS - 1)));
+                (hist && chosen < STAGED_NODES)
+                    ? hist + 4 * chosen
+                    : acc + 4 * (int64_t(chosen) * ACC_REPLICAS + (cta & (ACC_REPLICAS - 1)));
             atomicAdd(dst + 0, (unsigned long long)to_fix(v0 * 4294967296.0f));
             atomicAdd(dst + 1, (unsigned long long)to_fix(v1 * qscale));
             atomicAdd(dst + 2, (unsigned long long)to_fix(v2 * qscale));
             atomicAdd(dst + 3, (unsigned long long)to_fix(v3 * qscale));
+        }
+    }
+}
+
+// Add the CTA's histogram of the staged levels to the global accumulators
+// (integer adds: exact and order-free) and clear it.  Call after a
+// __syncthreads that follows descend_points.
+__device__ __forceinline__ void flush_node_hist(unsigned long long* hist, int n_staged,
+                                                unsigned long long* __restrict__ acc) {
+    static_assert(ACC_REPLICAS == 1, "one accumulator copy per node");
+    for (int i = threadIdx.x; i < 4 * n_staged; i += blockDim.x) {
+        const unsigned long long v = hist[i];
+        if (v) {
+            atomicAdd(acc + i, v);
+            hist[i] = 0ull;
         }
     }
 }
@@ -1037,61 +1065,125 @@ __device__ __forceinline__ void node_terms(const float4 p0, const float4 p1, con
     (void)M0;
 }
 
-// FP64 solve of the 6x6 normal equations and the pose update by one warp.
-// Lane i < 6 owns row i; the right-looking Cholesky updates all rows with
-// one instruction per column, so the FP64 instruction count of the critical
-// path (~70 cycles each on this part) is about a third of a one-thread
-// solve.  L is kept in shared memory for the back substitution.  Returns
-// false (uniformly) for a non-positive pivot.
-__device__ inline bool warp_solve_update(const double* tot, double (*Lsm)[6], double* T,
-                                  float* Rt, double* T_hist, int iter) {
+// One level of a warp reduce-scatter of 32 compensated (sum, error) pairs:
+// the lane keeps the half of its 2*O-long valid prefix selected by
+// bit O of its lane index and adds the partner's copy of that half.
+template <int O>
+__device__ __forceinline__ void rs_level(float (&v)[32], float (&c)[32], int lane) {
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < O; ++i) {
+        const float ss = up ? v[i] : v[i + O];
+        const float cs = up ? c[i] : c[i + O];
+        float sk = up ? v[i + O] : v[i];
+        float ck = up ? c[i + O] : c[i];
+        const float sr = __shfl_xor_sync(FULL, ss, O);
+        const float cr = __shfl_xor_sync(FULL, cs, O);
+        pair_add(sk, ck, sr, cr);
+        v[i] = sk;
+        c[i] = ck;
+    }
+}
+
+// Warp totals of 32 per-lane (sum, error) pairs (term t in v[t], c[t]): after
+// the five levels lane l holds the warp total of term l in (s, e).  31 pair
+// additions per lane instead of 160 for a butterfly over every term; the
+// tree over lanes is fixed, so the result is deterministic.
+__device__ __forceinline__ void warp_reduce_scatter32(float (&v)[32], float (&c)[32], float& s, float& e) {
     const int lane = threadIdx.x & 31;
-    const int row = lane < 6 ? lane : 5;
-    auto H = [&](int i, int j) {  // upper-packed 21 entries
-        if (i > j) { const int t = i; i = j; j = t; }
-        return tot[i * 6 - (i * (i - 1)) / 2 + (j - i)];
-    };
-    double a[6];
+    rs_level<16>(v, c, lane);
+    rs_level<8>(v, c, lane);
+    rs_level<4>(v, c, lane);
+    rs_level<2>(v, c, lane);
+    rs_level<1>(v, c, lane);
+    s = v[0];
+    e = c[0];
+}
+
+__host__ __device__ constexpr int up6(int i, int j) { return i * 6 - (i * (i - 1)) / 2 + (j - i); }
+
+// FP64 solve of the 6x6 normal equations H x = g (Eq. 16) and the pose update
+// by one warp.  One FP64 warp instruction holds this part's FP64 pipe for ~70
+// cycles whatever the active mask, so the solve is laid out to issue few of
+// them: lane L < 21 holds upper-packed entry L of H, lanes 21..26 hold g (the
+// layout of tot), and symmetric Gaussian elimination without pivoting (H is
+// positive definite) updates every entry of the trailing block and of g with
+// one multiply and one FMA per pivot; back substitution runs on the g lanes.
+// Pivots are checked with integer compares of their bit patterns (positive,
+// finite, above 1e-15 of the largest diagonal).  T <- dR T + dt with dR from
+// Rodrigues' formula, all in FP64.  Returns false (uniformly) for a
+// non-positive or tiny pivot, leaving T unchanged.
+__device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt, double* T_hist,
+                                         int iter) {
+    const int lane = threadIdx.x & 31;
+    // (row, column) of this lane's entry; column 6 = right-hand side, row -1 = idle
+    int ri = -1, rj = 0;
+    if (lane < 21) {
+        int k = lane;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) a[j] = H(row, j);
-    double g = tot[21 + row];
-    double dmax = 0.0;
+        for (int i = 0; i < 6; ++i) {
+            if (ri < 0 && k < 6 - i) {
+                ri = i;
+                rj = i + k;
+            }
+            if (ri < 0) k -= 6 - i;
+        }
+    } else if (lane < 27) {
+        ri = lane - 21;
+        rj = 6;
+    }
+    double a = lane < 27 ? tot[lane] : 0.0;
+    // pivot threshold from the largest diagonal entry, in FP32
+    float dm = (ri >= 0 && rj == ri) ? float(a) : 0.f;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) dmax = fmax(dmax, H(j, j));
+    for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(FULL, dm, o));
+    const long long thr = __double_as_longlong(double(1e-15f * dm));
     double r[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const double dk = __shfl_sync(FULL, a[k], k);
-        if (!(dk > 1e-15 * dmax)) return false;
-        r[k] = rsqrt_f64(dk);
-        const double lik = a[k] * r[k];  // L_ik for rows i >= k
-        if (lane < 6) Lsm[k][lane] = lik;
-#pragma unroll
-        for (int j = k + 1; j < 6; ++j) {
-            const double ljk = __shfl_sync(FULL, lik, j);
-            a[j] = fma(-lik, ljk, a[j]);
+        const double p = __shfl_sync(FULL, a, up6(k, k));
+        const long long pb = __double_as_longlong(p);
+        if (!(pb > thr && pb < 0x7FF0000000000000LL)) return false;
+        // reciprocal: FP32 seed, two Newton steps (exponent kept inside the
+        // FP32 range by the guard; the rare outsider takes the division)
+        const int ex = int((pb >> 52) & 0x7FF) - 1023;
+        double rp;
+        if (ex > -120 && ex < 120) {
+            rp = double(__frcp_rn(float(p)));
+            rp = rp * fma(-p, rp, 2.0);
+            rp = rp * fma(-p, rp, 2.0);
+        } else {
+            rp = 1.0 / p;
         }
+        r[k] = rp;
+        const bool upd = ri > k;
+        const int s1 = upd ? up6(k, ri) : 0;
+        const int s2 = upd ? (rj < 6 ? up6(k, rj) : 21 + k) : 0;
+        const double aki = __shfl_sync(FULL, a, s1);
+        const double akj = __shfl_sync(FULL, a, s2);
+        const double f = aki * rp;
+        if (upd) a = fma(-f, akj, a);
     }
-    __syncwarp();
-    // forward: L y = g (column k: y_k = g_k r_k, then rows i > k lose L_ik y_k)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const double yk = __shfl_sync(FULL, g, k) * r[k];
-        if (lane == k) g = yk;
-        else if (lane > k) g = fma(-Lsm[k][row], yk, g);
-    }
-    // backward: L^T x = y (x_k = y_k r_k, then rows j < k lose L_kj x_k)
+    // back substitution: x_k = b'_k / U_kk, then b'_i -= U_ik x_k (i < k)
     double x[6];
 #pragma unroll
     for (int k = 5; k >= 0; --k) {
-        const double xk = __shfl_sync(FULL, g, k) * r[k];
+        const double xk = __shfl_sync(FULL, a, 21 + k) * r[k];
         x[k] = xk;
-        if (lane < k) g = fma(-Lsm[lane][k], xk, g);
+        const bool upd = rj == 6 && ri < k;
+        const double uik = __shfl_sync(FULL, a, upd ? up6(ri, k) : 0);
+        if (upd) a = fma(-uik, xk, a);
     }
-    // dT = (Rodrigues(w), t); lane e < 12 computes entry e of the new [R|t]
-    const double th2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    // dR = I + a K + b K^2 (Rodrigues), K = [w]x, K^2 = w w^T - |w|^2 I, in
+    // FP64: a and b must keep their exact trigonometric relation or dR drifts
+    // off the rotation group.  Lane e < 12 forms entry (r, c) of
+    // dR T + dt = T + a K T + b (w (w^T T) - |w|^2 T) + dt without forming dR.
+    const double th2 = fma(x[0], x[0], fma(x[1], x[1], x[2] * x[2]));
     double ca, cb;
-    if (th2 < 0.25) {
+    if (th2 < 1e-4) {  // series truncated after th2^2: error < th2^3 / 5040
+        ca = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120));
+        cb = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720));
+    } else if (th2 < 0.25) {
         ca = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880 +
              th2 * (-1.0 / 39916800 + th2 * (1.0 / 6227020800.0))))));
         cb = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720 + th2 * (-1.0 / 40320 + th2 * (1.0 / 3628800 +
@@ -1103,16 +1195,20 @@ __device__ inline bool warp_solve_update(const double* tot, double (*Lsm)[6], do
     }
     const int e = lane < 12 ? lane : 11;
     const int rr = e >> 2, cc = e & 3;
-    // row rr of dR = I + a K + b K^2, K = [w]x, (K^2)_{rm} = w_r w_m - |w|^2 delta_rm
-    const double kr[3] = {rr == 0 ? 0.0 : (rr == 1 ? x[2] : -x[1]),
-                          rr == 0 ? -x[2] : (rr == 1 ? 0.0 : x[0]),
-                          rr == 0 ? x[1] : (rr == 1 ? -x[0] : 0.0)};
-    double acc = cc == 3 ? x[3 + rr] : 0.0;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const double drm = (m == rr ? 1.0 - cb * th2 : 0.0) + ca * kr[m] + cb * x[rr] * x[m];
-        acc = fma(drm, __ldcg(T + m * 4 + cc), acc);
-    }
+    const double t0 = __ldcg(T + cc), t1 = __ldcg(T + 4 + cc), t2 = __ldcg(T + 8 + cc);
+    const double trc = rr == 0 ? t0 : (rr == 1 ? t1 : t2);
+    // (K T)_rc: row r of K = [w]x has one zero
+    const double ka = rr == 0 ? -x[2] : (rr == 1 ? x[2] : -x[1]);
+    const double kb = rr == 0 ? x[1] : (rr == 1 ? -x[0] : x[0]);
+    const double ta = rr == 0 ? t1 : t0;
+    const double tb = rr == 0 ? t2 : (rr == 1 ? t2 : t1);
+    const double kt = fma(ka, ta, kb * tb);
+    const double wt = fma(x[0], t0, fma(x[1], t1, x[2] * t2));  // (w^T T)_c
+    const double wr = rr == 0 ? x[0] : (rr == 1 ? x[1] : x[2]);
+    const double u = fma(wr, wt, -th2 * trc);
+    double acc = cc == 3 ? trc + x[3 + rr] : trc;
+    acc = fma(ca, kt, acc);
+    acc = fma(cb, u, acc);
     __syncwarp();
     if (lane < 12) {
         T[e] = acc;
@@ -1121,6 +1217,31 @@ __device__ inline bool warp_solve_update(const double* tot, double (*Lsm)[6], do
     }
     if (T_hist && lane >= 12 && lane < 16) T_hist[16 * iter + lane] = lane == 15 ? 1.0 : 0.0;
     return true;
+}
+
+// Thread 0 waits (bounded) until *word - target >= 0 (a monotonic counter or
+// generation), then the CTA proceeds; on timeout it records ST_TIMEOUT and
+// every thread of the CTA gets false.  The acquire side of a release made by
+// the CTA that advanced the word (a fence before its atomic or store).
+__device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned target, int* status,
+                                              long long limit) {
+    __shared__ int ok_wait;
+    if (threadIdx.x == 0) {
+        const volatile unsigned* v = word;
+        int ok = 1;
+        long long spins = 0;
+        while (int(*v - target) < 0) {
+            if (++spins > limit) {
+                atomicOr(status, ST_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        ok_wait = ok;
+    }
+    __syncthreads();
+    return ok_wait != 0;
 }
 
 // Bounded grid-wide barrier for a cooperative launch (all CTAs co-resident):

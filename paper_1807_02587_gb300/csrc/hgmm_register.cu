@@ -42,8 +42,8 @@ __global__ void k_reg_init(const double* __restrict__ T_init, int n_nodes, float
             for (int c = 0; c < 3; ++c) Rt[r * 3 + c] = float(T[r * 4 + c]);
             Rt[9 + r] = float(T[r * 4 + 3]);
         }
-        bar[0] = 0u;
-        bar[2] = 0u;
+        for (int k = 0; k < 8; ++k)
+            if (k != 1) bar[k] = 0u;  // bar[1] is a generation: any start value works
         *obj = 0.0;
     }
 }
@@ -70,6 +70,8 @@ struct RegArgs {
 };
 
 constexpr int TRACE_EVENTS = 6;
+constexpr size_t REG_DYN_SMEM = 3 * STAGED_NODES * sizeof(float4) + 4 * STAGED_NODES * sizeof(unsigned long long);
+static_assert(REG_DYN_SMEM <= 96 * 1024, "two k_register CTAs must fit on one SM");
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -83,27 +85,33 @@ __device__ __forceinline__ void trace_mark(unsigned long long* tr, int it, int e
 
 // The whole registration loop in one cooperative launch.  Per round:
 //   A. Algorithm 1 for every source point (fixed-point node moments)
-//   -- grid barrier --
+//   -- every CTA arrives on a counter; only the CTAs that own nodes wait --
 //   B. per node with mass: its normal-equation and objective terms (FP32), compensated
 //      block sums -> one partial per CTA; the last CTA to finish
-//   C. reduces the partials in a fixed order, solves the 6x6 system in FP64
-//      and composes T <- dT T
-//   -- grid barrier --  (everyone reads the new T)
+//   C. reduces the partials in a fixed order, solves the 6x6 system in FP64,
+//      composes T <- dT T and publishes the round number as the pose generation
+//   -- every CTA waits for that generation, then reads the new T --
+// All counters are monotonic over the launch (zeroed by k_reg_init), so no
+// CTA resets a word that another may still be reading; every wait is bounded.
 __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     __shared__ float Rt_sm[12];
     __shared__ float2 sm[REG_THREADS / 32][NTERM];
     __shared__ float2 fin[8][NTERM];
     __shared__ double tot[NTERM];
-    __shared__ double Lsm[6][6];
     __shared__ bool last;
-    __shared__ float4 sm_est[3 * STAGED_NODES];
+    // dynamic: the staged top levels (3 float4 per node), then the CTA's
+    // fixed-point histogram of their moments (4 words per node)
+    extern __shared__ float4 reg_dyn[];
+    float4* sm_est = reg_dyn;
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(reg_dyn + 3 * STAGED_NODES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ns = a.n_nodes < STAGED_NODES ? a.n_nodes : STAGED_NODES;
     // the top levels of the tree are read by every point: stage them once
     // for all rounds (the stop flags were set by k_reg_init before launch)
     {
-        const int ns = a.n_nodes < STAGED_NODES ? a.n_nodes : STAGED_NODES;
         const float4* gsrc = reinterpret_cast<const float4*>(a.est);
         for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) sm_est[i] = gsrc[i];
+        for (int i = threadIdx.x; i < 4 * STAGED_NODES; i += blockDim.x) hist[i] = 0ull;
         __syncthreads();
     }
     const double ext = a.root->extent > 0.0 ? a.root->extent : 1.0;
@@ -112,16 +120,24 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
         trace_mark(a.trace, it, 0);
         if (threadIdx.x < 12) Rt_sm[threadIdx.x] = __ldcg(a.Rt + threadIdx.x);
         __syncthreads();
-        descend_points(a.src, a.n, a.est, sm_est, a.depth, Rt_sm, qscale, a.acc, blockIdx.x, gridDim.x);
+        descend_points(a.src, a.n, a.est, sm_est, a.depth, Rt_sm, qscale, a.acc, blockIdx.x, gridDim.x,
+                       hist);
+        __syncthreads();
+        flush_node_hist(hist, ns, a.acc);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();  // this CTA's moment atomics before its arrival
+            atomicAdd(a.bar + 4, 1u);
+        }
         trace_mark(a.trace, it, 1);
-        if (!grid_barrier(a.bar, a.status, BARRIER_SPIN_LIMIT)) return;
-        trace_mark(a.trace, it, 2);
         // ---- B: node terms (only the CTAs that own nodes take part)
         const int nb_nodes = (a.n_nodes + blockDim.x - 1) / blockDim.x;
         if (blockIdx.x < nb_nodes) {
-        float v[NTERM], c[NTERM];
+        if (!wait_at_least(a.bar + 4, unsigned(it + 1) * gridDim.x, a.status, BARRIER_SPIN_LIMIT)) return;
+        trace_mark(a.trace, it, 2);
+        float v[32], c[32];  // NTERM terms, padded to a warp's width
 #pragma unroll
-        for (int k = 0; k < NTERM; ++k) { v[k] = 0.f; c[k] = 0.f; }
+        for (int k = 0; k < 32; ++k) { v[k] = 0.f; c[k] = 0.f; }
         double* dbg = it == a.iters - 1 ? a.dbg : nullptr;
         for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_nodes; g += nb_nodes * blockDim.x) {
             long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
@@ -168,16 +184,11 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
                 dbg[4 * g + 3] = double(M0) * (double(cm.z) + double(o2));
             }
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int k = 0; k < NTERM; ++k) {
-                const float s2 = __shfl_xor_sync(FULL, v[k], off);
-                const float c2 = __shfl_xor_sync(FULL, c[k], off);
-                pair_add(v[k], c[k], s2, c2);
-            }
-        if (lane == 0)
-            for (int k = 0; k < NTERM; ++k) sm[warp][k] = make_float2(v[k], c[k]);
+        {
+            float ws, we;
+            warp_reduce_scatter32(v, c, ws, we);
+            if (lane < NTERM) sm[warp][lane] = make_float2(ws, we);
+        }
         __syncthreads();
         if (threadIdx.x < NTERM) {
             float S = 0.f, C = 0.f;
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
         }
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) last = (atomicAdd(a.bar + 2, 1u) == unsigned(nb_nodes) - 1);
+        if (threadIdx.x == 0) last = (atomicAdd(a.bar + 2, 1u) == unsigned(it + 1) * nb_nodes - 1);
         __syncthreads();
         trace_mark(a.trace, it, 3);
         if (last) {
@@ -221,19 +232,22 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
             __syncthreads();
             if (threadIdx.x == 32 && a.obj) *a.obj = tot[NTERM - 1];
             if (warp == 0) {
-                const bool solved = warp_solve_update(tot, Lsm, a.T, a.Rt, a.T_hist, it);
+                const bool solved = warp_solve_update(tot, a.T, a.Rt, a.T_hist, it);
                 if (!solved && lane == 0) {
                     atomicOr(a.status, ST_DEGENERATE);  // T kept for this round
                     if (a.T_hist)
                         for (int k = 0; k < 16; ++k) a.T_hist[16 * it + k] = __ldcg(a.T + k);
                 }
-                if (lane == 0) a.bar[2] = 0u;
-                __threadfence();
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();  // the new T and R|t before the generation
+                    atomicExch(a.bar + 3, unsigned(it + 1));
+                }
             }
             trace_mark(a.trace, it, 4);
         }
         }  // node-owning CTAs
-        if (!grid_barrier(a.bar, a.status, BARRIER_SPIN_LIMIT)) return;
+        if (!wait_at_least(a.bar + 3, unsigned(it + 1), a.status, BARRIER_SPIN_LIMIT)) return;
         trace_mark(a.trace, it, 5);
     }
 }
@@ -302,7 +316,7 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         void* args[] = {&a};
         ProfScope ps_(t, K_DESCEND, s);
         const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_register, dim3(t->reg_grid),
-                                                          dim3(REG_THREADS), args, 0, s);
+                                                          dim3(REG_THREADS), args, REG_DYN_SMEM, s);
         if (e != cudaSuccess) {
             fprintf(stderr, "hgmm: cooperative launch failed: %s\n", cudaGetErrorString(e));
             return HGMM_ECUDA;
@@ -322,7 +336,10 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
 
 int hgmm_register_grid(int n_sm) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_register, REG_THREADS, 0) != cudaSuccess ||
+    // static + dynamic shared memory exceeds the 48 KB default: opt in
+    if (cudaFuncSetAttribute(k_register, cudaFuncAttributeMaxDynamicSharedMemorySize, int(REG_DYN_SMEM)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_register, REG_THREADS, REG_DYN_SMEM) != cudaSuccess ||
         per_sm < 1)
         return 0;
     return n_sm * (per_sm < 2 ? per_sm : 2);  // <= co-resident CTAs (cooperative launch)
