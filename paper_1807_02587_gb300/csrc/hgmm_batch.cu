@@ -32,6 +32,7 @@ struct BatchWs {
     RootDev* root;
     float4* pts[2];
     uint32_t* codes;
+    Item* items;
     int* item_range;
     int* meta;
     float2* partials;
@@ -71,17 +72,6 @@ namespace {
 
 static_assert(ACC_REPLICAS == 1, "the batched node terms read one accumulator copy per node");
 
-struct BuildSmem {
-    union {
-        float2 red[EST_THREADS / 32][NPART];
-        MstepSmem msm;
-        double wmom[EST_THREADS / 32][NPART];
-        AssignSmem as;
-        RootSmem rs;
-        int warp_tot[33];
-    };
-};
-
 struct RegSmem {
     float Rt[12];
     float2 sm[EST_THREADS / 32][NTERM];
@@ -104,68 +94,40 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
     const float4* src = a.points + a.src_rng[2 * pair];
     const int n_s = int(a.src_rng[2 * pair + 1] - a.src_rng[2 * pair]);
     const int depth = a.depth[pair];
-    if (rank == 0 && threadIdx.x == 0) *w.status = 0;
-
-    // ---- root statistics
-    root_partial_cta(tgt, n_t, rank, cs, w.root_part + 32 * rank, bs.rs);
-    cl.sync();
-    if (rank == 0) root_final_cta(w.root_part, cs, tgt, n_t, a.eps_rel, w.root, w.status, bs.rs);
-    cl.sync();
-
-    // ---- levels
-    const float4* cur = tgt;
-    for (int l = 0; l < depth; ++l) {
-        const int n_par = l == 0 ? 1 : int(level_size(l - 1));
-        for (int p = gw; p < n_par; p += nwt)
-            if (lane < 8) init_child(l, p, lane, w.root, w.stat, w.est, w.seg_count, w.status);
-        if (rank == 0)
-            make_items_cta(l, n_t, n_par, w.seg_count, w.item_range, w.meta, cs, bs.warp_tot);
-        cl.sync();
-        const int n_items = __ldcg(w.meta);
-        const int C = __ldcg(w.meta + 1);
-        const ItemCalc items{l, n_t, n_par, w.item_range, w.seg_start, w.seg_count};
-        NodeEst* est_lvl = w.est + level_offset(l);
-        for (int k = 0; k < a.em_iters; ++k) {
-            estep_range<COMP>(cur, items, rank * C, min(rank * C + C, n_items), est_lvl, w.partials,
-                              bs.red);
+    // ---- the target's tree (shared with the single-pair build kernel)
+    {
+        BuildCtx x;
+        x.pts = tgt;
+        x.n = n_t;
+        x.depth = depth;
+        x.em_iters = a.em_iters;
+        x.n_min = a.n_min;
+        x.lam_c = a.lam_c;
+        x.eps_rel = a.eps_rel;
+        x.stop_level = 0;
+        x.stop_iters = 0;
+        x.est = w.est;
+        x.stat = w.stat;
+        x.rnode = w.rnode;
+        x.seg_start = w.seg_start;
+        x.seg_count = w.seg_count;
+        x.root = w.root;
+        x.buf[0] = w.pts[0];
+        x.buf[1] = w.pts[1];
+        for (int l = 0; l < HGMM_MAX_DEPTH; ++l) x.perm[l] = nullptr;
+        x.codes = w.codes;
+        x.items = w.items;
+        x.item_range = w.item_range;
+        x.meta = w.meta;
+        x.partials = w.partials;
+        x.item_cnt = w.item_cnt;
+        x.item_off = w.item_off;
+        x.root_part = w.root_part;
+        x.status = w.status;
+        build_levels<COMP>(x, rank, cs, bs, [&]() {
             cl.sync();
-            // parents with many runs: a whole CTA; the others: one warp each
-            for (int p = rank; p < n_par; p += cs) {
-                const int i0 = __ldcg(w.item_range + 2 * p), i1 = __ldcg(w.item_range + 2 * p + 1);
-                if (i0 < i1 && (i1 - 1) / C - i0 / C + 1 >= 8)
-                    mstep_parent<COMP>(l, n_t, p, i0, i1, C, w.partials, w.seg_count, w.root,
-                                       a.n_min, w.stat, w.est, w.status, bs.msm);
-            }
-            __syncthreads();
-            for (int p = gw; p < n_par; p += nwt) {
-                const int i0 = __ldcg(w.item_range + 2 * p), i1 = __ldcg(w.item_range + 2 * p + 1);
-                if (i0 < i1 && (i1 - 1) / C - i0 / C + 1 < 8)
-                    mstep_parent_warp<COMP>(l, n_t, p, i0, i1, C, w.partials, w.seg_count, w.root,
-                                            a.n_min, w.stat, w.est, w.status, bs.wmom[warp]);
-            }
-            cl.sync();
-        }
-        // hand-off: argmax, per-parent child offsets, stable partition
-        for (int it = rank; it < n_items; it += cs)
-            assign_item(cur, items(it), it, est_lvl, w.codes, w.item_cnt, bs.as);
-        cl.sync();
-        for (int p = gw; p < n_par; p += nwt) {
-            const int i0 = __ldcg(w.item_range + 2 * p), i1 = __ldcg(w.item_range + 2 * p + 1);
-            const int pstart = i0 < i1 ? items(i0).start
-                                       : (l == 0 ? 0 : __ldcg(w.seg_start + level_offset(l - 1) + p));
-            child_offsets_warp(l, p, i0, i1, pstart, w.item_cnt, w.item_off, w.seg_start,
-                               w.seg_count);
-        }
-        cl.sync();
-        float4* out = w.pts[l & 1];
-        for (int it = rank; it < n_items; it += cs)
-            scatter_item(cur, nullptr, items(it), it, w.codes, w.item_off, out, nullptr,
-                         threadIdx.x, blockDim.x);
-        const int64_t m = level_size(l);
-        for (int64_t i = int64_t(rank) * blockDim.x + threadIdx.x; i < m; i += int64_t(cs) * blockDim.x)
-            finalize_node(l, i, a.lam_c, w.root, w.stat, w.est, w.rnode);
-        cl.sync();
-        cur = out;
+            return true;
+        });
     }
 
     // ---- proposal features of the target (levels 0 and 1)
@@ -372,7 +334,8 @@ int hgmm_batch_create(int64_t max_points, int32_t max_depth, int32_t max_pairs, 
         good &= balloc(b, &w.est, nodes) && balloc(b, &w.stat, nodes) && balloc(b, &w.rnode, 3 * nodes);
         good &= balloc(b, &w.seg_start, nodes) && balloc(b, &w.seg_count, nodes);
         good &= balloc(b, &w.root, 1) && balloc(b, &w.pts[0], max_points) && balloc(b, &w.pts[1], max_points);
-        good &= balloc(b, &w.codes, max_points) && balloc(b, &w.item_range, 2 * parents);
+        good &= balloc(b, &w.codes, max_points) && balloc(b, &w.item_range, 2 * parents) &&
+                balloc(b, &w.items, items);
         good &= balloc(b, &w.meta, 4) && balloc(b, &w.partials, items * NPART);
         good &= balloc(b, &w.item_cnt, items * 8) && balloc(b, &w.item_off, items * 8);
         good &= balloc(b, &w.root_part, 32 * 16) && balloc(b, &w.acc, 4 * ACC_REPLICAS * nodes);

@@ -869,6 +869,144 @@ __device__ __forceinline__ void finalize_node(int level, int64_t i, float lam_c,
                                    float(s.mu[2] - double(a.z)), 0.f);
 }
 
+// ============================================================ whole build
+// Scratch of one build phase at a time.
+struct BuildSmem {
+    union {
+        float2 red[EST_THREADS / 32][NPART];
+        MstepSmem msm;
+        double wmom[EST_THREADS / 32][NPART];
+        AssignSmem as;
+        OffsetSmem os;
+        RootSmem rs;
+        int warp_tot[33];
+    };
+};
+
+// Device buffers of one tree build (the target's points are read, the
+// ping-pong buffers receive each level's sorted order).
+struct BuildCtx {
+    const float4* pts;
+    int n, depth, em_iters;
+    float n_min, lam_c, eps_rel;
+    int stop_level, stop_iters;  // stop after stop_iters EM iterations of level stop_level - 1
+    NodeEst* est;
+    NodeStat* stat;
+    float4* rnode;
+    int* seg_start;
+    int* seg_count;
+    RootDev* root;
+    float4* buf[2];
+    int* perm[HGMM_MAX_DEPTH];   // per level, or null (no input-order labels kept)
+    uint32_t* codes;
+    Item* items;                 // the level's work items, filled once per level
+    int* item_range;
+    int* meta;
+    float2* partials;
+    int* item_cnt;
+    int* item_off;
+    float* root_part;            // cs x 32
+    int* status;
+};
+
+// The top-down build (Sec. 3, Sec. 4.1 and the readings of the hot path) run
+// by cs CTAs of rank 0..cs-1 that meet at sync() between phases: root
+// statistics, then per level the child init, the work items, K EM
+// iterations (E-step over the items, M-step per parent: a whole CTA for
+// parents with many runs, one warp for the others), the argmax hand-off,
+// the stable partition into the other point buffer and the per-node
+// finalisation.  sync() returns false when a bounded wait gave up; the
+// build then stops.  Returns the buffer holding the last level's order.
+template <bool COMP, typename Sync>
+__device__ bool build_levels(const BuildCtx& x, int rank, int cs, BuildSmem& bs, Sync sync) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    if (rank == 0 && threadIdx.x == 0) *x.status = 0;
+    root_partial_cta(x.pts, x.n, rank, cs, x.root_part + 32 * rank, bs.rs);
+    if (!sync()) return false;
+    if (rank == 0) root_final_cta(x.root_part, cs, x.pts, x.n, x.eps_rel, x.root, x.status, bs.rs);
+    if (!sync()) return false;
+    const float4* cur = x.pts;
+    const int* perm_prev = nullptr;
+    for (int l = 0; l < x.depth; ++l) {
+        const int n_par = l == 0 ? 1 : int(level_size(l - 1));
+        // per-parent work goes to CTA (p + 1) mod cs, warp p / cs: the FP64
+        // chains of the parents land on every SM (one SM's FP64 pipe is
+        // narrow) and level 0's single parent runs beside CTA 0's item scan
+        const int prank = rank == 0 ? cs - 1 : rank - 1;  // parents p = prank + cs * j
+        for (int p = prank + cs * warp; p < n_par; p += cs * wpb)
+            if (lane < 8) init_child(l, p, lane, x.root, x.stat, x.est, x.seg_count, x.status);
+        if (rank == 0)
+            make_items_cta(l, x.n, n_par, x.seg_count, x.item_range, x.meta, cs, bs.warp_tot);
+        if (!sync()) return false;
+        const int n_items = __ldcg(x.meta);
+        const int C = __ldcg(x.meta + 1);
+        {
+            // materialise the items once: every later phase of the level reads them
+            const ItemCalc calc{l, x.n, n_par, x.item_range, x.seg_start, x.seg_count};
+            for (int j = rank * blockDim.x + threadIdx.x; j < n_items; j += cs * blockDim.x)
+                x.items[j] = calc(j);
+        }
+        if (!sync()) return false;
+        const ItemList items{x.items};
+        NodeEst* est_lvl = x.est + level_offset(l);
+        const bool stop_here = x.stop_level == l + 1;
+        const int K = stop_here ? x.stop_iters : x.em_iters;
+        for (int k = 0; k < K; ++k) {
+            estep_range<COMP>(cur, items, rank * C, min(rank * C + C, n_items), est_lvl, x.partials,
+                              bs.red);
+            if (!sync()) return false;
+            for (int p = prank; p < n_par; p += cs) {
+                const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
+                if (i0 < i1 && (i1 - 1) / C - i0 / C + 1 >= 8)
+                    mstep_parent<COMP>(l, x.n, p, i0, i1, C, x.partials, x.seg_count, x.root, x.n_min,
+                                       x.stat, x.est, x.status, bs.msm);
+            }
+            __syncthreads();
+            for (int p = prank + cs * warp; p < n_par; p += cs * wpb) {
+                const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
+                if (i0 < i1 && (i1 - 1) / C - i0 / C + 1 < 8)
+                    mstep_parent_warp<COMP>(l, x.n, p, i0, i1, C, x.partials, x.seg_count, x.root,
+                                            x.n_min, x.stat, x.est, x.status, bs.wmom[warp]);
+            }
+            if (!sync()) return false;
+        }
+        if (stop_here) return true;  // checking aid: parameters after K iterations
+        // hand-off: argmax, per-parent child offsets, stable partition
+        for (int it = rank; it < n_items; it += cs)
+            assign_item(cur, items(it), it, est_lvl, x.codes, x.item_cnt, bs.as);
+        if (!sync()) return false;
+        for (int p = prank; p < n_par; p += cs) {  // parents with many items: a whole CTA
+            const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
+            if (i1 - i0 >= 64) child_offsets_cta(l, p, i0, i1, items(i0).start, x.item_cnt, x.item_off,
+                                                 x.seg_start, x.seg_count, bs.os);
+        }
+        __syncthreads();
+        for (int p = prank + cs * warp; p < n_par; p += cs * wpb) {
+            const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
+            if (i1 - i0 >= 64) continue;
+            const int pstart = i0 < i1 ? items(i0).start
+                                       : (l == 0 ? 0 : __ldcg(x.seg_start + level_offset(l - 1) + p));
+            child_offsets_warp(l, p, i0, i1, pstart, x.item_cnt, x.item_off, x.seg_start, x.seg_count);
+        }
+        if (!sync()) return false;
+        float4* out = x.buf[l & 1];
+        int* perm_out = x.perm[l];
+        for (int it = rank; it < n_items; it += cs)
+            scatter_item(cur, perm_prev, items(it), it, x.codes, x.item_off, out, perm_out,
+                         threadIdx.x, blockDim.x);
+        // per-node finalisation: node r + cs t for thread t of CTA r, so the
+        // FP64 eigen chains spread over every CTA (each SM's FP64 pipe is narrow)
+        const int64_t m = level_size(l);
+        for (int64_t i = int64_t(threadIdx.x) * cs + rank; i < m; i += int64_t(cs) * blockDim.x)
+            finalize_node(l, i, x.lam_c, x.root, x.stat, x.est, x.rnode);
+        if (!sync()) return false;
+        cur = out;
+        perm_prev = perm_out;
+    }
+    return true;
+}
+
 // ============================================================ registration
 __device__ __forceinline__ long long to_fix(float v) {
     const float c = fminf(fmaxf(v, -FIX_CLAMP), FIX_CLAMP);
@@ -1242,6 +1380,21 @@ __device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned tar
     }
     __syncthreads();
     return ok_wait != 0;
+}
+
+// Grid-wide barrier of a cooperative launch on a monotonic arrival counter
+// (zeroed before the launch): every CTA adds one and waits until the counter
+// reaches target = (barriers passed so far) x gridDim.x.  Arrivals are
+// non-returning atomics and no word is ever reset, so no CTA can miss a
+// release; the wait is bounded (wait_at_least).
+__device__ __forceinline__ bool grid_sync_count(unsigned* ctr, unsigned target, int* status,
+                                                long long limit) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+    }
+    return wait_at_least(ctr, target, status, limit);
 }
 
 // Bounded grid-wide barrier for a cooperative launch (all CTAs co-resident):
