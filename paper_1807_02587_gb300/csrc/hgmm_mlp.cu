@@ -16,6 +16,7 @@
 //   db = column sums of dZ1, dZ2, dY (two-pass, fixed order: deterministic)
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -330,6 +331,8 @@ struct hgmm_mlp {
     float* part = nullptr;
     float* loss = nullptr;
     int* err = nullptr;
+    float* ws = nullptr;      // K-slice partials of the weight-gradient products
+    long long ws_cap = 0;     // floats
 };
 
 namespace {
@@ -353,13 +356,43 @@ bool operand_ok(const void* base, long long rs, long long ks, int rows, int K) {
     return false;
 }
 
+constexpr int MAX_SLICES = 32;
+
 template <int BN>
-int gemm(const GemmArgs& g, cudaStream_t s) {
+int gemm_launch(const GemmArgs& g, int slices, cudaStream_t s) {
+    const dim3 grid((g.M + tc::GEMM_BM - 1) / tc::GEMM_BM, (g.N + BN - 1) / BN, slices);
+    tc::k_gemm_bf16<BN><<<grid, tc::GEMM_THREADS, tc::gemm_smem_bytes(BN), s>>>(g);
+    return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
+}
+
+// D = A B^T with the fused epilogue of g.  N <= 16 runs 128 x 16 tiles,
+// larger N 128 x 128 tiles.  When the tiles alone cannot fill the GPU and K
+// is long (the weight gradients: K = batch), K is cut into 64-multiple
+// slices whose FP32 partials go to ws and are summed in a fixed order.
+int gemm(GemmArgs g, cudaStream_t s, float* ws = nullptr, long long ws_cap = 0) {
     if (g.M < 1 || g.N < 1 || g.K < 1 || !operand_ok(g.A, g.a_m, g.a_k, g.M, g.K) ||
         !operand_ok(g.B, g.b_n, g.b_k, g.N, g.K))
         return HGMM_EINVAL;
-    const dim3 grid((g.M + tc::GEMM_BM - 1) / tc::GEMM_BM, (g.N + BN - 1) / BN);
-    tc::k_gemm_bf16<BN><<<grid, tc::GEMM_THREADS, tc::gemm_smem_bytes(BN), s>>>(g);
+    const int bn = g.N <= 16 ? 16 : 128;
+    const int tiles = ((g.M + tc::GEMM_BM - 1) / tc::GEMM_BM) * ((g.N + bn - 1) / bn);
+    const int kt = (g.K + tc::GEMM_BK - 1) / tc::GEMM_BK;
+    int slices = 1;
+    if (ws && g.epi == tc::EPI_F32 && tiles < 128) slices = std::min(std::min(MAX_SLICES, kt), (304 + tiles - 1) / tiles);
+    g.k_split = ((kt + slices - 1) / slices) * tc::GEMM_BK;
+    slices = (g.K + g.k_split - 1) / g.k_split;
+    if (slices <= 1) {
+        g.split_stride = 0;
+        return bn == 16 ? gemm_launch<16>(g, 1, s) : gemm_launch<128>(g, 1, s);
+    }
+    // partials at the output's own offsets, one copy per slice
+    const long long span = (long long)(g.M - 1) * g.o_m + (long long)(g.N - 1) * g.o_n + 1;
+    if ((long long)slices * span > ws_cap) return HGMM_ECAPACITY;
+    float* out = g.out_f32;
+    g.out_f32 = ws;
+    g.split_stride = span;
+    const int rc = bn == 16 ? gemm_launch<16>(g, slices, s) : gemm_launch<128>(g, slices, s);
+    if (rc) return rc;
+    tc::k_sum_slices<<<304, 256, 0, s>>>(ws, slices, span, g.M, g.N, g.n_store, g.o_m, g.o_n, out);
     return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
 }
 
@@ -377,6 +410,8 @@ GemmArgs gargs(const bf16* A, long long a_m, long long a_k, const bf16* B, long 
     g.N = N;
     g.K = K;
     g.n_store = N;
+    g.k_split = K;
+    g.split_stride = 0;
     g.epi = epi;
     g.err = err;
     return g;
@@ -388,20 +423,27 @@ int forward_impl(hgmm_mlp* m, const bf16* X, int batch, float* Y, cudaStream_t s
     g.out_bf16 = m->H1;
     g.o_m = HID;
     g.o_n = 1;
-    if (int rc = gemm<256>(g, s)) return rc;
+    if (int rc = gemm(g, s, m->ws, m->ws_cap)) return rc;
     g = gargs(m->H1, HID, 1, m->W2, HID, 1, batch, HID, HID, tc::EPI_BIAS_RELU_BF16, m->err);
     g.bias = m->P + OFF_B2;
     g.out_bf16 = m->H2;
     g.o_m = HID;
     g.o_n = 1;
-    if (int rc = gemm<256>(g, s)) return rc;
+    if (int rc = gemm(g, s, m->ws, m->ws_cap)) return rc;
     g = gargs(m->H2, HID, 1, m->W3, HID, 1, batch, OUTP, HID, tc::EPI_BIAS_F32, m->err);
     g.bias = m->b3p;
     g.out_f32 = Y;
     g.o_m = OUT;
     g.o_n = 1;
     g.n_store = OUT;
-    return gemm<16>(g, s);
+    return gemm(g, s);
+}
+
+bool set_gemm_smem() {
+    return cudaFuncSetAttribute(tc::k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::gemm_smem_bytes(128)) == cudaSuccess &&
+           cudaFuncSetAttribute(tc::k_gemm_bf16<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::gemm_smem_bytes(16)) == cudaSuccess;
 }
 
 int check_dev(const hgmm_mlp* m) {
@@ -435,11 +477,9 @@ int hgmm_mlp_create(int32_t max_batch, hgmm_mlp** out) {
                 malloc_into(m, &m->dYf, B * OUTP) && malloc_into(m, &m->dZ2, B * HID) &&
                 malloc_into(m, &m->dZ1, B * HID) && malloc_into(m, &m->part, size_t(nchunks) * 3 * HID) &&
                 malloc_into(m, &m->loss, 1) && malloc_into(m, &m->err, 1);
-    good = good &&
-           cudaFuncSetAttribute(tc::k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::gemm_smem_bytes(256)) == cudaSuccess &&
-           cudaFuncSetAttribute(tc::k_gemm_bf16<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::gemm_smem_bytes(16)) == cudaSuccess;
+    m->ws_cap = (long long)MAX_SLICES * HID * IN;
+    good = good && malloc_into(m, &m->ws, size_t(m->ws_cap));
+    good = good && set_gemm_smem();
     if (!good) {
         hgmm_mlp_destroy(m);
         return HGMM_ENOMEM;
@@ -515,7 +555,7 @@ int hgmm_mlp_gradients(hgmm_mlp* m, const uint16_t* d_x, const float* d_labels, 
     g.o_m = 1;
     g.o_n = HID;
     g.n_store = OUT;
-    if (int rc = gemm<16>(g, s)) return rc;
+    if (int rc = gemm(g, s, m->ws, m->ws_cap)) return rc;
     // dZ2 = (dY W3) * [H2 > 0]: B[n = h][k = o] = W3[o][h]
     g = gargs(m->dY, OUTP, 1, m->W3, 1, HID, batch, HID, OUTP, tc::EPI_MASK_BF16, m->err);
     g.mask = m->H2;
@@ -523,13 +563,13 @@ int hgmm_mlp_gradients(hgmm_mlp* m, const uint16_t* d_x, const float* d_labels, 
     g.out_bf16 = m->dZ2;
     g.o_m = HID;
     g.o_n = 1;
-    if (int rc = gemm<256>(g, s)) return rc;
+    if (int rc = gemm(g, s, m->ws, m->ws_cap)) return rc;
     // dW2 = dZ2^T H1
     g = gargs(m->dZ2, 1, HID, m->H1, 1, HID, HID, HID, batch, tc::EPI_F32, m->err);
     g.out_f32 = m->G + OFF_W2;
     g.o_m = HID;
     g.o_n = 1;
-    if (int rc = gemm<256>(g, s)) return rc;
+    if (int rc = gemm(g, s, m->ws, m->ws_cap)) return rc;
     // dZ1 = (dZ2 W2) * [H1 > 0]
     g = gargs(m->dZ2, HID, 1, m->W2, 1, HID, batch, HID, HID, tc::EPI_MASK_BF16, m->err);
     g.mask = m->H1;
@@ -537,13 +577,13 @@ int hgmm_mlp_gradients(hgmm_mlp* m, const uint16_t* d_x, const float* d_labels, 
     g.out_bf16 = m->dZ1;
     g.o_m = HID;
     g.o_n = 1;
-    if (int rc = gemm<256>(g, s)) return rc;
+    if (int rc = gemm(g, s, m->ws, m->ws_cap)) return rc;
     // dW1 = dZ1^T x
     g = gargs(m->dZ1, 1, HID, X, 1, IN, HID, IN, batch, tc::EPI_F32, m->err);
     g.out_f32 = m->G + OFF_W1;
     g.o_m = IN;
     g.o_n = 1;
-    if (int rc = gemm<256>(g, s)) return rc;
+    if (int rc = gemm(g, s, m->ws, m->ws_cap)) return rc;
     const int nchunks = (batch + COLSUM_ROWS - 1) / COLSUM_ROWS;
     k_colsum_partial<<<dim3(nchunks, 3), 256, 0, s>>>(m->dZ1, m->dZ2, m->dYf, batch, m->part);
     k_colsum_final<<<3, 256, 0, s>>>(m->part, nchunks, m->G);
@@ -606,12 +646,10 @@ int hgmm_debug_gemm(const uint16_t* d_A, int64_t a_m, int64_t a_k, const uint16_
     if (!err && (cudaMalloc(&err, sizeof(int)) != cudaSuccess || cudaMemset(err, 0, sizeof(int)) != cudaSuccess))
         return HGMM_ECUDA;
     static bool attr = false;
+    static float* ws = nullptr;
+    const long long ws_cap = (long long)MAX_SLICES * 256 * 1536;
     if (!attr) {
-        if (cudaFuncSetAttribute(tc::k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 tc::gemm_smem_bytes(256)) != cudaSuccess ||
-            cudaFuncSetAttribute(tc::k_gemm_bf16<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 tc::gemm_smem_bytes(16)) != cudaSuccess)
-            return HGMM_ECUDA;
+        if (!set_gemm_smem() || cudaMalloc(&ws, size_t(ws_cap) * sizeof(float)) != cudaSuccess) return HGMM_ECUDA;
         attr = true;
     }
     GemmArgs g = gargs(reinterpret_cast<const bf16*>(d_A), a_m, a_k, reinterpret_cast<const bf16*>(d_B),
@@ -619,8 +657,7 @@ int hgmm_debug_gemm(const uint16_t* d_A, int64_t a_m, int64_t a_k, const uint16_
     g.out_f32 = d_out;
     g.o_m = N;
     g.o_n = 1;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return N <= 16 ? gemm<16>(g, s) : gemm<256>(g, s);
+    return gemm(g, static_cast<cudaStream_t>(stream), ws, ws_cap);
 }
 
 int hgmm_pose_select(int32_t n, const double* d_T_a, const double* d_obj_a, const double* d_T_b,

@@ -137,6 +137,8 @@ struct GemmArgs {
     const __nv_bfloat16* B;
     long long b_n, b_k;   // B[n][k] = B[n * b_n + k * b_k]
     int M, N, K;
+    int k_split;          // K elements per blockIdx.z slice (multiple of 64)
+    long long split_stride;  // EPI_F32 with slices: slice z writes out_f32 + z * split_stride
     int n_store;          // columns n >= n_store are not written
     int epi;
     const float* bias;
@@ -151,31 +153,46 @@ struct GemmArgs {
 constexpr int GEMM_BM = 128;
 constexpr int GEMM_BK = 64;
 constexpr int GEMM_THREADS = 128;
+constexpr int GEMM_STAGES = 4;
 constexpr int GEMM_A_STAGE = GEMM_BM * GEMM_BK * 2;  // bytes
 constexpr uint32_t CORE_LBO = 128;                   // core matrices adjacent along K
 constexpr uint32_t CORE_SBO = (GEMM_BK / 8) * 128;   // 8-row groups
 
 __host__ __device__ constexpr int gemm_b_stage(int bn) { return bn * GEMM_BK * 2; }
-__host__ __device__ constexpr int gemm_smem_bytes(int bn) { return 2 * (GEMM_A_STAGE + gemm_b_stage(bn)); }
-__host__ __device__ constexpr uint32_t gemm_tmem_cols(int bn) { return bn <= 32 ? 32u : (bn <= 64 ? 64u : (bn <= 128 ? 128u : 256u)); }
+__host__ __device__ constexpr int gemm_smem_bytes(int bn) {
+    return GEMM_STAGES * (GEMM_A_STAGE + gemm_b_stage(bn));
+}
+__host__ __device__ constexpr uint32_t gemm_tmem_cols(int bn) {
+    return bn <= 32 ? 32u : (bn <= 64 ? 64u : (bn <= 128 ? 128u : 256u));
+}
 
-// Fill one K-major operand tile (rows x 64) of shared memory from global,
-// element (row, k) at src[row * rs + k * ks].  ks == 1: 16-byte vectors
-// along K; otherwise rs == 1 and 16-byte vectors run along the row index
-// and are scattered per element.  Rows >= nrows_valid and k >= K read zero.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool pred) {
+    // src-size 0 fills the 16 bytes with zeros and reads nothing
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(pred ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// Fill one K-major operand tile (rows x 64) of shared memory, element (row,
+// k) from src[row * rs + k * ks]; rows >= nrows_valid and k >= k_end read
+// zero.  ks == 1: 16-byte asynchronous copies along K (cp.async; the caller
+// commits the group), consecutive threads on consecutive rows of one K
+// chunk so that eight threads fill one 128-byte core matrix.  Otherwise
+// rs == 1: 16-byte loads along the row index, scattered per element
+// (synchronous).
 __device__ __forceinline__ void stage_tile(unsigned char* dst, const __nv_bfloat16* src, int rows,
                                            int row0, int nrows_valid, long long rs, long long ks,
-                                           int k0, int K) {
+                                           int k0, int k_end) {
     if (ks == 1) {
-        // consecutive threads take consecutive rows of one 16-byte K chunk:
-        // eight threads fill one 128-byte core matrix (conflict-free stores)
+        const uint32_t d0 = smem_u32(dst);
         for (int q = threadIdx.x; q < rows * 8; q += GEMM_THREADS) {
             const int r = q % rows, c = q / rows;
             const int row = row0 + r, k = k0 + c * 8;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (row < nrows_valid && k < K)
-                v = __ldg(reinterpret_cast<const uint4*>(src + row * rs + k));
-            *reinterpret_cast<uint4*>(dst + (r >> 3) * CORE_SBO + c * CORE_LBO + (r & 7) * 16) = v;
+            const bool ok = row < nrows_valid && k < k_end;
+            cp_async16(d0 + (r >> 3) * CORE_SBO + c * CORE_LBO + (r & 7) * 16,
+                       ok ? (const void*)(src + row * rs + k) : (const void*)src, ok);
         }
     } else {
         const int groups = rows >> 3;
@@ -183,8 +200,7 @@ __device__ __forceinline__ void stage_tile(unsigned char* dst, const __nv_bfloat
             const int kk = q % GEMM_BK, g = q / GEMM_BK;
             const int k = k0 + kk, row = row0 + g * 8;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (row < nrows_valid && k < K)
-                v = __ldg(reinterpret_cast<const uint4*>(src + row + k * ks));
+            if (row < nrows_valid && k < k_end) v = __ldg(reinterpret_cast<const uint4*>(src + row + k * ks));
             const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
             unsigned char* d = dst + g * CORE_SBO + (kk >> 3) * CORE_LBO + (kk & 7) * 2;
 #pragma unroll
@@ -193,25 +209,34 @@ __device__ __forceinline__ void stage_tile(unsigned char* dst, const __nv_bfloat
     }
 }
 
+// One CTA: a 128 x BN tile of D over the K slice of blockIdx.z, in a ring of
+// GEMM_STAGES shared-memory stages.  Tile kt is loaded GEMM_STAGES - 1
+// steps ahead into the stage that tile kt - 1 used, after the mbarrier of
+// that stage says its MMAs are done; before the MMAs of tile kt every
+// thread waits for its own copies of that tile (cp.async.wait_group), makes
+// them visible to the tensor core (fence.proxy.async) and meets the others.
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_bf16(GemmArgs g) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "M = 128 needs N in [16, 256], step 16");
+    constexpr int S = GEMM_STAGES;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[S];
     __shared__ uint32_t tmem_slot;
     constexpr uint32_t NCOLS = gemm_tmem_cols(BN);
     constexpr uint32_t IDESC = idesc_bf16_f32(GEMM_BM, BN);
     constexpr int STAGE = GEMM_A_STAGE + gemm_b_stage(BN);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * GEMM_BM, n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * g.k_split;
+    const int ke = min(g.K, kb + g.k_split);
 
     if (warp == 0) {
         tmem_alloc(&tmem_slot, NCOLS);
         tmem_relinquish();
     }
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+#pragma unroll
+        for (int i = 0; i < S; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
     }
     fence_before_sync();
@@ -219,25 +244,28 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_bf16(GemmArgs g) {
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
-    const int nk = (g.K + GEMM_BK - 1) / GEMM_BK;
+    const int nk = ke > kb ? (ke - kb + GEMM_BK - 1) / GEMM_BK : 0;
+    auto load = [&](int t) {
+        unsigned char* sA = smem + (t % S) * STAGE;
+        stage_tile(sA, g.A, GEMM_BM, m0, g.M, g.a_m, g.a_k, kb + t * GEMM_BK, ke);
+        stage_tile(sA + GEMM_A_STAGE, g.B, BN, n0, g.N, g.b_n, g.b_k, kb + t * GEMM_BK, ke);
+    };
+#pragma unroll 1
+    for (int t = 0; t < S - 1; ++t) {
+        if (t < nk) load(t);
+        cp_async_commit();
+    }
     bool ok = true;
+#pragma unroll 1
     for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt & 1;
-        unsigned char* sA = smem + s * STAGE;
-        unsigned char* sB = sA + GEMM_A_STAGE;
-        if (kt >= 2) {
-            // the MMAs of step kt - 2 read this stage
-            const bool w = mbar_wait_bounded(&bars[s], ((kt - 2) >> 1) & 1, MBAR_SPIN_LIMIT);
-            ok = __syncthreads_and(w) != 0;
-            if (!ok) break;
-        }
-        stage_tile(sA, g.A, GEMM_BM, m0, g.M, g.a_m, g.a_k, kt * GEMM_BK, g.K);
-        stage_tile(sB, g.B, BN, n0, g.N, g.b_n, g.b_k, kt * GEMM_BK, g.K);
+        const int s = kt % S;
+        cp_async_wait<S - 2>();  // this thread's copies of tile kt have landed
         fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
             fence_after_sync();
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            unsigned char* sA = smem + s * STAGE;
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sA + GEMM_A_STAGE);
 #pragma unroll
             for (int kk = 0; kk < GEMM_BK / 16; ++kk) {
                 // one K = 16 step spans two core matrices along K
@@ -247,28 +275,42 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_bf16(GemmArgs g) {
             }
             mma_commit(&bars[s]);
         }
+        // refill the stage of tile kt - 1 with tile kt + S - 1
+        const int nt = kt + S - 1;
+        if (kt >= 1 && nt < nk) {
+            const int ps = (kt - 1) % S;
+            const bool w = mbar_wait_bounded(&bars[ps], ((kt - 1) / S) & 1, MBAR_SPIN_LIMIT);
+            ok = __syncthreads_and(w) != 0;
+            if (!ok) break;
+        }
+        if (nt < nk) load(nt);
+        cp_async_commit();
     }
+    cp_async_wait<0>();
     if (ok && nk > 0) {
         const int last = nk - 1;
-        const bool w = mbar_wait_bounded(&bars[last & 1], (last >> 1) & 1, MBAR_SPIN_LIMIT);
+        const bool w = mbar_wait_bounded(&bars[last % S], (last / S) & 1, MBAR_SPIN_LIMIT);
         ok = __syncthreads_and(w) != 0;
     }
     if (!ok) {
         if (threadIdx.x == 0) atomicOr(g.err, 1);
         // give MMAs still in flight a bounded chance to finish before freeing
-        if (nk > 0) {
-            const int last = nk - 1;
-            mbar_wait_bounded(&bars[last & 1], (last >> 1) & 1, MBAR_SPIN_LIMIT);
-        }
-    } else if (nk > 0) {
+        if (nk > 0) mbar_wait_bounded(&bars[(nk - 1) % S], ((nk - 1) / S) & 1, MBAR_SPIN_LIMIT);
+    } else {
         fence_after_sync();
         const int r = warp * 32 + lane;
         const int m = m0 + r;
         const uint32_t trow = tmem + (uint32_t(warp * 32) << 16);
+        float* outf = g.out_f32 ? g.out_f32 + blockIdx.z * g.split_stride : nullptr;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
-            tmem_ld16(trow + uint32_t(c0), v);
+            if (nk > 0) {
+                tmem_ld16(trow + uint32_t(c0), v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            }
             if (m >= g.M) continue;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
@@ -277,8 +319,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_bf16(GemmArgs g) {
                 float x = v[i];
                 const long long o = m * g.o_m + n * g.o_n;
                 switch (g.epi) {
-                    case EPI_F32: g.out_f32[o] = x; break;
-                    case EPI_BIAS_F32: g.out_f32[o] = x + g.bias[n]; break;
+                    case EPI_F32: outf[o] = x; break;
+                    case EPI_BIAS_F32: outf[o] = x + g.bias[n]; break;
                     case EPI_BIAS_RELU_BF16:
                         x += g.bias[n];
                         g.out_bf16[o] = __float2bfloat16_rn(x > 0.f ? x : 0.f);
@@ -294,6 +336,22 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_bf16(GemmArgs g) {
     fence_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+// Fixed-order sum of the K-slice partials: out[i] = sum_z ws[z * stride + i]
+// for the n_store columns of an M x N (row stride o_m) output.
+__global__ void k_sum_slices(const float* __restrict__ ws, int slices, long long stride, int M, int N,
+                             int n_store, long long o_m, long long o_n, float* __restrict__ out) {
+    const long long total = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int m = int(i / N), n = int(i % N);
+        if (n >= n_store) continue;
+        const long long o = m * o_m + n * o_n;
+        float acc = 0.f;
+        for (int z = 0; z < slices; ++z) acc += ws[z * stride + o];
+        out[o] = acc;
+    }
 }
 
 }  // namespace tc
