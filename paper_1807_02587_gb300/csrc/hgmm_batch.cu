@@ -77,13 +77,18 @@ struct RegSmem {
     float2 sm[EST_THREADS / 32][NTERM];
     double tot[NTERM];
     double fsm[FRAME_DOUBLES];
-    float4 est[3 * STAGED_NODES];
 };
+
+// dynamic shared memory of k_batch: the staged top levels of the current
+// pair's tree (3 float4 per node), then the CTA's fixed-point histogram of
+// their registration moments (4 words per node)
+constexpr size_t BATCH_DYN_SMEM =
+    3 * STAGED_NODES * sizeof(float4) + 4 * STAGED_NODES * sizeof(unsigned long long);
 
 // One pair, run by all CTAs of this cluster.
 template <bool COMP>
 __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::cluster_group& cl,
-                         BuildSmem& bs, RegSmem& rgs) {
+                         BuildSmem& bs, RegSmem& rgs, float4* sm_est, unsigned long long* hist) {
     const int cs = int(cl.num_blocks());
     const int rank = int(cl.block_rank());
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -149,7 +154,7 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
     {
         const int ns = n_nodes < STAGED_NODES ? n_nodes : STAGED_NODES;
         const float4* gsrc = reinterpret_cast<const float4*>(w.est);
-        for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) rgs.est[i] = __ldcg(gsrc + i);
+        for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) sm_est[i] = __ldcg(gsrc + i);
     }
     cl.sync();
     const double ext = __ldcg(&w.root->extent) > 0.0 ? __ldcg(&w.root->extent) : 1.0;
@@ -157,7 +162,9 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
     for (int it = 0; it < a.iters; ++it) {
         if (threadIdx.x < 12) rgs.Rt[threadIdx.x] = __ldcg(w.Rt + threadIdx.x);
         __syncthreads();
-        descend_points(src, n_s, w.est, rgs.est, depth, rgs.Rt, qscale, w.acc, rank, cs);
+        descend_points(src, n_s, w.est, sm_est, depth, rgs.Rt, qscale, w.acc, rank, cs, hist);
+        __syncthreads();
+        flush_node_hist(hist, n_nodes < STAGED_NODES ? n_nodes : STAGED_NODES, w.acc);
         cl.sync();
         float v[32], c[32];  // NTERM terms, padded to a warp's width
 #pragma unroll
@@ -226,6 +233,10 @@ __global__ void __launch_bounds__(EST_THREADS, 2) k_batch(BatchArgs a) {
     __shared__ BuildSmem bs;
     __shared__ RegSmem rgs;
     __shared__ int next_pair;
+    extern __shared__ float4 batch_dyn[];
+    float4* sm_est = batch_dyn;
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(batch_dyn + 3 * STAGED_NODES);
+    for (int i = threadIdx.x; i < 4 * STAGED_NODES; i += blockDim.x) hist[i] = 0ull;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = int(cl.num_blocks());
     const int cid = blockIdx.x / cs;
@@ -237,7 +248,7 @@ __global__ void __launch_bounds__(EST_THREADS, 2) k_batch(BatchArgs a) {
         const int k = *cl.map_shared_rank(&next_pair, 0);
         cl.sync();
         if (k >= a.n_pairs) break;
-        run_pair<COMP>(a, w, a.order[k], cl, bs, rgs);
+        run_pair<COMP>(a, w, a.order[k], cl, bs, rgs, sm_est, hist);
     }
 }
 
@@ -280,10 +291,22 @@ bool balloc(hgmm_batch* b, T** p, size_t count) {
     return true;
 }
 
+// static + dynamic shared memory exceeds the 48 KB default: opt in (once)
+bool batch_smem_attr() {
+    static const bool ok =
+        cudaFuncSetAttribute(k_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BATCH_DYN_SMEM)) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BATCH_DYN_SMEM)) ==
+            cudaSuccess;
+    return ok;
+}
+
 int clusters_for(int cs, bool comp) {
+    if (!batch_smem_attr()) return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * 64);
     cfg.blockDim = dim3(EST_THREADS);
+    cfg.dynamicSmemBytes = BATCH_DYN_SMEM;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
     attr.val.clusterDim.x = cs;
@@ -471,6 +494,7 @@ int launch_batch(hgmm_batch* b, const float* d_points, const hgmm_params* p, con
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nclu * cs);
     cfg.blockDim = dim3(EST_THREADS);
+    cfg.dynamicSmemBytes = BATCH_DYN_SMEM;
     cfg.stream = s;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;

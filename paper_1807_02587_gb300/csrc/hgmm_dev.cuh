@@ -490,6 +490,73 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
     flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
 }
 
+// The E-step of whole items by single warps (items first, first + stride,
+// ...): the same arithmetic as estep_range, but each item's moments are
+// reduced inside its warp (quads of lanes: 8 points per step) and stored as
+// the item's own partial, with no block-wide step.  For levels whose parents
+// are many and small, where a CTA's chunk would cross a parent boundary at
+// almost every item.
+template <bool COMP, class Items>
+__device__ __forceinline__ void estep_items_warp(const float4* __restrict__ pts, Items items, int first,
+                                                 int stride, int n_items,
+                                                 const NodeEst* __restrict__ est_lvl,
+                                                 float2* __restrict__ partials) {
+    const int lane = threadIdx.x & 31;
+    const int q = lane >> 2, k = lane & 3;
+    for (int it = first; it < n_items; it += stride) {
+        const Item w = items(it);
+        ChildRegs r0, r1;
+        load_child(est_lvl + 8 * w.parent + 2 * k, r0);
+        load_child(est_lvl + 8 * w.parent + 2 * k + 1, r1);
+        float in[20], s[20], c[20];
+#pragma unroll
+        for (int v = 0; v < 20; ++v) { in[v] = 0.f; s[v] = 0.f; c[v] = 0.f; }
+        int nfold = 0;
+        float4 znext = pts[w.start + min(q, w.count - 1)];
+        for (int base = 0; base < w.count; base += 8) {
+            const int idx = base + q;
+            const bool valid = idx < w.count;
+            const float4 z = znext;
+            if (base + 8 < w.count) znext = pts[w.start + min(idx + 8, w.count - 1)];
+            float e0x, e0y, e0z, e1x, e1y, e1z;
+            const float s0 = child_score(r0, z.x, z.y, z.z, e0x, e0y, e0z);
+            const float s1 = child_score(r1, z.x, z.y, z.z, e1x, e1y, e1z);
+            float m = fmaxf(s0, s1);
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
+            const bool any_live = m > -CUDART_INF_F;  // false for a leaf parent
+            const float p0 = any_live ? exp2f(s0 - m) : 0.f;
+            const float p1 = any_live ? exp2f(s1 - m) : 0.f;
+            float tot = p0 + p1;
+            tot += __shfl_xor_sync(FULL, tot, 1);
+            tot += __shfl_xor_sync(FULL, tot, 2);
+            const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
+            accum10(in, p0 * rinv, e0x, e0y, e0z);
+            accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
+            if (++nfold == 16) {
+                fold20<COMP>(in, s, c);
+                nfold = 0;
+            }
+        }
+        fold20<COMP>(in, s, c);
+#pragma unroll
+        for (int off = 4; off < 32; off <<= 1) {
+#pragma unroll
+            for (int v = 0; v < 20; ++v) {
+                const float s2 = __shfl_xor_sync(FULL, s[v], off);
+                const float c2 = __shfl_xor_sync(FULL, c[v], off);
+                if (COMP) pair_add(s[v], c[v], s2, c2);
+                else s[v] += s2;
+            }
+        }
+        if (lane < 4) {
+            float2* out = partials + int64_t(it) * NPART + k * 20;
+#pragma unroll
+            for (int v = 0; v < 20; ++v) out[v] = make_float2(s[v], COMP ? c[v] : 0.f);
+        }
+    }
+}
+
 // =================================================================== M-step
 // M-step of child c of parent p from its 10 reduced moments m (FP64): S0,
 // mean shift d = S1/S0 from the FP32 mean the E-step used, Sigma = S2/S0 -
@@ -952,21 +1019,29 @@ __device__ bool build_levels(const BuildCtx& x, int rank, int cs, BuildSmem& bs,
         NodeEst* est_lvl = x.est + level_offset(l);
         const bool stop_here = x.stop_level == l + 1;
         const int K = stop_here ? x.stop_iters : x.em_iters;
+        // many small parents per CTA: one warp per item, every item its own
+        // run (C = 1); otherwise each CTA takes a chunk of C items
+        const bool warp_items = n_par >= 4 * cs;
+        const int Crun = warp_items ? 1 : C;
         for (int k = 0; k < K; ++k) {
-            estep_range<COMP>(cur, items, rank * C, min(rank * C + C, n_items), est_lvl, x.partials,
-                              bs.red);
+            if (warp_items)
+                estep_items_warp<COMP>(cur, items, rank * wpb + warp, cs * wpb, n_items, est_lvl,
+                                       x.partials);
+            else
+                estep_range<COMP>(cur, items, rank * C, min(rank * C + C, n_items), est_lvl, x.partials,
+                                  bs.red);
             if (!sync()) return false;
             for (int p = prank; p < n_par; p += cs) {
                 const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
-                if (i0 < i1 && (i1 - 1) / C - i0 / C + 1 >= 8)
-                    mstep_parent<COMP>(l, x.n, p, i0, i1, C, x.partials, x.seg_count, x.root, x.n_min,
-                                       x.stat, x.est, x.status, bs.msm);
+                if (i0 < i1 && (i1 - 1) / Crun - i0 / Crun + 1 >= 8)
+                    mstep_parent<COMP>(l, x.n, p, i0, i1, Crun, x.partials, x.seg_count, x.root,
+                                       x.n_min, x.stat, x.est, x.status, bs.msm);
             }
             __syncthreads();
             for (int p = prank + cs * warp; p < n_par; p += cs * wpb) {
                 const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
-                if (i0 < i1 && (i1 - 1) / C - i0 / C + 1 < 8)
-                    mstep_parent_warp<COMP>(l, x.n, p, i0, i1, C, x.partials, x.seg_count, x.root,
+                if (i0 < i1 && (i1 - 1) / Crun - i0 / Crun + 1 < 8)
+                    mstep_parent_warp<COMP>(l, x.n, p, i0, i1, Crun, x.partials, x.seg_count, x.root,
                                             x.n_min, x.stat, x.est, x.status, bs.wmom[warp]);
             }
             if (!sync()) return false;
