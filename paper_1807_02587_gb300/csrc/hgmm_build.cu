@@ -101,6 +101,41 @@ __global__ void __launch_bounds__(256) k_mstep(int level, int n, const int* __re
                        status, msm);
 }
 
+// All K EM iterations of one parent by one CTA (blockIdx.x = parent): the
+// E-step over the parent's items as a single run, then the M-step of its 8
+// children, with nothing but __syncthreads between them (the parents of a
+// level are independent during EM).  For levels with many small parents,
+// where the level-wide E-step / M-step launches would be mostly latency.
+template <bool COMP>
+__global__ void __launch_bounds__(EST_THREADS, 2) k_em_local(int level, int n, int K,
+                                                            const float4* __restrict__ pts,
+                                                            const Item* __restrict__ items,
+                                                            const int* __restrict__ item_range,
+                                                            float2* __restrict__ partials,
+                                                            const int* __restrict__ seg_count,
+                                                            const RootDev* __restrict__ root, float n_min,
+                                                            NodeStat* __restrict__ stat,
+                                                            NodeEst* __restrict__ est,
+                                                            int* __restrict__ status) {
+    __shared__ union {
+        float2 red[EST_THREADS / 32][NPART];
+        MstepSmem msm;
+    } sm;
+    const int p = blockIdx.x;
+    const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
+    if (i0 >= i1) return;  // parent without points: children stay dead
+    const NodeEst* est_lvl = est + level_offset(level);
+    for (int k = 0; k < K; ++k) {
+        // one run [i0, i1): its partial lands at slot i0
+        estep_range<COMP>(pts, ItemList{items}, i0, i1, est_lvl, partials, sm.red);
+        __syncthreads();
+        // C = i1 makes [i0, i1) a single run for the M-step as well
+        mstep_parent<COMP>(level, n, p, i0, i1, i1, partials, seg_count, root, n_min, stat, est,
+                           status, sm.msm);
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(EST_THREADS) k_assign(const float4* __restrict__ pts,
                                                         const Item* __restrict__ items,
                                                         const int* __restrict__ meta,
@@ -187,6 +222,9 @@ using namespace hgmm;
         }                                                     \
     } while (0)
 
+// levels with at least this many parents run their EM parent-locally
+constexpr int LOCAL_EM_PARENTS = 256;
+
 int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                     const hgmm_params& p, cudaStream_t s) {
     const int n = int(n64);
@@ -220,7 +258,18 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
         HGMM_LAUNCH_CHECK();
         const bool stop_here = p.debug_stop_level == l + 1;
         const int em_iters = stop_here ? p.debug_stop_iters : p.em_iters;
-        for (int k = 0; k < em_iters; ++k) {
+        if (n_par >= LOCAL_EM_PARENTS && em_iters > 0) {
+            ProfScope ps_(t, K_ESTEP, s);
+            if (comp)
+                k_em_local<true><<<n_par, EST_THREADS, 0, s>>>(l, n, em_iters, cur, t->items, t->item_range,
+                                                              t->partials, t->seg_count, t->root, p.n_min,
+                                                              t->stat, t->est, t->status);
+            else
+                k_em_local<false><<<n_par, EST_THREADS, 0, s>>>(l, n, em_iters, cur, t->items, t->item_range,
+                                                               t->partials, t->seg_count, t->root, p.n_min,
+                                                               t->stat, t->est, t->status);
+        }
+        for (int k = 0; k < (n_par >= LOCAL_EM_PARENTS ? 0 : em_iters); ++k) {
             {
                 ProfScope ps_(t, K_ESTEP, s);
                 if (comp)
