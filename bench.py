@@ -347,6 +347,9 @@ def gpu_main(args, rank, world, local_rank):
     learned = None
     if not args.no_learned:
         learned = learned_section(args, B, torch)
+    large = None
+    if not args.no_large_build:
+        large = large_build_section(args, B, torch)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -377,6 +380,7 @@ def gpu_main(args, rank, world, local_rank):
         "kernels": kernels,
         "batched": batched,
         "learned": learned,
+        "large_build": large,
         "cpu_baseline": cpu,
         "clocks": clk,
         "accuracy": {"rot_err_deg_vs_truth": rot_err,
@@ -486,6 +490,49 @@ MLP_FWD_FLOPS = 2 * (1280 * 256 + 256 * 256 + 256 * 9)
 MLP_BWD_FLOPS = 2 * (256 * 9 + 9 * 256 + 256 * 256 + 256 * 256 + 256 * 1280)
 
 
+def large_cloud(n, seed):
+    """An n-point plane/box/sphere cloud (float4 on the device), sampled on
+    the host in eight chunks."""
+    import torch
+    from paper_1807_02587_gb300 import synth
+    scene = synth.primitive_scene(synth.make_rng(seed + 1))
+    parts = [synth._sample_primitives(synth.make_rng(seed + 10 + k), scene, n // 8, 0.005) for k in range(8)]
+    return torch.from_numpy(synth.to_float4(np.concatenate(parts))).cuda()
+
+
+def large_build_section(args, B, torch):
+    """The build on a cloud far larger than L2 (HBM-resident points): the
+    E-step's achieved point-read bandwidth against the measured HBM peak and
+    its FP32 rate against the ALU peak, from the event profile of one build."""
+    dev = large_cloud(args.large_points, args.seed)
+    n = int(dev.shape[0])
+    tree = B.Tree(n, 4)
+    tree.build(dev, 4)
+    tree.sync()
+    tree.profile(True)
+    tree.build(dev, 4)
+    tree.sync()
+    prof = tree.profile_read()
+    tree.profile(False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tree.build(dev, 4)
+    e1.record()
+    tree.sync()
+    es_ms, es_n = prof["estep"]
+    per = es_ms / max(es_n, 1) / 1e3
+    hbm, kind = _peaks()
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    alu = sm_count * 128 * 2 * 2070e6 / 1e12
+    return {"points": n, "depth": 4, "build_ms": e0.elapsed_time(e1),
+            "estep_launches": es_n, "estep_us_per_launch": per * 1e6,
+            "estep_point_read_GBps": 16 * n / per / 1e9, "hbm_peak_GBps": hbm, "peak_kind": kind,
+            "estep_hbm_frac": 16 * n / per / 1e9 / hbm,
+            "estep_TFLOPs": KERNEL_WORK["estep"]["flops"] * n / per / 1e12 if KERNEL_WORK["estep"]["flops"] else None,
+            "fp32_peak_TFLOPs": alu,
+            "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
+
+
 def learned_section(args, B, torch):
     """Learned pose proposal: the shipped network (trained on 100k pairs by
     paper_1807_02587_gb300.train_proposal) proposes, the plain method refines
@@ -574,6 +621,11 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-pairs", type=int, default=256)
     ap.add_argument("--learned-points", type=int, default=50000)
+    ap.add_argument("--profile-build", type=int, default=0, metavar="N",
+                    help="only build the depth-4 tree of an N-point plane/box/sphere cloud 3 times, "
+                         "for a profiler")
+    ap.add_argument("--no-large-build", action="store_true")
+    ap.add_argument("--large-points", type=int, default=16_000_000)
     ap.add_argument("--profile-mlp", action="store_true",
                     help="only run the proposal network (5 forwards of 8192 pairs, 3 training "
                          "steps of 1024), for a profiler")
@@ -588,6 +640,16 @@ def main():
         return reference_main(args, rank, world)
     if args.profile_mlp:
         return profile_mlp_main()
+    if args.profile_build:
+        import torch
+        from paper_1807_02587_gb300 import binding as B
+        dev = large_cloud(args.profile_build, args.seed)
+        tree = B.Tree(dev.shape[0], 4)
+        for _ in range(3):
+            tree.build(dev, 4)
+        tree.sync()
+        print(json.dumps({"profile_build": True, "points": int(dev.shape[0])}))
+        return 0
     return gpu_main(args, rank, world, local_rank)
 
 

@@ -222,8 +222,10 @@ using namespace hgmm;
         }                                                     \
     } while (0)
 
-// levels with at least this many parents run their EM parent-locally
+// levels with at least this many parents, of at most LOCAL_EM_POINTS points
+// on average, run their EM parent-locally (one CTA per parent)
 constexpr int LOCAL_EM_PARENTS = 256;
+constexpr int64_t LOCAL_EM_POINTS = 2048;
 
 int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                     const hgmm_params& p, cudaStream_t s) {
@@ -258,7 +260,8 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
         HGMM_LAUNCH_CHECK();
         const bool stop_here = p.debug_stop_level == l + 1;
         const int em_iters = stop_here ? p.debug_stop_iters : p.em_iters;
-        if (n_par >= LOCAL_EM_PARENTS && em_iters > 0) {
+        const bool local_em = n_par >= LOCAL_EM_PARENTS && n64 <= LOCAL_EM_POINTS * n_par;
+        if (local_em && em_iters > 0) {
             ProfScope ps_(t, K_ESTEP, s);
             if (comp)
                 k_em_local<true><<<n_par, EST_THREADS, 0, s>>>(l, n, em_iters, cur, t->items, t->item_range,
@@ -269,7 +272,7 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                                                                t->partials, t->seg_count, t->root, p.n_min,
                                                                t->stat, t->est, t->status);
         }
-        for (int k = 0; k < (n_par >= LOCAL_EM_PARENTS ? 0 : em_iters); ++k) {
+        for (int k = 0; k < (local_em ? 0 : em_iters); ++k) {
             {
                 ProfScope ps_(t, K_ESTEP, s);
                 if (comp)
