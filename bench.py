@@ -173,6 +173,27 @@ def reference_main(args, rank, world):
     return 0
 
 
+# ---------------------------------------------------------------- ranks
+def rank_seed(seed, rank):
+    """Weak scaling: every rank registers its own LiDAR pair (no data-path
+    collective; the ranks only meet to time and to add up their work)."""
+    return seed + rank
+
+
+def aggregate_over_ranks(points, ms, e2e_ms, world, device):
+    """Whole-job figures: points summed over the ranks, step times (device
+    and end to end) the maximum over the ranks."""
+    if world == 1:
+        return points, ms, e2e_ms
+    import torch
+    import torch.distributed as dist
+    p = torch.tensor([points], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    m = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(p[0]), float(m[0]), float(m[1])
+
+
 # ---------------------------------------------------------------- GPU leg
 def gpu_main(args, rank, world, local_rank):
     import torch
@@ -183,7 +204,7 @@ def gpu_main(args, rank, world, local_rank):
     from paper_1807_02587_gb300 import binding as B
     from paper_1807_02587_gb300 import synth
 
-    pair = synth.lidar_pair(args.seed + rank)
+    pair = synth.lidar_pair(rank_seed(args.seed, rank))
     tgt4 = synth.to_float4(pair["tgt"])
     src4 = synth.to_float4(pair["src"])
     n_t, n_s = tgt4.shape[0], src4.shape[0]
@@ -283,16 +304,7 @@ def gpu_main(args, rank, world, local_rank):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_step = float(np.mean(e2e_ms))
 
-    pts = float(n_t + n_s)
-    tot = torch.tensor([pts, ms_step, e2e_step], dtype=torch.float64, device="cuda")
-    if world > 1:
-        pts_all = tot[:1].clone()
-        dist.all_reduce(pts_all, op=dist.ReduceOp.SUM)
-        mx = tot[1:].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        pts_tot, ms_max, e2e_max = float(pts_all[0]), float(mx[0]), float(mx[1])
-    else:
-        pts_tot, ms_max, e2e_max = pts, ms_step, e2e_step
+    pts_tot, ms_max, e2e_max = aggregate_over_ranks(float(n_t + n_s), ms_step, e2e_step, world, "cuda")
     if rank != 0:
         dist.destroy_process_group()
         return 0
