@@ -362,6 +362,9 @@ def gpu_main(args, rank, world, local_rank):
     large = None
     if not args.no_large_build:
         large = large_build_section(args, B, torch)
+    odometry = None
+    if not args.no_odometry:
+        odometry = odometry_section(args, B, torch)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -393,6 +396,7 @@ def gpu_main(args, rank, world, local_rank):
         "batched": batched,
         "learned": learned,
         "large_build": large,
+        "odometry": odometry,
         "cpu_baseline": cpu,
         "clocks": clk,
         "accuracy": {"rot_err_deg_vs_truth": rot_err,
@@ -500,6 +504,55 @@ def batched_section(args, B, synth, torch, prm):
 # algorithmic FLOPs of the proposal network per pair (1280 -> 256 -> 256 -> 9)
 MLP_FWD_FLOPS = 2 * (1280 * 256 + 256 * 256 + 256 * 9)
 MLP_BWD_FLOPS = 2 * (256 * 9 + 9 * 256 + 256 * 256 + 256 * 256 + 256 * 1280)
+
+
+def odometry_section(args, B, torch):
+    """Frame-to-frame odometry over a LiDAR drive (each frame's tree is the
+    model of the next frame, three yaw starts per frame): frames/s with the
+    build of frame k overlapped with the registration of frame k on a second
+    stream and without, and the trajectory's drift for the default lambda_c
+    with three starts and with the constant-velocity start alone, and for
+    lambda_c = 0."""
+    from paper_1807_02587_gb300 import synth
+    from paper_1807_02587_gb300.odometry import Odometry, chain
+    seq = synth.lidar_sequence(args.seed + 11, frames=args.odometry_frames)
+    dev = [torch.from_numpy(synth.to_float4(f)).cuda() for f in seq["frames"]]
+    n = max(d.shape[0] for d in dev)
+    F = len(dev)
+    W_gt = np.linalg.inv(seq["W"][0]) @ seq["W"]
+    path = float(np.sum(np.linalg.norm(np.diff(W_gt[:, :3, 3], axis=0), axis=1)))
+    out = {"frames": F, "points_per_frame": int(np.mean([d.shape[0] for d in dev])), "path_m": path}
+    for overlap in (True, False):
+        odo = Odometry(n, depth=DEPTH, iters=ITERS, overlap=overlap)
+        odo.run(dev)
+        odo.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T = odo.run(dev)
+        odo.sync()
+        torch.cuda.synchronize()
+        out["frames_per_s_overlap" if overlap else "frames_per_s_sequential"] = F / (time.perf_counter() - t0)
+    for lam, yaws, key in ((None, (0.0, 3.0, -3.0), "default_lam_c"), (None, (0.0,), "default_lam_c_one_start"),
+                           (0.0, (0.0, 3.0, -3.0), "lam_c_0")):
+        prm = B.params(lam_c=lam) if lam is not None else None
+        odo = Odometry(n, depth=DEPTH, iters=ITERS, prm=prm, yaw_starts_deg=yaws)
+        T = odo.run(dev)
+        odo.sync()
+        Tn = T.cpu().numpy()
+        W = chain(Tn)
+        per = np.array([[_rot_err(Tn[k, :3, :3], seq["T_rel"][k][:3, :3]),
+                         float(np.linalg.norm(Tn[k, :3, 3] - seq["T_rel"][k][:3, 3]))] for k in range(1, F)])
+        out[key] = {"final_trans_err_m": float(np.linalg.norm(W[-1, :3, 3] - W_gt[-1, :3, 3])),
+                    "final_rot_err_deg": _rot_err(W[-1, :3, :3], W_gt[-1, :3, :3]),
+                    "per_frame_rot_err_deg_median": float(np.median(per[:, 0])),
+                    "per_frame_trans_err_m_median": float(np.median(per[:, 1])),
+                    "frames_rot_err_over_1deg": int(np.sum(per[:, 0] > 1.0))}
+    return out
+
+
+def _rot_err(Ra, Rb):
+    c = (np.trace(Ra.T @ Rb) - 1.0) / 2.0
+    return float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
 
 
 def large_cloud(n, seed):
@@ -637,6 +690,8 @@ def main():
                     help="only build the depth-4 tree of an N-point plane/box/sphere cloud 3 times, "
                          "for a profiler")
     ap.add_argument("--no-large-build", action="store_true")
+    ap.add_argument("--no-odometry", action="store_true")
+    ap.add_argument("--odometry-frames", type=int, default=20)
     ap.add_argument("--large-points", type=int, default=16_000_000)
     ap.add_argument("--profile-mlp", action="store_true",
                     help="only run the proposal network (5 forwards of 8192 pairs, 3 training "

@@ -125,10 +125,16 @@ int hgmm_pose_encode(const double* d_T, const double* d_frames, int32_t n, float
                      void* stream);
 
 /* Per pair: the pose whose objective is lower (a non-finite objective loses;
- * ties keep a) to d_T_out (n x 16), and which one (0 = a, 1 = b) to d_choice
- * if not NULL. */
+ * ties keep a) to d_T_out (n x 16), which one (0 = a, 1 = b) to d_choice and
+ * its objective to d_obj_out, each if not NULL (d_T_out and d_obj_out may be
+ * d_T_a and d_obj_a, so candidates can be folded in one by one). */
 int hgmm_pose_select(int32_t n, const double* d_T_a, const double* d_obj_a, const double* d_T_b,
-                     const double* d_obj_b, double* d_T_out, int32_t* d_choice, void* stream);
+                     const double* d_obj_b, double* d_T_out, int32_t* d_choice, double* d_obj_out,
+                     void* stream);
+
+/* d_out[i] = d_A[i] d_B[i] for n pairs of 4x4 FP64 row-major poses (device,
+ * n x 16 each; d_out may alias neither input). */
+int hgmm_pose_compose(int32_t n, const double* d_A, const double* d_B, double* d_out, void* stream);
 
 /* Checking entry point for the tensor-core GEMM the network runs on:
  * d_out[m * N + n] = sum_k A[m][k] B[n][k] (float32, device) with BF16

@@ -103,7 +103,8 @@ def _load():
         "hgmm_tree_features": (ctypes.c_int, [vp, vp, vp, vp]),
         "hgmm_pose_decode": (ctypes.c_int, [vp, vp, i32, vp, vp]),
         "hgmm_pose_encode": (ctypes.c_int, [vp, vp, i32, vp, vp]),
-        "hgmm_pose_select": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, vp, vp]),
+        "hgmm_pose_select": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "hgmm_pose_compose": (ctypes.c_int, [i32, vp, vp, vp, vp]),
         "hgmm_debug_gemm": (ctypes.c_int, [vp, i64, i64, vp, i64, i64, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -509,7 +510,7 @@ def hgmm_pose_encode(T, frames, labels, stream=None):
     return labels
 
 
-def hgmm_pose_select(T_a, obj_a, T_b, obj_b, T_out, choice=None, stream=None):
+def hgmm_pose_select(T_a, obj_a, T_b, obj_b, T_out, choice=None, stream=None, obj_out=None):
     import torch
     n = int(T_a.shape[0])
     _check(_lib.hgmm_pose_select(n, _need(T_a, torch.float64, 16 * n, "T_a"),
@@ -518,8 +519,19 @@ def hgmm_pose_select(T_a, obj_a, T_b, obj_b, T_out, choice=None, stream=None):
                                  _need(obj_b, torch.float64, n, "obj_b"),
                                  _need(T_out, torch.float64, 16 * n, "T_out"),
                                  None if choice is None else _need(choice, torch.int32, n, "choice"),
+                                 None if obj_out is None else _need(obj_out, torch.float64, n, "obj_out"),
                                  _stream_ptr(stream)), "hgmm_pose_select")
     return T_out
+
+
+def hgmm_pose_compose(A, Bm, out, stream=None):
+    """out[i] = A[i] @ B[i] for (n, 16) (or (n, 4, 4)) float64 CUDA tensors."""
+    import torch
+    n = int(A.shape[0])
+    _check(_lib.hgmm_pose_compose(n, _need(A, torch.float64, 16 * n, "A"), _need(Bm, torch.float64, 16 * n, "B"),
+                                  _need(out, torch.float64, 16 * n, "out"), _stream_ptr(stream)),
+           "hgmm_pose_compose")
+    return out
 
 
 def hgmm_debug_gemm(A, a_m: int, a_k: int, B, b_n: int, b_k: int, M: int, N: int, K: int, out,

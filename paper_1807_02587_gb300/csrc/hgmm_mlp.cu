@@ -288,16 +288,32 @@ __global__ void k_encode(const double* __restrict__ T, const double* __restrict_
     for (int a = 0; a < 3; ++a) l[9 + a] = float((Vt[a] * d[0] + Vt[3 + a] * d[1] + Vt[6 + a] * d[2]) / st);
 }
 
-__global__ void k_select(int n, const double* __restrict__ Ta, const double* __restrict__ oa,
-                         const double* __restrict__ Tb, const double* __restrict__ ob,
-                         double* __restrict__ To, int* __restrict__ choice) {
+// One thread per pair; inputs and outputs may alias (T_out = T_a, obj_out
+// = obj_a): every value is read before it is written.
+__global__ void k_select(int n, const double* Ta, const double* oa, const double* Tb, const double* ob,
+                         double* To, int* __restrict__ choice, double* oo) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double a = oa[i], b = ob[i];
     const bool take_b = isfinite(b) && (!isfinite(a) || b < a);
     const double* src = (take_b ? Tb : Ta) + 16 * int64_t(i);
-    for (int k = 0; k < 16; ++k) To[16 * int64_t(i) + k] = src[k];
+    double v[16];
+    for (int k = 0; k < 16; ++k) v[k] = src[k];
+    for (int k = 0; k < 16; ++k) To[16 * int64_t(i) + k] = v[k];
     if (choice) choice[i] = take_b ? 1 : 0;
+    if (oo) oo[i] = take_b ? b : a;
+}
+
+__global__ void k_compose(int n, const double* __restrict__ A, const double* __restrict__ Bm,
+                          double* __restrict__ O) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* a = A + 16 * int64_t(i);
+    const double* b = Bm + 16 * int64_t(i);
+    double* o = O + 16 * int64_t(i);
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c)
+            o[4 * r + c] = a[4 * r] * b[c] + a[4 * r + 1] * b[4 + c] + a[4 * r + 2] * b[8 + c] + a[4 * r + 3] * b[12 + c];
 }
 
 }  // namespace
@@ -661,10 +677,18 @@ int hgmm_debug_gemm(const uint16_t* d_A, int64_t a_m, int64_t a_k, const uint16_
 }
 
 int hgmm_pose_select(int32_t n, const double* d_T_a, const double* d_obj_a, const double* d_T_b,
-                     const double* d_obj_b, double* d_T_out, int32_t* d_choice, void* stream) {
+                     const double* d_obj_b, double* d_T_out, int32_t* d_choice, double* d_obj_out,
+                     void* stream) {
     if (n < 1 || !d_T_a || !d_obj_a || !d_T_b || !d_obj_b || !d_T_out) return HGMM_EINVAL;
     k_select<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(n, d_T_a, d_obj_a, d_T_b,
-                                                                             d_obj_b, d_T_out, d_choice);
+                                                                             d_obj_b, d_T_out, d_choice,
+                                                                             d_obj_out);
+    return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
+}
+
+int hgmm_pose_compose(int32_t n, const double* d_A, const double* d_B, double* d_out, void* stream) {
+    if (n < 1 || !d_A || !d_B || !d_out || d_out == d_A || d_out == d_B) return HGMM_EINVAL;
+    k_compose<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(n, d_A, d_B, d_out);
     return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
 }
 

@@ -148,12 +148,9 @@ def label_pairs(ps: PairSet, depth: int = 3, iters: int = 30, label_tol_deg: flo
     starts = [None] + list(eng.flip_starts())
     best = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
     best_obj = torch.full((n,), float("inf"), dtype=torch.float64, device="cuda")
-    tmp = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
     for k, T0 in enumerate(starts):
         T, o = eng.register(T0, iters)
-        B.hgmm_pose_select(best, best_obj, T, o, tmp)
-        best.copy_(tmp)
-        best_obj.copy_(torch.minimum(best_obj, torch.nan_to_num(o, nan=float("inf"))))
+        B.hgmm_pose_select(best, best_obj, T, o, best, obj_out=best_obj)
     labels = torch.zeros((n, 12), dtype=torch.float32, device="cuda")
     B.hgmm_pose_encode(best, eng.frames, labels)
     torch.cuda.synchronize()

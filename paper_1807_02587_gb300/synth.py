@@ -15,6 +15,8 @@ available here; the generators below stand in for them:
                       of Sec. 5 (random rotation, translation per axis).
 * ``lidar_pair``      two consecutive spinning-LiDAR sweeps of an urban
                       scene (ground, boxes, poles), analogue of Sec. 6 VLP-16.
+* ``lidar_sequence``  a drive of many such sweeps with known poses (frame-to-
+                      frame odometry).
 * ``depth_pair``      a back-projected pinhole depth image of a room,
                       analogue of the Lounge structured-light frames (Sec. 6).
 * ``batched_pairs``   hundreds of uneven plane/sphere/box pairs.
@@ -37,7 +39,7 @@ import numpy as np
 __all__ = [
     "make_rng", "axis_angle_matrix", "random_rotation", "uniform_rotation",
     "rigid", "apply", "to_float4", "corner_scene", "corner_pair",
-    "lidar_pair", "depth_pair", "primitive_scene", "primitive_pair",
+    "lidar_pair", "lidar_sequence", "depth_pair", "primitive_scene", "primitive_pair",
     "batched_pairs", "so3_pairs", "so3_scene_set", "mlp_init", "blob_cloud",
 ]
 
@@ -262,6 +264,34 @@ def lidar_pair(seed: int, forward: float = 1.0, max_yaw_deg: float = 2.0,
     src = _lidar_sweep(rng, scene, c2, yaw)
     T = rigid(axis_angle_matrix([0, 0, 1], yaw), c2 - c1)
     return {"src": src, "tgt": tgt, "T_gt": T, "name": "lidar", "seed": seed}
+
+
+def lidar_sequence(seed: int, frames: int = 20, forward: float = 1.0, max_yaw_deg: float = 2.0,
+                   height: float = 1.8, start_x: float = -10.0) -> dict:
+    """``frames`` sweeps of the 64-beam LiDAR of ``lidar_pair`` along a drive
+    through one urban scene: the sensor advances ``forward`` metres along its
+    heading per frame and turns by a yaw drawn in +-max_yaw_deg plus a pull
+    back towards the street axis.  ``frames`` holds each sweep in its own
+    sensor frame, ``W`` the sensor-to-world pose of every frame and ``T_rel``
+    the motion T_rel[k] = W[k-1]^-1 W[k] that maps frame k into frame k-1
+    (T_rel[0] = I)."""
+    rng = make_rng(seed)
+    scene = _urban_scene(rng)
+    W = np.empty((frames, 4, 4))
+    pts = []
+    c = np.array([start_x, 0.0, height])
+    psi = 0.0
+    for k in range(frames):
+        if k:
+            c = c + forward * np.array([np.cos(psi), np.sin(psi), 0.0])
+            psi = psi - 0.3 * psi - 0.02 * c[1] + np.deg2rad(rng.uniform(-max_yaw_deg, max_yaw_deg))
+        W[k] = rigid(axis_angle_matrix([0, 0, 1], psi), c)
+        pts.append(_lidar_sweep(rng, scene, c, psi))
+    T_rel = np.empty_like(W)
+    T_rel[0] = np.eye(4)
+    for k in range(1, frames):
+        T_rel[k] = np.linalg.inv(W[k - 1]) @ W[k]
+    return {"frames": pts, "W": W, "T_rel": T_rel, "name": "lidar_sequence", "seed": seed}
 
 
 # --------------------------------------------------------------------------

@@ -67,7 +67,8 @@ def test_host_side_argument_checks(lib):
     assert B._lib.hgmm_mlp_gradients(None, None, None, None, 4, 4, 1.0, None, None) == B.HGMM_EINVAL
     assert B._lib.hgmm_pose_decode(None, None, 4, None, None) == B.HGMM_EINVAL
     assert B._lib.hgmm_pose_encode(None, None, 4, None, None) == B.HGMM_EINVAL
-    assert B._lib.hgmm_pose_select(0, None, None, None, None, None, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_pose_select(0, None, None, None, None, None, None, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_pose_compose(1, None, None, None, None) == B.HGMM_EINVAL
     assert B._lib.hgmm_tree_features(None, None, None, None) == B.HGMM_EINVAL
     assert B._lib.hgmm_batch_features(None, None, None, None, None, None) == B.HGMM_EINVAL
     assert B._lib.hgmm_register_objective(None, None, None) == B.HGMM_EINVAL

@@ -278,6 +278,17 @@ def test_pose_encode_decode_select_match_oracle(B):
     s = sel.cpu().numpy()
     for i in range(n):
         assert np.array_equal(s[i], (Tout if want[i] else dT)[i].cpu().numpy())
+    # in place (output = first candidate) with the chosen objective, and the
+    # batched 4x4 product
+    Ta, oa2 = dT.clone(), oa.clone()
+    B.hgmm_pose_select(Ta, oa2, Tout, ob, Ta, obj_out=oa2)
+    P = torch.zeros_like(dT)
+    B.hgmm_pose_compose(dT, Tout, P)
+    torch.cuda.synchronize()
+    assert np.array_equal(Ta.cpu().numpy(), s)
+    assert np.array_equal(oa2.cpu().numpy(), np.where(want == 1, b, a))
+    want_p = np.einsum("nij,njk->nik", T, Tout.cpu().numpy().reshape(n, 4, 4))
+    assert np.allclose(P.cpu().numpy().reshape(n, 4, 4), want_p, rtol=0, atol=1e-12)
 
 
 def _oracle_objective(tree_o, Zsrc, T):
