@@ -38,6 +38,11 @@ notes of the repository):
   live children of its parent at the level where the descent stopped.
 * A point whose current node has no live children stops there.
 * Complexity(Theta) <= lambda_c stops the descent ("<=" as printed).
+* The flat "GMM J=n" variant (Sec. 5) does not say how its J components are
+  obtained: here they are the leaves of the tree (weights = products of the
+  within-parent weights), optionally refined by plain EM over all J, and the
+  registration associates every point with every component softly (Eq. 3
+  over all J, Eq. 8 moments), which is what removing the tree leaves.
 
 Parity pins: every function here is checked by ``tests/test_oracle_*.py``
 against closed forms, invariants and brute force (posteriors summing to one,
@@ -461,6 +466,126 @@ def flat_associate(Zp, pi, mu, Sigma):
                   for c in range(pi.shape[0])], axis=1)
     g, _ = posteriors(S)
     return g, np.argmax(S, axis=1)
+
+
+# --------------------------------------------------------------------------
+# Flat "GMM J=n" variant (Sec. 5, variant 3): a single-level GMM, every
+# point associated with every component (O(NJ)), the same Eq. 9-16 M-step
+# --------------------------------------------------------------------------
+@dataclass
+class Flat:
+    pi: np.ndarray      # (J,) mixing weights over the whole cloud (0 = dead)
+    mu: np.ndarray      # (J,3)
+    Sigma: np.ndarray   # (J,3,3)
+    node: np.ndarray    # (J,2) (level, index) of the tree node each started from
+    eps: float
+
+    @property
+    def live(self):
+        return self.pi > 0.0
+
+
+def flat_from_tree(tree: Tree, level=None) -> Flat:
+    """The single-level GMM a tree defines at the scale of `level` (default:
+    its deepest level).  Components: every live node of that level and every
+    live node of a shallower level without a live child (the leaves of the
+    tree cut below `level`).  Weight: the product of the within-parent
+    weights pi along the node's path from level 0 (the mixture weight the
+    hierarchy gives it), the weights renormalised to sum to one.  Ordered by
+    level, then by index within the level."""
+    L = len(tree.levels) if level is None else level + 1
+    glob = []
+    for l in range(L):
+        lv = tree.levels[l]
+        up = np.ones(lv.pi.shape[0]) if l == 0 else np.repeat(glob[l - 1], J)
+        glob.append(np.where(lv.live, lv.pi * up, 0.0))
+    pis, mus, Sigs, nodes = [], [], [], []
+    for l in range(L):
+        lv = tree.levels[l]
+        if l + 1 < L:
+            has_child = tree.levels[l + 1].live.reshape(-1, J).any(axis=1)
+        else:
+            has_child = np.zeros(lv.pi.shape[0], bool)
+        sel = np.nonzero(lv.live & ~has_child)[0]
+        pis.append(glob[l][sel])
+        mus.append(lv.mu[sel])
+        Sigs.append(lv.Sigma[sel])
+        nodes.append(np.stack([np.full(sel.size, l), sel], axis=1))
+    pi = np.concatenate(pis)
+    return Flat(pi=pi / pi.sum(), mu=np.concatenate(mus), Sigma=np.concatenate(Sigs),
+                node=np.concatenate(nodes), eps=tree.eps)
+
+
+def flat_scores(Zp, flat: Flat):
+    """(N, J) matrix of log(pi_j N(z_i | Theta_j)) (Eq. 2 terms); -inf for
+    dead components."""
+    inv, logdet = gauss_terms(flat.Sigma)
+    with np.errstate(divide="ignore"):
+        lp = np.log(flat.pi)
+    n = Zp.shape[0]
+    S = np.empty((n, flat.pi.shape[0]))
+    for c in range(flat.pi.shape[0]):
+        S[:, c] = lp[c] + log_gauss(Zp, np.broadcast_to(flat.mu[c], Zp.shape),
+                                    np.broadcast_to(inv[c], (n, 3, 3)), np.full(n, logdet[c]))
+    return S
+
+
+def flat_em(Z, flat: Flat, iters: int, n_min: float = 8.0):
+    """`iters` EM iterations of the flat GMM on cloud Z: Eq. 3 posteriors of
+    every point over all components, then pi_j = S0_j / N, mu_j = S1_j / S0_j,
+    Sigma_j = sum_i gamma_ij (z_i - mu_j)(z_i - mu_j)^T / S0_j + eps I.  A
+    component below n_min expected points dies (pi = 0) and keeps its last
+    parameters.  Returns the new Flat and the log-likelihood sum_i log p(z_i)
+    under the parameters each E-step used."""
+    Z = np.asarray(Z, np.float64)
+    pi, mu, Sigma = flat.pi.copy(), flat.mu.copy(), flat.Sigma.copy()
+    lls = []
+    for _ in range(iters):
+        g, ll = posteriors(flat_scores(Z, Flat(pi, mu, Sigma, flat.node, flat.eps)))
+        lls.append(float(ll.sum()))
+        S0 = g.sum(axis=0)
+        live = (pi > 0.0) & (S0 >= n_min) & (S0 > 0.0)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            mu_n = (g.T @ Z) / S0[:, None]
+        Sig_n = np.empty_like(Sigma)
+        for c in range(pi.shape[0]):
+            d = Z - mu_n[c]
+            with np.errstate(invalid="ignore", divide="ignore"):
+                Sig_n[c] = (g[:, c, None] * d).T @ d / S0[c] + flat.eps * np.eye(3)
+        mu = np.where(live[:, None], mu_n, mu)
+        Sigma = np.where(live[:, None, None], Sig_n, Sigma)
+        pi = np.where(live, S0 / Z.shape[0], 0.0)
+    return Flat(pi=pi, mu=mu, Sigma=Sigma, node=flat.node, eps=flat.eps), lls
+
+
+def flat_moments(flat: Flat, Zp):
+    """Eq. 8 with the flat model: M0_j = sum_i gamma_ij, M1_j = sum_i
+    gamma_ij z'_i over every point and component."""
+    g, _ = posteriors(flat_scores(Zp, flat))
+    return g.sum(axis=0), g.T @ Zp
+
+
+def register_flat(flat: Flat, Z2, T_init=None, iters=30, history=False):
+    """EM registration of source Z2 to the flat GMM (Eq. 1): each round the
+    flat moments at the current pose, then the same M-step as the tree
+    (Eq. 9-16 with lambda clamped at eps) and T <- dT T."""
+    Z2 = np.asarray(Z2, dtype=np.float64)
+    T = np.eye(4) if T_init is None else np.array(T_init, dtype=np.float64)
+    N = Z2.shape[0]
+    lam_all, vec_all = sym_eig(flat.Sigma)
+    lam_all = np.maximum(lam_all, flat.eps)
+    hist = []
+    for _ in range(iters):
+        Zp = Z2 @ T[:3, :3].T + T[:3, 3]
+        M0, M1 = flat_moments(flat, Zp)
+        used, pstar, mstar = cluster_stats(M0, M1, N)
+        x = solve_increment(mstar, pstar, flat.mu[used], lam_all[used], vec_all[used])
+        if history:
+            hist.append({"T_start": T.copy(), "x": x, "M0": M0, "M1": M1,
+                         "objective": objective(np.eye(4), mstar, pstar, flat.mu[used],
+                                                lam_all[used], vec_all[used])})
+        T = increment_matrix(x) @ T
+    return (T, hist) if history else T
 
 
 # --------------------------------------------------------------------------
