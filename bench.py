@@ -365,6 +365,9 @@ def gpu_main(args, rank, world, local_rank):
     odometry = None
     if not args.no_odometry:
         odometry = odometry_section(args, B, torch)
+    variants = None
+    if not args.no_variants:
+        variants = variants_section(args, B, torch, pair, tgt, src, fp32_peak_tflops)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -397,6 +400,7 @@ def gpu_main(args, rank, world, local_rank):
         "learned": learned,
         "large_build": large,
         "odometry": odometry,
+        "variants": variants,
         "cpu_baseline": cpu,
         "clocks": clk,
         "accuracy": {"rot_err_deg_vs_truth": rot_err,
@@ -550,6 +554,66 @@ def odometry_section(args, B, torch):
     return out
 
 
+# FP32 operations per (point, component) pair and round of the flat
+# registration: the score (3 sub, 15 for the triangular W (z - mu) and its
+# squared norm) twice, the running log-sum (max, exp2, add), gamma (sub,
+# exp2) and its four moments (add, 3 FMA)
+FLAT_FLOPS_PER_PAIR = 2 * 18 + 3 + 2 + 7
+
+
+def variants_section(args, B, torch, pair, tgt, src, fp32_peak_tflops):
+    """Sec. 5's variants on the bench's LiDAR pair (depth 4, 30 rounds, tree
+    built once): Adaptive (lambda_c = 0.01), GMM-Tree (lambda_c = 0) and the
+    flat GMM J=n (the tree's leaves; and after 4 EM iterations over all J):
+    registration time (CUDA events, median of 3), error against the known
+    motion, and for the flat model its (point, component) pair rate against
+    the FP32 peak."""
+    n = int(max(tgt.shape[0], src.shape[0]))
+    tree = B.Tree(n, DEPTH)
+    tree.build(tgt, DEPTH)
+    tree.sync()
+    extent = tree.root()["extent"]
+    T_gt = pair["T_gt"]
+    out = {"workload": WORKLOAD, "depth": DEPTH, "reg_iters": ITERS}
+
+    def timed(fn, reps=3):
+        s = torch.cuda.current_stream()
+        ts = []
+        res = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            res = fn()
+            b.record(s)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts)), res
+
+    def errs(T):
+        T = T.cpu().numpy()
+        return {"rot_err_deg": _rot_err(T[:3, :3], T_gt[:3, :3]),
+                "trans_err_m": float(np.linalg.norm(T[:3, 3] - T_gt[:3, 3]))}
+
+    for lam, key in ((-1.0, "adaptive"), (0.0, "gmm_tree")):
+        ms, T = timed(lambda: tree.register(src, iters=ITERS, lam_c=lam))
+        tree.sync()
+        out[key] = {"ms": ms, **errs(T)}
+    flat = B.Flat(n, int(B.hgmm_node_count(DEPTH)))
+    for em, key in ((0, "flat_leaves"), (4, "flat_em4")):
+        flat.from_tree(tree)
+        fit_ms, _ = timed(lambda: flat.fit(tgt, em), reps=1) if em else (0.0, None)
+        flat.sync()
+        J = flat.export()["J"]
+        ms, T = timed(lambda: flat.register(src, iters=ITERS))
+        flat.sync()
+        pairs = float(src.shape[0]) * J * ITERS
+        out[key] = {"J": J, "ms": ms, "fit_ms": fit_ms, **errs(T),
+                    "pairs_per_s": pairs / (ms / 1e3),
+                    "achieved_tflops": pairs * FLAT_FLOPS_PER_PAIR / (ms / 1e3) / 1e12,
+                    "frac_of_fp32_peak": pairs * FLAT_FLOPS_PER_PAIR / (ms / 1e3) / 1e12 / fp32_peak_tflops}
+    return out
+
+
 def _rot_err(Ra, Rb):
     c = (np.trace(Ra.T @ Rb) - 1.0) / 2.0
     return float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
@@ -691,6 +755,7 @@ def main():
                          "for a profiler")
     ap.add_argument("--no-large-build", action="store_true")
     ap.add_argument("--no-odometry", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--odometry-frames", type=int, default=20)
     ap.add_argument("--large-points", type=int, default=16_000_000)
     ap.add_argument("--profile-mlp", action="store_true",

@@ -1,4 +1,5 @@
-"""Thin ctypes binding of ``include/hgmm.h``.
+"""Thin ctypes binding of ``include/hgmm.h``, ``include/hgmm_proposal.h`` and
+``include/hgmm_flat.h``.
 
 Argument marshalling only: every function below forwards to the entry point
 of the same name in ``_lib/libhgmm.so``, passing raw device pointers taken
@@ -106,6 +107,15 @@ def _load():
         "hgmm_pose_select": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "hgmm_pose_compose": (ctypes.c_int, [i32, vp, vp, vp, vp]),
         "hgmm_debug_gemm": (ctypes.c_int, [vp, i64, i64, vp, i64, i64, i32, i32, i32, vp, vp]),
+        "hgmm_flat_create": (ctypes.c_int, [i64, i32, P(vp)]),
+        "hgmm_flat_destroy": (None, [vp]),
+        "hgmm_flat_from_tree": (ctypes.c_int, [vp, vp, i32, vp]),
+        "hgmm_flat_fit": (ctypes.c_int, [vp, vp, i64, i32, f32, vp]),
+        "hgmm_flat_register": (ctypes.c_int, [vp, vp, i64, vp, i32, vp, vp, vp]),
+        "hgmm_flat_objective": (ctypes.c_int, [vp, vp, vp]),
+        "hgmm_flat_export": (ctypes.c_int, [vp, vp, i64, P(i32), vp]),
+        "hgmm_flat_debug_moments": (ctypes.c_int, [vp, vp, i64, P(i32)]),
+        "hgmm_flat_sync": (ctypes.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -563,6 +573,113 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------ flat GMM J=n variant
+def hgmm_flat_create(max_points: int, max_components: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_lib.hgmm_flat_create(int(max_points), int(max_components), ctypes.byref(h)), "hgmm_flat_create")
+    return h
+
+
+def hgmm_flat_destroy(h) -> None:
+    _lib.hgmm_flat_destroy(h)
+
+
+def hgmm_flat_from_tree(h, tree_handle, level: int = -1, stream=None) -> None:
+    _check(_lib.hgmm_flat_from_tree(h, tree_handle, int(level), _stream_ptr(stream)), "hgmm_flat_from_tree")
+
+
+def hgmm_flat_fit(h, points, em_iters: int, n_min: float = 8.0, stream=None) -> None:
+    _check(_lib.hgmm_flat_fit(h, _dev_points(points, "points"), points.shape[0], int(em_iters), float(n_min),
+                              _stream_ptr(stream)), "hgmm_flat_fit")
+
+
+def hgmm_flat_register(h, src, T_init=None, iters: int = 30, stream=None, T_out=None, T_hist=None):
+    """Returns the device tensor T_out (4x4 float64)."""
+    import torch
+    if T_out is None:
+        T_out = torch.empty((4, 4), dtype=torch.float64, device=src.device)
+    for name, x in (("T_init", T_init), ("T_out", T_out), ("T_hist", T_hist)):
+        if x is not None and (x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous()):
+            raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
+    _check(_lib.hgmm_flat_register(h, _dev_points(src, "src"), src.shape[0], _dptr(T_init), int(iters),
+                                   _stream_ptr(stream), _dptr(T_out), _dptr(T_hist)), "hgmm_flat_register")
+    return T_out
+
+
+def hgmm_flat_objective(h, out, stream=None):
+    _check(_lib.hgmm_flat_objective(h, _dptr(out), _stream_ptr(stream)), "hgmm_flat_objective")
+    return out
+
+
+def hgmm_flat_export(h, cap: int):
+    """(J, components (min(J, cap), 10) float64, nodes (min(J, cap), 2) int32)."""
+    out = np.zeros((max(cap, 1), 10), np.float64)
+    node = np.zeros((max(cap, 1), 2), np.int32)
+    J = ctypes.c_int32()
+    _check(_lib.hgmm_flat_export(h, out.ctypes.data_as(ctypes.c_void_p), int(cap), ctypes.byref(J),
+                                 node.ctypes.data_as(ctypes.c_void_p)), "hgmm_flat_export")
+    m = min(J.value, cap)
+    return J.value, out[:m], node[:m]
+
+
+def hgmm_flat_debug_moments(h, cap: int) -> np.ndarray:
+    """(min(J, cap), 4) float64: M0, M1 of every component (last round)."""
+    out = np.zeros((max(cap, 1), 4), np.float64)
+    J = ctypes.c_int32()
+    _check(_lib.hgmm_flat_debug_moments(h, out.ctypes.data_as(ctypes.c_void_p), int(cap), ctypes.byref(J)),
+           "hgmm_flat_debug_moments")
+    return out[:min(J.value, cap)]
+
+
+def hgmm_flat_sync(h, stream=None) -> None:
+    _check(_lib.hgmm_flat_sync(h, _stream_ptr(stream)), "hgmm_flat_sync")
+
+
+class Flat:
+    """Owns one hgmm_flat: the single-level "GMM J=n" model of Sec. 5."""
+
+    def __init__(self, max_points: int, max_components: int):
+        self.handle = hgmm_flat_create(max_points, max_components)
+        self.max_components = max_components
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hgmm_flat_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def from_tree(self, tree, level: int = -1, stream=None):
+        hgmm_flat_from_tree(self.handle, tree.handle, level, stream)
+        return self
+
+    def fit(self, points, em_iters: int, n_min: float = 8.0, stream=None):
+        hgmm_flat_fit(self.handle, points, em_iters, n_min, stream)
+        return self
+
+    def register(self, src, T_init=None, iters: int = 30, stream=None, T_out=None, T_hist=None):
+        return hgmm_flat_register(self.handle, src, T_init, iters, stream, T_out, T_hist)
+
+    def sync(self, stream=None):
+        hgmm_flat_sync(self.handle, stream)
+
+    def export(self) -> dict:
+        J, a, node = hgmm_flat_export(self.handle, self.max_components)
+        S = np.empty((a.shape[0], 3, 3))
+        iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+        for k, (i, j) in enumerate(iu):
+            S[:, i, j] = a[:, 4 + k]
+            S[:, j, i] = a[:, 4 + k]
+        return {"J": J, "pi": a[:, 0], "mu": a[:, 1:4], "Sigma": S, "node": node}
+
+    def moments(self) -> np.ndarray:
+        return hgmm_flat_debug_moments(self.handle, self.max_components)
 
 
 # ---------------------------------------------------------------- convenience

@@ -35,7 +35,7 @@ def _nvcc():
 
 def _newest_input():
     files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    files.append(os.path.join(INCLUDE, "hgmm.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return max(os.path.getmtime(f) for f in files)
 
 
