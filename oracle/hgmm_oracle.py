@@ -38,6 +38,11 @@ notes of the repository):
   live children of its parent at the level where the descent stopped.
 * A point whose current node has no live children stops there.
 * Complexity(Theta) <= lambda_c stops the descent ("<=" as printed).
+* Sec. 4.1's remark that a parent's expectation is the sum of its children's
+  gives the variants of e_step_descent: gamma as the product of the sibling
+  posteriors along the path, and the threshold-pruned multi-path descent
+  (a child below tau is dropped with its subtree; each path stops as
+  Algorithm 1's does).
 * The flat "GMM J=n" variant (Sec. 5) does not say how its J components are
   obtained: here they are the leaves of the tree (weights = products of the
   within-parent weights), optionally refined by plain EM over all J, and the
@@ -362,6 +367,82 @@ def e_step_adaptive(tree: Tree, Zp, lam_c=None, want_m2=False):
     return out
 
 
+def e_step_descent(tree: Tree, Zp, mode: str, tau: float = 0.0, lam_c=None):
+    """Variants of Algorithm 1's descent (Sec. 4.1).  A node's expectation
+    for a point is the sum of its children's, so the expectation of a child
+    is its parent's times the child's posterior among its siblings.
+
+    mode "local":     the maximum-likelihood path; gamma = the stopping
+                      node's posterior among its siblings (e_step_adaptive).
+    mode "global":    the maximum-likelihood path; gamma = the product of the
+                      sibling posteriors along the path (the expectation).
+    mode "multipath": every live child whose expectation is >= tau is
+                      descended, the others are pruned with their subtrees;
+                      each path stops as Algorithm 1's does (complexity <=
+                      lambda_c, the leaf level, or no live children) and adds
+                      its expectation to the node where it stops.
+
+    Returns M0, M1 per level and the contributions as arrays (point, level,
+    node, gamma), one row per (point, stopping node)."""
+    lam_c = tree.params.lam_c if lam_c is None else lam_c
+    N = Zp.shape[0]
+    L = len(tree.levels)
+    # frontier: points whose search continues below node `par` (index within
+    # level l - 1; -1 = the root) with expectation g_par
+    pt = np.arange(N)
+    par = np.full(N, -1, np.int64)
+    g_par = np.ones(N)
+    out_i, out_l, out_n, out_g = [], [], [], []
+
+    def emit(i, l, node, g):
+        out_i.append(i), out_l.append(np.full(i.size, l)), out_n.append(node), out_g.append(g)
+
+    for l in range(L):
+        if pt.size == 0:
+            break
+        lv = tree.levels[l]
+        base = np.zeros(pt.size, np.int64) if l == 0 else par * J
+        cand = base[:, None] + np.arange(J)[None, :]
+        has_live = lv.live[cand].any(axis=1)
+        if l > 0:  # a node without live children stops its path
+            dead_end = ~has_live
+            emit(pt[dead_end], l - 1, par[dead_end], g_par[dead_end])
+        pt, par, g_par, cand = pt[has_live], par[has_live], g_par[has_live], cand[has_live]
+        if pt.size == 0:
+            break
+        S = child_scores(Zp[pt], np.maximum(par, 0), lv.pi, lv.mu, lv.Sigma)
+        post, _ = posteriors(S)
+        if mode in ("local", "global"):
+            k = np.argmax(S, axis=1)
+            rows = np.arange(pt.size)
+            child = cand[rows, k]
+            g = post[rows, k] * (g_par if mode == "global" else 1.0)
+            nxt_pt, nxt_child, nxt_g = pt, child, g
+        elif mode == "multipath":
+            g_all = post * g_par[:, None]
+            keep = lv.live[cand] & (g_all >= tau)
+            r, k = np.nonzero(keep)
+            nxt_pt, nxt_child, nxt_g = pt[r], cand[r, k], g_all[r, k]
+        else:
+            raise ValueError(mode)
+        stop = (lv.complexity[nxt_child] <= lam_c) | (l == L - 1)
+        emit(nxt_pt[stop], l, nxt_child[stop], nxt_g[stop])
+        go = ~stop
+        # g_par: what the path adds if it ends at this node (local mode: the
+        # node's own sibling posterior, as Algorithm 1 keeps it)
+        pt, par, g_par = nxt_pt[go], nxt_child[go], nxt_g[go]
+    ci, cl, cn, cg = (np.concatenate(a) if a else np.zeros(0) for a in (out_i, out_l, out_n, out_g))
+    ci, cl, cn = ci.astype(np.int64), cl.astype(np.int64), cn.astype(np.int64)
+    M0, M1 = [], []
+    for l in range(L):
+        m = tree.levels[l].pi.shape[0]
+        sel = cl == l
+        M0.append(np.bincount(cn[sel], weights=cg[sel], minlength=m))
+        M1.append(np.stack([np.bincount(cn[sel], weights=cg[sel] * Zp[ci[sel], a], minlength=m)
+                            for a in range(3)], axis=1))
+    return {"M0": M0, "M1": M1, "point": ci, "level": cl, "node": cn, "gamma": cg}
+
+
 # --------------------------------------------------------------------------
 # Registration M-step: Eq. 8-16
 # --------------------------------------------------------------------------
@@ -420,6 +501,34 @@ def model_eigen(tree: Tree, level: int, node):
     lv = tree.levels[level]
     lam = np.maximum(lv.lam[node], tree.eps)
     return lv.mu[node], lam, lv.vec[node]
+
+
+def register_descent(tree: Tree, Z2, mode: str, tau: float = 0.0, T_init=None, iters=30,
+                     lam_c=None, history=False):
+    """`register` with the E-step of e_step_descent(mode, tau); the M-step
+    (Eq. 8-16) and the update are the same."""
+    Z2 = np.asarray(Z2, dtype=np.float64)
+    T = np.eye(4) if T_init is None else np.array(T_init, dtype=np.float64)
+    N = Z2.shape[0]
+    hist = []
+    for _ in range(iters):
+        Zp = Z2 @ T[:3, :3].T + T[:3, 3]
+        E = e_step_descent(tree, Zp, mode, tau, lam_c)
+        ms, ps, mus, lams, vecs = [], [], [], [], []
+        for l in range(len(tree.levels)):
+            used, pstar, mstar = cluster_stats(E["M0"][l], E["M1"][l], N)
+            node = np.nonzero(used)[0]
+            mu, lam, vec = model_eigen(tree, l, node)
+            ms.append(mstar), ps.append(pstar), mus.append(mu)
+            lams.append(lam), vecs.append(vec)
+        mstar, pstar = np.concatenate(ms), np.concatenate(ps)
+        mu, lam, vec = np.concatenate(mus), np.concatenate(lams), np.concatenate(vecs)
+        x = solve_increment(mstar, pstar, mu, lam, vec)
+        if history:
+            hist.append({"T_start": T.copy(), "x": x, "M0": E["M0"], "M1": E["M1"],
+                         "objective": objective(np.eye(4), mstar, pstar, mu, lam, vec)})
+        T = increment_matrix(x) @ T
+    return (T, hist) if history else T
 
 
 def register(tree: Tree, Z2, T_init=None, iters=30, lam_c=None, history=False):
