@@ -127,6 +127,37 @@ int hgmm_register(hgmm_tree* t, const float* d_src, int64_t n,
  * device).  0 after a call with iters = 0. */
 int hgmm_register_objective(const hgmm_tree* t, double* d_obj, void* stream);
 
+/* Descent variants of the registration E-step (Sec. 4.1: a node's
+ * expectation for a point is the sum of its children's expectations, so a
+ * child's is its parent's times its posterior among its siblings). */
+#define HGMM_DESCENT_ML_LOCAL 0  /* Algorithm 1 as hgmm_register: the maximum-likelihood
+                                    path, gamma = the stopping node's sibling posterior */
+#define HGMM_DESCENT_ML_GLOBAL 1 /* the maximum-likelihood path, gamma = the product of
+                                    the sibling posteriors along the path */
+#define HGMM_DESCENT_MULTIPATH 2 /* every live child whose expectation is >= tau is
+                                    descended (the others are pruned with their
+                                    subtrees); each path stops as Algorithm 1's does and
+                                    adds its expectation to the node where it stops */
+
+typedef struct hgmm_descent {
+    int32_t mode;   /* HGMM_DESCENT_* */
+    float tau;      /* pruning threshold of HGMM_DESCENT_MULTIPATH, in [0, 1] */
+    float lam_c;    /* complexity threshold for this call (< 0: the build's) */
+    int32_t reserved;
+} hgmm_descent;
+
+/* hgmm_register with the E-step of descent variant d (host struct).  Per
+ * round: every (point, stopping node) contribution adds gamma and
+ * gamma (z' - mu_j) to the node's 64-bit fixed-point moments; then the same
+ * Eq. 9-16 solve and T <- dT T.  One launch per round for the descent (a
+ * warp-synchronous depth-first search per point with a bounded stack), one
+ * for the node terms, one for the solve.  hgmm_register_objective and
+ * hgmm_debug_reg_moments report on the last round.  Errors: as hgmm_register;
+ * HGMM_EINVAL for an unknown mode or tau outside [0, 1]. */
+int hgmm_register_descent(hgmm_tree* t, const float* d_src, int64_t n, const double* d_T_init,
+                          int32_t iters, const hgmm_descent* d, void* stream, double* d_T_out,
+                          double* d_T_hist);
+
 /* Synchronise `stream` and return the first error the device recorded for
  * this tree since the last hgmm_sync (HGMM_OK if none); clears it. */
 int hgmm_sync(hgmm_tree* t, void* stream);

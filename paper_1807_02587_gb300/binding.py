@@ -50,6 +50,16 @@ class hgmm_params(ctypes.Structure):
                 ("debug_stop_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+HGMM_DESCENT_ML_LOCAL = 0
+HGMM_DESCENT_ML_GLOBAL = 1
+HGMM_DESCENT_MULTIPATH = 2
+
+
+class hgmm_descent(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tau", ctypes.c_float), ("lam_c", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(
@@ -89,6 +99,7 @@ def _load():
                                              P(ctypes.c_int64)]),
         "hgmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "hgmm_register_objective": (ctypes.c_int, [vp, vp, vp]),
+        "hgmm_register_descent": (ctypes.c_int, [vp, vp, i64, vp, i32, P(hgmm_descent), vp, vp, vp]),
         "hgmm_batch_objective": (ctypes.c_int, [vp, vp, vp]),
         "hgmm_batch_features": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, vp, vp]),
         "hgmm_mlp_create": (ctypes.c_int, [i32, P(vp)]),
@@ -202,6 +213,22 @@ def hgmm_register(h, src, T_init=None, iters: int = 30, lam_c: float = -1.0, str
     _check(_lib.hgmm_register(h, _dev_points(src, "src"), src.shape[0], _dptr(T_init),
                               int(iters), float(lam_c), _stream_ptr(stream), _dptr(T_out),
                               _dptr(T_hist)), "hgmm_register")
+    return T_out
+
+
+def hgmm_register_descent(h, src, mode: int, tau: float = 0.0, T_init=None, iters: int = 30,
+                          lam_c: float = -1.0, stream=None, T_out=None, T_hist=None):
+    """hgmm_register with a descent variant (HGMM_DESCENT_*); returns T_out."""
+    import torch
+    if T_out is None:
+        T_out = torch.empty((4, 4), dtype=torch.float64, device=src.device)
+    for name, x in (("T_init", T_init), ("T_out", T_out), ("T_hist", T_hist)):
+        if x is not None and (x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous()):
+            raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
+    d = hgmm_descent(int(mode), float(tau), float(lam_c), 0)
+    _check(_lib.hgmm_register_descent(h, _dev_points(src, "src"), src.shape[0], _dptr(T_init), int(iters),
+                                      ctypes.byref(d), _stream_ptr(stream), _dptr(T_out), _dptr(T_hist)),
+           "hgmm_register_descent")
     return T_out
 
 
@@ -712,6 +739,10 @@ class Tree:
     def register(self, src, T_init=None, iters: int = 30, lam_c: float = -1.0, stream=None,
                  T_out=None, T_hist=None):
         return hgmm_register(self.handle, src, T_init, iters, lam_c, stream, T_out, T_hist)
+
+    def register_descent(self, src, mode: int, tau: float = 0.0, T_init=None, iters: int = 30,
+                         lam_c: float = -1.0, stream=None, T_out=None, T_hist=None):
+        return hgmm_register_descent(self.handle, src, mode, tau, T_init, iters, lam_c, stream, T_out, T_hist)
 
     def sync(self, stream=None):
         hgmm_sync(self.handle, stream)

@@ -123,7 +123,9 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
         delete t;
         return HGMM_ECUDA;
     }
-    const int64_t nb = t->reg_grid;  // one normal-equation partial per registration CTA
+    // one normal-equation partial per registration CTA, or per 32 nodes in
+    // the descent variants
+    const int64_t nb = std::max<int64_t>(t->reg_grid, (t->max_nodes + 31) / 32);
     bool good = true;
     good &= dalloc(&t->est, t->max_nodes);
     good &= dalloc(&t->stat, t->max_nodes);
@@ -213,6 +215,20 @@ int hgmm_register(hgmm_tree* t, const float* d_src, int64_t n, const double* d_T
     t->reg_n = n;
     return hgmm_register_impl(t, reinterpret_cast<const float4*>(d_src), n, d_T_init, iters,
                               lam_c, static_cast<cudaStream_t>(stream), d_T_out, d_T_hist);
+}
+
+int hgmm_register_descent(hgmm_tree* t, const float* d_src, int64_t n, const double* d_T_init,
+                          int32_t iters, const hgmm_descent* d, void* stream, double* d_T_out,
+                          double* d_T_hist) {
+    if (!t || !d_src || !d || n < 1 || iters < 0 || !t->built) return HGMM_EINVAL;
+    if (d->mode < HGMM_DESCENT_ML_LOCAL || d->mode > HGMM_DESCENT_MULTIPATH) return HGMM_EINVAL;
+    if (!(d->tau >= 0.0f && d->tau <= 1.0f)) return HGMM_EINVAL;
+    if (!aligned16(d_src)) return HGMM_EINVAL;
+    if (n > (int64_t(1) << 31) - 1) return HGMM_ECAPACITY;
+    if (int rc = check_device(t)) return rc;
+    t->reg_n = n;
+    return hgmm_register_descent_impl(t, reinterpret_cast<const float4*>(d_src), n, d_T_init, iters, *d,
+                                      static_cast<cudaStream_t>(stream), d_T_out, d_T_hist);
 }
 
 int hgmm_sync(hgmm_tree* t, void* stream) {

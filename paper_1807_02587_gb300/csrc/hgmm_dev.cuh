@@ -1107,6 +1107,34 @@ __device__ __forceinline__ void load_node(const NodeEst* __restrict__ est, const
     }
 }
 
+// Sums (v0..v3) over the lanes of the warp that hold the same key (all 32
+// lanes call it): a pairwise tree over the members' ranks (fixed order, so
+// deterministic).  Returns the lane's rank in its group; rank 0 holds the
+// group's sums, which it then adds to the node's fixed-point moments with
+// one atomic per value (integer adds are exact, so the node totals do not
+// depend on the order in which groups arrive).
+__device__ __forceinline__ int warp_group_sum4(int key, float& v0, float& v1, float& v2, float& v3) {
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(FULL, key);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const int gsize = __popc(peers);
+    const unsigned higher = lane == 31 ? 0u : (peers & ~((2u << lane) - 1u));
+#pragma unroll
+    for (int st = 1; st < 32; st <<= 1) {
+        unsigned h = higher;  // lane holding rank + st within my group
+        for (int k = 1; k < st; ++k) h &= h - 1u;
+        const int srcl = h ? __ffs(h) - 1 : lane;
+        const float o0 = __shfl_sync(FULL, v0, srcl);
+        const float o1 = __shfl_sync(FULL, v1, srcl);
+        const float o2 = __shfl_sync(FULL, v2, srcl);
+        const float o3 = __shfl_sync(FULL, v3, srcl);
+        if ((rank & (2 * st - 1)) == 0 && rank + st < gsize) {
+            v0 += o0; v1 += o1; v2 += o2; v3 += o3;
+        }
+    }
+    return rank;
+}
+
 // hist (shared memory, 4 x STAGED_NODES fixed-point words, zero on entry, or
 // null): the groups whose node is one of the staged top levels add into the
 // CTA's own histogram instead of global memory; flush_node_hist then moves it
@@ -1171,33 +1199,12 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             cmx = bx; cmy = by; cmz = bz;
             if (bstop != 0.f) break;  // Complexity <= lambda_c
         }
-        // Sum (gamma, gamma (z' - mu_j)) over the lanes of this warp that chose
-        // the same node j: a pairwise tree over the members' ranks (fixed order,
-        // so deterministic), then one fixed-point atomic per value and group.
-        // Integer adds are exact, so the node totals do not depend on the
-        // order in which groups arrive.
         const bool has = chosen >= 0;
         float v0 = has ? gamma : 0.f;
         float v1 = has ? gamma * (x - cmx) : 0.f;
         float v2 = has ? gamma * (y - cmy) : 0.f;
         float v3 = has ? gamma * (w - cmz) : 0.f;
-        const unsigned peers = __match_any_sync(FULL, chosen);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        const int gsize = __popc(peers);
-        const unsigned higher = lane == 31 ? 0u : (peers & ~((2u << lane) - 1u));
-#pragma unroll
-        for (int st = 1; st < 32; st <<= 1) {
-            unsigned h = higher;  // lane holding rank + st within my group
-            for (int k = 1; k < st; ++k) h &= h - 1u;
-            const int srcl = h ? __ffs(h) - 1 : lane;
-            const float o0 = __shfl_sync(FULL, v0, srcl);
-            const float o1 = __shfl_sync(FULL, v1, srcl);
-            const float o2 = __shfl_sync(FULL, v2, srcl);
-            const float o3 = __shfl_sync(FULL, v3, srcl);
-            if ((rank & (2 * st - 1)) == 0 && rank + st < gsize) {
-                v0 += o0; v1 += o1; v2 += o2; v3 += o3;
-            }
-        }
+        const int rank = warp_group_sum4(chosen, v0, v1, v2, v3);
         if (has && rank == 0) {
             unsigned long long* dst =
                 (hist && chosen < STAGED_NODES)
@@ -1430,6 +1437,42 @@ __device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt
     }
     if (T_hist && lane >= 12 && lane < 16) T_hist[16 * iter + lane] = lane == 15 ? 1.0 : 0.0;
     return true;
+}
+
+// Fixed-order sum of nb per-CTA partials of the NTERM normal-equation and
+// objective terms (compensated pairs) by a CTA of at least 8 warps (warp w
+// takes partials w, w + 8, ...; then the eight group sums in order), the
+// objective to *obj, and the FP64 solve and pose update by warp 0.  A
+// singular system records ST_DEGENERATE and keeps T (also in T_hist).
+__device__ inline void sum_terms_and_solve(const float2* __restrict__ tpart, int nb, int it, double* T,
+                                           float* Rt, double* T_hist, double* obj, int* status) {
+    __shared__ float2 fin[8][32];
+    __shared__ double tot[NTERM];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < 8) {
+        float S = 0.f, C = 0.f;
+        if (lane < NTERM)
+            for (int b = warp; b < nb; b += 8) {
+                const float2 x = tpart[NTERM * b + lane];
+                pair_add(S, C, x.x, x.y);
+            }
+        fin[warp][lane] = make_float2(S, C);
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    if (lane < NTERM) {
+        float S = 0.f, C = 0.f;
+        for (int w = 0; w < 8; ++w) pair_add(S, C, fin[w][lane].x, fin[w][lane].y);
+        tot[lane] = double(S) + double(C);
+    }
+    __syncwarp();
+    if (lane == 0 && obj) *obj = tot[NTERM - 1];
+    const bool solved = warp_solve_update(tot, T, Rt, T_hist, it);
+    if (!solved && lane == 0) {
+        atomicOr(status, ST_DEGENERATE);
+        if (T_hist)
+            for (int k = 0; k < 16; ++k) T_hist[16 * it + k] = T[k];
+    }
 }
 
 // Thread 0 waits (bounded) until *word - target >= 0 (a monotonic counter or

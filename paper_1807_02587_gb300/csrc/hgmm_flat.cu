@@ -467,39 +467,11 @@ k_flat_terms(const float2* __restrict__ part, int max_ctas, const int* __restric
     if (lane < NTERM) tpart[NTERM * blockIdx.x + lane] = make_float2(ws, we);
 }
 
-// Fixed-order sum of the per-CTA term partials (eight groups, then the
-// groups in order), the FP64 solve and the pose update.
 __global__ void __launch_bounds__(MOM_THREADS)
 k_flat_solve(const float2* __restrict__ tpart, const int* __restrict__ meta, int it,
              double* __restrict__ T, float* __restrict__ Rt, double* __restrict__ T_hist,
              double* __restrict__ obj, int* __restrict__ status) {
-    __shared__ float2 fin[RED_WARPS][32];
-    __shared__ double tot[NTERM];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nb = (meta[0] + RED_COMPS - 1) / RED_COMPS;
-    float S = 0.f, C = 0.f;
-    if (lane < NTERM)
-        for (int b = warp; b < nb; b += RED_WARPS) {
-            const float2 x = tpart[NTERM * b + lane];
-            pair_add(S, C, x.x, x.y);
-        }
-    fin[warp][lane] = make_float2(S, C);
-    __syncthreads();
-    if (warp != 0) return;
-    if (lane < NTERM) {
-        S = 0.f;
-        C = 0.f;
-        for (int w = 0; w < RED_WARPS; ++w) pair_add(S, C, fin[w][lane].x, fin[w][lane].y);
-        tot[lane] = double(S) + double(C);
-    }
-    __syncwarp();
-    if (lane == 0) *obj = tot[NTERM - 1];
-    const bool solved = warp_solve_update(tot, T, Rt, T_hist, it);
-    if (!solved && lane == 0) {
-        atomicOr(status, ST_DEGENERATE);  // T kept for this round
-        if (T_hist)
-            for (int k = 0; k < 16; ++k) T_hist[16 * it + k] = T[k];
-    }
+    sum_terms_and_solve(tpart, (meta[0] + RED_COMPS - 1) / RED_COMPS, it, T, Rt, T_hist, obj, status);
 }
 
 __global__ void k_flat_copy_T(const double* __restrict__ T, double* __restrict__ out) {

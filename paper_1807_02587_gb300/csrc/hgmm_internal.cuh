@@ -176,6 +176,9 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n, int depth,
 int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n,
                        const double* T_init, int iters, float lam_c,
                        cudaStream_t s, double* T_out, double* T_hist);
+int hgmm_register_descent_impl(hgmm_tree* t, const float4* src, int64_t n, const double* T_init,
+                               int iters, const hgmm_descent& d, cudaStream_t s, double* T_out,
+                               double* T_hist);
 int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s);
 int hgmm_register_grid(int n_sm);
 int hgmm_barrier_timeout_probe_impl(hgmm_tree* t, long long limit, cudaStream_t s);

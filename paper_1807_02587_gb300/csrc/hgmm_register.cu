@@ -17,6 +17,7 @@
 //               closed form: sum_l (1/lambda_l) n_l n_l^T = P, Eq. 10).  FP64.
 //               The last CTA to finish reduces the per-CTA sums in a fixed
 //               order, solves (Cholesky) and composes T <- dT T.
+#include <algorithm>
 #include <cstdio>
 
 #include "hgmm_dev.cuh"
@@ -275,6 +276,195 @@ __global__ void k_copy_T(const double* __restrict__ T, double* __restrict__ out)
     if (threadIdx.x < 16) out[threadIdx.x] = T[threadIdx.x];
 }
 
+// ---------------------------------------------------- descent variants
+// One round's E-step under a variant of the descent (Sec. 4.1).  Every warp
+// takes 32 points; each lane runs a depth-first search over the tree with a
+// stack of (node, level | terminal bit, gamma).  One step pops one entry: a
+// terminal entry (a node where its path stops: complexity <= lambda_c or the
+// last level) is emitted; any other entry is expanded (the 8 children scored
+// as in Algorithm 1) and pushes the child the variant keeps (the
+// maximum-likelihood one, or every live child whose expectation reaches
+// tau), or, if it has no live child, is emitted itself.  Emissions of the
+// warp's step are summed per node (warp_group_sum4) and added to the node's
+// fixed-point moments.  The stack bound 8 x depth holds for any tau: a step
+// removes one entry and adds at most 8, and a level never holds more than 7
+// pending siblings.
+constexpr int VAR_THREADS = 256;
+constexpr int VAR_STACK = 8 * HGMM_MAX_DEPTH;
+constexpr int VAR_TERMINAL = 1 << 8;
+
+template <int MODE>
+__global__ void __launch_bounds__(VAR_THREADS)
+k_descend_var(const float4* __restrict__ src, int n, const NodeEst* __restrict__ est, int depth, float tau,
+              const float* __restrict__ Rt, const RootDev* __restrict__ root,
+              unsigned long long* __restrict__ acc, int* __restrict__ status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double ext = root->extent > 0.0 ? root->extent : 1.0;
+    const float qscale = float(FIX / ext);
+    const float r00 = Rt[0], r01 = Rt[1], r02 = Rt[2], r10 = Rt[3], r11 = Rt[4], r12 = Rt[5];
+    const float r20 = Rt[6], r21 = Rt[7], r22 = Rt[8], tx = Rt[9], ty = Rt[10], tz = Rt[11];
+    const int warps_total = gridDim.x * (VAR_THREADS / 32);
+    for (int base = (blockIdx.x * (VAR_THREADS / 32) + warp) * 32; base < n; base += warps_total * 32) {
+        const int i = base + lane;
+        float4 p = i < n ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        bool valid = i < n;
+        if (valid && !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) {
+            atomicOr(status, ST_NONFINITE);
+            valid = false;
+        }
+        const float x = fmaf(r00, p.x, fmaf(r01, p.y, fmaf(r02, p.z, tx)));
+        const float y = fmaf(r10, p.x, fmaf(r11, p.y, fmaf(r12, p.z, ty)));
+        const float w = fmaf(r20, p.x, fmaf(r21, p.y, fmaf(r22, p.z, tz)));
+        int sn[VAR_STACK], sm[VAR_STACK];
+        float sg[VAR_STACK];
+        int sp = 0;
+        if (valid) {  // the root: its children are the level-0 nodes
+            sn[0] = -1;
+            sm[0] = -1 & 0xff;
+            sg[0] = 1.f;
+            sp = 1;
+        }
+        while (__any_sync(FULL, sp > 0)) {
+            int out_node = -1;
+            float out_g = 0.f;
+            if (sp > 0) {
+                --sp;
+                const int g = sn[sp], meta = sm[sp];
+                const float gam = sg[sp];
+                const int l = (meta & 0xff) == 0xff ? -1 : (meta & 0xff);
+                if (meta & VAR_TERMINAL) {
+                    out_node = g;
+                    out_g = gam;
+                } else {
+                    const int cl = l + 1;
+                    const int64_t first = d_level_offset(cl) + 8 * (l < 0 ? 0 : int64_t(g) - d_level_offset(l));
+                    float sc8[8], st8[8];
+                    float best = -CUDART_INF_F;
+                    int bi = -1;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const NodeEst* e = est + first + c;
+                        const float4 ea = __ldg(&e->a), eb = __ldg(&e->b), ec = __ldg(&e->c);
+                        const float ex = x - ea.x, ey = y - ea.y, ez = w - ea.z;
+                        const float d0 = eb.x * ex;
+                        const float d1 = fmaf(eb.z, ey, eb.y * ex);
+                        const float d2 = fmaf(ec.y, ez, fmaf(ec.x, ey, eb.w * ex));
+                        float sc = fmaf(-d0, d0, ea.w);
+                        sc = fmaf(-d1, d1, sc);
+                        sc = fmaf(-d2, d2, sc);
+                        sc8[c] = sc;
+                        st8[c] = ec.z;
+                        if (sc > best) {
+                            best = sc;
+                            bi = c;
+                        }
+                    }
+                    if (bi < 0) {  // no live child: the path ends here
+                        if (l >= 0) {
+                            out_node = g;
+                            out_g = gam;
+                        }
+                    } else {
+                        float sum = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) sum += exp2f(sc8[c] - best);
+                        const float inv = 1.0f / sum;
+                        const bool last = cl == depth - 1;
+                        if (MODE == HGMM_DESCENT_MULTIPATH) {
+                            for (int c = 7; c >= 0; --c) {
+                                const float cg = gam * (exp2f(sc8[c] - best) * inv);
+                                if (sc8[c] > -CUDART_INF_F && cg >= tau && sp < VAR_STACK) {
+                                    sn[sp] = int(first + c);
+                                    sm[sp] = cl | ((last || st8[c] != 0.f) ? VAR_TERMINAL : 0);
+                                    sg[sp] = cg;
+                                    ++sp;
+                                }
+                            }
+                        } else {
+                            const float pc = inv;  // the best child's posterior: 2^0 / sum
+                            sn[sp] = int(first + bi);
+                            sm[sp] = cl | ((last || st8[bi] != 0.f) ? VAR_TERMINAL : 0);
+                            sg[sp] = MODE == HGMM_DESCENT_ML_GLOBAL ? gam * pc : pc;
+                            ++sp;
+                        }
+                    }
+                }
+            }
+            float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+            if (out_node >= 0) {
+                const float4 a = __ldg(&est[out_node].a);
+                v0 = out_g;
+                v1 = out_g * (x - a.x);
+                v2 = out_g * (y - a.y);
+                v3 = out_g * (w - a.z);
+            }
+            const int rank = warp_group_sum4(out_node, v0, v1, v2, v3);
+            if (out_node >= 0 && rank == 0) {
+                unsigned long long* dst = acc + 4 * int64_t(out_node) * ACC_REPLICAS;
+                atomicAdd(dst + 0, (unsigned long long)to_fix(v0 * 4294967296.0f));
+                atomicAdd(dst + 1, (unsigned long long)to_fix(v1 * qscale));
+                atomicAdd(dst + 2, (unsigned long long)to_fix(v2 * qscale));
+                atomicAdd(dst + 3, (unsigned long long)to_fix(v3 * qscale));
+            }
+        }
+    }
+}
+
+// Node terms of one round from the fixed-point moments (256 nodes per CTA,
+// a warp reduce-scatter per 32 nodes, the CTA's eight warp sums in order);
+// the accumulators are cleared for the next round.
+__global__ void __launch_bounds__(VAR_THREADS)
+k_var_terms(int n_nodes, int n, const NodeEst* __restrict__ est, const float4* __restrict__ rnode,
+            const RootDev* __restrict__ root, unsigned long long* __restrict__ acc,
+            float2* __restrict__ part, double* __restrict__ dbg) {
+    __shared__ float2 sm[VAR_THREADS / 32][NTERM];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = blockIdx.x * VAR_THREADS + threadIdx.x;
+    const double ext = root->extent > 0.0 ? root->extent : 1.0;
+    const float qscale = float(FIX / ext);
+    float v[32], c[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) { v[k] = 0.f; c[k] = 0.f; }
+    if (g < n_nodes) {
+        unsigned long long* ap = acc + 4 * int64_t(g) * ACC_REPLICAS;
+        const long long a0 = (long long)ap[0], a1 = (long long)ap[1], a2 = (long long)ap[2],
+                        a3 = (long long)ap[3];
+        if (a0 | a1 | a2 | a3) ap[0] = ap[1] = ap[2] = ap[3] = 0ull;
+        const float4 cm = est[g].a;
+        float M0 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
+        if (a0 > 0) {
+            float wv[NTERM];
+            M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
+            const float inv = 1.0f / (qscale * M0);
+            o0 = float(a1) * inv;
+            o1 = float(a2) * inv;
+            o2 = float(a3) * inv;
+            node_terms(rnode[3 * g], rnode[3 * g + 1], rnode[3 * g + 2], cm, M0, o0, o1, o2, M0 / float(n), wv);
+#pragma unroll
+            for (int k = 0; k < NTERM; ++k) pair_add(v[k], c[k], wv[k], 0.f);
+        }
+        dbg[4 * g + 0] = double(a0) * INV_FIX;
+        dbg[4 * g + 1] = double(M0) * (double(cm.x) + double(o0));
+        dbg[4 * g + 2] = double(M0) * (double(cm.y) + double(o1));
+        dbg[4 * g + 3] = double(M0) * (double(cm.z) + double(o2));
+    }
+    float ws, we;
+    warp_reduce_scatter32(v, c, ws, we);
+    if (lane < NTERM) sm[warp][lane] = make_float2(ws, we);
+    __syncthreads();
+    if (threadIdx.x < NTERM) {
+        float S = 0.f, C = 0.f;
+        for (int k = 0; k < VAR_THREADS / 32; ++k) pair_add(S, C, sm[k][threadIdx.x].x, sm[k][threadIdx.x].y);
+        part[NTERM * blockIdx.x + threadIdx.x] = make_float2(S, C);
+    }
+}
+
+__global__ void __launch_bounds__(VAR_THREADS)
+k_var_solve(const float2* __restrict__ part, int nb, int it, double* __restrict__ T, float* __restrict__ Rt,
+            double* __restrict__ T_hist, double* __restrict__ obj, int* __restrict__ status) {
+    sum_terms_and_solve(part, nb, it, T, Rt, T_hist, obj, status);
+}
+
 }  // namespace
 
 }  // namespace hgmm
@@ -287,6 +477,9 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
     const int n_nodes = int(hgmm_node_count(t->depth));
     {
         ProfScope ps_(t, K_REG_INIT, s);
+        // lam_c < 0: the build's threshold (set here too, so that an earlier
+        // call with another threshold does not leave its stop flags behind)
+        if (lam_c < 0.f) lam_c = t->prm.lam_c;
         k_reg_init<<<(n_nodes + 255) / 256, 256, 0, s>>>(T_init, n_nodes, lam_c, t->stat, t->est,
                                                           t->reg_acc, t->reg_T, t->reg_Rt,
                                                           t->reg_bar, t->reg_obj);
@@ -326,6 +519,44 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         ProfScope ps_(t, K_COPY_T, s);
         k_copy_T<<<1, 32, 0, s>>>(t->reg_T, T_out);
     }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "hgmm: launch failed: %s\n", cudaGetErrorString(e));
+        return HGMM_ECUDA;
+    }
+    return HGMM_OK;
+}
+
+int hgmm_register_descent_impl(hgmm_tree* t, const float4* src, int64_t n64, const double* T_init,
+                               int iters, const hgmm_descent& d, cudaStream_t s, double* T_out,
+                               double* T_hist) {
+    const int n = int(n64);
+    const int n_nodes = int(hgmm_node_count(t->depth));
+    const float lam_c = d.lam_c >= 0.f ? d.lam_c : t->prm.lam_c;
+    k_reg_init<<<(n_nodes + 255) / 256, 256, 0, s>>>(T_init, n_nodes, lam_c, t->stat, t->est, t->reg_acc,
+                                                      t->reg_T, t->reg_Rt, t->reg_bar, t->reg_obj);
+    const int tgrid = (n_nodes + VAR_THREADS - 1) / VAR_THREADS;
+    const int dgrid = std::max(1, std::min(4 * t->n_sm, (n + VAR_THREADS - 1) / VAR_THREADS));
+    for (int it = 0; it < iters; ++it) {
+        switch (d.mode) {
+            case HGMM_DESCENT_ML_LOCAL:
+                k_descend_var<HGMM_DESCENT_ML_LOCAL><<<dgrid, VAR_THREADS, 0, s>>>(
+                    src, n, t->est, t->depth, d.tau, t->reg_Rt, t->root, t->reg_acc, t->status);
+                break;
+            case HGMM_DESCENT_ML_GLOBAL:
+                k_descend_var<HGMM_DESCENT_ML_GLOBAL><<<dgrid, VAR_THREADS, 0, s>>>(
+                    src, n, t->est, t->depth, d.tau, t->reg_Rt, t->root, t->reg_acc, t->status);
+                break;
+            default:
+                k_descend_var<HGMM_DESCENT_MULTIPATH><<<dgrid, VAR_THREADS, 0, s>>>(
+                    src, n, t->est, t->depth, d.tau, t->reg_Rt, t->root, t->reg_acc, t->status);
+        }
+        k_var_terms<<<tgrid, VAR_THREADS, 0, s>>>(n_nodes, n, t->est, t->rnode, t->root, t->reg_acc,
+                                                  t->reg_part, t->reg_dbg);
+        k_var_solve<<<1, VAR_THREADS, 0, s>>>(t->reg_part, tgrid, it, t->reg_T, t->reg_Rt, T_hist, t->reg_obj,
+                                              t->status);
+    }
+    if (T_out) k_copy_T<<<1, 32, 0, s>>>(t->reg_T, T_out);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         fprintf(stderr, "hgmm: launch failed: %s\n", cudaGetErrorString(e));

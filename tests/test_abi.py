@@ -32,7 +32,7 @@ def test_header_declares_the_boundary():
                  "hgmm_register_pair_host", "hgmm_sync", "hgmm_strerror",
                  "hgmm_batch_register", "hgmm_batch_features", "hgmm_mlp_forward",
                  "hgmm_mlp_train_step", "hgmm_pose_decode", "hgmm_pose_select",
-                 "hgmm_register_objective", "hgmm_flat_register", "hgmm_flat_fit"]:
+                 "hgmm_register_objective", "hgmm_flat_register", "hgmm_flat_fit", "hgmm_register_descent"]:
         assert must in names
 
 
@@ -73,6 +73,8 @@ def test_host_side_argument_checks(lib):
     assert B._lib.hgmm_batch_features(None, None, None, None, None, None) == B.HGMM_EINVAL
     assert B._lib.hgmm_register_objective(None, None, None) == B.HGMM_EINVAL
     assert B.HGMM_MLP_PARAMS == 256 * 1280 + 256 + 256 * 256 + 256 + 9 * 256 + 9
+    d = B.hgmm_descent(B.HGMM_DESCENT_MULTIPATH, 0.01, -1.0, 0)
+    assert B._lib.hgmm_register_descent(None, None, 100, None, 3, ctypes.byref(d), None, None, None) == B.HGMM_EINVAL
     # flat GMM J=n variant: rejected before any CUDA call
     assert B._lib.hgmm_flat_create(0, 16, ctypes.byref(h)) == B.HGMM_EINVAL
     assert B._lib.hgmm_flat_create(1000, 0, ctypes.byref(h)) == B.HGMM_EINVAL
