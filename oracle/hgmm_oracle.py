@@ -43,6 +43,10 @@ notes of the repository):
   posteriors along the path, and the threshold-pruned multi-path descent
   (a child below tau is dropped with its subtree; each path stops as
   Algorithm 1's does).
+* Eq. 8 replaces Eq. 7's double sum by one term per cluster and so drops the
+  scatter of each cluster's points about mu*_j, which depends on R unless
+  Sigma_j is isotropic; register_eq7 keeps it (Gauss-Newton over the point
+  contributions).
 * The flat "GMM J=n" variant (Sec. 5) does not say how its J components are
   obtained: here they are the leaves of the tree (weights = products of the
   within-parent weights), optionally refined by plain EM over all J, and the
@@ -527,6 +531,69 @@ def register_descent(tree: Tree, Z2, mode: str, tau: float = 0.0, T_init=None, i
         if history:
             hist.append({"T_start": T.copy(), "x": x, "M0": E["M0"], "M1": E["M1"],
                          "objective": objective(np.eye(4), mstar, pstar, mu, lam, vec)})
+        T = increment_matrix(x) @ T
+    return (T, hist) if history else T
+
+
+def eq7_objective(T, Z2, contrib, mu, P):
+    """Eq. 7: sum over (point i, node j) contributions of
+    gamma_ij (T(z_i) - mu_j)^T Sigma_j^-1 (T(z_i) - mu_j), with Sigma_j^-1
+    taken as P_j = V diag(1 / max(lambda, eps)) V^T; contrib = (point, row,
+    gamma) with `row` indexing mu / P."""
+    i, r, g = contrib
+    y = Z2[i] @ T[:3, :3].T + T[:3, 3] - mu[r]
+    return float(np.sum(g * np.einsum("ka,kab,kb->k", y, P[r], y)))
+
+
+def eq7_increment(Zp, contrib, mu, lam, vec):
+    """Gauss-Newton step of Eq. 7 at the current pose (the points already
+    moved, Zp = T(Z2)): for every contribution and every eigen-direction l a
+    point-to-plane row w [z'_i x n_l, n_l] with right-hand side
+    w n_l^T (mu_j - z'_i), w = sqrt(gamma_ij / lambda_jl) (Eq. 10 applied to
+    each point instead of to mu*_j), solved by least squares."""
+    i, r, g = contrib
+    rows, rhs = [], []
+    for l in range(3):
+        n = vec[r, :, l]
+        w = np.sqrt(g / lam[r, l])
+        rows.append(w[:, None] * np.concatenate([np.cross(Zp[i], n), n], axis=1))
+        rhs.append(w * np.einsum("ka,ka->k", n, mu[r] - Zp[i]))
+    x, *_ = np.linalg.lstsq(np.concatenate(rows), np.concatenate(rhs), rcond=None)
+    return x
+
+
+def _node_table(tree):
+    """Every node of the tree stacked level by level: mu, eigen (lambda
+    floored at eps), precision P."""
+    mus, lams, vecs = [], [], []
+    for l, lv in enumerate(tree.levels):
+        idx = np.arange(lv.pi.shape[0])
+        mu, lam, vec = model_eigen(tree, l, idx)
+        mus.append(mu), lams.append(lam), vecs.append(vec)
+    mu, lam, vec = np.concatenate(mus), np.concatenate(lams), np.concatenate(vecs)
+    P = np.einsum("kal,kl,kbl->kab", vec, 1.0 / lam, vec)
+    offs = np.cumsum([0] + [lv.pi.shape[0] for lv in tree.levels])
+    return mu, lam, vec, P, offs
+
+
+def register_eq7(tree: Tree, Z2, mode: str = "local", tau: float = 0.0, T_init=None, iters=30,
+                 lam_c=None, history=False):
+    """EM registration with the full Eq. 7 M-step: the E-step of
+    e_step_descent(mode, tau), then one Gauss-Newton step of Eq. 7 over the
+    (point, node) contributions (keeping the scatter of each node's points
+    that Eq. 8-9 drop) and T <- dT T."""
+    Z2 = np.asarray(Z2, dtype=np.float64)
+    T = np.eye(4) if T_init is None else np.array(T_init, dtype=np.float64)
+    mu, lam, vec, P, offs = _node_table(tree)
+    hist = []
+    for _ in range(iters):
+        Zp = Z2 @ T[:3, :3].T + T[:3, 3]
+        E = e_step_descent(tree, Zp, mode, tau, lam_c)
+        contrib = (E["point"], offs[E["level"]] + E["node"], E["gamma"])
+        x = eq7_increment(Zp, contrib, mu, lam, vec)
+        if history:
+            hist.append({"T_start": T.copy(), "x": x,
+                         "objective": eq7_objective(np.eye(4), Zp, contrib, mu, P) / Z2.shape[0]})
         T = increment_matrix(x) @ T
     return (T, hist) if history else T
 
