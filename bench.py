@@ -565,7 +565,7 @@ def variants_section(args, B, torch, pair, tgt, src, fp32_peak_tflops):
     """Sec. 5's variants on the bench's LiDAR pair (depth 4, 30 rounds, tree
     built once): Adaptive (lambda_c = 0.01), GMM-Tree (lambda_c = 0), the
     descent variants of Sec. 4.1 (path-product gamma; multi-path descent
-    pruned at tau) and the flat GMM J=n (the tree's leaves; and after 4 EM
+    pruned at tau), the full Eq. 7 M-step (scatter kept) and the flat GMM J=n (the tree's leaves; and after 4 EM
     iterations over all J):
     registration time (CUDA events, median of 3), error against the known
     motion, and for the flat model its (point, component) pair rate against
@@ -601,9 +601,10 @@ def variants_section(args, B, torch, pair, tgt, src, fp32_peak_tflops):
         tree.sync()
         out[key] = {"ms": ms, **errs(T)}
     # descent variants (Sec. 4.1): path-product gamma, threshold-pruned paths
-    for mode, tau, key in ((1, 0.0, "ml_path_product_gamma"), (2, 0.01, "multipath_tau_0.01"),
-                           (2, 0.1, "multipath_tau_0.1")):
-        ms, T = timed(lambda: tree.register_descent(src, mode, tau, iters=ITERS))
+    for mode, tau, full, key in ((1, 0.0, False, "ml_path_product_gamma"), (2, 0.01, False, "multipath_tau_0.01"),
+                                 (2, 0.1, False, "multipath_tau_0.1"), (0, 0.0, True, "full_eq7"),
+                                 (0, 0.0, False, "algorithm1_via_variant_kernel")):
+        ms, T = timed(lambda: tree.register_descent(src, mode, tau, iters=ITERS, full_eq7=full))
         tree.sync()
         out[key] = {"ms": ms, **errs(T)}
     flat = B.Flat(n, int(B.hgmm_node_count(DEPTH)))

@@ -140,16 +140,22 @@ int hgmm_register_objective(const hgmm_tree* t, double* d_obj, void* stream);
                                     adds its expectation to the node where it stops */
 
 typedef struct hgmm_descent {
-    int32_t mode;   /* HGMM_DESCENT_* */
-    float tau;      /* pruning threshold of HGMM_DESCENT_MULTIPATH, in [0, 1] */
-    float lam_c;    /* complexity threshold for this call (< 0: the build's) */
-    int32_t reserved;
+    int32_t mode;     /* HGMM_DESCENT_* */
+    float tau;        /* pruning threshold of HGMM_DESCENT_MULTIPATH, in [0, 1] */
+    float lam_c;      /* complexity threshold for this call (< 0: the build's) */
+    int32_t full_eq7; /* 0: the M-step of Eq. 9-16 (per-node means); 1: the full
+                         Eq. 7 (Gauss-Newton over the point contributions, i.e.
+                         Eq. 9-16 plus each node's scatter S_j = sum gamma
+                         (z' - mu*_j)(z' - mu*_j)^T, which Eq. 8 drops): adds
+                         sum_j [d]x P_j [d]x^T-type terms to the rotation block
+                         and tr(P_j S_j) / N to the objective */
 } hgmm_descent;
 
 /* hgmm_register with the E-step of descent variant d (host struct).  Per
  * round: every (point, stopping node) contribution adds gamma and
  * gamma (z' - mu_j) to the node's 64-bit fixed-point moments; then the same
- * Eq. 9-16 solve and T <- dT T.  One launch per round for the descent (a
+ * Eq. 9-16 solve (or the full Eq. 7 one, with second moments as well) and
+ * T <- dT T.  One launch per round for the descent (a
  * warp-synchronous depth-first search per point with a bounded stack), one
  * for the node terms, one for the solve.  hgmm_register_objective and
  * hgmm_debug_reg_moments report on the last round.  Errors: as hgmm_register;

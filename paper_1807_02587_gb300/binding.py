@@ -57,7 +57,7 @@ HGMM_DESCENT_MULTIPATH = 2
 
 class hgmm_descent(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tau", ctypes.c_float), ("lam_c", ctypes.c_float),
-                ("reserved", ctypes.c_int32)]
+                ("full_eq7", ctypes.c_int32)]
 
 
 def _load():
@@ -217,15 +217,16 @@ def hgmm_register(h, src, T_init=None, iters: int = 30, lam_c: float = -1.0, str
 
 
 def hgmm_register_descent(h, src, mode: int, tau: float = 0.0, T_init=None, iters: int = 30,
-                          lam_c: float = -1.0, stream=None, T_out=None, T_hist=None):
-    """hgmm_register with a descent variant (HGMM_DESCENT_*); returns T_out."""
+                          lam_c: float = -1.0, stream=None, T_out=None, T_hist=None, full_eq7: bool = False):
+    """hgmm_register with a descent variant (HGMM_DESCENT_*) and optionally the
+    full Eq. 7 M-step; returns T_out."""
     import torch
     if T_out is None:
         T_out = torch.empty((4, 4), dtype=torch.float64, device=src.device)
     for name, x in (("T_init", T_init), ("T_out", T_out), ("T_hist", T_hist)):
         if x is not None and (x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous()):
             raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
-    d = hgmm_descent(int(mode), float(tau), float(lam_c), 0)
+    d = hgmm_descent(int(mode), float(tau), float(lam_c), int(bool(full_eq7)))
     _check(_lib.hgmm_register_descent(h, _dev_points(src, "src"), src.shape[0], _dptr(T_init), int(iters),
                                       ctypes.byref(d), _stream_ptr(stream), _dptr(T_out), _dptr(T_hist)),
            "hgmm_register_descent")
@@ -741,8 +742,9 @@ class Tree:
         return hgmm_register(self.handle, src, T_init, iters, lam_c, stream, T_out, T_hist)
 
     def register_descent(self, src, mode: int, tau: float = 0.0, T_init=None, iters: int = 30,
-                         lam_c: float = -1.0, stream=None, T_out=None, T_hist=None):
-        return hgmm_register_descent(self.handle, src, mode, tau, T_init, iters, lam_c, stream, T_out, T_hist)
+                         lam_c: float = -1.0, stream=None, T_out=None, T_hist=None, full_eq7: bool = False):
+        return hgmm_register_descent(self.handle, src, mode, tau, T_init, iters, lam_c, stream, T_out, T_hist,
+                                     full_eq7)
 
     def sync(self, stream=None):
         hgmm_sync(self.handle, stream)

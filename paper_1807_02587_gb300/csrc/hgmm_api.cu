@@ -45,7 +45,7 @@ void free_tree(hgmm_tree* t) {
     clear_prof(t);
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
                     t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
-                    t->item_off, t->root, t->root_part, t->root_counter, t->status, t->reg_acc, t->reg_part,
+                    t->item_off, t->root, t->root_part, t->root_counter, t->status, t->reg_acc, t->reg_acc2, t->reg_part,
                     t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->reg_obj, t->rnode, t->trace, t->stage_tgt,
                     t->stage_src, t->stage_T};
     for (void* p : ptrs)
@@ -146,6 +146,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->root_counter, 1);
     good &= dalloc(&t->status, 1);
     good &= dalloc(&t->reg_acc, 4 * ACC_REPLICAS * t->max_nodes);
+    good &= dalloc(&t->reg_acc2, 6 * t->max_nodes);
     good &= dalloc(&t->reg_part, NTERM * nb);
     good &= dalloc(&t->rnode, 3 * t->max_nodes);
     good &= dalloc(&t->trace, int64_t(TRACE_MAX_ITERS) * t->reg_grid * 6);
@@ -222,6 +223,7 @@ int hgmm_register_descent(hgmm_tree* t, const float* d_src, int64_t n, const dou
                           double* d_T_hist) {
     if (!t || !d_src || !d || n < 1 || iters < 0 || !t->built) return HGMM_EINVAL;
     if (d->mode < HGMM_DESCENT_ML_LOCAL || d->mode > HGMM_DESCENT_MULTIPATH) return HGMM_EINVAL;
+    if (d->full_eq7 != 0 && d->full_eq7 != 1) return HGMM_EINVAL;
     if (!(d->tau >= 0.0f && d->tau <= 1.0f)) return HGMM_EINVAL;
     if (!aligned16(d_src)) return HGMM_EINVAL;
     if (n > (int64_t(1) << 31) - 1) return HGMM_ECAPACITY;

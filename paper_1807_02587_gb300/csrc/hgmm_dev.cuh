@@ -1113,7 +1113,8 @@ __device__ __forceinline__ void load_node(const NodeEst* __restrict__ est, const
 // group's sums, which it then adds to the node's fixed-point moments with
 // one atomic per value (integer adds are exact, so the node totals do not
 // depend on the order in which groups arrive).
-__device__ __forceinline__ int warp_group_sum4(int key, float& v0, float& v1, float& v2, float& v3) {
+template <int NV>
+__device__ __forceinline__ int warp_group_sum(int key, float (&v)[NV]) {
     const int lane = threadIdx.x & 31;
     const unsigned peers = __match_any_sync(FULL, key);
     const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -1124,14 +1125,21 @@ __device__ __forceinline__ int warp_group_sum4(int key, float& v0, float& v1, fl
         unsigned h = higher;  // lane holding rank + st within my group
         for (int k = 1; k < st; ++k) h &= h - 1u;
         const int srcl = h ? __ffs(h) - 1 : lane;
-        const float o0 = __shfl_sync(FULL, v0, srcl);
-        const float o1 = __shfl_sync(FULL, v1, srcl);
-        const float o2 = __shfl_sync(FULL, v2, srcl);
-        const float o3 = __shfl_sync(FULL, v3, srcl);
+        float o[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) o[q] = __shfl_sync(FULL, v[q], srcl);
         if ((rank & (2 * st - 1)) == 0 && rank + st < gsize) {
-            v0 += o0; v1 += o1; v2 += o2; v3 += o3;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) v[q] += o[q];
         }
     }
+    return rank;
+}
+
+__device__ __forceinline__ int warp_group_sum4(int key, float& v0, float& v1, float& v2, float& v3) {
+    float v[4] = {v0, v1, v2, v3};
+    const int rank = warp_group_sum<4>(key, v);
+    v0 = v[0]; v1 = v[1]; v2 = v[2]; v3 = v[3];
     return rank;
 }
 

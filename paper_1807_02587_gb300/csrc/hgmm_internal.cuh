@@ -133,6 +133,7 @@ struct hgmm_tree {
     int* status = nullptr;
     // registration
     unsigned long long* reg_acc = nullptr;  // nodes x ACC_REPLICAS x 4 fixed point
+    unsigned long long* reg_acc2 = nullptr; // nodes x 6 fixed-point second moments (full Eq. 7)
     float2* reg_part = nullptr;             // blocks x 27 (sum, compensation)
     float4* rnode = nullptr;                // nodes x 3: P (6), mu - mu32 (3), FP32
     unsigned* reg_bar = nullptr;            // grid barrier words (8)

@@ -293,14 +293,20 @@ constexpr int VAR_THREADS = 256;
 constexpr int VAR_STACK = 8 * HGMM_MAX_DEPTH;
 constexpr int VAR_TERMINAL = 1 << 8;
 
-template <int MODE>
+// Fixed-point units of the second moments gamma (z' - mu_j)_a (z' - mu_j)_b
+// per squared extent.
+constexpr double FIX2 = 4294967296.0;
+
+template <int MODE, bool M2>
 __global__ void __launch_bounds__(VAR_THREADS)
 k_descend_var(const float4* __restrict__ src, int n, const NodeEst* __restrict__ est, int depth, float tau,
               const float* __restrict__ Rt, const RootDev* __restrict__ root,
-              unsigned long long* __restrict__ acc, int* __restrict__ status) {
+              unsigned long long* __restrict__ acc, unsigned long long* __restrict__ acc2,
+              int* __restrict__ status) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double ext = root->extent > 0.0 ? root->extent : 1.0;
     const float qscale = float(FIX / ext);
+    const float q2 = float(FIX2 / (ext * ext));
     const float r00 = Rt[0], r01 = Rt[1], r02 = Rt[2], r10 = Rt[3], r11 = Rt[4], r12 = Rt[5];
     const float r20 = Rt[6], r21 = Rt[7], r22 = Rt[8], tx = Rt[9], ty = Rt[10], tz = Rt[11];
     const int warps_total = gridDim.x * (VAR_THREADS / 32);
@@ -390,33 +396,104 @@ k_descend_var(const float4* __restrict__ src, int n, const NodeEst* __restrict__
                     }
                 }
             }
-            float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+            constexpr int NV = M2 ? 10 : 4;
+            float v[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) v[q] = 0.f;
             if (out_node >= 0) {
                 const float4 a = __ldg(&est[out_node].a);
-                v0 = out_g;
-                v1 = out_g * (x - a.x);
-                v2 = out_g * (y - a.y);
-                v3 = out_g * (w - a.z);
+                const float dx = x - a.x, dy = y - a.y, dz = w - a.z;
+                v[0] = out_g;
+                v[1] = out_g * dx;
+                v[2] = out_g * dy;
+                v[3] = out_g * dz;
+                if (M2) {
+                    v[4] = v[1] * dx;
+                    v[5] = v[1] * dy;
+                    v[6] = v[1] * dz;
+                    v[7] = v[2] * dy;
+                    v[8] = v[2] * dz;
+                    v[9] = v[3] * dz;
+                }
             }
-            const int rank = warp_group_sum4(out_node, v0, v1, v2, v3);
+            const int rank = warp_group_sum<NV>(out_node, v);
             if (out_node >= 0 && rank == 0) {
                 unsigned long long* dst = acc + 4 * int64_t(out_node) * ACC_REPLICAS;
-                atomicAdd(dst + 0, (unsigned long long)to_fix(v0 * 4294967296.0f));
-                atomicAdd(dst + 1, (unsigned long long)to_fix(v1 * qscale));
-                atomicAdd(dst + 2, (unsigned long long)to_fix(v2 * qscale));
-                atomicAdd(dst + 3, (unsigned long long)to_fix(v3 * qscale));
+                atomicAdd(dst + 0, (unsigned long long)to_fix(v[0] * 4294967296.0f));
+                atomicAdd(dst + 1, (unsigned long long)to_fix(v[1] * qscale));
+                atomicAdd(dst + 2, (unsigned long long)to_fix(v[2] * qscale));
+                atomicAdd(dst + 3, (unsigned long long)to_fix(v[3] * qscale));
+                if (M2) {
+                    unsigned long long* d2 = acc2 + 6 * int64_t(out_node);
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) atomicAdd(d2 + q, (unsigned long long)to_fix(v[4 + q] * q2));
+                }
             }
         }
     }
 }
 
+// Levi-Civita symbol on indices 0..2.
+__host__ __device__ constexpr int lc3(int i, int j, int k) { return (i - j) * (j - k) * (k - i) / 2; }
+
+// The full Eq. 7 additions of one node from its scatter S = sum gamma d d^T
+// (d = z' - mu*): the rotation block gains sum gamma [d]x P [d]x^T, i.e.
+// entry (a, b) = sum eps(a,j,k) eps(b,n,m) P_km S_jn, the rotation part of
+// the right-hand side gains -sum gamma d x (P d), i.e. entry a =
+// -sum eps(a,j,k) P_km S_jm, and the objective tr(P S); all times 1 / N.
+__device__ __forceinline__ void scatter_terms(const float (&P)[3][3], const float (&S)[3][3], float inv_n,
+                                              float* w) {
+    const int rr[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    const int slot[6] = {0, 1, 2, 6, 7, 11};  // upper-packed 6x6 positions of the rotation block
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const int a = rr[e][0], b = rr[e][1];
+        float h = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (lc3(a, j, k) == 0) continue;
+#pragma unroll
+                for (int nn = 0; nn < 3; ++nn)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        if (lc3(b, nn, m) == 0) continue;
+                        h = fmaf(float(lc3(a, j, k) * lc3(b, nn, m)) * P[k][m], S[j][nn], h);
+                    }
+            }
+        w[slot[e]] += inv_n * h;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float gsum = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (lc3(a, j, k) == 0) continue;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) gsum = fmaf(float(lc3(a, j, k)) * P[k][m], S[j][m], gsum);
+            }
+        w[21 + a] -= inv_n * gsum;
+    }
+    float tr = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) tr = fmaf(P[k][m], S[k][m], tr);
+    w[27] += inv_n * tr;
+}
+
 // Node terms of one round from the fixed-point moments (256 nodes per CTA,
 // a warp reduce-scatter per 32 nodes, the CTA's eight warp sums in order);
-// the accumulators are cleared for the next round.
+// the accumulators are cleared for the next round.  FULL adds the scatter
+// terms of the full Eq. 7 from the second moments.
+template <bool FULL>
 __global__ void __launch_bounds__(VAR_THREADS)
 k_var_terms(int n_nodes, int n, const NodeEst* __restrict__ est, const float4* __restrict__ rnode,
             const RootDev* __restrict__ root, unsigned long long* __restrict__ acc,
-            float2* __restrict__ part, double* __restrict__ dbg) {
+            unsigned long long* __restrict__ acc2, float2* __restrict__ part, double* __restrict__ dbg) {
     __shared__ float2 sm[VAR_THREADS / 32][NTERM];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = blockIdx.x * VAR_THREADS + threadIdx.x;
@@ -440,8 +517,33 @@ k_var_terms(int n_nodes, int n, const NodeEst* __restrict__ est, const float4* _
             o1 = float(a2) * inv;
             o2 = float(a3) * inv;
             node_terms(rnode[3 * g], rnode[3 * g + 1], rnode[3 * g + 2], cm, M0, o0, o1, o2, M0 / float(n), wv);
+            if (FULL) {
+                // scatter about mu*: S = M2 - M1 M1^T / M0 (moments centred on
+                // the FP32 mean), formed in FP64
+                unsigned long long* bp = acc2 + 6 * int64_t(g);
+                const double i1 = 1.0 / double(qscale), i2 = 1.0 / double(float(FIX2 / (ext * ext)));
+                const double m0 = double(a0) * INV_FIX;
+                const double m1[3] = {double(a1) * i1, double(a2) * i1, double(a3) * i1};
+                double m2[6];
+                for (int q = 0; q < 6; ++q) m2[q] = double((long long)bp[q]) * i2;
+                const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+                float Sm[3][3];
+                for (int q = 0; q < 6; ++q) {
+                    const int r = ij[q][0], cc = ij[q][1];
+                    const float sv = float(m2[q] - m1[r] * m1[cc] / m0);
+                    Sm[r][cc] = sv;
+                    Sm[cc][r] = sv;
+                }
+                const float4 p0 = rnode[3 * g], p1 = rnode[3 * g + 1];
+                const float Pm[3][3] = {{p0.x, p0.y, p0.z}, {p0.y, p0.w, p1.x}, {p0.z, p1.x, p1.y}};
+                scatter_terms(Pm, Sm, 1.0f / float(n), wv);
+            }
 #pragma unroll
             for (int k = 0; k < NTERM; ++k) pair_add(v[k], c[k], wv[k], 0.f);
+        }
+        if (FULL) {
+            unsigned long long* bp = acc2 + 6 * int64_t(g);
+            for (int q = 0; q < 6; ++q) bp[q] = 0ull;
         }
         dbg[4 * g + 0] = double(a0) * INV_FIX;
         dbg[4 * g + 1] = double(M0) * (double(cm.x) + double(o0));
@@ -537,22 +639,26 @@ int hgmm_register_descent_impl(hgmm_tree* t, const float4* src, int64_t n64, con
                                                       t->reg_T, t->reg_Rt, t->reg_bar, t->reg_obj);
     const int tgrid = (n_nodes + VAR_THREADS - 1) / VAR_THREADS;
     const int dgrid = std::max(1, std::min(4 * t->n_sm, (n + VAR_THREADS - 1) / VAR_THREADS));
+    const bool full = d.full_eq7 != 0;
+    if (full) cudaMemsetAsync(t->reg_acc2, 0, size_t(6) * n_nodes * sizeof(unsigned long long), s);
     for (int it = 0; it < iters; ++it) {
-        switch (d.mode) {
-            case HGMM_DESCENT_ML_LOCAL:
-                k_descend_var<HGMM_DESCENT_ML_LOCAL><<<dgrid, VAR_THREADS, 0, s>>>(
-                    src, n, t->est, t->depth, d.tau, t->reg_Rt, t->root, t->reg_acc, t->status);
-                break;
-            case HGMM_DESCENT_ML_GLOBAL:
-                k_descend_var<HGMM_DESCENT_ML_GLOBAL><<<dgrid, VAR_THREADS, 0, s>>>(
-                    src, n, t->est, t->depth, d.tau, t->reg_Rt, t->root, t->reg_acc, t->status);
-                break;
-            default:
-                k_descend_var<HGMM_DESCENT_MULTIPATH><<<dgrid, VAR_THREADS, 0, s>>>(
-                    src, n, t->est, t->depth, d.tau, t->reg_Rt, t->root, t->reg_acc, t->status);
+#define HGMM_DESCEND(M, F)                                                                          \
+    k_descend_var<M, F><<<dgrid, VAR_THREADS, 0, s>>>(src, n, t->est, t->depth, d.tau, t->reg_Rt, t->root, \
+                                                      t->reg_acc, t->reg_acc2, t->status)
+        if (d.mode == HGMM_DESCENT_ML_LOCAL) {
+            if (full) HGMM_DESCEND(HGMM_DESCENT_ML_LOCAL, true); else HGMM_DESCEND(HGMM_DESCENT_ML_LOCAL, false);
+        } else if (d.mode == HGMM_DESCENT_ML_GLOBAL) {
+            if (full) HGMM_DESCEND(HGMM_DESCENT_ML_GLOBAL, true); else HGMM_DESCEND(HGMM_DESCENT_ML_GLOBAL, false);
+        } else {
+            if (full) HGMM_DESCEND(HGMM_DESCENT_MULTIPATH, true); else HGMM_DESCEND(HGMM_DESCENT_MULTIPATH, false);
         }
-        k_var_terms<<<tgrid, VAR_THREADS, 0, s>>>(n_nodes, n, t->est, t->rnode, t->root, t->reg_acc,
-                                                  t->reg_part, t->reg_dbg);
+#undef HGMM_DESCEND
+        if (full)
+            k_var_terms<true><<<tgrid, VAR_THREADS, 0, s>>>(n_nodes, n, t->est, t->rnode, t->root, t->reg_acc,
+                                                            t->reg_acc2, t->reg_part, t->reg_dbg);
+        else
+            k_var_terms<false><<<tgrid, VAR_THREADS, 0, s>>>(n_nodes, n, t->est, t->rnode, t->root, t->reg_acc,
+                                                             t->reg_acc2, t->reg_part, t->reg_dbg);
         k_var_solve<<<1, VAR_THREADS, 0, s>>>(t->reg_part, tgrid, it, t->reg_T, t->reg_Rt, T_hist, t->reg_obj,
                                               t->status);
     }

@@ -2,7 +2,9 @@
 FP64 oracle on the GPU's own tree: Algorithm 1 through the variant kernel
 (against hgmm_register too), the path-product gamma, and the threshold-pruned
 multi-path descent; first-round moments, 30 rounds, the LiDAR workload's
-first round, mass conservation and determinism."""
+first round, mass conservation and determinism; and the full Eq. 7 M-step
+(second moments, scatter terms) against the oracle's Gauss-Newton step over
+the point contributions."""
 import numpy as np
 import pytest
 
@@ -121,3 +123,36 @@ def test_threshold_override_does_not_persist(B):
     b = tree.register(src, iters=10).cpu().numpy()
     tree.sync()
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode,tau,name", [("local", 0.0, "corner"), ("multipath", 0.01, "corner"),
+                                           ("local", 0.0, "lidar")])
+def test_full_eq7_first_round_matches_oracle(B, mode, tau, name):
+    """The full Eq. 7 M-step (scatter kept): the first round's pose and
+    objective against the oracle's Gauss-Newton step over the point
+    contributions."""
+    import torch
+    p, depth = (_small(), 3) if name == "corner" else (synth.lidar_pair(0), 4)
+    tree, ot, src, Zs = _setup(B, p, depth)
+    T1 = tree.register_descent(src, MODES[mode], tau, iters=1, full_eq7=True).cpu().numpy()
+    obj = torch.zeros(1, dtype=torch.float64, device="cuda")
+    B.hgmm_register_objective(tree.handle, obj)
+    tree.sync()
+    T_o, h = O.register_eq7(ot, Zs, mode, tau, iters=1, history=True)
+    r, t = PT.pose_errors(T1, T_o, ot.extent)
+    T9 = O.register_descent(ot, Zs, mode, tau, iters=1)
+    print(name, mode, "eq7 GPU vs oracle", r, t, "objective", obj.item(), h[0]["objective"],
+          "eq7 vs eq9 step", PT.pose_errors(T_o, T9, ot.extent))
+    assert r < 2e-3 and t < 2e-5
+    assert obj.item() == pytest.approx(h[0]["objective"], rel=1e-3)
+
+
+def test_full_eq7_thirty_rounds_match_oracle(B):
+    p = _small()
+    tree, ot, src, Zs = _setup(B, p, 3)
+    T = tree.register_descent(src, 0, 0.0, iters=30, full_eq7=True).cpu().numpy()
+    tree.sync()
+    T_o = O.register_eq7(ot, Zs, "local", 0.0, iters=30)
+    r, t = PT.pose_errors(T, T_o, ot.extent)
+    print("eq7 30 rounds GPU vs oracle", r, t, "GPU vs truth", PT.pose_errors(T, p["T_gt"], ot.extent))
+    assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL
