@@ -765,6 +765,8 @@ def main():
     ap.add_argument("--no-large-build", action="store_true")
     ap.add_argument("--no-odometry", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile-variants", action="store_true",
+                    help="plain launches of the flat, multi-path and full Eq. 7 variants for a profiler")
     ap.add_argument("--odometry-frames", type=int, default=20)
     ap.add_argument("--large-points", type=int, default=16_000_000)
     ap.add_argument("--profile-mlp", action="store_true",
@@ -781,6 +783,8 @@ def main():
         return reference_main(args, rank, world)
     if args.profile_mlp:
         return profile_mlp_main()
+    if args.profile_variants:
+        return profile_variants_main(args)
     if args.profile_build:
         import torch
         from paper_1807_02587_gb300 import binding as B
@@ -792,6 +796,34 @@ def main():
         print(json.dumps({"profile_build": True, "points": int(dev.shape[0])}))
         return 0
     return gpu_main(args, rank, world, local_rank)
+
+
+def profile_variants_main(args):
+    """Plain launches of the Sec. 5 / Sec. 4.1 variants on the bench's LiDAR
+    pair for an external profiler: per variant two warm-up registrations of
+    2 rounds, then one of 2 rounds (flat J=n from the depth-4 leaves; the
+    multi-path descent at tau = 0.01; the full Eq. 7 M-step)."""
+    import torch
+    from paper_1807_02587_gb300 import binding as B
+    from paper_1807_02587_gb300 import synth
+    pair = synth.lidar_pair(args.seed)
+    tgt = torch.from_numpy(synth.to_float4(pair["tgt"])).cuda()
+    src = torch.from_numpy(synth.to_float4(pair["src"])).cuda()
+    n = int(max(tgt.shape[0], src.shape[0]))
+    tree = B.Tree(n, DEPTH)
+    tree.build(tgt, DEPTH)
+    flat = B.Flat(n, int(B.hgmm_node_count(DEPTH)))
+    flat.from_tree(tree)
+    for _ in range(3):
+        flat.register(src, iters=2)
+    flat.sync()
+    for _ in range(3):
+        tree.register_descent(src, B.HGMM_DESCENT_MULTIPATH, 0.01, iters=2)
+    for _ in range(3):
+        tree.register_descent(src, B.HGMM_DESCENT_ML_LOCAL, 0.0, iters=2, full_eq7=True)
+    tree.sync()
+    print(json.dumps({"profile_variants": True, "J": flat.export()["J"]}))
+    return 0
 
 
 def profile_mlp_main():
