@@ -211,7 +211,7 @@ def gpu_main(args, rank, world, local_rank):
     tgt = torch.from_numpy(tgt4).cuda()
     src = torch.from_numpy(src4).cuda()
     tree = B.Tree(max(n_t, n_s), DEPTH)
-    prm = B.params()
+    prm = B.params(flags=B.HGMM_FLAG_EM_COOPERATIVE if args.em_cooperative else 0)
     s = torch.cuda.Stream()
     T_out = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
 
@@ -765,6 +765,8 @@ def main():
     ap.add_argument("--no-large-build", action="store_true")
     ap.add_argument("--no-odometry", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--em-cooperative", action="store_true",
+                    help="build EM of each level in one cooperative launch (default: launches per iteration)")
     ap.add_argument("--profile-variants", action="store_true",
                     help="plain launches of the flat, multi-path and full Eq. 7 variants for a profiler")
     ap.add_argument("--odometry-frames", type=int, default=20)

@@ -74,7 +74,8 @@ typedef struct hgmm_tree hgmm_tree; /* opaque, device-resident, library-owned */
  *               debug_stop_level = L + 1 the build finishes levels < L, then
  *               runs only debug_stop_iters EM iterations of level L and stops
  *               (no hand-off), so hgmm_tree_export(L) shows the parameters
- *               after that many iterations (0 = the initial children). */
+ *               after that many iterations (0 = the initial children).
+ *   flags     : HGMM_FLAG_* bits (default 0). */
 typedef struct hgmm_params {
     int32_t em_iters;
     float n_min;
@@ -83,8 +84,16 @@ typedef struct hgmm_params {
     int32_t precision;
     int32_t debug_stop_level;
     int32_t debug_stop_iters;
-    int32_t reserved;
+    int32_t flags;
 } hgmm_params;
+
+/* Run all EM iterations of each multi-launch level of the build in one
+ * cooperative launch (arrival counters per parent, the M-step of each parent
+ * in a fixed owner CTA) instead of separate E-step and M-step launches per
+ * iteration.  The result is the same bit for bit; under a CUDA graph the
+ * separate launches are faster on the bench workload, so this is off by
+ * default. */
+#define HGMM_FLAG_EM_COOPERATIVE 1
 
 /* Per-node record written by hgmm_tree_export: 16 float64 per node,
  * [pi, mu_x, mu_y, mu_z, S_xx, S_xy, S_xz, S_yy, S_yz, S_zz, live, count,

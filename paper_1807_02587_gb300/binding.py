@@ -47,7 +47,7 @@ class hgmm_params(ctypes.Structure):
     _fields_ = [("em_iters", ctypes.c_int32), ("n_min", ctypes.c_float),
                 ("lam_c", ctypes.c_float), ("eps_rel", ctypes.c_float),
                 ("precision", ctypes.c_int32), ("debug_stop_level", ctypes.c_int32),
-                ("debug_stop_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("debug_stop_iters", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 HGMM_DESCENT_ML_LOCAL = 0
@@ -148,12 +148,15 @@ def _check(rc: int, where: str):
         raise HgmmError(rc, where)
 
 
+HGMM_FLAG_EM_COOPERATIVE = 1
+
+
 def params(em_iters=8, n_min=8.0, lam_c=0.01, eps_rel=1e-3, precision=0,
-           debug_stop_level=0, debug_stop_iters=0) -> hgmm_params:
+           debug_stop_level=0, debug_stop_iters=0, flags=0) -> hgmm_params:
     p = hgmm_params()
     _lib.hgmm_params_default(ctypes.byref(p))
     p.em_iters, p.n_min, p.lam_c, p.eps_rel, p.precision = em_iters, n_min, lam_c, eps_rel, precision
-    p.debug_stop_level, p.debug_stop_iters = debug_stop_level, debug_stop_iters
+    p.debug_stop_level, p.debug_stop_iters, p.flags = debug_stop_level, debug_stop_iters, flags
     return p
 
 

@@ -45,7 +45,7 @@ void free_tree(hgmm_tree* t) {
     clear_prof(t);
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
                     t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
-                    t->item_off, t->root, t->root_part, t->root_counter, t->status, t->reg_acc, t->reg_acc2, t->reg_part,
+                    t->item_off, t->root, t->root_part, t->root_counter, t->em_cnt, t->status, t->reg_acc, t->reg_acc2, t->reg_part,
                     t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->reg_obj, t->rnode, t->trace, t->stage_tgt,
                     t->stage_src, t->stage_T};
     for (void* p : ptrs)
@@ -119,6 +119,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     t->max_items = (max_points + TILE - 1) / TILE + parents;
     t->est_grid = t->n_sm * 2;
     t->reg_grid = hgmm_register_grid(t->n_sm);
+    t->em_coop = hgmm_em_coop_fits(t->n_sm, t->est_grid);
     if (t->reg_grid < 1) {
         delete t;
         return HGMM_ECUDA;
@@ -144,6 +145,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->root, 1);
     good &= dalloc(&t->root_part, int64_t(t->est_grid) * 32);
     good &= dalloc(&t->root_counter, 1);
+    good &= dalloc(&t->em_cnt, level_size(std::max(0, max_depth - 1)) + 1);
     good &= dalloc(&t->status, 1);
     good &= dalloc(&t->reg_acc, 4 * ACC_REPLICAS * t->max_nodes);
     good &= dalloc(&t->reg_acc2, 6 * t->max_nodes);

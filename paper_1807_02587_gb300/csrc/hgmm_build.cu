@@ -136,6 +136,59 @@ __global__ void __launch_bounds__(EST_THREADS, 2) k_em_local(int level, int n, i
     }
 }
 
+// All K EM iterations of one level in one cooperative launch (levels whose
+// parents are few, or large).  Per iteration every CTA runs the E-step of
+// its chunk of items, reading the children's constants through L2 (they
+// change between iterations), and adds one arrival to each parent its chunk
+// touched; the CTA owning parent p (p mod gridDim) waits for all of p's runs,
+// runs the same fixed-order reduction and FP64 M-step as k_mstep and counts
+// p as done; the next iteration starts once every parent is done.  The
+// arithmetic is that of k_estep + k_mstep, so the result is the same bit
+// for bit.  cnt: n_par arrival counters, then the done counter, all zero at
+// launch and monotonic; every wait is bounded (ST_TIMEOUT, then return).
+template <bool COMP>
+__global__ void __launch_bounds__(EST_THREADS, 2)
+k_em_coop(int level, int n, int n_par, int K, const float4* __restrict__ pts, const Item* __restrict__ items,
+          const int* __restrict__ meta, const int* __restrict__ item_range, float2* __restrict__ partials,
+          const int* __restrict__ seg_count, const RootDev* __restrict__ root, float n_min,
+          NodeStat* __restrict__ stat, NodeEst* __restrict__ est, unsigned* __restrict__ cnt,
+          int* __restrict__ status) {
+    __shared__ union {
+        float2 red[EST_THREADS / 32][NPART];
+        MstepSmem msm;
+    } sm;
+    const int n_items = meta[0], C = meta[1];
+    const int ib = blockIdx.x * C, ie = min(ib + C, n_items);
+    const NodeEst* est_lvl = est + level_offset(level);
+    unsigned* done = cnt + n_par;
+    // the parents this CTA's chunk touches (items are ordered by parent)
+    const int p_first = ib < ie ? items[ib].parent : 0;
+    const int p_last = ib < ie ? items[ie - 1].parent : -1;
+    for (int k = 0; k < K; ++k) {
+        if (k > 0 && !wait_at_least(done, unsigned(k) * unsigned(n_par), status, BARRIER_SPIN_LIMIT, 128)) return;
+        estep_range<COMP, ItemList, true>(pts, ItemList{items}, ib, ie, est_lvl, partials, sm.red);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();  // the partials before the arrivals
+            for (int p = p_first; p <= p_last; ++p) atomicAdd(cnt + p, 1u);
+        }
+        for (int p = blockIdx.x; p < n_par; p += gridDim.x) {
+            const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
+            if (i0 < i1) {  // a parent without points has no runs; its children stay dead
+                const unsigned runs = unsigned((i1 - 1) / C - i0 / C + 1);
+                if (!wait_at_least(cnt + p, unsigned(k + 1) * runs, status, BARRIER_SPIN_LIMIT)) return;
+                mstep_parent<COMP>(level, n, p, i0, i1, C, partials, seg_count, root, n_min, stat, est, status,
+                                   sm.msm);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();  // the children's new constants before the count
+                atomicAdd(done, 1u);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(EST_THREADS) k_assign(const float4* __restrict__ pts,
                                                         const Item* __restrict__ items,
                                                         const int* __restrict__ meta,
@@ -227,6 +280,18 @@ using namespace hgmm;
 constexpr int LOCAL_EM_PARENTS = 256;
 constexpr int64_t LOCAL_EM_POINTS = 2048;
 
+// Whether est_grid CTAs of the cooperative EM kernel fit on the device at
+// once (a cooperative launch needs them co-resident).
+bool hgmm_em_coop_fits(int n_sm, int est_grid) {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_em_coop<true>, EST_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_em_coop<false>, EST_THREADS, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return std::min(a, b) * n_sm >= est_grid;
+}
+
 int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                     const hgmm_params& p, cudaStream_t s) {
     const int n = int(n64);
@@ -272,7 +337,21 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                                                                t->partials, t->seg_count, t->root, p.n_min,
                                                                t->stat, t->est, t->status);
         }
-        for (int k = 0; k < (local_em ? 0 : em_iters); ++k) {
+        const bool coop_em = !local_em && em_iters > 0 && t->em_coop && (p.flags & HGMM_FLAG_EM_COOPERATIVE);
+        if (coop_em) {
+            ProfScope ps_(t, K_ESTEP, s);
+            cudaMemsetAsync(t->em_cnt, 0, size_t(n_par + 1) * sizeof(unsigned), s);
+            int lv = l, nn = n, np = n_par, K = em_iters;
+            float nmin = p.n_min;
+            void* args[] = {&lv, &nn, &np, &K, &cur, &t->items, &t->meta, &t->item_range, &t->partials,
+                            &t->seg_count, &t->root, &nmin, &t->stat, &t->est, &t->em_cnt, &t->status};
+            const void* fn = comp ? (const void*)k_em_coop<true> : (const void*)k_em_coop<false>;
+            if (cudaLaunchCooperativeKernel(fn, dim3(G), dim3(EST_THREADS), args, 0, s) != cudaSuccess) {
+                fprintf(stderr, "hgmm: cooperative EM launch failed\n");
+                return HGMM_ECUDA;
+            }
+        }
+        for (int k = 0; k < (local_em || coop_em ? 0 : em_iters); ++k) {
             {
                 ProfScope ps_(t, K_ESTEP, s);
                 if (comp)

@@ -340,8 +340,11 @@ struct ChildRegs {
     float mx, my, mz, C, w00, w10, w11, w20, w21, w22;
 };
 
+// CG: read through L2 only (constants that other CTAs of a persistent
+// launch rewrite between uses).
+template <bool CG = false>
 __device__ __forceinline__ void load_child(const NodeEst* __restrict__ e, ChildRegs& r) {
-    const float4 a = e->a, b = e->b, c = e->c;
+    const float4 a = CG ? __ldcg(&e->a) : e->a, b = CG ? __ldcg(&e->b) : e->b, c = CG ? __ldcg(&e->c) : e->c;
     r.mx = a.x; r.my = a.y; r.mz = a.z; r.C = a.w;
     r.w00 = b.x; r.w10 = b.y; r.w11 = b.z; r.w20 = b.w;
     r.w21 = c.x; r.w22 = c.y;
@@ -432,7 +435,7 @@ __device__ __forceinline__ void flush_run(float* s, float* c, float2 (*red)[NPAR
 // moments of each child centred on the child's current FP32 mean, one
 // partial per run of consecutive items with the same parent, stored at the
 // run's first item.
-template <bool COMP, class Items>
+template <bool COMP, class Items, bool CG = false>
 __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Items items, int ib,
                                             int ie, const NodeEst* __restrict__ est_lvl,
                                             float2* __restrict__ partials,
@@ -456,8 +459,8 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
             }
             cur = w.parent;
             run = it;
-            load_child(est_lvl + 8 * cur + 2 * k, r0);
-            load_child(est_lvl + 8 * cur + 2 * k + 1, r1);
+            load_child<CG>(est_lvl + 8 * cur + 2 * k, r0);
+            load_child<CG>(est_lvl + 8 * cur + 2 * k + 1, r1);
         }
         float4 znext = pts[w.start + min(warp * 8 + q, w.count - 1)];
         for (int base = 0; base < w.count; base += 64) {
@@ -1487,8 +1490,10 @@ __device__ inline void sum_terms_and_solve(const float2* __restrict__ tpart, int
 // generation), then the CTA proceeds; on timeout it records ST_TIMEOUT and
 // every thread of the CTA gets false.  The acquire side of a release made by
 // the CTA that advanced the word (a fence before its atomic or store).
+// sleep_ns > 0 backs off between polls (many CTAs polling one word slow
+// down the CTA that will advance it); the limit then counts polls.
 __device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned target, int* status,
-                                              long long limit) {
+                                              long long limit, unsigned sleep_ns = 0) {
     __shared__ int ok_wait;
     if (threadIdx.x == 0) {
         const volatile unsigned* v = word;
@@ -1500,6 +1505,7 @@ __device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned tar
                 ok = 0;
                 break;
             }
+            if (sleep_ns) __nanosleep(sleep_ns);
         }
         __threadfence();
         ok_wait = ok;

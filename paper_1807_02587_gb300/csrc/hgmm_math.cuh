@@ -267,12 +267,14 @@ __device__ inline bool pack_est(double pi, const double mu[3], const double S_in
     double L[6], R[3];
     bool clean = true;
     double boost = eps > 0.0 ? eps : 1e-30;
-    for (int tries = 0; tries < 8 && !chol3(S, L, R); ++tries) {
+    bool ok = chol3(S, L, R);
+    for (int tries = 0; tries < 8 && !ok; ++tries) {
         clean = false;
         S[0] += boost; S[3] += boost; S[5] += boost;
         boost *= 10.0;
+        ok = chol3(S, L, R);
     }
-    if (!chol3(S, L, R)) {  // hopeless (NaN input): make it an isotropic unit Gaussian
+    if (!ok) {  // hopeless (NaN input): make it an isotropic unit Gaussian
         L[0] = 1; L[1] = 0; L[2] = 1; L[3] = 0; L[4] = 0; L[5] = 1;
         R[0] = 1; R[1] = 1; R[2] = 1;
         clean = false;

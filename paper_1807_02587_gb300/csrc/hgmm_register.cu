@@ -304,9 +304,16 @@ k_descend_var(const float4* __restrict__ src, int n, const NodeEst* __restrict__
               unsigned long long* __restrict__ acc, unsigned long long* __restrict__ acc2,
               int* __restrict__ status) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double ext = root->extent > 0.0 ? root->extent : 1.0;
-    const float qscale = float(FIX / ext);
-    const float q2 = float(FIX2 / (ext * ext));
+    // the fixed-point scales from the FP64 extent, once per CTA (FP64
+    // division is slow on this part)
+    __shared__ float s_scale[2];
+    if (threadIdx.x == 0) {
+        const double ext = root->extent > 0.0 ? root->extent : 1.0;
+        s_scale[0] = float(FIX / ext);
+        s_scale[1] = float(FIX2 / (ext * ext));
+    }
+    __syncthreads();
+    const float qscale = s_scale[0], q2 = s_scale[1];
     const float r00 = Rt[0], r01 = Rt[1], r02 = Rt[2], r10 = Rt[3], r11 = Rt[4], r12 = Rt[5];
     const float r20 = Rt[6], r21 = Rt[7], r22 = Rt[8], tx = Rt[9], ty = Rt[10], tz = Rt[11];
     const int warps_total = gridDim.x * (VAR_THREADS / 32);
@@ -497,8 +504,14 @@ k_var_terms(int n_nodes, int n, const NodeEst* __restrict__ est, const float4* _
     __shared__ float2 sm[VAR_THREADS / 32][NTERM];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = blockIdx.x * VAR_THREADS + threadIdx.x;
-    const double ext = root->extent > 0.0 ? root->extent : 1.0;
-    const float qscale = float(FIX / ext);
+    __shared__ float s_scale[2];
+    if (threadIdx.x == 0) {
+        const double ext = root->extent > 0.0 ? root->extent : 1.0;
+        s_scale[0] = float(FIX / ext);
+        s_scale[1] = float(FIX2 / (ext * ext));
+    }
+    __syncthreads();
+    const float qscale = s_scale[0];
     float v[32], c[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) { v[k] = 0.f; c[k] = 0.f; }
@@ -521,7 +534,7 @@ k_var_terms(int n_nodes, int n, const NodeEst* __restrict__ est, const float4* _
                 // scatter about mu*: S = M2 - M1 M1^T / M0 (moments centred on
                 // the FP32 mean), formed in FP64
                 unsigned long long* bp = acc2 + 6 * int64_t(g);
-                const double i1 = 1.0 / double(qscale), i2 = 1.0 / double(float(FIX2 / (ext * ext)));
+                const double i1 = 1.0 / double(qscale), i2 = 1.0 / double(s_scale[1]);
                 const double m0 = double(a0) * INV_FIX;
                 const double m1[3] = {double(a1) * i1, double(a2) * i1, double(a3) * i1};
                 double m2[6];

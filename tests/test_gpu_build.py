@@ -91,3 +91,29 @@ def test_plain_fp32_sums_differ_but_stay_close(B):
     for r in res["levels"]:
         assert r["live_mismatch"] == 0
         assert r["mu"] < 1e-3 and r["S"] < 1e-3
+
+
+@pytest.mark.parametrize("case", list(_cases()))
+def test_cooperative_em_equals_per_iteration_launches(B, case):
+    """One cooperative launch per level for all EM iterations performs the
+    same E-step and M-step arithmetic as the per-iteration launches: the
+    trees, their labels and a stopped build agree bit for bit."""
+    make, depth = _cases()[case]
+    dev, Z = PT.device_cloud(make())
+    out = []
+    for flags in (0, B.HGMM_FLAG_EM_COOPERATIVE):
+        tree = B.Tree(Z.shape[0], depth)
+        tree.build(dev, depth, B.params(flags=flags))
+        tree.sync()
+        levels = [tree.export(l) for l in range(depth)]
+        labels = [tree.labels(l) for l in range(depth)]
+        stopped = B.Tree(Z.shape[0], depth)
+        stopped.build(dev, depth, B.params(flags=flags, debug_stop_level=depth, debug_stop_iters=3))
+        stopped.sync()
+        out.append((levels, labels, stopped.export(depth - 1)))
+    for l in range(depth):
+        for k in ("pi", "mu", "Sigma", "live", "count"):
+            np.testing.assert_array_equal(out[0][0][l][k], out[1][0][l][k])
+        np.testing.assert_array_equal(out[0][1][l], out[1][1][l])
+    for k in ("pi", "mu", "Sigma", "live"):
+        np.testing.assert_array_equal(out[0][2][k], out[1][2][k])
