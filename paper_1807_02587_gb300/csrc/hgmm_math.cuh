@@ -182,19 +182,23 @@ __device__ inline void eig3(const double S[6], double lam[3], double V[9]) {
     for (int r = 0; r < 3; ++r)
         for (int c = r; c < 3; ++c)
             B[r][c] = B[c][r] = U[0][r] * SU[0][c] + U[1][r] * SU[1][c] + U[2][r] * SU[2][c];
-    // 4) FP64 Jacobi sweeps on the nearly diagonal B
+    // 4) FP64 Jacobi sweeps on the nearly diagonal B.  After the FP32 sweeps
+    // the off-diagonal entries are ~1e-7 of the diagonal, so a rotation's
+    // tan(phi) is apq / gap up to O(t^3) (t ~ 1e-7: far below FP64 rounding)
+    // and cos(phi) = 1 - t^2 / 2 to O(t^4); one sweep leaves off-diagonals of
+    // O(t^2).  The convergence test comes after the sweep: a second sweep
+    // runs only where a pair with nearly equal eigenvalues took an exact
+    // (large) rotation and refilled the others.  FP64 instructions hold this
+    // part's FP64 pipe ~64 cycles each, so the common path is kept short.
     for (int sweep = 0; sweep < 3; ++sweep) {
-        const double off = B[0][1] * B[0][1] + B[0][2] * B[0][2] + B[1][2] * B[1][2];
-        const double dia = B[0][0] * B[0][0] + B[1][1] * B[1][1] + B[2][2] * B[2][2];
-        if (!(off > 1e-30 * dia)) break;
         for (int pq = 0; pq < 3; ++pq) {
             const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
             const double apq = B[p][q];
             if (apq == 0.0) continue;
             const double gap = B[q][q] - B[p][p];
             double t, c;
-            if (fabs(apq) < 1e-8 * fabs(gap)) {
-                // small angle: t = tan(phi) ~ apq / gap to O(t^3) < 1e-24
+            if (fabs(apq) < 1e-5 * fabs(gap)) {
+                // small angle: t = tan(phi) ~ apq / gap to O(t^3) < 1e-15 t
                 t = apq * rcp_f64(gap);
                 c = 1.0 - 0.5 * t * t;
             } else {
@@ -222,6 +226,9 @@ __device__ inline void eig3(const double S[6], double lam[3], double V[9]) {
                 U[k][q] = s * ukp + c * ukq;
             }
         }
+        const double off = B[0][1] * B[0][1] + B[0][2] * B[0][2] + B[1][2] * B[1][2];
+        const double dia = B[0][0] * B[0][0] + B[1][1] * B[1][1] + B[2][2] * B[2][2];
+        if (!(off > 1e-26 * dia)) break;
     }
     int idx[3] = {0, 1, 2};
     const double d[3] = {B[0][0], B[1][1], B[2][2]};

@@ -117,3 +117,26 @@ def test_cooperative_em_equals_per_iteration_launches(B, case):
         np.testing.assert_array_equal(out[0][1][l], out[1][1][l])
     for k in ("pi", "mu", "Sigma", "live"):
         np.testing.assert_array_equal(out[0][2][k], out[1][2][k])
+
+
+@pytest.mark.parametrize("case", ["corner10k_d3", "lidar_d4"])
+def test_node_eigen_decomposition_is_fp64_accurate(B, case):
+    """Every live node's eigenvalues (Sec. 4.1 complexity, Eq. 10 PCA form)
+    against numpy's eigh of the same exported FP64 covariance: the FP32
+    Jacobi + FP64 refinement must be accurate to FP64 level."""
+    make, depth = _cases()[case]
+    dev, Z = PT.device_cloud(make())
+    tree = B.Tree(Z.shape[0], depth)
+    tree.build(dev, depth)
+    tree.sync()
+    worst_l = worst_c = 0.0
+    for l in range(depth):
+        e = tree.export(l)
+        live = e["live"]
+        w = np.linalg.eigvalsh(e["Sigma"][live])[:, ::-1]
+        err = np.abs(e["lam"][live] - w) / w[:, :1]
+        cplx = w[:, 2] / w.sum(axis=1)
+        worst_l = max(worst_l, float(err.max(initial=0)))
+        worst_c = max(worst_c, float(np.abs(e["complexity"][live] - cplx).max(initial=0)))
+    print(case, "eigenvalue rel err", worst_l, "complexity err", worst_c)
+    assert worst_l < 1e-11 and worst_c < 1e-11
