@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "hgmm_dev.cuh"
+#include "hgmm_async.cuh"
 
 namespace hgmm {
 
@@ -73,16 +74,113 @@ __global__ void k_fill_items(int level, int n, int n_parents, const int* __restr
     items[j] = item_at(j, level, n, n_parents, item_range, seg_start, seg_count);
 }
 
+// The level-wide E-step: the arithmetic of estep_range (so the result is
+// the same bit for bit), with each item's points (one contiguous run of at
+// most TILE float4) brought into shared memory by one bulk asynchronous copy,
+// ESTEP_STAGES items ahead of the compute, so that no warp waits on a global
+// load.  One thread issues the copies; each completes on its stage's
+// mbarrier; a stage is refilled after the CTA's barrier at the end of the
+// item that used it (with an async-proxy fence).  All waits are bounded: on
+// a timeout the CTA records ST_TIMEOUT, waits (bounded) for its copies in
+// flight and stops.
+constexpr int ESTEP_STAGES = 4;
+
 template <bool COMP>
 __global__ void __launch_bounds__(EST_THREADS, 2)
 k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
         const int* __restrict__ meta, const NodeEst* __restrict__ est_lvl,
-        float2* __restrict__ partials) {
+        float2* __restrict__ partials, int* __restrict__ status) {
     __shared__ float2 red[EST_THREADS / 32][NPART];
+    __shared__ __align__(16) float4 stage[ESTEP_STAGES][TILE];
+    __shared__ __align__(8) uint64_t full[ESTEP_STAGES];
     const int n_items = meta[0];
     const int C = meta[1];
-    const int ib = blockIdx.x * C;
-    estep_range<COMP>(pts, ItemList{items}, ib, min(ib + C, n_items), est_lvl, partials, red);
+    const int ib = blockIdx.x * C, ie = min(ib + C, n_items);
+    if (ib >= ie) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 2, k = lane & 3;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < ESTEP_STAGES; ++st) tc::mbar_init(&full[st], 1);
+        tc::fence_mbar_init();
+        for (int it = ib; it < min(ie, ib + ESTEP_STAGES); ++it) {
+            const Item w = items[it];
+            const int st = (it - ib) % ESTEP_STAGES;
+            tc::mbar_arrive_expect_tx(&full[st], uint32_t(w.count) * 16u);
+            tc::bulk_g2s(tc::smem_u32(stage[st]), pts + w.start, uint32_t(w.count) * 16u, &full[st]);
+        }
+    }
+    __syncthreads();
+    float in[20], s[20], c[20];
+#pragma unroll
+    for (int v = 0; v < 20; ++v) { in[v] = 0.f; s[v] = 0.f; c[v] = 0.f; }
+    int nfold = 0;
+    int cur = -1, run = -1;
+    ChildRegs r0, r1;
+    int it = ib;
+    for (; it < ie; ++it) {
+        const Item w = items[it];
+        if (w.parent != cur) {
+            if (cur >= 0) {
+                fold20<COMP>(in, s, c);
+                nfold = 0;
+                flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+            }
+            cur = w.parent;
+            run = it;
+            load_child(est_lvl + 8 * cur + 2 * k, r0);
+            load_child(est_lvl + 8 * cur + 2 * k + 1, r1);
+        }
+        const int st = (it - ib) % ESTEP_STAGES;
+        const uint32_t parity = uint32_t((it - ib) / ESTEP_STAGES) & 1u;
+        const bool landed = tc::mbar_wait_bounded(&full[st], parity, tc::MBAR_SPIN_LIMIT);
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+            break;
+        }
+        const float4* zs = stage[st];
+        for (int base = 0; base < w.count; base += 64) {
+            const int idx = base + warp * 8 + q;
+            const bool valid = idx < w.count;
+            const float4 z = zs[min(idx, w.count - 1)];
+            float e0x, e0y, e0z, e1x, e1y, e1z;
+            const float s0 = child_score(r0, z.x, z.y, z.z, e0x, e0y, e0z);
+            const float s1 = child_score(r1, z.x, z.y, z.z, e1x, e1y, e1z);
+            float m = fmaxf(s0, s1);
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
+            const bool any_live = m > -CUDART_INF_F;  // false for a leaf parent
+            const float p0 = any_live ? exp2f(s0 - m) : 0.f;
+            const float p1 = any_live ? exp2f(s1 - m) : 0.f;
+            float tot = p0 + p1;
+            tot += __shfl_xor_sync(FULL, tot, 1);
+            tot += __shfl_xor_sync(FULL, tot, 2);
+            const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
+            accum10(in, p0 * rinv, e0x, e0y, e0z);
+            accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
+            if (++nfold == 16) {
+                fold20<COMP>(in, s, c);
+                nfold = 0;
+            }
+        }
+        __syncthreads();  // every thread is done with this stage
+        if (threadIdx.x == 0 && it + ESTEP_STAGES < ie) {
+            const Item wn = items[it + ESTEP_STAGES];
+            tc::fence_proxy_async();
+            tc::mbar_arrive_expect_tx(&full[st], uint32_t(wn.count) * 16u);
+            tc::bulk_g2s(tc::smem_u32(stage[st]), pts + wn.start, uint32_t(wn.count) * 16u, &full[st]);
+        }
+    }
+    if (it < ie) {
+        // timed out: let the copies in flight land (bounded) before the CTA
+        // and its shared memory go away
+        if (threadIdx.x == 0)
+            for (int j = it; j < min(ie, it + ESTEP_STAGES); ++j)
+                tc::mbar_wait_bounded(&full[(j - ib) % ESTEP_STAGES], uint32_t((j - ib) / ESTEP_STAGES) & 1u,
+                                      tc::MBAR_SPIN_LIMIT);
+        return;
+    }
+    fold20<COMP>(in, s, c);
+    flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
 }
 
 template <bool COMP>
@@ -355,9 +453,9 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
             {
                 ProfScope ps_(t, K_ESTEP, s);
                 if (comp)
-                    k_estep<true><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials);
+                    k_estep<true><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials, t->status);
                 else
-                    k_estep<false><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials);
+                    k_estep<false><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials, t->status);
             }
             {
                 ProfScope ps_(t, K_MSTEP, s);
@@ -547,12 +645,12 @@ extern "C" int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const h
     for (int k = 0; k < prm.em_iters; ++k) {
         if (prm.precision == 0) {
             k_estep<true><<<G, EST_THREADS, 0, s>>>(reinterpret_cast<const float4*>(d_points), items,
-                                                    meta, est, partials);
+                                                    meta, est, partials, status);
             k_mstep<true><<<1, 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
                                             prm.n_min, stat, est, status);
         } else {
             k_estep<false><<<G, EST_THREADS, 0, s>>>(reinterpret_cast<const float4*>(d_points), items,
-                                                     meta, est, partials);
+                                                     meta, est, partials, status);
             k_mstep<false><<<1, 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
                                              prm.n_min, stat, est, status);
         }
