@@ -117,9 +117,14 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     // widest parent level: level max_depth-2 (8^(max_depth-1) nodes), or the root
     const int64_t parents = max_depth >= 2 ? level_size(max_depth - 2) : 1;
     t->max_items = (max_points + TILE - 1) / TILE + parents;
-    t->est_grid = t->n_sm * 2;
+    t->est_grid = t->n_sm * 3;  // three k_estep CTAs fit on an SM
     t->reg_grid = hgmm_register_grid(t->n_sm);
-    t->em_coop = hgmm_em_coop_fits(t->n_sm, t->est_grid);
+    t->em_coop_grid = hgmm_em_coop_grid(t->n_sm, t->est_grid);
+    if (!hgmm_estep_smem_attr()) {
+        cudaGetLastError();
+        delete t;
+        return HGMM_ECUDA;
+    }
     if (t->reg_grid < 1) {
         delete t;
         return HGMM_ECUDA;

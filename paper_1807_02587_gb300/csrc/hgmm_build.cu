@@ -84,21 +84,79 @@ __global__ void k_fill_items(int level, int n, int n_parents, const int* __restr
 // a timeout the CTA records ST_TIMEOUT, waits (bounded) for its copies in
 // flight and stops.
 constexpr int ESTEP_STAGES = 4;
+// Dynamic shared memory of k_estep: the compensated sums (s, c) of every
+// lane's ten packed moment pairs, [value][thread], kept out of the register
+// file so that three CTAs fit on an SM.
+constexpr size_t ESTEP_DYN_SMEM = size_t(2) * 10 * EST_THREADS * sizeof(float2);
+
+// fold_pair with the compensated sums in shared memory (the same arithmetic).
+template <bool COMP>
+__device__ __forceinline__ void fold_pair_smem(float2 (&in)[10], float2* acc_s, float2* acc_c) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < 10; ++v) {
+        float2 sv = acc_s[v * EST_THREADS + t];
+        if (COMP) {
+            float2 cv = acc_c[v * EST_THREADS + t];
+            const float2 tt = __fadd2_rn(sv, in[v]);
+            const float2 bp = sub2(tt, sv);
+            const float2 e = __fadd2_rn(sub2(sv, sub2(tt, bp)), sub2(in[v], bp));
+            sv = tt;
+            cv = __fadd2_rn(cv, e);
+            acc_c[v * EST_THREADS + t] = cv;
+        } else {
+            sv = __fadd2_rn(sv, in[v]);
+        }
+        acc_s[v * EST_THREADS + t] = sv;
+        in[v] = make_float2(0.f, 0.f);
+    }
+}
 
 template <bool COMP>
-__global__ void __launch_bounds__(EST_THREADS, 2)
+__device__ __forceinline__ void flush_pair_smem(float2* acc_s, float2* acc_c, float2 (*red)[NPART],
+                                                float2* __restrict__ out) {
+    float2 s2[10], c2[10];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < 10; ++v) {
+        s2[v] = acc_s[v * EST_THREADS + t];
+        c2[v] = COMP ? acc_c[v * EST_THREADS + t] : make_float2(0.f, 0.f);
+        acc_s[v * EST_THREADS + t] = make_float2(0.f, 0.f);
+        acc_c[v * EST_THREADS + t] = make_float2(0.f, 0.f);
+    }
+    flush_pair<COMP>(s2, c2, red, out);
+}
+
+// The level-wide E-step: the arithmetic of estep_range (so the result is
+// the same bit for bit), with each item's points (one contiguous run of at
+// most TILE float4) brought into shared memory by one bulk asynchronous copy,
+// ESTEP_STAGES items ahead of the compute, so that no warp waits on a global
+// load, and the compensated sums in shared memory.  One thread issues the
+// copies; each completes on its stage's mbarrier; a stage is refilled after
+// the CTA's barrier at the end of the item that used it (with an async-proxy
+// fence).  All waits are bounded: on a timeout the CTA records ST_TIMEOUT,
+// waits (bounded) for its copies in flight and stops.
+template <bool COMP>
+__global__ void __launch_bounds__(EST_THREADS, 3)
 k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
         const int* __restrict__ meta, const NodeEst* __restrict__ est_lvl,
         float2* __restrict__ partials, int* __restrict__ status) {
     __shared__ float2 red[EST_THREADS / 32][NPART];
     __shared__ __align__(16) float4 stage[ESTEP_STAGES][TILE];
     __shared__ __align__(8) uint64_t full[ESTEP_STAGES];
+    extern __shared__ float2 estep_dyn[];
+    float2* acc_s = estep_dyn;
+    float2* acc_c = estep_dyn + 10 * EST_THREADS;
     const int n_items = meta[0];
     const int C = meta[1];
     const int ib = blockIdx.x * C, ie = min(ib + C, n_items);
     if (ib >= ie) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = lane >> 2, k = lane & 3;
+    for (int v = 0; v < 10; ++v) {
+        acc_s[v * EST_THREADS + threadIdx.x] = make_float2(0.f, 0.f);
+        acc_c[v * EST_THREADS + threadIdx.x] = make_float2(0.f, 0.f);
+    }
     if (threadIdx.x == 0) {
         for (int st = 0; st < ESTEP_STAGES; ++st) tc::mbar_init(&full[st], 1);
         tc::fence_mbar_init();
@@ -110,25 +168,24 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
         }
     }
     __syncthreads();
-    float in[20], s[20], c[20];
+    float2 in[10];
 #pragma unroll
-    for (int v = 0; v < 20; ++v) { in[v] = 0.f; s[v] = 0.f; c[v] = 0.f; }
+    for (int v = 0; v < 10; ++v) in[v] = make_float2(0.f, 0.f);
     int nfold = 0;
     int cur = -1, run = -1;
-    ChildRegs r0, r1;
+    ChildPair cp;
     int it = ib;
     for (; it < ie; ++it) {
         const Item w = items[it];
         if (w.parent != cur) {
             if (cur >= 0) {
-                fold20<COMP>(in, s, c);
+                fold_pair_smem<COMP>(in, acc_s, acc_c);
                 nfold = 0;
-                flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+                flush_pair_smem<COMP>(acc_s, acc_c, red, partials + int64_t(run) * NPART);
             }
             cur = w.parent;
             run = it;
-            load_child(est_lvl + 8 * cur + 2 * k, r0);
-            load_child(est_lvl + 8 * cur + 2 * k + 1, r1);
+            load_child_pair(est_lvl + 8 * cur + 2 * k, cp);
         }
         const int st = (it - ib) % ESTEP_STAGES;
         const uint32_t parity = uint32_t((it - ib) / ESTEP_STAGES) & 1u;
@@ -142,23 +199,9 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
             const int idx = base + warp * 8 + q;
             const bool valid = idx < w.count;
             const float4 z = zs[min(idx, w.count - 1)];
-            float e0x, e0y, e0z, e1x, e1y, e1z;
-            const float s0 = child_score(r0, z.x, z.y, z.z, e0x, e0y, e0z);
-            const float s1 = child_score(r1, z.x, z.y, z.z, e1x, e1y, e1z);
-            float m = fmaxf(s0, s1);
-            m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
-            m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
-            const bool any_live = m > -CUDART_INF_F;  // false for a leaf parent
-            const float p0 = any_live ? exp2f(s0 - m) : 0.f;
-            const float p1 = any_live ? exp2f(s1 - m) : 0.f;
-            float tot = p0 + p1;
-            tot += __shfl_xor_sync(FULL, tot, 1);
-            tot += __shfl_xor_sync(FULL, tot, 2);
-            const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
-            accum10(in, p0 * rinv, e0x, e0y, e0z);
-            accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
+            estep_point_pair(cp, z, valid, in);
             if (++nfold == 16) {
-                fold20<COMP>(in, s, c);
+                fold_pair_smem<COMP>(in, acc_s, acc_c);
                 nfold = 0;
             }
         }
@@ -179,8 +222,8 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
                                       tc::MBAR_SPIN_LIMIT);
         return;
     }
-    fold20<COMP>(in, s, c);
-    flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+    fold_pair_smem<COMP>(in, acc_s, acc_c);
+    flush_pair_smem<COMP>(acc_s, acc_c, red, partials + int64_t(run) * NPART);
 }
 
 template <bool COMP>
@@ -246,29 +289,31 @@ __global__ void __launch_bounds__(EST_THREADS, 2) k_em_local(int level, int n, i
 // launch and monotonic; every wait is bounded (ST_TIMEOUT, then return).
 template <bool COMP>
 __global__ void __launch_bounds__(EST_THREADS, 2)
-k_em_coop(int level, int n, int n_par, int K, const float4* __restrict__ pts, const Item* __restrict__ items,
-          const int* __restrict__ meta, const int* __restrict__ item_range, float2* __restrict__ partials,
-          const int* __restrict__ seg_count, const RootDev* __restrict__ root, float n_min,
-          NodeStat* __restrict__ stat, NodeEst* __restrict__ est, unsigned* __restrict__ cnt,
+k_em_coop(int level, int n, int n_par, int K, int n_chunks, const float4* __restrict__ pts,
+          const Item* __restrict__ items, const int* __restrict__ meta, const int* __restrict__ item_range,
+          float2* __restrict__ partials, const int* __restrict__ seg_count, const RootDev* __restrict__ root,
+          float n_min, NodeStat* __restrict__ stat, NodeEst* __restrict__ est, unsigned* __restrict__ cnt,
           int* __restrict__ status) {
     __shared__ union {
         float2 red[EST_THREADS / 32][NPART];
         MstepSmem msm;
     } sm;
     const int n_items = meta[0], C = meta[1];
-    const int ib = blockIdx.x * C, ie = min(ib + C, n_items);
     const NodeEst* est_lvl = est + level_offset(level);
     unsigned* done = cnt + n_par;
-    // the parents this CTA's chunk touches (items are ordered by parent)
-    const int p_first = ib < ie ? items[ib].parent : 0;
-    const int p_last = ib < ie ? items[ie - 1].parent : -1;
     for (int k = 0; k < K; ++k) {
         if (k > 0 && !wait_at_least(done, unsigned(k) * unsigned(n_par), status, BARRIER_SPIN_LIMIT, 128)) return;
-        estep_range<COMP, ItemList, true>(pts, ItemList{items}, ib, ie, est_lvl, partials, sm.red);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();  // the partials before the arrivals
-            for (int p = p_first; p <= p_last; ++p) atomicAdd(cnt + p, 1u);
+        // the item chunks of the level-wide E-step (n_chunks of C items),
+        // each an E-step over its items and one arrival per parent it touches
+        for (int b = blockIdx.x; b < n_chunks; b += gridDim.x) {
+            const int ib = b * C, ie = min(ib + C, n_items);
+            if (ib >= ie) continue;
+            estep_range<COMP, ItemList, true>(pts, ItemList{items}, ib, ie, est_lvl, partials, sm.red);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();  // the partials before the arrivals
+                for (int p = items[ib].parent; p <= items[ie - 1].parent; ++p) atomicAdd(cnt + p, 1u);
+            }
         }
         for (int p = blockIdx.x; p < n_par; p += gridDim.x) {
             const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
@@ -380,14 +425,25 @@ constexpr int64_t LOCAL_EM_POINTS = 2048;
 
 // Whether est_grid CTAs of the cooperative EM kernel fit on the device at
 // once (a cooperative launch needs them co-resident).
-bool hgmm_em_coop_fits(int n_sm, int est_grid) {
+// k_estep's dynamic shared memory plus its static part exceeds the 48 KB
+// default: opt in (per device, before the first launch).
+bool hgmm_estep_smem_attr() {
+    return cudaFuncSetAttribute(k_estep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ESTEP_DYN_SMEM)) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_estep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ESTEP_DYN_SMEM)) ==
+               cudaSuccess;
+}
+
+// CTAs of the cooperative EM kernel that fit on the device at once (a
+// cooperative launch needs them co-resident), at most est_grid; 0 if none.
+int hgmm_em_coop_grid(int n_sm, int est_grid) {
     int a = 0, b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_em_coop<true>, EST_THREADS, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_em_coop<false>, EST_THREADS, 0) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return std::min(a, b) * n_sm >= est_grid;
+    return std::min(std::min(a, b) * n_sm, est_grid);
 }
 
 int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
@@ -435,16 +491,16 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
                                                                t->partials, t->seg_count, t->root, p.n_min,
                                                                t->stat, t->est, t->status);
         }
-        const bool coop_em = !local_em && em_iters > 0 && t->em_coop && (p.flags & HGMM_FLAG_EM_COOPERATIVE);
+        const bool coop_em = !local_em && em_iters > 0 && t->em_coop_grid > 0 && (p.flags & HGMM_FLAG_EM_COOPERATIVE);
         if (coop_em) {
             ProfScope ps_(t, K_ESTEP, s);
             cudaMemsetAsync(t->em_cnt, 0, size_t(n_par + 1) * sizeof(unsigned), s);
-            int lv = l, nn = n, np = n_par, K = em_iters;
+            int lv = l, nn = n, np = n_par, K = em_iters, chunks = G;
             float nmin = p.n_min;
-            void* args[] = {&lv, &nn, &np, &K, &cur, &t->items, &t->meta, &t->item_range, &t->partials,
+            void* args[] = {&lv, &nn, &np, &K, &chunks, &cur, &t->items, &t->meta, &t->item_range, &t->partials,
                             &t->seg_count, &t->root, &nmin, &t->stat, &t->est, &t->em_cnt, &t->status};
             const void* fn = comp ? (const void*)k_em_coop<true> : (const void*)k_em_coop<false>;
-            if (cudaLaunchCooperativeKernel(fn, dim3(G), dim3(EST_THREADS), args, 0, s) != cudaSuccess) {
+            if (cudaLaunchCooperativeKernel(fn, dim3(t->em_coop_grid), dim3(EST_THREADS), args, 0, s) != cudaSuccess) {
                 fprintf(stderr, "hgmm: cooperative EM launch failed\n");
                 return HGMM_ECUDA;
             }
@@ -453,9 +509,9 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
             {
                 ProfScope ps_(t, K_ESTEP, s);
                 if (comp)
-                    k_estep<true><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials, t->status);
+                    k_estep<true><<<G, EST_THREADS, ESTEP_DYN_SMEM, s>>>(cur, t->items, t->meta, est_lvl, t->partials, t->status);
                 else
-                    k_estep<false><<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->partials, t->status);
+                    k_estep<false><<<G, EST_THREADS, ESTEP_DYN_SMEM, s>>>(cur, t->items, t->meta, est_lvl, t->partials, t->status);
             }
             {
                 ProfScope ps_(t, K_MSTEP, s);
@@ -644,12 +700,12 @@ extern "C" int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const h
                                                             items);
     for (int k = 0; k < prm.em_iters; ++k) {
         if (prm.precision == 0) {
-            k_estep<true><<<G, EST_THREADS, 0, s>>>(reinterpret_cast<const float4*>(d_points), items,
+            k_estep<true><<<G, EST_THREADS, ESTEP_DYN_SMEM, s>>>(reinterpret_cast<const float4*>(d_points), items,
                                                     meta, est, partials, status);
             k_mstep<true><<<1, 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
                                             prm.n_min, stat, est, status);
         } else {
-            k_estep<false><<<G, EST_THREADS, 0, s>>>(reinterpret_cast<const float4*>(d_points), items,
+            k_estep<false><<<G, EST_THREADS, ESTEP_DYN_SMEM, s>>>(reinterpret_cast<const float4*>(d_points), items,
                                                      meta, est, partials, status);
             k_mstep<false><<<1, 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
                                              prm.n_min, stat, est, status);

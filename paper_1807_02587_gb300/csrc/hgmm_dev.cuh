@@ -365,6 +365,105 @@ __device__ __forceinline__ float child_score(const ChildRegs& r, float zx, float
     return s;
 }
 
+// ---- packed pair of children (Blackwell FP32x2 arithmetic) -----------------
+// Children 2k and 2k + 1 of a parent in the .x and .y halves: every packed
+// instruction performs the two lanes' IEEE round-to-nearest operations, so
+// the results are those of the scalar code (child_score, accum10, two_sum)
+// bit for bit, in half the instructions.  The means and log-normalisers are
+// stored negated so that subtractions become packed additions.
+struct ChildPair {
+    float2 nmx, nmy, nmz, nC, w00, w10, w11, w20, w21, w22;
+};
+
+template <bool CG = false>
+__device__ __forceinline__ void load_child_pair(const NodeEst* __restrict__ e, ChildPair& p) {
+    ChildRegs a, b;
+    load_child<CG>(e, a);
+    load_child<CG>(e + 1, b);
+    p.nmx = make_float2(-a.mx, -b.mx);
+    p.nmy = make_float2(-a.my, -b.my);
+    p.nmz = make_float2(-a.mz, -b.mz);
+    p.nC = make_float2(-a.C, -b.C);
+    p.w00 = make_float2(a.w00, b.w00);
+    p.w10 = make_float2(a.w10, b.w10);
+    p.w11 = make_float2(a.w11, b.w11);
+    p.w20 = make_float2(a.w20, b.w20);
+    p.w21 = make_float2(a.w21, b.w21);
+    p.w22 = make_float2(a.w22, b.w22);
+}
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+// x - y, rounded once (as __fsub_rn)
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, f2(-1.f), x); }
+
+// u = -log2(pi N(z | child)) of both children (exactly the negated
+// child_score) and the offsets e = z - mu.
+__device__ __forceinline__ float2 neg_score_pair(const ChildPair& p, float zx, float zy, float zz, float2& ex,
+                                                 float2& ey, float2& ez) {
+    ex = __fadd2_rn(f2(zx), p.nmx);
+    ey = __fadd2_rn(f2(zy), p.nmy);
+    ez = __fadd2_rn(f2(zz), p.nmz);
+    const float2 d0 = __fmul2_rn(p.w00, ex);
+    const float2 d1 = __ffma2_rn(p.w11, ey, __fmul2_rn(p.w10, ex));
+    const float2 d2 = __ffma2_rn(p.w22, ez, __ffma2_rn(p.w21, ey, __fmul2_rn(p.w20, ex)));
+    float2 u = __ffma2_rn(d0, d0, p.nC);
+    u = __ffma2_rn(d1, d1, u);
+    return __ffma2_rn(d2, d2, u);
+}
+
+// accum10 of both children: a[v].x / .y = moment v of child 2k / 2k + 1.
+__device__ __forceinline__ void accum_pair(float2 (&a)[10], float2 g, float2 ex, float2 ey, float2 ez) {
+    const float2 gx = __fmul2_rn(g, ex), gy = __fmul2_rn(g, ey), gz = __fmul2_rn(g, ez);
+    a[0] = __fadd2_rn(a[0], g);
+    a[1] = __fadd2_rn(a[1], gx);
+    a[2] = __fadd2_rn(a[2], gy);
+    a[3] = __fadd2_rn(a[3], gz);
+    a[4] = __ffma2_rn(gx, ex, a[4]);
+    a[5] = __ffma2_rn(gx, ey, a[5]);
+    a[6] = __ffma2_rn(gx, ez, a[6]);
+    a[7] = __ffma2_rn(gy, ey, a[7]);
+    a[8] = __ffma2_rn(gy, ez, a[8]);
+    a[9] = __ffma2_rn(gz, ez, a[9]);
+}
+
+// fold20 on packed accumulators (two_sum per half).
+template <bool COMP>
+__device__ __forceinline__ void fold_pair(float2 (&in)[10], float2 (&s)[10], float2 (&c)[10]) {
+#pragma unroll
+    for (int v = 0; v < 10; ++v) {
+        if (COMP) {
+            const float2 t = __fadd2_rn(s[v], in[v]);
+            const float2 bp = sub2(t, s[v]);
+            const float2 e = __fadd2_rn(sub2(s[v], sub2(t, bp)), sub2(in[v], bp));
+            s[v] = t;
+            c[v] = __fadd2_rn(c[v], e);
+        } else {
+            s[v] = __fadd2_rn(s[v], in[v]);
+        }
+        in[v] = make_float2(0.f, 0.f);
+    }
+}
+
+// One E-step point of a quad lane: Eq. 3 posteriors of the point over the
+// parent's 8 children (this lane holds two, its quad the rest: max and sum
+// by shuffles) and the lane's two children's moments.
+__device__ __forceinline__ void estep_point_pair(const ChildPair& cp, const float4 z, bool valid, float2 (&in)[10]) {
+    float2 ex, ey, ez;
+    const float2 u = neg_score_pair(cp, z.x, z.y, z.z, ex, ey, ez);
+    float umin = fminf(u.x, u.y);
+    umin = fminf(umin, __shfl_xor_sync(FULL, umin, 1));
+    umin = fminf(umin, __shfl_xor_sync(FULL, umin, 2));
+    const bool any_live = umin < CUDART_INF_F;  // false for a leaf parent
+    const float2 arg = sub2(f2(umin), u);      // = score - max score
+    const float p0 = any_live ? exp2f(arg.x) : 0.f;
+    const float p1 = any_live ? exp2f(arg.y) : 0.f;
+    float tot = p0 + p1;
+    tot += __shfl_xor_sync(FULL, tot, 1);
+    tot += __shfl_xor_sync(FULL, tot, 2);
+    const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
+    accum_pair(in, __fmul2_rn(make_float2(p0, p1), f2(rinv)), ex, ey, ez);
+}
+
 __device__ __forceinline__ void accum10(float* a, float g, float ex, float ey, float ez) {
     const float gx = g * ex, gy = g * ey, gz = g * ez;
     a[0] += g;
@@ -430,6 +529,24 @@ __device__ __forceinline__ void flush_run(float* s, float* c, float2 (*red)[NPAR
 }
 
 
+// flush_run of packed accumulators (child 2k's ten values, then child
+// 2k + 1's, as flush_run expects), which are cleared.
+template <bool COMP>
+__device__ __forceinline__ void flush_pair(float2 (&s2)[10], float2 (&c2)[10], float2 (*red)[NPART],
+                                           float2* __restrict__ out) {
+    float s[20], c[20];
+#pragma unroll
+    for (int v = 0; v < 10; ++v) {
+        s[v] = s2[v].x;
+        s[10 + v] = s2[v].y;
+        c[v] = c2[v].x;
+        c[10 + v] = c2[v].y;
+        s2[v] = make_float2(0.f, 0.f);
+        c2[v] = make_float2(0.f, 0.f);
+    }
+    flush_run<COMP>(s, c, red, out);
+}
+
 // E-step of items [ib, ie) by one CTA: Eq. 3 posteriors of every point over
 // the 8 children of its parent (log2 domain, max subtracted), gamma-weighted
 // moments of each child centred on the child's current FP32 mean, one
@@ -443,24 +560,23 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
     if (ib >= ie) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = lane >> 2, k = lane & 3;
-    float in[20], s[20], c[20];
+    float2 in[10], s[10], c[10];
 #pragma unroll
-    for (int v = 0; v < 20; ++v) { in[v] = 0.f; s[v] = 0.f; c[v] = 0.f; }
+    for (int v = 0; v < 10; ++v) { in[v] = make_float2(0.f, 0.f); s[v] = in[v]; c[v] = in[v]; }
     int nfold = 0;
     int cur = -1, run = -1;
-    ChildRegs r0, r1;
+    ChildPair cp;
     for (int it = ib; it < ie; ++it) {
         const Item w = items(it);
         if (w.parent != cur) {
             if (cur >= 0) {
-                fold20<COMP>(in, s, c);
+                fold_pair<COMP>(in, s, c);
                 nfold = 0;
-                flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+                flush_pair<COMP>(s, c, red, partials + int64_t(run) * NPART);
             }
             cur = w.parent;
             run = it;
-            load_child<CG>(est_lvl + 8 * cur + 2 * k, r0);
-            load_child<CG>(est_lvl + 8 * cur + 2 * k + 1, r1);
+            load_child_pair<CG>(est_lvl + 8 * cur + 2 * k, cp);
         }
         float4 znext = pts[w.start + min(warp * 8 + q, w.count - 1)];
         for (int base = 0; base < w.count; base += 64) {
@@ -468,29 +584,15 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
             const bool valid = idx < w.count;
             const float4 z = znext;
             if (base + 64 < w.count) znext = pts[w.start + min(idx + 64, w.count - 1)];
-            float e0x, e0y, e0z, e1x, e1y, e1z;
-            const float s0 = child_score(r0, z.x, z.y, z.z, e0x, e0y, e0z);
-            const float s1 = child_score(r1, z.x, z.y, z.z, e1x, e1y, e1z);
-            float m = fmaxf(s0, s1);
-            m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
-            m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
-            const bool any_live = m > -CUDART_INF_F;  // false for a leaf parent
-            const float p0 = any_live ? exp2f(s0 - m) : 0.f;
-            const float p1 = any_live ? exp2f(s1 - m) : 0.f;
-            float tot = p0 + p1;
-            tot += __shfl_xor_sync(FULL, tot, 1);
-            tot += __shfl_xor_sync(FULL, tot, 2);
-            const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
-            accum10(in, p0 * rinv, e0x, e0y, e0z);
-            accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
+            estep_point_pair(cp, z, valid, in);
             if (++nfold == 16) {
-                fold20<COMP>(in, s, c);
+                fold_pair<COMP>(in, s, c);
                 nfold = 0;
             }
         }
     }
-    fold20<COMP>(in, s, c);
-    flush_run<COMP>(s, c, red, partials + int64_t(run) * NPART);
+    fold_pair<COMP>(in, s, c);
+    flush_pair<COMP>(s, c, red, partials + int64_t(run) * NPART);
 }
 
 // The E-step of whole items by single warps (items first, first + stride,

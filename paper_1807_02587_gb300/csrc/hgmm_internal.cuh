@@ -106,7 +106,7 @@ struct hgmm_tree {
     int64_t max_items = 0;
     int64_t max_nodes = 0;
     int est_grid = 0;   // CTAs of the persistent build E-step
-    bool em_coop = false;  // the cooperative per-level EM kernel fits est_grid CTAs
+    int em_coop_grid = 0;  // co-resident CTAs of the cooperative per-level EM kernel (0: unavailable)
     int reg_grid = 0;   // CTAs of the descent
     // last build
     int64_t n = 0;
@@ -184,6 +184,7 @@ int hgmm_register_descent_impl(hgmm_tree* t, const float4* src, int64_t n, const
                                double* T_hist);
 int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s);
 int hgmm_register_grid(int n_sm);
-bool hgmm_em_coop_fits(int n_sm, int est_grid);
+int hgmm_em_coop_grid(int n_sm, int est_grid);
+bool hgmm_estep_smem_attr();
 int hgmm_barrier_timeout_probe_impl(hgmm_tree* t, long long limit, cudaStream_t s);
 int hgmm_trace_read_impl(hgmm_tree* t, unsigned long long* h, int64_t cap);
