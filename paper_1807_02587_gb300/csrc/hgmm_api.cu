@@ -45,7 +45,7 @@ void free_tree(hgmm_tree* t) {
     clear_prof(t);
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
                     t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
-                    t->item_off, t->root, t->root_part, t->root_counter, t->em_cnt, t->status, t->reg_acc, t->reg_acc2, t->reg_part,
+                    t->item_off, t->root, t->root_part, t->root_counter, t->em_cnt, t->mslices, t->mcnt, t->status, t->reg_acc, t->reg_acc2, t->reg_part,
                     t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->reg_obj, t->rnode, t->trace, t->stage_tgt,
                     t->stage_src, t->stage_T};
     for (void* p : ptrs)
@@ -151,6 +151,8 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->root_part, int64_t(t->est_grid) * 32);
     good &= dalloc(&t->root_counter, 1);
     good &= dalloc(&t->em_cnt, level_size(std::max(0, max_depth - 1)) + 1);
+    good &= dalloc(&t->mslices, int64_t(MSTEP_SLICED_PARENTS) * MSTEP_SLICES * NPART);
+    good &= dalloc(&t->mcnt, MSTEP_SLICED_PARENTS);
     good &= dalloc(&t->status, 1);
     good &= dalloc(&t->reg_acc, 4 * ACC_REPLICAS * t->max_nodes);
     good &= dalloc(&t->reg_acc2, 6 * t->max_nodes);
@@ -172,6 +174,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= ok(cudaMemset(t->status, 0, sizeof(int)), "cudaMemset");
     good &= ok(cudaMemset(t->reg_bar, 0, 8 * sizeof(unsigned)), "cudaMemset");
     good &= ok(cudaMemset(t->root_counter, 0, sizeof(unsigned)), "cudaMemset");
+    good &= ok(cudaMemset(t->mcnt, 0, MSTEP_SLICED_PARENTS * sizeof(unsigned)), "cudaMemset");
     good &= ok(cudaMemset(t->reg_acc, 0, 4 * ACC_REPLICAS * t->max_nodes * sizeof(unsigned long long)),
                "cudaMemset");
     good &= ok(cudaMemset(t->stat, 0, t->max_nodes * sizeof(NodeStat)), "cudaMemset");

@@ -226,6 +226,10 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
     flush_pair_smem<COMP>(acc_s, acc_c, red, partials + int64_t(run) * NPART);
 }
 
+// The level-wide M-step: CTA (p, j) reduces slice j of parent p's runs into
+// the slice buffer; the last of the parent's n_slices CTAs to finish
+// (arrival counter, reset by that CTA) combines the slices in order and runs
+// the FP64 M-step of the 8 children.
 template <bool COMP>
 __global__ void __launch_bounds__(256) k_mstep(int level, int n, const int* __restrict__ item_range,
                                                const int* __restrict__ meta,
@@ -233,13 +237,34 @@ __global__ void __launch_bounds__(256) k_mstep(int level, int n, const int* __re
                                                const int* __restrict__ seg_count,
                                                const RootDev* __restrict__ root, float n_min,
                                                NodeStat* __restrict__ stat,
-                                               NodeEst* __restrict__ est, int* __restrict__ status) {
+                                               NodeEst* __restrict__ est, int* __restrict__ status,
+                                               float2* __restrict__ slices, unsigned* __restrict__ mcnt) {
     __shared__ MstepSmem msm;
-    const int p = blockIdx.x;
+    __shared__ float2 own[NPART];
+    __shared__ bool last;
+    const int p = blockIdx.x, j = blockIdx.y, ns = gridDim.y;
     const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
     if (i0 >= i1) return;  // parent without points: children stay dead
-    mstep_parent<COMP>(level, n, p, i0, i1, meta[1], partials, seg_count, root, n_min, stat, est,
-                       status, msm);
+    if (ns == 1) {
+        reduce_run_slice<COMP>(i0, i1, meta[1], 0, 1, partials, msm, own);
+        mstep_from_slices<COMP, false>(level, n, p, own, 1, seg_count, root, n_min, stat, est, status, msm);
+        return;
+    }
+    float2* mine = slices + (int64_t(p) * ns + j) * NPART;
+    reduce_run_slice<COMP>(i0, i1, meta[1], j, ns, partials, msm, mine);
+    if (threadIdx.x < NPART) __threadfence();  // each writer's slice values before the arrival
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last = atomicAdd(mcnt + p, 1u) == unsigned(ns - 1);
+        if (last) {
+            mcnt[p] = 0u;  // every slice has arrived: ready for the next launch
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    mstep_from_slices<COMP, true>(level, n, p, slices + int64_t(p) * ns * NPART, ns, seg_count, root, n_min, stat,
+                                  est, status, msm);
 }
 
 // All K EM iterations of one parent by one CTA (blockIdx.x = parent): the
@@ -296,7 +321,10 @@ k_em_coop(int level, int n, int n_par, int K, int n_chunks, const float4* __rest
           int* __restrict__ status) {
     __shared__ union {
         float2 red[EST_THREADS / 32][NPART];
-        MstepSmem msm;
+        struct {
+            MstepSmem msm;
+            float2 slice[MSTEP_SLICES][NPART];
+        };
     } sm;
     const int n_items = meta[0], C = meta[1];
     const NodeEst* est_lvl = est + level_offset(level);
@@ -320,8 +348,12 @@ k_em_coop(int level, int n, int n_par, int K, int n_chunks, const float4* __rest
             if (i0 < i1) {  // a parent without points has no runs; its children stay dead
                 const unsigned runs = unsigned((i1 - 1) / C - i0 / C + 1);
                 if (!wait_at_least(cnt + p, unsigned(k + 1) * runs, status, BARRIER_SPIN_LIMIT)) return;
-                mstep_parent<COMP>(level, n, p, i0, i1, C, partials, seg_count, root, n_min, stat, est, status,
-                                   sm.msm);
+                // the level-wide M-step's slices, reduced one after another
+                const int ns = mstep_slices(n_par);
+                for (int j = 0; j < ns; ++j)
+                    reduce_run_slice<COMP>(i0, i1, C, j, ns, partials, sm.msm, sm.slice[j]);
+                mstep_from_slices<COMP, false>(level, n, p, &sm.slice[0][0], ns, seg_count, root, n_min, stat, est,
+                                               status, sm.msm);
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -516,13 +548,13 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
             {
                 ProfScope ps_(t, K_MSTEP, s);
                 if (comp)
-                    k_mstep<true><<<n_par, 256, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
-                                                        t->seg_count, t->root, p.n_min, t->stat,
-                                                        t->est, t->status);
+                    k_mstep<true><<<dim3(n_par, mstep_slices(n_par)), 256, 0, s>>>(
+                        l, n, t->item_range, t->meta, t->partials, t->seg_count, t->root, p.n_min, t->stat,
+                        t->est, t->status, t->mslices, t->mcnt);
                 else
-                    k_mstep<false><<<n_par, 256, 0, s>>>(l, n, t->item_range, t->meta, t->partials,
-                                                         t->seg_count, t->root, p.n_min, t->stat,
-                                                         t->est, t->status);
+                    k_mstep<false><<<dim3(n_par, mstep_slices(n_par)), 256, 0, s>>>(
+                        l, n, t->item_range, t->meta, t->partials, t->seg_count, t->root, p.n_min, t->stat,
+                        t->est, t->status, t->mslices, t->mcnt);
             }
         }
         HGMM_LAUNCH_CHECK();
@@ -667,6 +699,7 @@ extern "C" int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const h
             int n_sm = 0;
             if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 return HGMM_ECUDA;
+            if (!hgmm_estep_smem_attr()) return HGMM_ECUDA;
             devs[dev].grid = std::min(2 * n_sm, NA_MAX_GRID);
             devs[dev].base = static_cast<unsigned char*>(ptr);
         }
@@ -702,13 +735,13 @@ extern "C" int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const h
         if (prm.precision == 0) {
             k_estep<true><<<G, EST_THREADS, ESTEP_DYN_SMEM, s>>>(reinterpret_cast<const float4*>(d_points), items,
                                                     meta, est, partials, status);
-            k_mstep<true><<<1, 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
-                                            prm.n_min, stat, est, status);
+            k_mstep<true><<<dim3(1, 1), 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
+                                            prm.n_min, stat, est, status, nullptr, nullptr);
         } else {
             k_estep<false><<<G, EST_THREADS, ESTEP_DYN_SMEM, s>>>(reinterpret_cast<const float4*>(d_points), items,
                                                      meta, est, partials, status);
-            k_mstep<false><<<1, 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
-                                             prm.n_min, stat, est, status);
+            k_mstep<false><<<dim3(1, 1), 256, 0, s>>>(0, ni, item_range, meta, partials, seg, root,
+                                             prm.n_min, stat, est, status, nullptr, nullptr);
         }
     }
     k_finalize<<<1, 32, 0, s>>>(0, prm.lam_c, root, stat, est, rnode);

@@ -769,6 +769,82 @@ __device__ void mstep_parent(int level, int n, int p, int i0, int i1, int C,
     __syncthreads();
 }
 
+// The runs of a parent split into MSTEP_SLICES slices (slice j: runs
+// [j * nruns / S, (j + 1) * nruns / S)), each reduced by one CTA in the order
+// of mstep_parent's first phase; the slice sums are then combined in slice
+// order.  The level-wide M-step reduces the slices of a parent in parallel
+// CTAs; the cooperative EM's owner reduces them one after another: the same
+// arithmetic either way.
+template <bool COMP>
+__device__ void reduce_run_slice(int i0, int i1, int C, int j, int n_slices, const float2* __restrict__ partials,
+                                 MstepSmem& sm, float2* out) {
+    const int nruns = (i1 - 1) / C - i0 / C + 1;
+    const int ra = int((int64_t(j) * nruns) / n_slices), rb = int((int64_t(j + 1) * nruns) / n_slices);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    float S[3] = {0.f, 0.f, 0.f}, Cc[3] = {0.f, 0.f, 0.f};
+    for (int r0 = ra + warp; r0 < rb; r0 += 4 * nw) {
+        float2 x[4][3];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u * nw;
+            const int slot = r == 0 ? i0 : (i0 / C + r) * C;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int v = lane + 32 * q;
+                x[u][q] = (r < rb && v < NPART) ? __ldcg(&partials[int64_t(slot) * NPART + v])
+                                                 : make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (COMP) pair_add(S[q], Cc[q], x[u][q].x, x[u][q].y);
+                else S[q] += x[u][q].x;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int v = lane + 32 * q;
+        if (v < NPART) sm.grp[warp][v] = make_float2(S[q], Cc[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        float Sx = 0.f, Cx = 0.f;
+        for (int w = 0; w < nw; ++w) {
+            if (COMP) pair_add(Sx, Cx, sm.grp[w][threadIdx.x].x, sm.grp[w][threadIdx.x].y);
+            else Sx += sm.grp[w][threadIdx.x].x;
+        }
+        out[threadIdx.x] = make_float2(Sx, Cx);
+    }
+    __syncthreads();
+}
+
+// Combine the n_slices slice sums (NPART each; GLOBAL: written by other
+// CTAs, read through L2; else shared memory) in slice order and run the
+// M-step of the parent's 8 children.
+template <bool COMP, bool GLOBAL>
+__device__ void mstep_from_slices(int level, int n, int p, const float2* slices, int n_slices,
+                                  const int* __restrict__ seg_count, const RootDev* __restrict__ root,
+                                  float n_min, NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
+                                  int* __restrict__ status, MstepSmem& sm) {
+    if (threadIdx.x < NPART) {
+        float S = 0.f, Cc = 0.f;
+        for (int j = 0; j < n_slices; ++j) {
+            const float2 x = GLOBAL ? __ldcg(&slices[j * NPART + threadIdx.x]) : slices[j * NPART + threadIdx.x];
+            if (COMP) pair_add(S, Cc, x.x, x.y);
+            else S += x.x;
+        }
+        sm.mom[threadIdx.x] = double(S) + double(Cc);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8)
+        child_mstep(level, n, p, threadIdx.x, sm.mom + threadIdx.x * NMOM, seg_count, root, n_min, stat,
+                    est, status);
+    __syncthreads();
+}
+
 // The same M-step for a parent with few runs, by one warp (no block
 // barriers): lane l sums values l, l+32, l+64 over the runs in order; lanes
 // 0..7 then build the children.  mom = 80 doubles of shared memory per warp.

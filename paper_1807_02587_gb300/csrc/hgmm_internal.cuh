@@ -40,6 +40,10 @@ constexpr int MSTEP_THREADS = 128;    // registration M-step CTA
 constexpr int NTERM = 28;             // per-round sums: 21 of H, 6 of g, the objective
 constexpr int TRACE_MAX_ITERS = 64;   // rounds the registration trace can hold
 constexpr int ACC_REPLICAS = 1;       // copies of each node's registration moments
+constexpr int MSTEP_SLICES = 8;        // run slices per parent in the level-wide M-step
+constexpr int MSTEP_SLICED_PARENTS = 64;  // levels with at most this many parents are sliced
+
+__host__ __device__ inline int mstep_slices(int n_par) { return n_par <= MSTEP_SLICED_PARENTS ? MSTEP_SLICES : 1; }
 
 // status bits (device word, OR-ed)
 constexpr int ST_NONFINITE = 1;
@@ -132,6 +136,8 @@ struct hgmm_tree {
     float* root_part = nullptr;  // est_grid x 32
     unsigned* root_counter = nullptr;
     unsigned* em_cnt = nullptr;  // cooperative EM: per-parent arrivals + done counter
+    float2* mslices = nullptr;   // M-step slice sums (sliced levels: parents x slices x NPART)
+    unsigned* mcnt = nullptr;    // M-step slice arrivals per parent (zero between launches)
     int* status = nullptr;
     // registration
     unsigned long long* reg_acc = nullptr;  // nodes x ACC_REPLICAS x 4 fixed point
