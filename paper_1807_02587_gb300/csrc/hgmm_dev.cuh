@@ -663,49 +663,120 @@ __device__ __forceinline__ void estep_items_warp(const float4* __restrict__ pts,
 }
 
 // =================================================================== M-step
-// M-step of child c of parent p from its 10 reduced moments m (FP64): S0,
-// mean shift d = S1/S0 from the FP32 mean the E-step used, Sigma = S2/S0 -
-// d d^T + eps I, pi = S0 / n_p; a child below n_min expected points dies (a
-// parent whose children all die stays a leaf); FP64 Cholesky -> new FP32
-// E-step constants.
-__device__ __forceinline__ void child_mstep(int level, int n, int p, int c, const double* m,
-                                            const int* __restrict__ seg_count,
-                                            const RootDev* __restrict__ root, float n_min,
-                                            NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
-                                            int* __restrict__ status) {
+// The M-step of the 8 children of parent p by one warp, a quad of lanes per
+// child (lane 4c + r: child c, role r): the two reciprocals share one
+// instruction stream (role 1 takes the parent's count), the mean offset,
+// the six covariance entries and the FP32 constants are split over the
+// roles and gathered by shuffles, and only the 3x3 Cholesky (which needs
+// all six entries) runs on every lane of the quad.  One FP64 warp
+// instruction holds the SMSP's FP64 pipe ~64 cycles whatever the active
+// mask, so this issues about half the FP64 instructions of one lane per
+// child.  Same rules as before: S0 below n_min kills the child; Sigma =
+// S2/S0 - d d^T + eps I with d = S1/S0 (moments about the child's FP32
+// mean); pi = S0 / n_p.  mom: 80 doubles (child c's ten at c * NMOM), shared
+// or global.  All 32 lanes of the warp call it.
+__device__ __forceinline__ void child_mstep_quad(int level, int n, int p, const double* mom,
+                                                 const int* __restrict__ seg_count,
+                                                 const RootDev* __restrict__ root, float n_min,
+                                                 NodeStat* __restrict__ stat, NodeEst* __restrict__ est,
+                                                 int* __restrict__ status) {
+    const int lane = threadIdx.x & 31, c = lane >> 2, r = lane & 3, q0 = lane & ~3;
+    const unsigned qm = 0xFu << q0;
     const int64_t g = d_level_offset(level) + 8 * int64_t(p) + c;
     NodeStat& cs = stat[g];
     NodeEst& ce = est[g];
+    const double* m = mom + c * NMOM;
     const double S0 = m[0];
     const double n_p = level == 0 ? double(n) : double(seg_count[d_level_offset(level - 1) + p]);
     // a child below n_min expected points dies; if all eight die the parent
     // stays a leaf (its points keep zero posteriors from then on)
-    const bool live = cs.live && S0 >= double(n_min) && S0 > 0.0;
+    const bool live = cs.live && S0 >= double(n_min) && S0 > 0.0;  // the same on the quad
     if (!live) {
-        cs.live = 0;
-        cs.pi = 0.0;
-        ce.a.w = -CUDART_INF_F;
-        ce.b = make_float4(0.f, 0.f, 0.f, 0.f);
-        ce.c.x = 0.f;
-        ce.c.y = 0.f;
+        if (r == 0) {
+            cs.live = 0;
+            cs.pi = 0.0;
+            ce.a.w = -CUDART_INF_F;
+            ce.b = make_float4(0.f, 0.f, 0.f, 0.f);
+            ce.c.x = 0.f;
+            ce.c.y = 0.f;
+        }
         return;
     }
     const double eps = root->eps;
-    const double inv = rcp_f64(S0);
-    const double d[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
-    const double mu[3] = {double(ce.a.x) + d[0], double(ce.a.y) + d[1], double(ce.a.z) + d[2]};
+    const double rx = rcp_f64(r == 1 ? n_p : S0);
+    const double inv = __shfl_sync(qm, rx, q0);
+    const double rnp = __shfl_sync(qm, rx, q0 | 1);
+    // role a < 3: the mean offset d_a and the new mean mu_a
+    const float4 ca = ce.a;
+    const int a = r < 3 ? r : 2;
+    const double da = m[1 + a] * inv;
+    const double mua = double(a == 0 ? ca.x : (a == 1 ? ca.y : ca.z)) + da;
+    const double d0 = __shfl_sync(qm, da, q0), d1 = __shfl_sync(qm, da, q0 | 1), d2 = __shfl_sync(qm, da, q0 | 2);
+    // role r: covariance entries r and (r < 2) r + 4; packing xx xy xz yy yz zz
+    auto entry = [&](int v) {
+        const double di = v < 3 ? d0 : (v < 5 ? d1 : d2);
+        const double dj = v == 0 ? d0 : (v == 1 || v == 3 ? d1 : d2);
+        double e = fma(-di, dj, m[4 + v] * inv);
+        if (v == 0 || v == 3 || v == 5) e += eps;
+        return e;
+    };
+    const double e0 = entry(r), e1 = entry(r < 2 ? r + 4 : 5);
     double S[6];
-    S[0] = m[4] * inv - d[0] * d[0] + eps;
-    S[1] = m[5] * inv - d[0] * d[1];
-    S[2] = m[6] * inv - d[0] * d[2];
-    S[3] = m[7] * inv - d[1] * d[1] + eps;
-    S[4] = m[8] * inv - d[1] * d[2];
-    S[5] = m[9] * inv - d[2] * d[2] + eps;
-    const double pi = S0 * rcp_f64(n_p);
-    cs.pi = pi;
-    for (int a = 0; a < 3; ++a) cs.mu[a] = mu[a];
-    for (int v = 0; v < 6; ++v) cs.S[v] = S[v];
-    if (!pack_est(pi, mu, S, eps, 0.f, ce)) atomicOr(status, ST_CHOL);
+    S[0] = __shfl_sync(qm, e0, q0);
+    S[1] = __shfl_sync(qm, e0, q0 | 1);
+    S[2] = __shfl_sync(qm, e0, q0 | 2);
+    S[3] = __shfl_sync(qm, e0, q0 | 3);
+    S[4] = __shfl_sync(qm, e1, q0);
+    S[5] = __shfl_sync(qm, e1, q0 | 1);
+    const double pi = S0 * rnp;
+    if (r == 0) cs.pi = pi;
+    if (r < 3) cs.mu[r] = mua;
+    cs.S[r] = e0;
+    if (r < 2) cs.S[r + 4] = e1;
+    // Cholesky of Sigma (every lane of the quad), with the diagonal loading
+    // of pack_est when it is not positive definite
+    double L[6], R[3];
+    bool clean = true;
+    double boost = eps > 0.0 ? eps : 1e-30;
+    bool ok = chol3(S, L, R);
+    for (int tries = 0; tries < 8 && !ok; ++tries) {
+        clean = false;
+        S[0] += boost; S[3] += boost; S[5] += boost;
+        boost *= 10.0;
+        ok = chol3(S, L, R);
+    }
+    if (!ok) {  // hopeless (NaN input): make it an isotropic unit Gaussian
+        L[0] = 1; L[1] = 0; L[2] = 1; L[3] = 0; L[4] = 0; L[5] = 1;
+        R[0] = 1; R[1] = 1; R[2] = 1;
+        clean = false;
+    }
+    if (!clean && r == 0) atomicOr(status, ST_CHOL);
+    // W = sqrt(log2(e) / 2) L^-1: role r forms entries r and (r < 2) r + 4 of
+    // (m00, m10, m11, m20, m21, m22)
+    const double k = 0.8493218002880191;  // sqrt(log2(e) / 2)
+    const double m00 = R[0], m11 = R[1], m22 = R[2];
+    const double m10 = -L[1] * m00 * m11;
+    const double m21 = -L[4] * m11 * m22;
+    const double m20 = -(L[3] * m00 + L[4] * m10) * m22;
+    const double wa = r == 0 ? m00 : (r == 1 ? m10 : (r == 2 ? m11 : m20));
+    const double wb = r == 0 ? m21 : m22;
+    const float f0 = float(k * wa), f1 = float(k * wb);
+    const float w00 = __shfl_sync(qm, f0, q0), w10 = __shfl_sync(qm, f0, q0 | 1);
+    const float w11 = __shfl_sync(qm, f0, q0 | 2), w20 = __shfl_sync(qm, f0, q0 | 3);
+    const float w21 = __shfl_sync(qm, f1, q0), w22 = __shfl_sync(qm, f1, q0 | 1);
+    const float mf = float(mua);
+    const float mx = __shfl_sync(qm, mf, q0), my = __shfl_sync(qm, mf, q0 | 1), mz = __shfl_sync(qm, mf, q0 | 2);
+    if (r == 0) {
+        // log-normaliser in FP32: log2 det(L) from the FP64 product split
+        // into exponent and mantissa
+        int ex = 0;
+        const double mant = frexp(L[0] * L[2] * L[5], &ex);
+        const float C = log2f(float(pi)) - 3.9547135f /* 1.5 log2(2 pi) */ -
+                        (float(ex) + log2f(float(mant)));
+        ce.a = make_float4(mx, my, mz, C);
+        ce.b = make_float4(w00, w10, w11, w20);
+        ce.c = make_float4(w21, w22, 0.f, 0.f);
+    }
 }
 
 struct MstepSmem {
@@ -763,9 +834,7 @@ __device__ void mstep_parent(int level, int n, int p, int i0, int i1, int C,
         sm.mom[threadIdx.x] = double(S) + double(Cc);
     }
     __syncthreads();
-    if (threadIdx.x < 8)
-        child_mstep(level, n, p, threadIdx.x, sm.mom + threadIdx.x * NMOM, seg_count, root, n_min, stat,
-                    est, status);
+    if (threadIdx.x < 32) child_mstep_quad(level, n, p, sm.mom, seg_count, root, n_min, stat, est, status);
     __syncthreads();
 }
 
@@ -839,9 +908,7 @@ __device__ void mstep_from_slices(int level, int n, int p, const float2* slices,
         sm.mom[threadIdx.x] = double(S) + double(Cc);
     }
     __syncthreads();
-    if (threadIdx.x < 8)
-        child_mstep(level, n, p, threadIdx.x, sm.mom + threadIdx.x * NMOM, seg_count, root, n_min, stat,
-                    est, status);
+    if (threadIdx.x < 32) child_mstep_quad(level, n, p, sm.mom, seg_count, root, n_min, stat, est, status);
     __syncthreads();
 }
 
@@ -875,8 +942,7 @@ __device__ void mstep_parent_warp(int level, int n, int p, int i0, int i1, int C
         if (v < NPART) mom[v] = double(S[j]) + double(Cc[j]);
     }
     __syncwarp();
-    if (lane < 8)
-        child_mstep(level, n, p, lane, mom + lane * NMOM, seg_count, root, n_min, stat, est, status);
+    child_mstep_quad(level, n, p, mom, seg_count, root, n_min, stat, est, status);
     __syncwarp();
 }
 
