@@ -1608,6 +1608,11 @@ __device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt
         rj = 6;
     }
     double a = lane < 27 ? tot[lane] : 0.0;
+    // this lane's column of the current pose, loaded now so that the L2
+    // latency overlaps the elimination (entry (rr, cc) below)
+    const int e = lane < 12 ? lane : 11;
+    const int rr = e >> 2, cc = e & 3;
+    const double t0 = __ldcg(T + cc), t1 = __ldcg(T + 4 + cc), t2 = __ldcg(T + 8 + cc);
     // pivot threshold from the largest diagonal entry, in FP32
     float dm = (ri >= 0 && rj == ri) ? float(a) : 0.f;
 #pragma unroll
@@ -1619,13 +1624,14 @@ __device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt
         const double p = __shfl_sync(FULL, a, up6(k, k));
         const long long pb = __double_as_longlong(p);
         if (!(pb > thr && pb < 0x7FF0000000000000LL)) return false;
-        // reciprocal: FP32 seed, two Newton steps (exponent kept inside the
-        // FP32 range by the guard; the rare outsider takes the division)
+        // reciprocal: FP32 seed (relative error <= 2^-23) and one Newton
+        // step (-> ~2^-46, far below what the FP32-summed terms carry);
+        // exponent kept inside the FP32 range by the guard, the rare
+        // outsider takes the division
         const int ex = int((pb >> 52) & 0x7FF) - 1023;
         double rp;
         if (ex > -120 && ex < 120) {
             rp = double(__frcp_rn(float(p)));
-            rp = rp * fma(-p, rp, 2.0);
             rp = rp * fma(-p, rp, 2.0);
         } else {
             rp = 1.0 / p;
@@ -1668,9 +1674,6 @@ __device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt
         ca = sin(th) / th;
         cb = (1.0 - cos(th)) / th2;
     }
-    const int e = lane < 12 ? lane : 11;
-    const int rr = e >> 2, cc = e & 3;
-    const double t0 = __ldcg(T + cc), t1 = __ldcg(T + 4 + cc), t2 = __ldcg(T + 8 + cc);
     const double trc = rr == 0 ? t0 : (rr == 1 ? t1 : t2);
     // (K T)_rc: row r of K = [w]x has one zero
     const double ka = rr == 0 ? -x[2] : (rr == 1 ? x[2] : -x[1]);
