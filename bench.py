@@ -662,7 +662,39 @@ def large_build_section(args, B, torch):
     hbm, kind = _peaks()
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     alu = sm_count * 128 * 2 * 2070e6 / 1e12
-    return {"points": n, "depth": 4, "build_ms": e0.elapsed_time(e1),
+    # registration at this size: the cloud itself moved by a known motion
+    # (2 degrees, 1 % of the extent), 10 rounds against its tree
+    from paper_1807_02587_gb300 import synth
+    extent = tree.root()["extent"]
+    T_gt = synth.rigid(synth.axis_angle_matrix([1.0, -2.0, 3.0], np.deg2rad(2.0)), np.full(3, 0.01 * extent / np.sqrt(3)))
+    Ti = torch.from_numpy(np.linalg.inv(T_gt)).to(device="cuda", dtype=torch.float32)
+    src = dev.clone()
+    src[:, :3] = dev[:, :3] @ Ti[:3, :3].T + Ti[:3, 3]
+    iters = 10
+    tree.register(src, iters=iters)
+    tree.sync()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record()
+    T = tree.register(src, iters=iters)
+    r1.record()
+    tree.sync()
+    reg_ms = r0.elapsed_time(r1)
+    T = T.cpu().numpy()
+    m = tree.reg_moments()  # levels visited: node depth of each point's last round
+    lv = 1.0
+    if m.size:
+        offs = np.cumsum([0] + [8 ** (l + 1) for l in range(4)])
+        w = np.array([m[offs[l]:offs[l + 1], 0].sum() for l in range(4)])
+        lv = float((w * np.arange(1, 5)).sum() / max(w.sum(), 1e-30))
+    flops_pt = 30 + 168 * lv
+    register = {"rounds": iters, "ms": reg_ms, "us_per_round": reg_ms * 1e3 / iters,
+                "gpts_per_s_per_round": n * iters / (reg_ms / 1e3) / 1e9,
+                "point_read_GBps": 16 * n * iters / (reg_ms / 1e3) / 1e9,
+                "levels_visited": lv, "fp32_TFLOPs": flops_pt * n * iters / (reg_ms / 1e3) / 1e12,
+                "fp32_frac": flops_pt * n * iters / (reg_ms / 1e3) / 1e12 / alu,
+                "rot_err_deg_vs_truth": _rot_err(T[:3, :3], T_gt[:3, :3]),
+                "trans_err_rel_extent": float(np.linalg.norm(T[:3, 3] - T_gt[:3, 3]) / extent)}
+    return {"points": n, "depth": 4, "build_ms": e0.elapsed_time(e1), "register": register,
             "estep_launches": es_n, "estep_us_per_launch": per * 1e6,
             "estep_point_read_GBps": 16 * n / per / 1e9, "hbm_peak_GBps": hbm, "peak_kind": kind,
             "estep_hbm_frac": 16 * n / per / 1e9 / hbm,

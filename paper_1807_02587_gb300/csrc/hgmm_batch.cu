@@ -80,10 +80,10 @@ struct RegSmem {
 };
 
 // dynamic shared memory of k_batch: the staged top levels of the current
-// pair's tree (3 float4 per node), then the CTA's fixed-point histogram of
-// their registration moments (4 words per node)
+// pair's tree (3 float4 per node, padded per block of 8 siblings), then the
+// CTA's fixed-point histogram of their registration moments (4 words per node)
 constexpr size_t BATCH_DYN_SMEM =
-    3 * STAGED_NODES * sizeof(float4) + 4 * STAGED_NODES * sizeof(unsigned long long);
+    STAGED_F4 * sizeof(float4) + 4 * STAGED_NODES * sizeof(unsigned long long);
 
 // One pair, run by all CTAs of this cluster.
 template <bool COMP>
@@ -153,8 +153,7 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
     }
     {
         const int ns = n_nodes < STAGED_NODES ? n_nodes : STAGED_NODES;
-        const float4* gsrc = reinterpret_cast<const float4*>(w.est);
-        for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) sm_est[i] = __ldcg(gsrc + i);
+        stage_nodes(sm_est, w.est, ns);
     }
     cl.sync();
     const double ext = __ldcg(&w.root->extent) > 0.0 ? __ldcg(&w.root->extent) : 1.0;
@@ -235,7 +234,7 @@ __global__ void __launch_bounds__(EST_THREADS, 2) k_batch(BatchArgs a) {
     __shared__ int next_pair;
     extern __shared__ float4 batch_dyn[];
     float4* sm_est = batch_dyn;
-    unsigned long long* hist = reinterpret_cast<unsigned long long*>(batch_dyn + 3 * STAGED_NODES);
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(batch_dyn + STAGED_F4);
     for (int i = threadIdx.x; i < 4 * STAGED_NODES; i += blockDim.x) hist[i] = 0ull;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = int(cl.num_blocks());

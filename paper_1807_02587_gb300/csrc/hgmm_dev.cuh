@@ -1339,15 +1339,37 @@ __device__ __forceinline__ long long to_fix(float v) {
 // current transform; adds each point's (gamma, gamma (z' - mu_j)) to the
 // chosen node's fixed-point moments.
 constexpr int STAGED_NODES = 584;  // levels 0..2 (8 + 64 + 512 nodes) live in shared memory
+// Staged layout: node g at float4 slot 3 g + g / 8, i.e. one float4 of padding
+// after each block of 8 siblings (100 words), so that the same child of
+// different parents falls on different banks (block b starts at bank 4 b mod
+// 32): the lanes of a warp descending under different parents load without
+// conflicts between up to 8 consecutive parents.
+constexpr int STAGED_F4 = 3 * STAGED_NODES + STAGED_NODES / 8;
+static_assert(STAGED_NODES % 8 == 0, "whole sibling blocks are staged");
 
-__device__ __forceinline__ void load_node(const NodeEst* __restrict__ est, const float4* sm_est,
-                                          int64_t g, float4& ea, float4& eb, float4& ec) {
-    if (g < STAGED_NODES) {
-        ea = sm_est[3 * g];
-        eb = sm_est[3 * g + 1];
-        ec = sm_est[3 * g + 2];
+__device__ __forceinline__ int staged_slot(int g) { return 3 * g + (g >> 3); }
+
+// Copy the first ns nodes (ns <= STAGED_NODES) of est to the staged layout
+// (all threads of the CTA; the caller synchronises).
+__device__ __forceinline__ void stage_nodes(float4* sm_est, const NodeEst* __restrict__ est, int ns) {
+    const float4* g = reinterpret_cast<const float4*>(est);
+    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) {
+        const int node = i / 3;
+        sm_est[i + (node >> 3)] = __ldcg(g + i);
+    }
+}
+
+// Child c of the sibling block that starts at node `first` (a multiple of 8:
+// level offsets and 8 x parent index are); `staged` = the block lies in the
+// staged levels, and `blk` is its first slot there (staged_slot(first)).
+__device__ __forceinline__ void load_child(const NodeEst* __restrict__ est, const float4* blk, bool staged,
+                                           int64_t first, int c, float4& ea, float4& eb, float4& ec) {
+    if (staged) {
+        ea = blk[3 * c];
+        eb = blk[3 * c + 1];
+        ec = blk[3 * c + 2];
     } else {
-        const NodeEst* e = est + g;
+        const NodeEst* e = est + first + c;
         ea = __ldg(&e->a);
         eb = __ldg(&e->b);
         ec = __ldg(&e->c);
@@ -1422,11 +1444,13 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             float sc8[8];
             float best = -CUDART_INF_F;
             int bi = -1;
-#pragma unroll
             float bx = 0.f, by = 0.f, bz = 0.f, bstop = 0.f;  // the best child's mean, stop flag
+            const bool staged = first < STAGED_NODES;
+            const float4* blk = sm_est + (staged ? staged_slot(int(first)) : 0);
+#pragma unroll
             for (int c = 0; c < 8; ++c) {
                 float4 ea, eb, ec;
-                load_node(est, sm_est, first + c, ea, eb, ec);
+                load_child(est, blk, staged, first, c, ea, eb, ec);
                 const float ex = x - ea.x, ey = y - ea.y, ez = w - ea.z;
                 const float d0 = eb.x * ex;
                 const float d1 = fmaf(eb.z, ey, eb.y * ex);

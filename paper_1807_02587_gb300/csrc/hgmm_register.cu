@@ -71,7 +71,7 @@ struct RegArgs {
 };
 
 constexpr int TRACE_EVENTS = 6;
-constexpr size_t REG_DYN_SMEM = 3 * STAGED_NODES * sizeof(float4) + 4 * STAGED_NODES * sizeof(unsigned long long);
+constexpr size_t REG_DYN_SMEM = STAGED_F4 * sizeof(float4) + 4 * STAGED_NODES * sizeof(unsigned long long);
 static_assert(REG_DYN_SMEM <= 96 * 1024, "two k_register CTAs must fit on one SM");
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -100,18 +100,17 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     __shared__ float2 fin[8][NTERM];
     __shared__ double tot[NTERM];
     __shared__ bool last;
-    // dynamic: the staged top levels (3 float4 per node), then the CTA's
+    // dynamic: the staged top levels (3 float4 per node, padded), then the CTA's
     // fixed-point histogram of their moments (4 words per node)
     extern __shared__ float4 reg_dyn[];
     float4* sm_est = reg_dyn;
-    unsigned long long* hist = reinterpret_cast<unsigned long long*>(reg_dyn + 3 * STAGED_NODES);
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(reg_dyn + STAGED_F4);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ns = a.n_nodes < STAGED_NODES ? a.n_nodes : STAGED_NODES;
     // the top levels of the tree are read by every point: stage them once
     // for all rounds (the stop flags were set by k_reg_init before launch)
     {
-        const float4* gsrc = reinterpret_cast<const float4*>(a.est);
-        for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) sm_est[i] = gsrc[i];
+        stage_nodes(sm_est, a.est, ns);
         for (int i = threadIdx.x; i < 4 * STAGED_NODES; i += blockDim.x) hist[i] = 0ull;
         __syncthreads();
     }
