@@ -189,23 +189,37 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
         }
         const int st = (it - ib) % ESTEP_STAGES;
         const uint32_t parity = uint32_t((it - ib) / ESTEP_STAGES) & 1u;
+        // a thread whose wait ran out computes on whatever the stage holds
+        // (in bounds, discarded): the CTA's vote at the end of the item stops it
         const bool landed = tc::mbar_wait_bounded(&full[st], parity, tc::MBAR_SPIN_LIMIT);
-        if (__syncthreads_or(!landed)) {
-            if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-            break;
-        }
         const float4* zs = stage[st];
-        for (int base = 0; base < w.count; base += 64) {
-            const int idx = base + warp * 8 + q;
-            const bool valid = idx < w.count;
-            const float4 z = zs[min(idx, w.count - 1)];
-            estep_point_pair(cp, z, valid, in);
+        // two CTA steps of 64 points per pass: both points' posteriors side
+        // by side, then accumulated in step order (as one step at a time)
+        for (int base = 0; base < w.count; base += 128) {
+            const int ia = base + warp * 8 + q, ib2 = ia + 64;
+            const float4 za = zs[min(ia, w.count - 1)], zb = zs[min(ib2, w.count - 1)];
+            float2 xa, ya, wa, xb, yb, wb;
+            const float2 ga = posterior_pair(cp, za, ia < w.count, xa, ya, wa);
+            const float2 gb = posterior_pair(cp, zb, ib2 < w.count, xb, yb, wb);
+            accum_pair(in, ga, xa, ya, wa);
             if (++nfold == 16) {
                 fold_pair_smem<COMP>(in, acc_s, acc_c);
                 nfold = 0;
             }
+            if (base + 64 < w.count) {
+                accum_pair(in, gb, xb, yb, wb);
+                if (++nfold == 16) {
+                    fold_pair_smem<COMP>(in, acc_s, acc_c);
+                    nfold = 0;
+                }
+            }
         }
-        __syncthreads();  // every thread is done with this stage
+        // every thread is done with this stage (one barrier per item, which
+        // also carries the timeout vote)
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+            break;
+        }
         if (threadIdx.x == 0 && it + ESTEP_STAGES < ie) {
             const Item wn = items[it + ESTEP_STAGES];
             tc::fence_proxy_async();
@@ -561,7 +575,7 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
         if (stop_here) return HGMM_OK;  // checking aid: parameters after em_iters
         {
             ProfScope ps_(t, K_ASSIGN, s);
-            k_assign<<<G, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->codes, t->item_cnt);
+            k_assign<<<t->n_sm * 4, EST_THREADS, 0, s>>>(cur, t->items, t->meta, est_lvl, t->codes, t->item_cnt);
         }
         {
             ProfScope ps_(t, K_OFFSETS, s);

@@ -444,11 +444,13 @@ __device__ __forceinline__ void fold_pair(float2 (&in)[10], float2 (&s)[10], flo
     }
 }
 
-// One E-step point of a quad lane: Eq. 3 posteriors of the point over the
-// parent's 8 children (this lane holds two, its quad the rest: max and sum
-// by shuffles) and the lane's two children's moments.
-__device__ __forceinline__ void estep_point_pair(const ChildPair& cp, const float4 z, bool valid, float2 (&in)[10]) {
-    float2 ex, ey, ez;
+// Eq. 3 posteriors of one point over the parent's 8 children for a quad
+// lane (this lane holds two, its quad the rest: max and sum by shuffles),
+// with the lane's two offsets z - mu.  Kept apart from accum_pair so that
+// two points' posteriors can be formed side by side (their shuffle and MUFU
+// latencies overlapped) and still be accumulated in point order.
+__device__ __forceinline__ float2 posterior_pair(const ChildPair& cp, const float4 z, bool valid, float2& ex,
+                                                 float2& ey, float2& ez) {
     const float2 u = neg_score_pair(cp, z.x, z.y, z.z, ex, ey, ez);
     float umin = fminf(u.x, u.y);
     umin = fminf(umin, __shfl_xor_sync(FULL, umin, 1));
@@ -461,7 +463,15 @@ __device__ __forceinline__ void estep_point_pair(const ChildPair& cp, const floa
     tot += __shfl_xor_sync(FULL, tot, 1);
     tot += __shfl_xor_sync(FULL, tot, 2);
     const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
-    accum_pair(in, __fmul2_rn(make_float2(p0, p1), f2(rinv)), ex, ey, ez);
+    return __fmul2_rn(make_float2(p0, p1), f2(rinv));
+}
+
+// One E-step point of a quad lane: the posteriors above and the lane's two
+// children's moments.
+__device__ __forceinline__ void estep_point_pair(const ChildPair& cp, const float4 z, bool valid, float2 (&in)[10]) {
+    float2 ex, ey, ez;
+    const float2 g = posterior_pair(cp, z, valid, ex, ey, ez);
+    accum_pair(in, g, ex, ey, ez);
 }
 
 __device__ __forceinline__ void accum10(float* a, float g, float ex, float ey, float ez) {
@@ -578,16 +588,33 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
             run = it;
             load_child_pair<CG>(est_lvl + 8 * cur + 2 * k, cp);
         }
-        float4 znext = pts[w.start + min(warp * 8 + q, w.count - 1)];
-        for (int base = 0; base < w.count; base += 64) {
-            const int idx = base + warp * 8 + q;
-            const bool valid = idx < w.count;
-            const float4 z = znext;
-            if (base + 64 < w.count) znext = pts[w.start + min(idx + 64, w.count - 1)];
-            estep_point_pair(cp, z, valid, in);
+        // two CTA steps of 64 points per pass (the next pass's points loaded
+        // ahead): both points' posteriors side by side, then accumulated in
+        // step order, as one step at a time would
+        const int last = w.count - 1;
+        float4 na = pts[w.start + min(warp * 8 + q, last)];
+        float4 nb = pts[w.start + min(warp * 8 + q + 64, last)];
+        for (int base = 0; base < w.count; base += 128) {
+            const int ia = base + warp * 8 + q, ib2 = ia + 64;
+            const float4 za = na, zb = nb;
+            if (base + 128 < w.count) {
+                na = pts[w.start + min(ia + 128, last)];
+                nb = pts[w.start + min(ib2 + 128, last)];
+            }
+            float2 xa, ya, wa, xb, yb, wb;
+            const float2 ga = posterior_pair(cp, za, ia < w.count, xa, ya, wa);
+            const float2 gb = posterior_pair(cp, zb, ib2 < w.count, xb, yb, wb);
+            accum_pair(in, ga, xa, ya, wa);
             if (++nfold == 16) {
                 fold_pair<COMP>(in, s, c);
                 nfold = 0;
+            }
+            if (base + 64 < w.count) {
+                accum_pair(in, gb, xb, yb, wb);
+                if (++nfold == 16) {
+                    fold_pair<COMP>(in, s, c);
+                    nfold = 0;
+                }
             }
         }
     }
@@ -948,34 +975,40 @@ __device__ void mstep_parent_warp(int level, int n, int p, int i0, int i1, int C
 
 
 // ================================================================= hand-off
+static_assert(TILE % 64 == 0 && EST_THREADS == 256, "an item is whole CTA steps of 64 points");
 struct AssignSmem {
-    int cnt[EST_THREADS / 32][8];
-    int base[8];
+    int cnt[TILE / 64][EST_THREADS / 32][8];  // [step][warp][child]
 };
 
 // Argmax hand-off (ties -> lowest index) of one item's points by one CTA,
 // with each point's rank among the item's points that chose the same child
 // (ballots, so deterministic and stable): codes[pos] = child | rank << 3 and
-// item_cnt[8 it + c] = the item's count per child.
+// item_cnt[8 it + c] = the item's count per child.  All of the item's
+// points (up to TILE, 64 per CTA step) are loaded and labelled first, with
+// the per-step, per-warp child counts in shared memory, so one barrier
+// serves the whole item: a point's rank is the counts of the steps before
+// its own, plus those of the warps before its own, plus its rank in its warp.
 __device__ __forceinline__ void assign_item(const float4* __restrict__ pts, const Item w, int it,
                                             const NodeEst* __restrict__ est_lvl,
                                             uint32_t* __restrict__ codes,
                                             int* __restrict__ item_cnt, AssignSmem& as) {
+    constexpr int NS = TILE / 64;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = lane >> 2, k = lane & 3;
     const unsigned lt = (1u << lane) - 1u;
     ChildRegs r0, r1;
     load_child(est_lvl + 8 * w.parent + 2 * k, r0);
     load_child(est_lvl + 8 * w.parent + 2 * k + 1, r1);
-    if (threadIdx.x < 8) as.base[threadIdx.x] = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < w.count; b0 += 64) {
-        const int idx = b0 + warp * 8 + q;
-        const bool valid = idx < w.count;
-        const float4 z = pts[w.start + (valid ? idx : 0)];
+    float4 z[NS];
+#pragma unroll
+    for (int st = 0; st < NS; ++st) z[st] = pts[w.start + min(64 * st + warp * 8 + q, w.count - 1)];
+    int lab_s[NS], rank_s[NS];
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+        const bool valid = 64 * st + warp * 8 + q < w.count;
         float ex, ey, ez;
-        const float s0 = child_score(r0, z.x, z.y, z.z, ex, ey, ez);
-        const float s1 = child_score(r1, z.x, z.y, z.z, ex, ey, ez);
+        const float s0 = child_score(r0, z[st].x, z[st].y, z[st].z, ex, ey, ez);
+        const float s1 = child_score(r1, z[st].x, z[st].y, z[st].z, ex, ey, ez);
         float best = s0;
         int lab = 2 * k;
         if (s1 > best) { best = s1; lab = 2 * k + 1; }
@@ -990,24 +1023,33 @@ __device__ __forceinline__ void assign_item(const float4* __restrict__ pts, cons
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) {
             const unsigned bal = __ballot_sync(FULL, lead && lab == cc);
-            if (lane == 0) as.cnt[warp][cc] = __popc(bal);
+            if (lane == 0) as.cnt[st][warp][cc] = __popc(bal);
             if (lab == cc) my_rank = __popc(bal & lt);
         }
-        __syncthreads();
-        if (lead) {
-            int r = as.base[lab] + my_rank;
-            for (int w2 = 0; w2 < warp; ++w2) r += as.cnt[w2][lab];
+        lab_s[st] = lab;
+        rank_s[st] = my_rank;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+        const int idx = 64 * st + warp * 8 + q;
+        if (k == 0 && idx < w.count) {
+            const int lab = lab_s[st];
+            int r = rank_s[st];
+            for (int s2 = 0; s2 < st; ++s2)
+#pragma unroll
+                for (int w2 = 0; w2 < EST_THREADS / 32; ++w2) r += as.cnt[s2][w2][lab];
+            for (int w2 = 0; w2 < warp; ++w2) r += as.cnt[st][w2][lab];
             codes[w.start + idx] = uint32_t(lab) | (uint32_t(r) << 3);
         }
-        __syncthreads();
-        if (threadIdx.x < 8) {
-            int tsum = 0;
-            for (int w2 = 0; w2 < EST_THREADS / 32; ++w2) tsum += as.cnt[w2][threadIdx.x];
-            as.base[threadIdx.x] += tsum;
-        }
-        __syncthreads();
     }
-    if (threadIdx.x < 8) item_cnt[8 * it + threadIdx.x] = as.base[threadIdx.x];
+    if (threadIdx.x < 8) {
+        int tsum = 0;
+        for (int s2 = 0; s2 < NS; ++s2)
+#pragma unroll
+            for (int w2 = 0; w2 < EST_THREADS / 32; ++w2) tsum += as.cnt[s2][w2][threadIdx.x];
+        item_cnt[8 * it + threadIdx.x] = tsum;
+    }
     __syncthreads();
 }
 
