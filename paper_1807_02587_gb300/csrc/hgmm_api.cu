@@ -45,7 +45,7 @@ void free_tree(hgmm_tree* t) {
     clear_prof(t);
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
                     t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
-                    t->item_off, t->root, t->root_part, t->root_counter, t->em_cnt, t->mslices, t->mcnt, t->status, t->reg_acc, t->reg_acc2, t->reg_part,
+                    t->item_off, t->slice_tot, t->root, t->root_part, t->root_counter, t->em_cnt, t->mslices, t->mcnt, t->status, t->reg_acc, t->reg_acc2, t->reg_part,
                     t->reg_bar, t->reg_T, t->reg_Rt, t->reg_dbg, t->reg_obj, t->rnode, t->trace, t->stage_tgt,
                     t->stage_src, t->stage_T};
     for (void* p : ptrs)
@@ -147,6 +147,8 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->partials, t->max_items * NPART);
     good &= dalloc(&t->item_cnt, t->max_items * 8);
     good &= dalloc(&t->item_off, t->max_items * 8);
+    t->max_slices = t->max_items / OFFSET_SLICE_ITEMS + 2;
+    good &= dalloc(&t->slice_tot, t->max_slices * 8);
     good &= dalloc(&t->root, 1);
     good &= dalloc(&t->root_part, int64_t(t->est_grid) * 32);
     good &= dalloc(&t->root_counter, 1);

@@ -16,6 +16,8 @@
 //                     constants )
 //   k_assign          argmax hand-off (ties -> lowest index) with in-item ranks
 //   k_child_offsets   per parent: child segment starts and per-item offsets
+//                     (parents of many items: per slice of their items, after
+//                     k_offset_slices has summed each slice's counts)
 //   k_scatter         stable 8-way partition of every parent's segment
 //   k_finalize        FP64 eigen, complexity, precision matrix of level l
 #include <algorithm>
@@ -193,25 +195,14 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
         // (in bounds, discarded): the CTA's vote at the end of the item stops it
         const bool landed = tc::mbar_wait_bounded(&full[st], parity, tc::MBAR_SPIN_LIMIT);
         const float4* zs = stage[st];
-        // two CTA steps of 64 points per pass: both points' posteriors side
-        // by side, then accumulated in step order (as one step at a time)
-        for (int base = 0; base < w.count; base += 128) {
-            const int ia = base + warp * 8 + q, ib2 = ia + 64;
-            const float4 za = zs[min(ia, w.count - 1)], zb = zs[min(ib2, w.count - 1)];
-            float2 xa, ya, wa, xb, yb, wb;
-            const float2 ga = posterior_pair(cp, za, ia < w.count, xa, ya, wa);
-            const float2 gb = posterior_pair(cp, zb, ib2 < w.count, xb, yb, wb);
-            accum_pair(in, ga, xa, ya, wa);
+        for (int base = 0; base < w.count; base += 64) {
+            const int idx = base + warp * 8 + q;
+            const bool valid = idx < w.count;
+            const float4 z = zs[min(idx, w.count - 1)];
+            estep_point_pair(cp, z, valid, in);
             if (++nfold == 16) {
                 fold_pair_smem<COMP>(in, acc_s, acc_c);
                 nfold = 0;
-            }
-            if (base + 64 < w.count) {
-                accum_pair(in, gb, xb, yb, wb);
-                if (++nfold == 16) {
-                    fold_pair_smem<COMP>(in, acc_s, acc_c);
-                    nfold = 0;
-                }
             }
         }
         // every thread is done with this stage (one barrier per item, which
@@ -390,21 +381,82 @@ __global__ void __launch_bounds__(EST_THREADS) k_assign(const float4* __restrict
         assign_item(pts, items[it], it, est_lvl, codes, item_cnt, as);
 }
 
-// One CTA (256 threads) per parent.
+// Slice j of the nsl slices of a parent's items [i0, i1).
+__device__ __forceinline__ void offset_slice(int i0, int i1, int nsl, int j, int& a, int& b) {
+    const int per = (i1 - i0 + nsl - 1) / nsl;
+    a = min(i1, i0 + j * per);
+    b = min(i1, a + per);
+}
+
+// Parents with many items (the hand-off of large clouds' top levels): CTA
+// (p, j) sums the item counts of slice j of parent p per child.
+__global__ void __launch_bounds__(256) k_offset_slices(const int* __restrict__ item_range,
+                                                       const int* __restrict__ item_cnt, int nsl,
+                                                       int* __restrict__ slice_tot) {
+    __shared__ int tot[8][8];
+    const int p = blockIdx.x, j = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int a, b;
+    offset_slice(item_range[2 * p], item_range[2 * p + 1], nsl, j, a, b);
+    int t8[8] = {};
+    for (int i = a + threadIdx.x; i < b; i += blockDim.x)
+        for (int cc = 0; cc < 8; ++cc) t8[cc] += item_cnt[8 * i + cc];
+    for (int cc = 0; cc < 8; ++cc) {
+        int x = t8[cc];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+        if (lane == 0) tot[warp][cc] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        int x = 0;
+        for (int w = 0; w < 8; ++w) x += tot[w][threadIdx.x];
+        slice_tot[(int64_t(p) * nsl + j) * 8 + threadIdx.x] = x;
+    }
+}
+
+// CTA (p, j) of 256 threads: the child segments of parent p and the item
+// offsets of slice j of its items (nsl = 1: the whole parent in one CTA;
+// nsl > 1: the slices' sums from k_offset_slices give each slice's start).
 __global__ void __launch_bounds__(256) k_child_offsets(int level, int n,
                                                        const int* __restrict__ item_range,
                                                        const Item* __restrict__ items,
                                                        const int* __restrict__ item_cnt,
                                                        int* __restrict__ item_off,
                                                        int* __restrict__ seg_start,
-                                                       int* __restrict__ seg_count) {
+                                                       int* __restrict__ seg_count, int nsl,
+                                                       const int* __restrict__ slice_tot) {
     __shared__ OffsetSmem os;
-    const int p = blockIdx.x;
+    const int p = blockIdx.x, j = blockIdx.y;
     const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
     // an empty parent's children get empty segments at the parent's start
     const int pstart = i0 < i1 ? items[i0].start
                                : (level == 0 ? 0 : seg_start[d_level_offset(level - 1) + p]);
-    child_offsets_cta(level, p, i0, i1, pstart, item_cnt, item_off, seg_start, seg_count, os);
+    if (nsl == 1) {
+        child_offsets_cta(level, p, i0, i1, pstart, item_cnt, item_off, seg_start, seg_count, os);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        const int* st = slice_tot + int64_t(p) * nsl * 8;
+        const int64_t g0 = d_level_offset(level) + 8 * int64_t(p);
+        int run = pstart;
+        for (int cc = 0; cc < 8; ++cc) {
+            int tot = 0, pre = 0;
+            for (int jj = 0; jj < nsl; ++jj) {
+                if (jj == j) pre = tot;
+                tot += st[8 * jj + cc];
+            }
+            os.carry[cc] = run + pre;
+            if (j == 0) {
+                seg_start[g0 + cc] = run;
+                seg_count[g0 + cc] = tot;
+            }
+            run += tot;
+        }
+    }
+    __syncthreads();
+    int a, b;
+    offset_slice(i0, i1, nsl, j, a, b);
+    child_offsets_scan(a, b, item_cnt, item_off, os);
 }
 
 __global__ void __launch_bounds__(256) k_scatter(const float4* __restrict__ pts_in,
@@ -579,8 +631,16 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
         }
         {
             ProfScope ps_(t, K_OFFSETS, s);
-            k_child_offsets<<<n_par, 256, 0, s>>>(l, n, t->item_range, t->items, t->item_cnt,
-                                                  t->item_off, t->seg_start, t->seg_count);
+            // parents of many items (top levels of large clouds) are scanned
+            // in slices of about OFFSET_SLICE_ITEMS items by parallel CTAs
+            const int64_t items_est = (n64 + TILE - 1) / TILE + n_par;
+            int nsl = int(std::min<int64_t>(OFFSET_MAX_SLICES, std::max<int64_t>(1, items_est / n_par / OFFSET_SLICE_ITEMS)));
+            while (nsl > 1 && int64_t(n_par) * nsl > t->max_slices) --nsl;
+            if (nsl > 1)
+                k_offset_slices<<<dim3(n_par, nsl), 256, 0, s>>>(t->item_range, t->item_cnt, nsl, t->slice_tot);
+            k_child_offsets<<<dim3(n_par, nsl), 256, 0, s>>>(l, n, t->item_range, t->items, t->item_cnt,
+                                                             t->item_off, t->seg_start, t->seg_count, nsl,
+                                                             t->slice_tot);
         }
         float4* out = t->pts[l & 1];
         {

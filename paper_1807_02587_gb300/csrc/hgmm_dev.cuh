@@ -444,13 +444,11 @@ __device__ __forceinline__ void fold_pair(float2 (&in)[10], float2 (&s)[10], flo
     }
 }
 
-// Eq. 3 posteriors of one point over the parent's 8 children for a quad
-// lane (this lane holds two, its quad the rest: max and sum by shuffles),
-// with the lane's two offsets z - mu.  Kept apart from accum_pair so that
-// two points' posteriors can be formed side by side (their shuffle and MUFU
-// latencies overlapped) and still be accumulated in point order.
-__device__ __forceinline__ float2 posterior_pair(const ChildPair& cp, const float4 z, bool valid, float2& ex,
-                                                 float2& ey, float2& ez) {
+// One E-step point of a quad lane: Eq. 3 posteriors of the point over the
+// parent's 8 children (this lane holds two, its quad the rest: max and sum
+// by shuffles) and the lane's two children's moments.
+__device__ __forceinline__ void estep_point_pair(const ChildPair& cp, const float4 z, bool valid, float2 (&in)[10]) {
+    float2 ex, ey, ez;
     const float2 u = neg_score_pair(cp, z.x, z.y, z.z, ex, ey, ez);
     float umin = fminf(u.x, u.y);
     umin = fminf(umin, __shfl_xor_sync(FULL, umin, 1));
@@ -463,15 +461,7 @@ __device__ __forceinline__ float2 posterior_pair(const ChildPair& cp, const floa
     tot += __shfl_xor_sync(FULL, tot, 1);
     tot += __shfl_xor_sync(FULL, tot, 2);
     const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
-    return __fmul2_rn(make_float2(p0, p1), f2(rinv));
-}
-
-// One E-step point of a quad lane: the posteriors above and the lane's two
-// children's moments.
-__device__ __forceinline__ void estep_point_pair(const ChildPair& cp, const float4 z, bool valid, float2 (&in)[10]) {
-    float2 ex, ey, ez;
-    const float2 g = posterior_pair(cp, z, valid, ex, ey, ez);
-    accum_pair(in, g, ex, ey, ez);
+    accum_pair(in, __fmul2_rn(make_float2(p0, p1), f2(rinv)), ex, ey, ez);
 }
 
 __device__ __forceinline__ void accum10(float* a, float g, float ex, float ey, float ez) {
@@ -588,33 +578,16 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
             run = it;
             load_child_pair<CG>(est_lvl + 8 * cur + 2 * k, cp);
         }
-        // two CTA steps of 64 points per pass (the next pass's points loaded
-        // ahead): both points' posteriors side by side, then accumulated in
-        // step order, as one step at a time would
-        const int last = w.count - 1;
-        float4 na = pts[w.start + min(warp * 8 + q, last)];
-        float4 nb = pts[w.start + min(warp * 8 + q + 64, last)];
-        for (int base = 0; base < w.count; base += 128) {
-            const int ia = base + warp * 8 + q, ib2 = ia + 64;
-            const float4 za = na, zb = nb;
-            if (base + 128 < w.count) {
-                na = pts[w.start + min(ia + 128, last)];
-                nb = pts[w.start + min(ib2 + 128, last)];
-            }
-            float2 xa, ya, wa, xb, yb, wb;
-            const float2 ga = posterior_pair(cp, za, ia < w.count, xa, ya, wa);
-            const float2 gb = posterior_pair(cp, zb, ib2 < w.count, xb, yb, wb);
-            accum_pair(in, ga, xa, ya, wa);
+        float4 znext = pts[w.start + min(warp * 8 + q, w.count - 1)];
+        for (int base = 0; base < w.count; base += 64) {
+            const int idx = base + warp * 8 + q;
+            const bool valid = idx < w.count;
+            const float4 z = znext;
+            if (base + 64 < w.count) znext = pts[w.start + min(idx + 64, w.count - 1)];
+            estep_point_pair(cp, z, valid, in);
             if (++nfold == 16) {
                 fold_pair<COMP>(in, s, c);
                 nfold = 0;
-            }
-            if (base + 64 < w.count) {
-                accum_pair(in, gb, xb, yb, wb);
-                if (++nfold == 16) {
-                    fold_pair<COMP>(in, s, c);
-                    nfold = 0;
-                }
             }
         }
     }
@@ -1058,6 +1031,9 @@ struct OffsetSmem {
     int carry[8];
 };
 
+__device__ __forceinline__ void child_offsets_scan(int ia, int ib, const int* __restrict__ item_cnt,
+                                                   int* __restrict__ item_off, OffsetSmem& os);
+
 // Child segments of parent p (items [i0, i1), segment start pstart) by one
 // CTA of 256 threads: per child, an exclusive scan over the parent's items
 // of the item counts -> absolute destination offsets; children's seg_start /
@@ -1090,7 +1066,18 @@ __device__ __forceinline__ void child_offsets_cta(int level, int p, int i0, int 
         }
     }
     __syncthreads();
-    for (int b = i0; b < i1; b += blockDim.x) {
+    child_offsets_scan(i0, i1, item_cnt, item_off, os);
+}
+
+// Items [ia, ib) of a parent by one CTA of 256 threads, os.carry[c] = the
+// destination of child c's first point in item ia (set and synchronised by
+// the caller): per child, an exclusive scan of the item counts ->
+// item_off.  carry ends past the range.
+__device__ __forceinline__ void child_offsets_scan(int ia, int ib, const int* __restrict__ item_cnt,
+                                                   int* __restrict__ item_off, OffsetSmem& os) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i1 = ib;
+    for (int b = ia; b < i1; b += blockDim.x) {
         const int i = b + threadIdx.x;
         int v8[8];
         for (int cc = 0; cc < 8; ++cc) v8[cc] = i < i1 ? item_cnt[8 * i + cc] : 0;

@@ -35,6 +35,8 @@ constexpr int NMOM = 10;              // S0, S1 (3), S2 (6 upper)
 constexpr int NPART = J * NMOM;       // 80 moment values per parent run
 constexpr int TILE = 256;             // points per build work item
 constexpr int EST_THREADS = 256;      // build E-step CTA
+constexpr int OFFSET_SLICE_ITEMS = 1024;  // hand-off scan: items per slice of a large parent
+constexpr int OFFSET_MAX_SLICES = 64;
 constexpr int REG_THREADS = 256;      // registration descent CTA
 constexpr int MSTEP_THREADS = 128;    // registration M-step CTA
 constexpr int NTERM = 28;             // per-round sums: 21 of H, 6 of g, the objective
@@ -132,6 +134,8 @@ struct hgmm_tree {
     float2* partials = nullptr;  // max_items x NPART (sum, compensation)
     int* item_cnt = nullptr;     // max_items x 8
     int* item_off = nullptr;     // max_items x 8
+    int* slice_tot = nullptr;    // hand-off of large parents: parents x slices x 8 item-count sums
+    int64_t max_slices = 0;      // parents x slices that slice_tot holds
     hgmm::RootDev* root = nullptr;
     float* root_part = nullptr;  // est_grid x 32
     unsigned* root_counter = nullptr;

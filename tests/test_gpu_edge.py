@@ -139,3 +139,22 @@ def test_bounded_wait_times_out_without_fault(B):
     tree.build(dev, 2)
     tree.register(dev, iters=2)
     tree.sync()
+
+
+def test_large_parent_handoff_in_slices(B):
+    """A level-0 parent of ~2,100 items: its hand-off scan runs in two slices
+    on parallel CTAs; the partition stays consistent (every point once, in
+    its chosen child's segment) and level 1, built from those segments,
+    matches the oracle."""
+    n = 530_001
+    P = synth.primitive_pair(5, n)["tgt"]
+    dev, Z = PT.device_cloud(P)
+    tree = B.Tree(n, 2)
+    tree.build(dev, 2)
+    tree.sync()
+    _consistent(tree, n, 2)
+    res = PT.check_build(tree, Z, PT.oracle_params(B.params(), 2), conditioning=False)
+    for r in res["levels"]:
+        assert r["count_mismatch"] == 0 and r["live_mismatch"] == 0, r
+        assert r["mu"] < PT.MEAN_TOL and r["S"] < PT.COV_TOL, r
+        assert r["label_disagree_not_tie"] == 0, r
