@@ -93,7 +93,6 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
     const int rank = int(cl.block_rank());
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const int gw = rank * wpb + warp, nwt = cs * wpb;
     const float4* tgt = a.points + a.tgt_rng[2 * pair];
     const int n_t = int(a.tgt_rng[2 * pair + 1] - a.tgt_rng[2 * pair]);
     const float4* src = a.points + a.src_rng[2 * pair];
