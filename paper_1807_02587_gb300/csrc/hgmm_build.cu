@@ -273,8 +273,9 @@ __global__ void __launch_bounds__(256) k_mstep(int level, int n, const int* __re
 }
 
 // All K EM iterations of one parent by one CTA (blockIdx.x = parent): the
-// E-step over the parent's items as a single run, then the M-step of its 8
-// children, with nothing but __syncthreads between them (the parents of a
+// E-step over the parent's items as a single run (its moments kept in shared
+// memory), then the M-step of its 8 children, with nothing but
+// __syncthreads between them (the parents of a
 // level are independent during EM).  For levels with many small parents,
 // where the level-wide E-step / M-step launches would be mostly latency.
 template <bool COMP>
@@ -282,7 +283,6 @@ __global__ void __launch_bounds__(EST_THREADS, 2) k_em_local(int level, int n, i
                                                             const float4* __restrict__ pts,
                                                             const Item* __restrict__ items,
                                                             const int* __restrict__ item_range,
-                                                            float2* __restrict__ partials,
                                                             const int* __restrict__ seg_count,
                                                             const RootDev* __restrict__ root, float n_min,
                                                             NodeStat* __restrict__ stat,
@@ -292,17 +292,20 @@ __global__ void __launch_bounds__(EST_THREADS, 2) k_em_local(int level, int n, i
         float2 red[EST_THREADS / 32][NPART];
         MstepSmem msm;
     } sm;
+    __shared__ float2 run_sm[NPART];
     const int p = blockIdx.x;
     const int i0 = item_range[2 * p], i1 = item_range[2 * p + 1];
     if (i0 >= i1) return;  // parent without points: children stay dead
     const NodeEst* est_lvl = est + level_offset(level);
     for (int k = 0; k < K; ++k) {
-        // one run [i0, i1): its partial lands at slot i0
-        estep_range<COMP>(pts, ItemList{items}, i0, i1, est_lvl, partials, sm.red);
+        // [i0, i1) is one run: its partial stays in shared memory (the
+        // flush ends with a block barrier)
+        estep_range<COMP, ItemList, false, true>(pts, ItemList{items}, i0, i1, est_lvl, run_sm, sm.red);
+        // the moments mstep_parent forms from a single run: sum + compensation
+        if (threadIdx.x < NPART) sm.msm.mom[threadIdx.x] = double(run_sm[threadIdx.x].x) + double(run_sm[threadIdx.x].y);
         __syncthreads();
-        // C = i1 makes [i0, i1) a single run for the M-step as well
-        mstep_parent<COMP>(level, n, p, i0, i1, i1, partials, seg_count, root, n_min, stat, est,
-                           status, sm.msm);
+        if (threadIdx.x < 32)
+            child_mstep_quad(level, n, p, sm.msm.mom, seg_count, root, n_min, stat, est, status);
         __syncthreads();
     }
 }
@@ -582,11 +585,11 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
             ProfScope ps_(t, K_ESTEP, s);
             if (comp)
                 k_em_local<true><<<n_par, EST_THREADS, 0, s>>>(l, n, em_iters, cur, t->items, t->item_range,
-                                                              t->partials, t->seg_count, t->root, p.n_min,
+                                                              t->seg_count, t->root, p.n_min,
                                                               t->stat, t->est, t->status);
             else
                 k_em_local<false><<<n_par, EST_THREADS, 0, s>>>(l, n, em_iters, cur, t->items, t->item_range,
-                                                               t->partials, t->seg_count, t->root, p.n_min,
+                                                               t->seg_count, t->root, p.n_min,
                                                                t->stat, t->est, t->status);
         }
         const bool coop_em = !local_em && em_iters > 0 && t->em_coop_grid > 0 && (p.flags & HGMM_FLAG_EM_COOPERATIVE);

@@ -494,24 +494,51 @@ __device__ __forceinline__ void fold20(float* in, float* s, float* c) {
     }
 }
 
+// One level of the flush's reduce-scatter over the eight lanes of a warp
+// that hold the same children (lanes k, k + 4, ..., k + 28): of the lane's
+// first 2H values (H = N / 2 rounded up) it keeps the half chosen by bit O
+// of its lane index (the first H, or the remaining N - H) and adds the
+// partner's copy of that half, which lands at positions 0.. of s and c.
+template <bool COMP, int N, int O>
+__device__ __forceinline__ void flush_rs_level(float* s, float* c, int lane) {
+    constexpr int H = (N + 1) / 2, L = N - H;  // kept by the lower / upper lane
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        // lower lane keeps i < H and sends i + H (i < L); upper keeps H + i (i < L), sends i
+        const float ss = up ? s[i] : (i < L ? s[H + i] : 0.f);
+        const float cs = up ? c[i] : (i < L ? c[H + i] : 0.f);
+        float sk = up ? (i < L ? s[H + i] : 0.f) : s[i];
+        float ck = up ? (i < L ? c[H + i] : 0.f) : c[i];
+        const float sr = __shfl_xor_sync(FULL, ss, O);
+        const float cr = __shfl_xor_sync(FULL, cs, O);
+        if (COMP) pair_add(sk, ck, sr, cr);
+        else sk += sr;
+        s[i] = sk;
+        c[i] = ck;
+    }
+}
+
 // Block-wide reduction of the (s, c) accumulators into partial slot `run`.
+// Within a warp the eight lanes of each child pair reduce-scatter their 20
+// values (18 compensated additions and 36 shuffles per lane instead of 60
+// and 120 for a butterfly); each value's warp total then sits in exactly
+// one lane, which stores it for the fixed-order sum over the warps.
 template <bool COMP>
 __device__ __forceinline__ void flush_run(float* s, float* c, float2 (*red)[NPART],
                                           float2* __restrict__ out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, k = lane & 3;
+    flush_rs_level<COMP, 20, 16>(s, c, lane);  // 10 values left
+    flush_rs_level<COMP, 10, 8>(s, c, lane);   // 5
+    flush_rs_level<COMP, 5, 4>(s, c, lane);    // 3 (lower lane) or 2 (upper lane)
+    {
+        // the values this lane now holds: a half of 20 by lane bit 4, of
+        // that a half of 10 by bit 3, of that the first 3 or last 2 by bit 2
+        const int base = ((lane & 16) ? 10 : 0) + ((lane & 8) ? 5 : 0) + ((lane & 4) ? 3 : 0);
+        const int cnt = (lane & 4) ? 2 : 3;
 #pragma unroll
-    for (int off = 4; off < 32; off <<= 1) {
-#pragma unroll
-        for (int v = 0; v < 20; ++v) {
-            const float s2 = __shfl_xor_sync(FULL, s[v], off);
-            const float c2 = __shfl_xor_sync(FULL, c[v], off);
-            if (COMP) pair_add(s[v], c[v], s2, c2);
-            else s[v] += s2;
-        }
-    }
-    if (lane < 4) {
-#pragma unroll
-        for (int v = 0; v < 20; ++v) red[warp][k * 20 + v] = make_float2(s[v], COMP ? c[v] : 0.f);
+        for (int i = 0; i < 3; ++i)
+            if (i < cnt) red[warp][k * 20 + base + i] = make_float2(s[i], COMP ? c[i] : 0.f);
     }
     __syncthreads();
     if (threadIdx.x < NPART) {
@@ -551,8 +578,9 @@ __device__ __forceinline__ void flush_pair(float2 (&s2)[10], float2 (&c2)[10], f
 // the 8 children of its parent (log2 domain, max subtracted), gamma-weighted
 // moments of each child centred on the child's current FP32 mean, one
 // partial per run of consecutive items with the same parent, stored at the
-// run's first item.
-template <bool COMP, class Items, bool CG = false>
+// run's first item (ONE_RUN: the items are one parent's, and its single
+// partial goes to partials[0..NPART), e.g. in shared memory).
+template <bool COMP, class Items, bool CG = false, bool ONE_RUN = false>
 __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Items items, int ib,
                                             int ie, const NodeEst* __restrict__ est_lvl,
                                             float2* __restrict__ partials,
@@ -572,7 +600,7 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
             if (cur >= 0) {
                 fold_pair<COMP>(in, s, c);
                 nfold = 0;
-                flush_pair<COMP>(s, c, red, partials + int64_t(run) * NPART);
+                flush_pair<COMP>(s, c, red, ONE_RUN ? partials : partials + int64_t(run) * NPART);
             }
             cur = w.parent;
             run = it;
@@ -592,7 +620,7 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
         }
     }
     fold_pair<COMP>(in, s, c);
-    flush_pair<COMP>(s, c, red, partials + int64_t(run) * NPART);
+    flush_pair<COMP>(s, c, red, ONE_RUN ? partials : partials + int64_t(run) * NPART);
 }
 
 // The E-step of whole items by single warps (items first, first + stride,
@@ -644,21 +672,16 @@ __device__ __forceinline__ void estep_items_warp(const float4* __restrict__ pts,
             }
         }
         fold20<COMP>(in, s, c);
+        // the reduce-scatter of flush_run: each value's warp total lands in one lane
+        flush_rs_level<COMP, 20, 16>(s, c, lane);
+        flush_rs_level<COMP, 10, 8>(s, c, lane);
+        flush_rs_level<COMP, 5, 4>(s, c, lane);
+        const int base = ((lane & 16) ? 10 : 0) + ((lane & 8) ? 5 : 0) + ((lane & 4) ? 3 : 0);
+        const int cnt = (lane & 4) ? 2 : 3;
+        float2* out = partials + int64_t(it) * NPART + k * 20 + base;
 #pragma unroll
-        for (int off = 4; off < 32; off <<= 1) {
-#pragma unroll
-            for (int v = 0; v < 20; ++v) {
-                const float s2 = __shfl_xor_sync(FULL, s[v], off);
-                const float c2 = __shfl_xor_sync(FULL, c[v], off);
-                if (COMP) pair_add(s[v], c[v], s2, c2);
-                else s[v] += s2;
-            }
-        }
-        if (lane < 4) {
-            float2* out = partials + int64_t(it) * NPART + k * 20;
-#pragma unroll
-            for (int v = 0; v < 20; ++v) out[v] = make_float2(s[v], COMP ? c[v] : 0.f);
-        }
+        for (int i = 0; i < 3; ++i)
+            if (i < cnt) out[i] = make_float2(s[i], COMP ? c[i] : 0.f);
     }
 }
 
