@@ -455,12 +455,12 @@ __device__ __forceinline__ void estep_point_pair(const ChildPair& cp, const floa
     umin = fminf(umin, __shfl_xor_sync(FULL, umin, 2));
     const bool any_live = umin < CUDART_INF_F;  // false for a leaf parent
     const float2 arg = sub2(f2(umin), u);      // = score - max score
-    const float p0 = any_live ? exp2f(arg.x) : 0.f;
-    const float p1 = any_live ? exp2f(arg.y) : 0.f;
+    const float p0 = any_live ? ex2_fast(arg.x) : 0.f;
+    const float p1 = any_live ? ex2_fast(arg.y) : 0.f;
     float tot = p0 + p1;
     tot += __shfl_xor_sync(FULL, tot, 1);
     tot += __shfl_xor_sync(FULL, tot, 2);
-    const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
+    const float rinv = (valid && any_live) ? rcp_fast(tot) : 0.0f;
     accum_pair(in, __fmul2_rn(make_float2(p0, p1), f2(rinv)), ex, ey, ez);
 }
 
@@ -658,12 +658,12 @@ __device__ __forceinline__ void estep_items_warp(const float4* __restrict__ pts,
             m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
             m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
             const bool any_live = m > -CUDART_INF_F;  // false for a leaf parent
-            const float p0 = any_live ? exp2f(s0 - m) : 0.f;
-            const float p1 = any_live ? exp2f(s1 - m) : 0.f;
+            const float p0 = any_live ? ex2_fast(s0 - m) : 0.f;
+            const float p1 = any_live ? ex2_fast(s1 - m) : 0.f;
             float tot = p0 + p1;
             tot += __shfl_xor_sync(FULL, tot, 1);
             tot += __shfl_xor_sync(FULL, tot, 2);
-            const float rinv = (valid && any_live) ? 1.0f / tot : 0.0f;
+            const float rinv = (valid && any_live) ? rcp_fast(tot) : 0.0f;
             accum10(in, p0 * rinv, e0x, e0y, e0z);
             accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
             if (++nfold == 16) {
@@ -1523,8 +1523,8 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             if (bi < 0) break;  // the current node has no live children
             float sum = 0.f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) sum += exp2f(sc8[c] - best);
-            gamma = 1.0f / sum;
+            for (int c = 0; c < 8; ++c) sum += ex2_fast(sc8[c] - best);
+            gamma = rcp_fast(sum);
             chosen = int(first + bi);
             local = 8 * local + bi;
             cmx = bx; cmy = by; cmz = bz;

@@ -23,6 +23,26 @@
 
 namespace hgmm {
 
+// ------------------------------------------------- FP32 special functions
+// 2^x and 1/x by the multi-function unit's approximations (PTX ex2.approx /
+// rcp.approx, .ftz): one instruction each.  The E-step and the descent take
+// exponentials of max-subtracted log2 scores (x <= 0; a result below the
+// smallest normal flushes to zero, a negligible posterior) and one
+// reciprocal of a posterior sum in [1, 8]; the approximations' relative
+// errors (about 2^-22 and 2^-23) are below the FP32 rounding that the
+// moment sums carry anyway.
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_fast(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---------------------------------------------------------------- FP32 sums
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
