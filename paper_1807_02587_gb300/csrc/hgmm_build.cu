@@ -175,6 +175,7 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
     for (int v = 0; v < 10; ++v) in[v] = make_float2(0.f, 0.f);
     int nfold = 0;
     int cur = -1, run = -1;
+    bool live = false;
     ChildPair cp;
     int it = ib;
     for (; it < ie; ++it) {
@@ -188,6 +189,7 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
             cur = w.parent;
             run = it;
             load_child_pair(est_lvl + 8 * cur + 2 * k, cp);
+            live = parent_has_live_child(cp);
         }
         const int st = (it - ib) % ESTEP_STAGES;
         const uint32_t parity = uint32_t((it - ib) / ESTEP_STAGES) & 1u;
@@ -195,12 +197,13 @@ k_estep(const float4* __restrict__ pts, const Item* __restrict__ items,
         // (in bounds, discarded): the CTA's vote at the end of the item stops it
         const bool landed = tc::mbar_wait_bounded(&full[st], parity, tc::MBAR_SPIN_LIMIT);
         const float4* zs = stage[st];
-        for (int base = 0; base < w.count; base += 64) {
+        // a parent without a live child: zero posteriors, nothing to add
+        for (int base = 0; live && base < w.count; base += 64) {
             const int idx = base + warp * 8 + q;
             const bool valid = idx < w.count;
             const float4 z = zs[min(idx, w.count - 1)];
             estep_point_pair(cp, z, valid, in);
-            if (++nfold == 16) {
+            if (++nfold == EST_FOLD) {
                 fold_pair_smem<COMP>(in, acc_s, acc_c);
                 nfold = 0;
             }

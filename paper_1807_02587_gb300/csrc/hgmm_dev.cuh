@@ -334,7 +334,7 @@ struct ItemCalc {
 // Lane layout: a quad of 4 lanes handles one point, lane k of the quad owns
 // children 2k and 2k+1 (their constants live in registers); a warp handles 8
 // points per step, the CTA (EST_THREADS) 64.  Each lane accumulates the 10
-// moments of its two children: plain FP32 over up to 16 points, then
+// moments of its two children: plain FP32 over up to EST_FOLD points, then
 // folded into a compensated (sum, error) pair.
 struct ChildRegs {
     float mx, my, mz, C, w00, w10, w11, w20, w21, w22;
@@ -444,23 +444,31 @@ __device__ __forceinline__ void fold_pair(float2 (&in)[10], float2 (&s)[10], flo
     }
 }
 
-// One E-step point of a quad lane: Eq. 3 posteriors of the point over the
-// parent's 8 children (this lane holds two, its quad the rest: max and sum
-// by shuffles) and the lane's two children's moments.
+// Whether the parent whose children this quad lane holds (cp) has a live
+// child: all lanes of the warp work on the same parent, so a warp vote
+// answers for the quad.  A parent without one (a leaf) carries its points
+// down with zero posteriors, so its items need no E-step arithmetic.
+__device__ __forceinline__ bool parent_has_live_child(const ChildPair& cp) {
+    return __any_sync(FULL, cp.nC.x < CUDART_INF_F || cp.nC.y < CUDART_INF_F);
+}
+
+// One E-step point of a quad lane (parent with a live child): Eq. 3
+// posteriors of the point over the parent's 8 children (this lane holds two,
+// its quad the rest: max and sum by shuffles) and the lane's two children's
+// moments.
 __device__ __forceinline__ void estep_point_pair(const ChildPair& cp, const float4 z, bool valid, float2 (&in)[10]) {
     float2 ex, ey, ez;
     const float2 u = neg_score_pair(cp, z.x, z.y, z.z, ex, ey, ez);
     float umin = fminf(u.x, u.y);
     umin = fminf(umin, __shfl_xor_sync(FULL, umin, 1));
     umin = fminf(umin, __shfl_xor_sync(FULL, umin, 2));
-    const bool any_live = umin < CUDART_INF_F;  // false for a leaf parent
-    const float2 arg = sub2(f2(umin), u);      // = score - max score
-    const float p0 = any_live ? ex2_fast(arg.x) : 0.f;
-    const float p1 = any_live ? ex2_fast(arg.y) : 0.f;
+    const float2 arg = sub2(f2(umin), u);  // = score - max score
+    const float p0 = ex2_fast(arg.x);
+    const float p1 = ex2_fast(arg.y);
     float tot = p0 + p1;
     tot += __shfl_xor_sync(FULL, tot, 1);
     tot += __shfl_xor_sync(FULL, tot, 2);
-    const float rinv = (valid && any_live) ? rcp_fast(tot) : 0.0f;
+    const float rinv = valid ? rcp_fast(tot) : 0.0f;
     accum_pair(in, __fmul2_rn(make_float2(p0, p1), f2(rinv)), ex, ey, ez);
 }
 
@@ -593,6 +601,7 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
     for (int v = 0; v < 10; ++v) { in[v] = make_float2(0.f, 0.f); s[v] = in[v]; c[v] = in[v]; }
     int nfold = 0;
     int cur = -1, run = -1;
+    bool live = false;
     ChildPair cp;
     for (int it = ib; it < ie; ++it) {
         const Item w = items(it);
@@ -605,7 +614,9 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
             cur = w.parent;
             run = it;
             load_child_pair<CG>(est_lvl + 8 * cur + 2 * k, cp);
+            live = parent_has_live_child(cp);
         }
+        if (!live) continue;  // zero posteriors: nothing to add
         float4 znext = pts[w.start + min(warp * 8 + q, w.count - 1)];
         for (int base = 0; base < w.count; base += 64) {
             const int idx = base + warp * 8 + q;
@@ -613,7 +624,7 @@ __device__ __forceinline__ void estep_range(const float4* __restrict__ pts, Item
             const float4 z = znext;
             if (base + 64 < w.count) znext = pts[w.start + min(idx + 64, w.count - 1)];
             estep_point_pair(cp, z, valid, in);
-            if (++nfold == 16) {
+            if (++nfold == EST_FOLD) {
                 fold_pair<COMP>(in, s, c);
                 nfold = 0;
             }
@@ -645,8 +656,10 @@ __device__ __forceinline__ void estep_items_warp(const float4* __restrict__ pts,
 #pragma unroll
         for (int v = 0; v < 20; ++v) { in[v] = 0.f; s[v] = 0.f; c[v] = 0.f; }
         int nfold = 0;
+        // a parent without a live child: zero posteriors, zero partial
+        const bool live = __any_sync(FULL, r0.C > -CUDART_INF_F || r1.C > -CUDART_INF_F);
         float4 znext = pts[w.start + min(q, w.count - 1)];
-        for (int base = 0; base < w.count; base += 8) {
+        for (int base = 0; live && base < w.count; base += 8) {
             const int idx = base + q;
             const bool valid = idx < w.count;
             const float4 z = znext;
@@ -657,16 +670,15 @@ __device__ __forceinline__ void estep_items_warp(const float4* __restrict__ pts,
             float m = fmaxf(s0, s1);
             m = fmaxf(m, __shfl_xor_sync(FULL, m, 1));
             m = fmaxf(m, __shfl_xor_sync(FULL, m, 2));
-            const bool any_live = m > -CUDART_INF_F;  // false for a leaf parent
-            const float p0 = any_live ? ex2_fast(s0 - m) : 0.f;
-            const float p1 = any_live ? ex2_fast(s1 - m) : 0.f;
+            const float p0 = ex2_fast(s0 - m);
+            const float p1 = ex2_fast(s1 - m);
             float tot = p0 + p1;
             tot += __shfl_xor_sync(FULL, tot, 1);
             tot += __shfl_xor_sync(FULL, tot, 2);
-            const float rinv = (valid && any_live) ? rcp_fast(tot) : 0.0f;
+            const float rinv = valid ? rcp_fast(tot) : 0.0f;
             accum10(in, p0 * rinv, e0x, e0y, e0z);
             accum10(in + 10, p1 * rinv, e1x, e1y, e1z);
-            if (++nfold == 16) {
+            if (++nfold == EST_FOLD) {
                 fold20<COMP>(in, s, c);
                 nfold = 0;
             }

@@ -35,6 +35,7 @@ constexpr int NMOM = 10;              // S0, S1 (3), S2 (6 upper)
 constexpr int NPART = J * NMOM;       // 80 moment values per parent run
 constexpr int TILE = 256;             // points per build work item
 constexpr int EST_THREADS = 256;      // build E-step CTA
+constexpr int EST_FOLD = 16;          // E-step points summed in plain FP32 before a compensated fold
 constexpr int OFFSET_SLICE_ITEMS = 1024;  // hand-off scan: items per slice of a large parent
 constexpr int OFFSET_MAX_SLICES = 64;
 constexpr int REG_THREADS = 256;      // registration descent CTA
