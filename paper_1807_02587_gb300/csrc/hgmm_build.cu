@@ -360,7 +360,7 @@ k_em_coop(int level, int n, int n_par, int K, int n_chunks, const float4* __rest
                 const unsigned runs = unsigned((i1 - 1) / C - i0 / C + 1);
                 if (!wait_at_least(cnt + p, unsigned(k + 1) * runs, status, BARRIER_SPIN_LIMIT)) return;
                 // the level-wide M-step's slices, reduced one after another
-                const int ns = mstep_slices(n_par);
+                const int ns = mstep_slices(n_par, n, n_chunks);
                 for (int j = 0; j < ns; ++j)
                     reduce_run_slice<COMP>(i0, i1, C, j, ns, partials, sm.msm, sm.slice[j]);
                 mstep_from_slices<COMP, false>(level, n, p, &sm.slice[0][0], ns, seg_count, root, n_min, stat, est,
@@ -620,11 +620,11 @@ int hgmm_build_impl(hgmm_tree* t, const float4* pts, int64_t n64, int depth,
             {
                 ProfScope ps_(t, K_MSTEP, s);
                 if (comp)
-                    k_mstep<true><<<dim3(n_par, mstep_slices(n_par)), 256, 0, s>>>(
+                    k_mstep<true><<<dim3(n_par, mstep_slices(n_par, n64, G)), 256, 0, s>>>(
                         l, n, t->item_range, t->meta, t->partials, t->seg_count, t->root, p.n_min, t->stat,
                         t->est, t->status, t->mslices, t->mcnt);
                 else
-                    k_mstep<false><<<dim3(n_par, mstep_slices(n_par)), 256, 0, s>>>(
+                    k_mstep<false><<<dim3(n_par, mstep_slices(n_par, n64, G)), 256, 0, s>>>(
                         l, n, t->item_range, t->meta, t->partials, t->seg_count, t->root, p.n_min, t->stat,
                         t->est, t->status, t->mslices, t->mcnt);
             }

@@ -45,8 +45,17 @@ constexpr int TRACE_MAX_ITERS = 64;   // rounds the registration trace can hold
 constexpr int ACC_REPLICAS = 1;       // copies of each node's registration moments
 constexpr int MSTEP_SLICES = 8;        // run slices per parent in the level-wide M-step
 constexpr int MSTEP_SLICED_PARENTS = 64;  // levels with at most this many parents are sliced
+constexpr int MSTEP_SLICE_MIN_RUNS = 32;  // ... when a parent has about this many runs or more
 
-__host__ __device__ inline int mstep_slices(int n_par) { return n_par <= MSTEP_SLICED_PARENTS ? MSTEP_SLICES : 1; }
+// Run slices per parent in the level-wide M-step of a level with n_par
+// parents over n points, the E-step on `grid` CTAs: a parent's runs are
+// about min(items, grid) / n_par; few runs are reduced by one CTA directly.
+__host__ __device__ inline int mstep_slices(int n_par, int64_t n, int grid) {
+    int64_t items = (n + TILE - 1) / TILE;
+    if (items > grid) items = grid;
+    const int64_t runs = items / (n_par > 0 ? n_par : 1);
+    return n_par <= MSTEP_SLICED_PARENTS && runs >= MSTEP_SLICE_MIN_RUNS ? MSTEP_SLICES : 1;
+}
 
 // status bits (device word, OR-ed)
 constexpr int ST_NONFINITE = 1;
