@@ -34,8 +34,9 @@
  *   - No entry point except hgmm_tree_create / hgmm_tree_destroy allocates or
  *     frees device memory, so build + register can be captured in a CUDA graph
  *     (the registration is one cooperative launch).
- *   - Device-side waits are bounded: the registration's grid barriers give up
- *     after about a second, record HGMM_ETIMEOUT and return.
+ *   - Device-side waits are bounded: the registration's arrival and pose
+ *     generation waits give up after about a second, record HGMM_ETIMEOUT and
+ *     return.
  */
 #ifndef HGMM_H
 #define HGMM_H
@@ -64,7 +65,8 @@ typedef struct hgmm_tree hgmm_tree; /* opaque, device-resident, library-owned */
  * the others are this library's readings of the build it cites.
  *   em_iters  : EM iterations per tree level (K, default 8).
  *   n_min     : a child whose expected point count falls below n_min dies
- *               (weight 0) unless it is its parent's heaviest child (default 8).
+ *               (weight 0); a parent whose children all die stays a leaf
+ *               and its points ride down with zero posteriors (default 8).
  *   lam_c     : complexity threshold lambda_c of Algorithm 1 (default 0.01).
  *   eps_rel   : covariances get eps*I with eps = (eps_rel * extent)^2, extent
  *               = bounding-box diagonal of the modelled cloud (default 1e-3).
@@ -197,6 +199,17 @@ int hgmm_tree_export(hgmm_tree* t, int32_t level, double* h_nodes, int64_t cap);
  * (argmax child), in the caller's original point order (n int32). */
 int hgmm_debug_labels(hgmm_tree* t, int32_t level, int32_t* h_labels, int64_t cap);
 
+/* Eq. 3 posteriors (Sec. 3) of every input point over the 8 children of its
+ * parent at `level`, with the parameters the level ended its EM with: the
+ * parent is the point's node of level - 1 (hgmm_debug_labels), or the whole
+ * cloud at level 0, and gamma_c = pi_c N(z | c) / sum_k pi_k N(z | k) over
+ * those 8 children (dead children 0; all 0 for a parent without a live
+ * child).  Computed with the build's FP32 scores.  h_gamma: n x 8 float32
+ * (host, caller-owned), row i = input point i, column c = child 8 p + c;
+ * cap = its capacity in floats.  Needs a complete build (no debug stop).
+ * Errors: HGMM_EINVAL, HGMM_ECAPACITY (cap < 8 n), HGMM_ECUDA. */
+int hgmm_debug_posteriors(hgmm_tree* t, int32_t level, float* h_gamma, int64_t cap);
+
 /* Root statistics of the last build: [n, mu(3), Sigma(6 upper), extent, eps]
  * (12 float64). */
 int hgmm_debug_root(hgmm_tree* t, double* h_root12);
@@ -227,11 +240,13 @@ int hgmm_profile_read(hgmm_tree* t, int32_t kernel, const char** name, double* t
 
 /* Registration phase trace: with hgmm_trace(t, 1) the next hgmm_register
  * (up to 64 rounds) records, per round and per CTA of its cooperative launch,
- * 6 %globaltimer stamps in ns: round start, descent done, first grid barrier
- * passed, node terms done, solve done (only the CTA that solved; 0
- * elsewhere), second grid barrier passed.  hgmm_trace_read synchronises and
- * copies iters x ctas x 6 int64 (cap = capacity in int64) and reports the
- * dimensions.  Tracing only adds the stamps; results are unchanged. */
+ * 6 %globaltimer stamps in ns: round start; descent and moment flush done
+ * (the CTA's arrival); all arrivals seen (only the CTAs that own nodes wait
+ * for them, 0 elsewhere); node terms done (0 on CTAs without nodes); solve
+ * done (only the CTA that solved, 0 elsewhere); the round's pose generation
+ * seen.  hgmm_trace_read synchronises and copies iters x ctas x 6 int64
+ * (cap = capacity in int64) and reports the dimensions.  Tracing only adds
+ * the stamps; results are unchanged. */
 int hgmm_trace(hgmm_tree* t, int32_t enable);
 int hgmm_trace_read(hgmm_tree* t, int64_t* h_events, int64_t cap, int32_t* iters,
                     int32_t* ctas);
@@ -248,12 +263,18 @@ int hgmm_trace_read(hgmm_tree* t, int64_t* h_events, int64_t cap, int32_t* iters
  *   p        : build parameters (NULL = defaults); debug fields ignored
  *   d_out    : 129 float64, device, caller-owned: 8 node records laid out as
  *              in hgmm_tree_export (hard count = -1, no hand-off is run),
- *              then a status word (0, or HGMM_ENONFINITE for NaN/Inf input)
+ *              then a status word the caller must check once the stream has
+ *              run: 0, HGMM_ENONFINITE (NaN/Inf input) or HGMM_ETIMEOUT (a
+ *              bounded wait of the E-step gave up), in that order of
+ *              precedence, as hgmm_sync reports them; with either error the
+ *              nodes are not valid
  * Allocates nothing: its scratch is one static device array (~2.8 MB) that
  * every GPU loading this library holds until exit.  The first call on a
  * device resolves that array's address, so make it before any stream
- * capture.  All calls in the process share the array, so calls that overlap
- * on the GPU (other streams, other threads) race; serialise them.
+ * capture; every later call made outside a capture resolves it again (so a
+ * call after cudaDeviceReset must also come before any capture).  All calls
+ * in the process share the array, so calls that overlap on the GPU (other
+ * streams, other threads) race; serialise them.
  * Asynchronous on `stream`.  Errors: HGMM_EINVAL, HGMM_ECAPACITY, HGMM_ECUDA. */
 int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const hgmm_params* p,
                             void* stream, double* d_out);
@@ -304,12 +325,27 @@ int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params*
 /* Run the planned batch: d_points = all clouds (float4, device), p = build
  * parameters (NULL = defaults), d_T_init = n_pairs x 16 float64 initial
  * transforms (device; NULL = identity), iters registration rounds.  Writes
- * d_T_out (n_pairs x 16 float64, device) and, if not NULL, d_pair_status
- * (n_pairs int32: 0, HGMM_ENONFINITE or HGMM_EDEGENERATE).  One launch on
- * `stream`, graph-capturable.  Errors: HGMM_EINVAL, HGMM_ECUDA. */
+ * d_T_out (n_pairs x 16 float64, device), if not NULL d_pair_status
+ * (n_pairs int32: 0, HGMM_ENONFINITE, HGMM_ETIMEOUT or HGMM_EDEGENERATE,
+ * in that order of precedence), and if not NULL
+ * d_T_hist (n_pairs x iters x 16 float64, device: pair i's pose after round
+ * k at [16 (i iters + k)]).  One launch on `stream`, graph-capturable.
+ * Errors: HGMM_EINVAL, HGMM_ECUDA. */
 int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params* p,
                         const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
-                        int32_t* d_pair_status);
+                        int32_t* d_pair_status, double* d_T_hist);
+
+/* Checking: the tree that the last launch built for pair `pair`, level
+ * `level` (< the pair's depth), as hgmm_tree_export writes it (cap float64
+ * at h_nodes), and its root statistics as hgmm_debug_root writes them.
+ * Every cluster's workspace keeps the tree of the last pair it ran, so a
+ * pair's tree is available only while no later pair has reused its
+ * workspace (a plan of one pair always qualifies).  Synchronous.
+ * Errors: HGMM_EINVAL (bad pair or level, or the tree was overwritten),
+ * HGMM_ECAPACITY, HGMM_ECUDA. */
+int hgmm_batch_debug_tree(const hgmm_batch* b, int32_t pair, int32_t level, double* h_nodes,
+                          int64_t cap);
+int hgmm_batch_debug_root(const hgmm_batch* b, int32_t pair, double* h_root12);
 
 /* Per pair of the last hgmm_batch_register: the Eq. 11 objective of its
  * last round (as hgmm_register_objective), n_pairs float64 to d_obj. */

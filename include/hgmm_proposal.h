@@ -116,6 +116,17 @@ int hgmm_tree_features(hgmm_tree* t, uint16_t* d_feat, double* d_frame, void* st
 int hgmm_batch_features(hgmm_batch* b, const float* d_points, const hgmm_params* p,
                         uint16_t* d_feat, double* d_frame, void* stream);
 
+/* The network's proposal for one pair in a single call: the features and
+ * frames of the source tree `src` and the target tree `tgt` (each as
+ * hgmm_tree_features gives them, depth >= 2), the forward pass and the
+ * decode, i.e. d_T_out (16 float64, device, caller-owned) = the pose that
+ * maps the source cloud into the target's frame, ready to start
+ * hgmm_register on `tgt`.  Uses buffers of the network handle, so calls on
+ * one handle must not overlap.  Enqueued on `stream`; graph-capturable.
+ * Errors: HGMM_EINVAL (a NULL argument, a tree not built or of depth < 2),
+ * HGMM_ECUDA. */
+int hgmm_propose(hgmm_tree* tgt, hgmm_tree* src, hgmm_mlp* m, void* stream, double* d_T_out);
+
 /* Poses (n x 16 float64, row-major 4x4) from network outputs (n x 9) and
  * the per-pair frames (n x 32: source frame, target frame). */
 int hgmm_pose_decode(const float* d_y, const double* d_frames, int32_t n, double* d_T, void* stream);

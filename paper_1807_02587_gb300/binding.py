@@ -80,6 +80,8 @@ def _load():
         "hgmm_tree_export": (ctypes.c_int, [vp, i32, vp, i64]),
         "hgmm_debug_labels": (ctypes.c_int, [vp, i32, vp, i64]),
         "hgmm_debug_root": (ctypes.c_int, [vp, vp]),
+        "hgmm_debug_posteriors": (ctypes.c_int, [vp, i32, vp, i64]),
+        "hgmm_propose": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "hgmm_debug_reg_moments": (ctypes.c_int, [vp, vp, i64]),
         "hgmm_node_count": (i64, [i32]),
         "hgmm_profile": (ctypes.c_int, [vp, i32]),
@@ -92,7 +94,9 @@ def _load():
         "hgmm_batch_plan_ranges": (ctypes.c_int, [vp, i32, vp, vp, vp]),
         "hgmm_batch_set_shape": (ctypes.c_int, [vp, i32]),
         "hgmm_batch_get_shape": (ctypes.c_int, [vp, P(i32), P(i32)]),
-        "hgmm_batch_register": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp]),
+        "hgmm_batch_register": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp, vp]),
+        "hgmm_batch_debug_tree": (ctypes.c_int, [vp, i32, i32, vp, i64]),
+        "hgmm_batch_debug_root": (ctypes.c_int, [vp, i32, vp]),
         "hgmm_batch_autotune": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp]),
         "hgmm_trace_read": (ctypes.c_int, [vp, vp, i64, P(i32), P(i32)]),
         "hgmm_profile_read": (ctypes.c_int, [vp, i32, P(ctypes.c_char_p), P(ctypes.c_double),
@@ -280,6 +284,15 @@ def hgmm_debug_labels(h, level: int, n: int) -> np.ndarray:
     return out
 
 
+def hgmm_debug_posteriors(h, level: int, n: int) -> np.ndarray:
+    """(n, 8) float32 Eq. 3 posteriors of each input point over its parent's
+    children at ``level`` (synchronous)."""
+    out = np.zeros((n, 8), np.float32)
+    _check(_lib.hgmm_debug_posteriors(h, int(level), ctypes.c_void_p(out.ctypes.data), out.size),
+           "hgmm_debug_posteriors")
+    return out
+
+
 def hgmm_debug_root(h) -> np.ndarray:
     out = np.empty(12, dtype=np.float64)
     _check(_lib.hgmm_debug_root(h, ctypes.c_void_p(out.ctypes.data)), "hgmm_debug_root")
@@ -303,7 +316,10 @@ def hgmm_debug_barrier_timeout(h, spin_limit: int, stream=None) -> None:
 
 def hgmm_fit_level0_noalloc(points, prm: hgmm_params | None = None, stream=None, out=None):
     """Allocation-free level-0 GMM fit; `out` is a caller-owned (129,) float64
-    CUDA tensor (8 node records of 16 + a status word), returned."""
+    CUDA tensor (8 node records of 16 + a status word), returned.  The call is
+    asynchronous: once the stream has run, out[128] holds 0 or an HGMM_E*
+    code (non-finite input, a wait that timed out, a degenerate covariance)
+    that the caller must check before using the nodes."""
     import torch
     if out is None:
         raise ValueError("out: a (129,) float64 CUDA tensor owned by the caller is required")
@@ -314,6 +330,23 @@ def hgmm_fit_level0_noalloc(points, prm: hgmm_params | None = None, stream=None,
                                         _stream_ptr(stream), ctypes.c_void_p(out.data_ptr())),
            "hgmm_fit_level0_noalloc")
     return out
+
+
+def _node_dict(a: np.ndarray) -> dict:
+    """(m, 16) exported node records -> named fields (Sigma as (m, 3, 3))."""
+    m = a.shape[0]
+    S = np.empty((m, 3, 3))
+    iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    for k, (i, j) in enumerate(iu):
+        S[:, i, j] = a[:, 4 + k]
+        S[:, j, i] = a[:, 4 + k]
+    return {"pi": a[:, 0], "mu": a[:, 1:4], "Sigma": S, "live": a[:, 10] > 0.5,
+            "count": a[:, 11].astype(np.int64), "complexity": a[:, 12], "lam": a[:, 13:16]}
+
+
+def _root_dict(r: np.ndarray) -> dict:
+    S = np.array([[r[4], r[5], r[6]], [r[5], r[7], r[8]], [r[6], r[8], r[9]]])
+    return {"n": r[0], "mu": r[1:4], "Sigma": S, "extent": r[10], "eps": r[11]}
 
 
 def hgmm_batch_create(max_points: int, max_depth: int, max_pairs: int):
@@ -360,12 +393,31 @@ def hgmm_batch_get_shape(h):
 
 
 def hgmm_batch_register(h, points, T_out, prm: hgmm_params | None = None, T_init=None,
-                        iters: int = 30, stream=None, pair_status=None):
+                        iters: int = 30, stream=None, pair_status=None, T_hist=None):
+    """T_hist (optional): n_pairs x iters x 16 float64 CUDA tensor, the pose
+    of every pair after every round."""
     _check(_lib.hgmm_batch_register(h, _dev_points(points, "points"),
                                     None if prm is None else ctypes.byref(prm), _dptr(T_init),
                                     int(iters), _stream_ptr(stream), _dptr(T_out),
-                                    _dptr(pair_status)), "hgmm_batch_register")
+                                    _dptr(pair_status), _dptr(T_hist)), "hgmm_batch_register")
     return T_out
+
+
+def hgmm_batch_debug_tree(h, pair: int, level: int) -> dict:
+    """Level ``level`` of the tree the last launch built for ``pair`` (the
+    hgmm_tree_export fields), while its workspace still holds it."""
+    m = 8 ** (level + 1)
+    buf = np.zeros((m, HGMM_NODE_DOUBLES), np.float64)
+    _check(_lib.hgmm_batch_debug_tree(h, int(pair), int(level), ctypes.c_void_p(buf.ctypes.data),
+                                      buf.size), "hgmm_batch_debug_tree")
+    return _node_dict(buf)
+
+
+def hgmm_batch_debug_root(h, pair: int) -> dict:
+    r = np.zeros(12, np.float64)
+    _check(_lib.hgmm_batch_debug_root(h, int(pair), ctypes.c_void_p(r.ctypes.data)),
+           "hgmm_batch_debug_root")
+    return _root_dict(r)
 
 
 def hgmm_batch_autotune(h, points, T_out, prm: hgmm_params | None = None, T_init=None,
@@ -531,6 +583,13 @@ def hgmm_tree_features(h, feat, frame, stream=None):
                                    _need(frame, torch.float64, HGMM_FRAME_DOUBLES, "frame"),
                                    _stream_ptr(stream)), "hgmm_tree_features")
     return feat, frame
+
+
+def hgmm_propose(tgt_tree, src_tree, mlp, T_out, stream=None):
+    """The network's initial pose for one pair (16 float64 CUDA tensor) in
+    one library call: features of both trees, forward, decode."""
+    _check(_lib.hgmm_propose(tgt_tree, src_tree, mlp, _stream_ptr(stream), _dptr(T_out)), "hgmm_propose")
+    return T_out
 
 
 def hgmm_pose_decode(y, frames, T, stream=None):
@@ -753,23 +812,16 @@ class Tree:
         hgmm_sync(self.handle, stream)
 
     def export(self, level: int) -> dict:
-        m = 8 ** (level + 1)
-        a = hgmm_tree_export(self.handle, level, m)
-        S = np.empty((m, 3, 3))
-        iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
-        for k, (i, j) in enumerate(iu):
-            S[:, i, j] = a[:, 4 + k]
-            S[:, j, i] = a[:, 4 + k]
-        return {"pi": a[:, 0], "mu": a[:, 1:4], "Sigma": S, "live": a[:, 10] > 0.5,
-                "count": a[:, 11].astype(np.int64), "complexity": a[:, 12], "lam": a[:, 13:16]}
+        return _node_dict(hgmm_tree_export(self.handle, level, 8 ** (level + 1)))
 
     def labels(self, level: int) -> np.ndarray:
         return hgmm_debug_labels(self.handle, level, self.n)
 
+    def posteriors(self, level: int) -> np.ndarray:
+        return hgmm_debug_posteriors(self.handle, level, self.n)
+
     def root(self) -> dict:
-        r = hgmm_debug_root(self.handle)
-        S = np.array([[r[4], r[5], r[6]], [r[5], r[7], r[8]], [r[6], r[8], r[9]]])
-        return {"n": r[0], "mu": r[1:4], "Sigma": S, "extent": r[10], "eps": r[11]}
+        return _root_dict(hgmm_debug_root(self.handle))
 
     def profile(self, enable: bool):
         hgmm_profile(self.handle, enable)

@@ -303,17 +303,7 @@ int hgmm_tree_export(hgmm_tree* t, int32_t level, double* h_nodes, int64_t cap) 
         return HGMM_ECUDA;
     if (!ok(cudaMemcpy(cnt.data(), t->seg_count + off, m * sizeof(int), cudaMemcpyDeviceToHost), "D2H"))
         return HGMM_ECUDA;
-    for (int64_t i = 0; i < m; ++i) {
-        double* o = h_nodes + i * HGMM_NODE_DOUBLES;
-        const NodeStat& s = st[i];
-        o[0] = s.live ? s.pi : 0.0;
-        for (int a = 0; a < 3; ++a) o[1 + a] = s.mu[a];
-        for (int v = 0; v < 6; ++v) o[4 + v] = s.S[v];
-        o[10] = s.live ? 1.0 : 0.0;
-        o[11] = double(cnt[i]);
-        o[12] = s.complexity;
-        for (int a = 0; a < 3; ++a) o[13 + a] = s.lam[a];
-    }
+    for (int64_t i = 0; i < m; ++i) node_record(st[i], cnt[i], h_nodes + i * HGMM_NODE_DOUBLES);
     return HGMM_OK;
 }
 
@@ -329,16 +319,21 @@ int hgmm_debug_labels(hgmm_tree* t, int32_t level, int32_t* h_labels, int64_t ca
     return rc;
 }
 
+int hgmm_debug_posteriors(hgmm_tree* t, int32_t level, float* h_gamma, int64_t cap) {
+    if (!t || !h_gamma || !t->built || level < 0 || level >= t->depth || t->prm.debug_stop_level != 0)
+        return HGMM_EINVAL;
+    if (cap < 8 * t->n) return HGMM_ECAPACITY;
+    if (int rc = check_device(t)) return rc;
+    if (!ok(cudaDeviceSynchronize(), "sync")) return HGMM_ECUDA;
+    return hgmm_debug_posteriors_impl(t, level, h_gamma);
+}
+
 int hgmm_debug_root(hgmm_tree* t, double* h_root12) {
     if (!t || !h_root12 || !t->built) return HGMM_EINVAL;
     RootDev r;
     if (!ok(cudaDeviceSynchronize(), "sync")) return HGMM_ECUDA;
     if (!ok(cudaMemcpy(&r, t->root, sizeof(r), cudaMemcpyDeviceToHost), "D2H")) return HGMM_ECUDA;
-    h_root12[0] = r.n;
-    for (int a = 0; a < 3; ++a) h_root12[1 + a] = r.mu[a];
-    for (int v = 0; v < 6; ++v) h_root12[4 + v] = r.S[v];
-    h_root12[10] = r.extent;
-    h_root12[11] = r.eps;
+    root_record(r, h_root12);
     return HGMM_OK;
 }
 

@@ -54,6 +54,8 @@ struct BatchArgs {
     const int* order;           // [n_pairs] pair to run k-th
     const double* T_init;       // [n_pairs x 16] or null (identity)
     double* T_out;              // [n_pairs x 16]
+    double* T_hist;             // [n_pairs x iters x 16] pose after every round, or null
+    int* ws_pair;               // [clusters] pair whose tree each workspace holds
     int* pair_status;           // [n_pairs] HGMM error code per pair
     double* obj;                // [n_pairs] Eq. 11 objective of the last round, or null
     __nv_bfloat16* feat;        // [n_pairs x 640] target-cloud features, or null
@@ -87,7 +89,7 @@ constexpr size_t BATCH_DYN_SMEM =
 
 // One pair, run by all CTAs of this cluster.
 template <bool COMP>
-__device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::cluster_group& cl,
+__device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair, cg::cluster_group& cl,
                          BuildSmem& bs, RegSmem& rgs, float4* sm_est, unsigned long long* hist) {
     const int cs = int(cl.num_blocks());
     const int rank = int(cl.block_rank());
@@ -98,6 +100,8 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
     const float4* src = a.points + a.src_rng[2 * pair];
     const int n_s = int(a.src_rng[2 * pair + 1] - a.src_rng[2 * pair]);
     const int depth = a.depth[pair];
+    if (rank == 0 && threadIdx.x == 0) a.ws_pair[cid] = pair;
+    double* T_hist = a.T_hist ? a.T_hist + int64_t(16) * a.iters * pair : nullptr;
     // ---- the target's tree (shared with the single-pair build kernel)
     {
         BuildCtx x;
@@ -210,8 +214,12 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
             __syncthreads();
             if (threadIdx.x == 32 && a.obj && it == a.iters - 1) a.obj[pair] = rgs.tot[NTERM - 1];
             if (warp == 0) {
-                const bool solved = warp_solve_update(rgs.tot, w.T, w.Rt, nullptr, it);
-                if (!solved && lane == 0) atomicOr(w.status, ST_DEGENERATE);
+                const bool solved = warp_solve_update(rgs.tot, w.T, w.Rt, T_hist, it);
+                if (!solved && lane == 0) {
+                    atomicOr(w.status, ST_DEGENERATE);
+                    if (T_hist)
+                        for (int k = 0; k < 16; ++k) T_hist[16 * it + k] = w.T[k];
+                }
             }
         }
         cl.sync();
@@ -220,8 +228,10 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int pair, cg::clu
         a.T_out[16 * pair + threadIdx.x] = __ldcg(w.T + threadIdx.x);
         if (threadIdx.x == 0) {
             const int st = __ldcg(w.status);
-            a.pair_status[pair] = (st & ST_NONFINITE) ? HGMM_ENONFINITE
-                                  : (st & ST_DEGENERATE) ? HGMM_EDEGENERATE : HGMM_OK;
+            a.pair_status[pair] = (st & ST_NONFINITE)    ? HGMM_ENONFINITE
+                                  : (st & ST_TIMEOUT)    ? HGMM_ETIMEOUT
+                                  : (st & ST_DEGENERATE) ? HGMM_EDEGENERATE
+                                                         : HGMM_OK;
         }
     }
 }
@@ -246,7 +256,7 @@ __global__ void __launch_bounds__(EST_THREADS, 2) k_batch(BatchArgs a) {
         const int k = *cl.map_shared_rank(&next_pair, 0);
         cl.sync();
         if (k >= a.n_pairs) break;
-        run_pair<COMP>(a, w, a.order[k], cl, bs, rgs, sm_est, hist);
+        run_pair<COMP>(a, w, cid, a.order[k], cl, bs, rgs, sm_est, hist);
     }
 }
 
@@ -266,7 +276,9 @@ struct hgmm_batch {
     int cluster_ctas = 2;      // current cluster shape
     int n_pairs = 0;
     std::vector<void*> allocs;
+    std::vector<BatchWs> ws;        // host copy of the workspace pointers
     BatchWs* d_ws = nullptr;
+    int* d_ws_pair = nullptr;       // per workspace: the pair whose tree it holds (-1: none)
     int64_t* d_tgt_rng = nullptr;
     int64_t* d_src_rng = nullptr;
     int* d_depth = nullptr;
@@ -276,6 +288,7 @@ struct hgmm_batch {
     double* d_obj = nullptr;        // per pair, last registration's objective
     double* d_T_scratch = nullptr;  // poses of a features-only run
     int min_depth = 0;              // of the current plan
+    std::vector<int> h_depth;       // of the current plan, per pair
 };
 
 namespace {
@@ -369,9 +382,11 @@ int hgmm_batch_create(int64_t max_points, int32_t max_depth, int32_t max_pairs, 
            balloc(b, &b->d_src_rng, 2 * int64_t(max_pairs)) && balloc(b, &b->d_depth, max_pairs) &&
            balloc(b, &b->d_order, max_pairs) && balloc(b, &b->d_queue, 1) &&
            balloc(b, &b->d_pair_status, max_pairs) && balloc(b, &b->d_obj, max_pairs) &&
-           balloc(b, &b->d_T_scratch, 16 * int64_t(max_pairs));
+           balloc(b, &b->d_T_scratch, 16 * int64_t(max_pairs)) && balloc(b, &b->d_ws_pair, mc);
     if (good)
-        good = cudaMemcpy(b->d_ws, ws.data(), mc * sizeof(BatchWs), cudaMemcpyHostToDevice) == cudaSuccess;
+        good = cudaMemcpy(b->d_ws, ws.data(), mc * sizeof(BatchWs), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemset(b->d_ws_pair, 0xff, mc * sizeof(int)) == cudaSuccess;
+    b->ws = ws;
     if (!good) {
         hgmm_batch_destroy(b);
         return HGMM_ENOMEM;
@@ -418,6 +433,7 @@ int hgmm_batch_plan_ranges(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_
     if (!good) return HGMM_ECUDA;
     b->n_pairs = n_pairs;
     b->min_depth = min_depth;
+    b->h_depth.assign(h_depth, h_depth + n_pairs);
     return HGMM_OK;
 }
 
@@ -455,7 +471,7 @@ namespace {
 
 int launch_batch(hgmm_batch* b, const float* d_points, const hgmm_params* p, const double* d_T_init,
                  int32_t iters, void* stream, double* d_T_out, int32_t* d_pair_status,
-                 __nv_bfloat16* d_feat, double* d_frame) {
+                 __nv_bfloat16* d_feat, double* d_frame, double* d_T_hist) {
     if (!b || !d_points || !d_T_out || b->n_pairs < 1 || iters < 0) return HGMM_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0) return HGMM_EINVAL;
     int cur = -1;
@@ -476,6 +492,8 @@ int launch_batch(hgmm_batch* b, const float* d_points, const hgmm_params* p, con
     a.order = b->d_order;
     a.T_init = d_T_init;
     a.T_out = d_T_out;
+    a.T_hist = iters > 0 ? d_T_hist : nullptr;
+    a.ws_pair = b->d_ws_pair;
     a.pair_status = d_pair_status ? d_pair_status : b->d_pair_status;
     a.obj = b->d_obj;
     a.feat = d_feat;
@@ -516,9 +534,57 @@ extern "C" {
 
 int hgmm_batch_register(hgmm_batch* b, const float* d_points, const hgmm_params* p,
                         const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
-                        int32_t* d_pair_status) {
+                        int32_t* d_pair_status, double* d_T_hist) {
     return launch_batch(b, d_points, p, d_T_init, iters, stream, d_T_out, d_pair_status, nullptr,
-                        nullptr);
+                        nullptr, d_T_hist);
+}
+
+namespace {
+
+// The workspace that still holds pair `pair`'s tree after the last launch
+// (synchronous), or -1.
+int ws_of_pair(const hgmm_batch* b, int pair) {
+    std::vector<int> wp(b->max_clusters);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(wp.data(), b->d_ws_pair, wp.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -2;
+    for (int c = 0; c < b->max_clusters; ++c)
+        if (wp[c] == pair) return c;
+    return -1;
+}
+
+}  // namespace
+
+int hgmm_batch_debug_tree(const hgmm_batch* b, int32_t pair, int32_t level, double* h_nodes,
+                          int64_t cap) {
+    if (!b || !h_nodes || pair < 0 || pair >= b->n_pairs || level < 0 || level >= b->h_depth[pair])
+        return HGMM_EINVAL;
+    const int64_t m = level_size(level);
+    if (cap < m * HGMM_NODE_DOUBLES) return HGMM_ECAPACITY;
+    const int c = ws_of_pair(b, pair);
+    if (c == -2) return HGMM_ECUDA;
+    if (c < 0) return HGMM_EINVAL;
+    std::vector<NodeStat> st(m);
+    std::vector<int> cnt(m);
+    const int64_t off = level_offset(level);
+    if (cudaMemcpy(st.data(), b->ws[c].stat + off, m * sizeof(NodeStat), cudaMemcpyDeviceToHost) !=
+            cudaSuccess ||
+        cudaMemcpy(cnt.data(), b->ws[c].seg_count + off, m * sizeof(int), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return HGMM_ECUDA;
+    for (int64_t i = 0; i < m; ++i) node_record(st[i], cnt[i], h_nodes + i * HGMM_NODE_DOUBLES);
+    return HGMM_OK;
+}
+
+int hgmm_batch_debug_root(const hgmm_batch* b, int32_t pair, double* h_root12) {
+    if (!b || !h_root12 || pair < 0 || pair >= b->n_pairs) return HGMM_EINVAL;
+    const int c = ws_of_pair(b, pair);
+    if (c == -2) return HGMM_ECUDA;
+    if (c < 0) return HGMM_EINVAL;
+    RootDev r;
+    if (cudaMemcpy(&r, b->ws[c].root, sizeof(r), cudaMemcpyDeviceToHost) != cudaSuccess) return HGMM_ECUDA;
+    root_record(r, h_root12);
+    return HGMM_OK;
 }
 
 int hgmm_batch_objective(const hgmm_batch* b, double* d_obj, void* stream) {
@@ -535,7 +601,7 @@ int hgmm_batch_features(hgmm_batch* b, const float* d_points, const hgmm_params*
     if ((reinterpret_cast<uintptr_t>(d_feat) & 15u) != 0 || (reinterpret_cast<uintptr_t>(d_frame) & 7u) != 0)
         return HGMM_EINVAL;
     return launch_batch(b, d_points, p, nullptr, 0, stream, b->d_T_scratch, nullptr,
-                        reinterpret_cast<__nv_bfloat16*>(d_feat), d_frame);
+                        reinterpret_cast<__nv_bfloat16*>(d_feat), d_frame, nullptr);
 }
 
 int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params* p,
@@ -554,10 +620,10 @@ int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params*
         float ms = -1.f;
         if (clusters_for(shapes[k], true) > 0) {
             // one untimed run, then one timed run of the whole batch
-            rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr);
+            rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr, nullptr);
             if (rc == HGMM_OK) {
                 cudaEventRecord(e0, s);
-                rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr);
+                rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr, nullptr);
                 cudaEventRecord(e1, s);
                 if (cudaEventSynchronize(e1) != cudaSuccess) rc = HGMM_ECUDA;
                 else cudaEventElapsedTime(&ms, e0, e1);

@@ -506,6 +506,55 @@ __global__ void k_labels(int level, int n, const int* __restrict__ perm,
     if (dst >= 0 && dst < n) out[dst] = int(lo);
 }
 
+// ------------------------------------------------------------ posteriors
+// Eq. 3 posteriors of every point over the 8 children of its parent at
+// `level` (the parent being the point's node of level - 1, or the root),
+// from the level's final parameters, with the build's own FP32 scores
+// (log2 domain, maximum subtracted).  A parent without a live child gives
+// zero posteriors, as in the build's E-step.  The points are read in the
+// order of the deepest level's hand-off (pts, perm); children [4 half,
+// 4 half + 4) of input point perm[i] go to out[perm[i]] (float4).
+__global__ void k_posteriors(int level, int depth, int half, int n, const float4* __restrict__ pts,
+                             const int* __restrict__ perm, const int* __restrict__ seg_start,
+                             const NodeEst* __restrict__ est, float4* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int leaf = depth - 1;
+    const int64_t off = d_level_offset(leaf);
+    // node of the deepest level holding sorted position i
+    int64_t lo = 0, hi = (int64_t(1) << (3 * depth)) - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (seg_start[off + mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t parent = level == 0 ? 0 : (lo >> (3 * (leaf - level + 1)));
+    const NodeEst* ch = est + d_level_offset(level) + 8 * parent;
+    const float4 z = pts[i];
+    float sc[8];
+    float mx = -CUDART_INF_F;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        ChildRegs r;
+        load_child(ch + c, r);
+        float ex, ey, ez;
+        sc[c] = child_score(r, z.x, z.y, z.z, ex, ey, ez);
+        mx = fmaxf(mx, sc[c]);
+    }
+    float g[8];
+    float tot = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        g[c] = mx > -CUDART_INF_F ? ex2_fast(sc[c] - mx) : 0.f;
+        tot += g[c];
+    }
+    const float rinv = tot > 0.f ? rcp_fast(tot) : 0.f;
+    const int dst = perm[i];
+    if (dst >= 0 && dst < n)
+        out[dst] = half ? make_float4(g[4] * rinv, g[5] * rinv, g[6] * rinv, g[7] * rinv)
+                        : make_float4(g[0] * rinv, g[1] * rinv, g[2] * rinv, g[3] * rinv);
+}
+
 }  // namespace
 
 }  // namespace hgmm
@@ -680,6 +729,24 @@ int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s)
     return HGMM_OK;
 }
 
+int hgmm_debug_posteriors_impl(hgmm_tree* t, int level, float* h_gamma) {
+    const int n = int(t->n);
+    const int d = t->depth;
+    // the deepest level's hand-off left the points in pts[(d - 1) & 1]; the
+    // other ping-pong buffer (n float4) is free after the build
+    const float4* pts = t->pts[(d - 1) & 1];
+    float4* buf = t->pts[d & 1];
+    for (int half = 0; half < 2; ++half) {
+        k_posteriors<<<(n + 255) / 256, 256>>>(level, d, half, n, pts, t->perm[d - 1], t->seg_start, t->est,
+                                               buf);
+        HGMM_LAUNCH_CHECK();
+        if (cudaMemcpy2D(h_gamma + 4 * half, 8 * sizeof(float), buf, sizeof(float4), sizeof(float4), size_t(n),
+                         cudaMemcpyDeviceToHost) != cudaSuccess)
+            return HGMM_ECUDA;
+    }
+    return HGMM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the level-0 fit.
 //
@@ -727,8 +794,12 @@ __global__ void k_noalloc_out(const NodeStat* __restrict__ stat, const int* __re
         for (int a = 0; a < 3; ++a) o[13 + a] = s.lam[a];
     }
     if (c == 8) {
+        // the codes hgmm_sync reports for a tree, in the same order
         const int st = *status;
-        out[128] = (st & ST_NONFINITE) ? double(HGMM_ENONFINITE) : 0.0;
+        out[128] = (st & ST_NONFINITE)    ? double(HGMM_ENONFINITE)
+                   : (st & ST_TIMEOUT)    ? double(HGMM_ETIMEOUT)
+                   : (st & ST_DEGENERATE) ? double(HGMM_EDEGENERATE)
+                                          : 0.0;
     }
 }
 
@@ -760,17 +831,22 @@ extern "C" int hgmm_fit_level0_noalloc(const float* d_points, int64_t n, const h
     } else {
         hgmm_params_default(&prm);
     }
-    // one-time set-up per device, with that device current: resolve the
-    // scratch array's device address (host code cannot use the symbol itself)
+    // set-up per device, with that device current: resolve the scratch
+    // array's device address (host code cannot use the symbol itself).  Done
+    // on every call made outside a stream capture (cheap; it also picks up a
+    // new context after cudaDeviceReset); a call made while the stream is
+    // being captured uses the address the last such call resolved.
     constexpr int MAX_DEV = 64;
     static NoAllocDevice devs[MAX_DEV];
     static std::mutex mu;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return HGMM_ECUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) return HGMM_ECUDA;
     NoAllocDevice d;
     {
         std::lock_guard<std::mutex> lock(mu);
-        if (!devs[dev].base) {
+        if (!devs[dev].base || cap == cudaStreamCaptureStatusNone) {
             void* ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
                 fprintf(stderr, "hgmm_fit_level0_noalloc: cudaGetSymbolAddress failed\n");

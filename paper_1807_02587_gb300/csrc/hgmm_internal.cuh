@@ -107,6 +107,26 @@ struct ProfRecord {
     cudaEvent_t a, b;
 };
 
+// The exported form of one node (HGMM_NODE_DOUBLES float64, layout in hgmm.h).
+inline void node_record(const NodeStat& s, int count, double* o) {
+    o[0] = s.live ? s.pi : 0.0;
+    for (int a = 0; a < 3; ++a) o[1 + a] = s.mu[a];
+    for (int v = 0; v < 6; ++v) o[4 + v] = s.S[v];
+    o[10] = s.live ? 1.0 : 0.0;
+    o[11] = double(count);
+    o[12] = s.complexity;
+    for (int a = 0; a < 3; ++a) o[13 + a] = s.lam[a];
+}
+
+// The exported form of the root statistics (12 float64, layout in hgmm.h).
+inline void root_record(const RootDev& r, double* o) {
+    o[0] = r.n;
+    for (int a = 0; a < 3; ++a) o[1 + a] = r.mu[a];
+    for (int v = 0; v < 6; ++v) o[4 + v] = r.S[v];
+    o[10] = r.extent;
+    o[11] = r.eps;
+}
+
 __host__ __device__ inline int64_t level_size(int l) { return int64_t(1) << (3 * (l + 1)); }
 __host__ __device__ inline int64_t level_offset(int l) {
     return ((int64_t(1) << (3 * (l + 1))) - 8) / 7;
@@ -203,6 +223,7 @@ int hgmm_register_descent_impl(hgmm_tree* t, const float4* src, int64_t n, const
                                int iters, const hgmm_descent& d, cudaStream_t s, double* T_out,
                                double* T_hist);
 int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s);
+int hgmm_debug_posteriors_impl(hgmm_tree* t, int level, float* h_gamma);
 int hgmm_register_grid(int n_sm);
 int hgmm_em_coop_grid(int n_sm, int est_grid);
 bool hgmm_estep_smem_attr();

@@ -349,6 +349,9 @@ struct hgmm_mlp {
     int* err = nullptr;
     float* ws = nullptr;      // K-slice partials of the weight-gradient products
     long long ws_cap = 0;     // floats
+    bf16* prop_x = nullptr;   // hgmm_propose: one pair's input (1280)
+    double* prop_fr = nullptr;  // ... its frames (source, target: 32)
+    float* prop_y = nullptr;  // ... the network's output (9)
 };
 
 namespace {
@@ -492,7 +495,9 @@ int hgmm_mlp_create(int32_t max_batch, hgmm_mlp** out) {
                 malloc_into(m, &m->Y, B * OUT) && malloc_into(m, &m->dY, B * OUTP) &&
                 malloc_into(m, &m->dYf, B * OUTP) && malloc_into(m, &m->dZ2, B * HID) &&
                 malloc_into(m, &m->dZ1, B * HID) && malloc_into(m, &m->part, size_t(nchunks) * 3 * HID) &&
-                malloc_into(m, &m->loss, 1) && malloc_into(m, &m->err, 1);
+                malloc_into(m, &m->loss, 1) && malloc_into(m, &m->err, 1) &&
+                malloc_into(m, &m->prop_x, IN) && malloc_into(m, &m->prop_fr, 2 * HGMM_FRAME_DOUBLES) &&
+                malloc_into(m, &m->prop_y, 16);
     m->ws_cap = (long long)MAX_SLICES * HID * IN;
     good = good && malloc_into(m, &m->ws, size_t(m->ws_cap));
     good = good && set_gemm_smem();
@@ -641,6 +646,18 @@ int hgmm_tree_features(hgmm_tree* t, uint16_t* d_feat, double* d_frame, void* st
     k_tree_features<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(
         t->root, t->stat, reinterpret_cast<bf16*>(d_feat), d_frame);
     return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
+}
+
+int hgmm_propose(hgmm_tree* tgt, hgmm_tree* src, hgmm_mlp* m, void* stream, double* d_T_out) {
+    if (!tgt || !src || !m || !d_T_out) return HGMM_EINVAL;
+    if (int rc = check_dev(m)) return rc;
+    uint16_t* x = reinterpret_cast<uint16_t*>(m->prop_x);
+    // network input: [features(source), features(target)], frames likewise
+    if (int rc = hgmm_tree_features(src, x, m->prop_fr, stream)) return rc;
+    if (int rc = hgmm_tree_features(tgt, x + HGMM_FEAT_PER_CLOUD, m->prop_fr + HGMM_FRAME_DOUBLES, stream))
+        return rc;
+    if (int rc = hgmm_mlp_forward(m, x, 1, m->prop_y, stream)) return rc;
+    return hgmm_pose_decode(m->prop_y, m->prop_fr, 1, d_T_out, stream);
 }
 
 int hgmm_pose_decode(const float* d_y, const double* d_frames, int32_t n, double* d_T, void* stream) {

@@ -58,11 +58,17 @@ def node_errors(g, o):
 
 def handoff_check(Z, parent, g):
     """GPU labels of a level vs the oracle's argmax under the GPU's own final
-    parameters (teacher forcing).  Returns (n_disagree, n_disagree_not_tie)."""
+    parameters (teacher forcing).  Returns (reference labels, top-two margin
+    per point).  A point whose parent has no live child has no decision to
+    make: it rides down on the parent's first child (margin +inf, so any
+    disagreement there counts as a real one); a point with one live child
+    gets +inf too."""
     pi = np.where(g["live"], g["pi"], 0.0)
     S = O.child_scores(Z, parent, pi, g["mu"], safe_sigma(g))
     srt = np.sort(S, axis=1)
-    margin = srt[:, -1] - srt[:, -2]
+    with np.errstate(invalid="ignore"):
+        margin = srt[:, -1] - srt[:, -2]
+    margin = np.where(np.isfinite(srt[:, -1]), margin, np.inf)
     ref = parent * 8 + np.argmax(S, axis=1)
     return ref, margin
 
@@ -211,3 +217,20 @@ def tree_from_gpu(tree, prm_o, extent):
 def pose_errors(Ta, Tb, extent):
     return (O.rotation_error_deg(Ta[:3, :3], Tb[:3, :3]),
             float(np.linalg.norm(Ta[:3, 3] - Tb[:3, 3]) / extent))
+
+
+def per_round_teacher_forced(ot, Zs, hist, extent, rounds=None, T0=None):
+    """Registration with per-round teacher forcing: for each round k (0-based)
+    the oracle runs one round of Algorithm 1 + Eq. 9-16 on tree ``ot`` from
+    the GPU's pose after round k-1 (``T0``, default identity, for k = 0) and
+    is compared with the GPU's pose after round k.  Works whether or not the
+    trajectory converges.  Returns [(k, rot_deg, trans_rel)]."""
+    n = hist.shape[0]
+    rounds = range(n) if rounds is None else rounds
+    out = []
+    for k in rounds:
+        Tprev = (np.eye(4) if T0 is None else T0) if k == 0 else hist[k - 1]
+        T_o = O.register(ot, Zs, T_init=Tprev, iters=1)
+        r, t = pose_errors(hist[k], T_o, extent)
+        out.append((k, r, t))
+    return out

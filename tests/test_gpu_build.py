@@ -4,6 +4,7 @@ parent parameters) - GMM-tree build of Sec. 3 / Sec. 4.1, Eq. 2-3."""
 import numpy as np
 import pytest
 
+from oracle import hgmm_oracle as O
 from paper_1807_02587_gb300 import synth
 from tests import parity as PT
 
@@ -140,3 +141,37 @@ def test_node_eigen_decomposition_is_fp64_accurate(B, case):
         worst_c = max(worst_c, float(np.abs(e["complexity"][live] - cplx).max(initial=0)))
     print(case, "eigenvalue rel err", worst_l, "complexity err", worst_c)
     assert worst_l < 1e-11 and worst_c < 1e-11
+
+
+@pytest.mark.parametrize("name", ["corner", "lidar"])
+def test_debug_posteriors_match_oracle(B, name):
+    """hgmm_debug_posteriors: the Eq. 3 posteriors of every point over its
+    parent's children at every level, element by element against the
+    oracle's (log-sum-exp in FP64) under the GPU's own parameters and parent
+    labels (teacher forcing).  FP32 scores carry an absolute error of about
+    1e-7 of the squared Mahalanobis distance, which moves a posterior by at
+    most a quarter of it."""
+    if name == "corner":
+        P, depth = synth.corner_pair(2)["tgt"], 3
+    else:
+        P, depth = synth.lidar_pair(0)["tgt"], 4
+    dev, Z = PT.device_cloud(P)
+    tree = B.Tree(Z.shape[0], depth)
+    tree.build(dev, depth)
+    tree.sync()
+    N = Z.shape[0]
+    parent = np.zeros(N, np.int64)
+    for l in range(depth):
+        g = tree.export(l)
+        got = tree.posteriors(l).astype(np.float64)
+        pi = np.where(g["live"], g["pi"], 0.0)
+        ref, _ = O.posteriors(O.child_scores(Z, parent, pi, g["mu"], PT.safe_sigma(g)))
+        err = np.abs(got - ref)
+        leaf = ~np.isfinite(O.child_scores(Z, parent, pi, g["mu"], PT.safe_sigma(g)).max(axis=1))
+        print(f"{name} level {l}: max |dgamma| {err.max():.2e}, p99.9 {np.percentile(err, 99.9):.2e}, "
+              f"leaf-parent points {int(leaf.sum())}")
+        assert np.all(got[leaf] == 0.0)
+        sums = got[~leaf].sum(axis=1)
+        assert np.all(np.abs(sums - 1.0) < 1e-5)
+        assert err.max() < 1e-3 and np.percentile(err, 99.9) < 1e-5, (l, err.max())
+        parent = tree.labels(l).astype(np.int64)

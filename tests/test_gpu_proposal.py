@@ -346,3 +346,46 @@ def test_batch_objective_matches_single_pair(B):
         B.hgmm_register_objective(tree.handle, o1)
         tree.sync()
         assert abs(ob[i].item() - o1.item()) < 1e-4 * o1.item(), (i, ob[i].item(), o1.item())
+
+
+def test_propose_single_call(B):
+    """hgmm_propose (features of both trees, forward, decode in one library
+    call) gives the pose the composed calls give, bit for bit, and the
+    oracle's pose from the same trees: oracle features (BF16-rounded) ->
+    FP64 network with BF16 storage points -> decode."""
+    import os
+    import torch
+    from paper_1807_02587_gb300 import proposal as P
+    p = synth.so3_pairs(77, 1, 20000)[0]
+    tgt, _ = PT.device_cloud(p["tgt"])
+    src, _ = PT.device_cloud(p["src"])
+    tt, st = B.Tree(20000, 3), B.Tree(20000, 3)
+    tt.build(tgt, 3)
+    st.build(src, 3)
+    params = np.load(os.path.join(os.path.dirname(P.__file__), "weights", "proposal_mlp.npz"))["params"]
+    net = B.Mlp(4)
+    B.hgmm_mlp_set_params(net.handle, params)
+    T1 = torch.zeros(16, dtype=torch.float64, device="cuda")
+    B.hgmm_propose(tt.handle, st.handle, net.handle, T1)
+    feat = torch.zeros((1, 1280), dtype=torch.bfloat16, device="cuda")
+    frame = torch.zeros((1, 32), dtype=torch.float64, device="cuda")
+    B.hgmm_tree_features(st.handle, feat[0, :640], frame[0, :16])
+    B.hgmm_tree_features(tt.handle, feat[0, 640:], frame[0, 16:])
+    y = torch.zeros((1, 9), dtype=torch.float32, device="cuda")
+    B.hgmm_mlp_forward(net.handle, feat, y)
+    T2 = torch.zeros((1, 16), dtype=torch.float64, device="cuda")
+    B.hgmm_pose_decode(y, frame, T2)
+    B.hgmm_mlp_sync(net.handle)
+    T1 = T1.cpu().numpy().reshape(4, 4)
+    assert np.array_equal(T1, T2.cpu().numpy().reshape(4, 4))
+    # oracle from the same trees
+    rs, rt = st.root(), tt.root()
+    Fs, frs = M.features(_oracle_levels(st), rs["mu"], rs["Sigma"])
+    Ft, frt = M.features(_oracle_levels(tt), rt["mu"], rt["Sigma"])
+    X = M.bf16(np.concatenate([Fs, Ft])[None].astype(np.float32))
+    y_o, _ = M.forward(params.astype(np.float64), X, act_bf16=True)
+    T_o = M.decode(y_o[0], frs, frt)
+    r, t = PT.pose_errors(T1, T_o, 1.0)
+    print(f"hgmm_propose vs oracle: {r:.2e} deg, {t:.2e} (scene units); "
+          f"vs truth {PT.pose_errors(T1, p['T_gt'], 1.0)}")
+    assert r < 0.2 and t < 2e-3, (r, t)

@@ -57,7 +57,7 @@ def test_register_on_gpu_tree_matches_oracle(B, name):
     assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (r, t)
 
 
-@pytest.mark.parametrize("name", ["lidar", "corner_small"])
+@pytest.mark.parametrize("name", ["lidar", "corner_small", "depth"])
 def test_first_round_moments_match_oracle(B, name):
     p, depth = _pair(name)
     tree, Zt, Zs, T_gpu, _ = _gpu_run(B, p, depth, 1)
@@ -108,4 +108,86 @@ def test_gmm_tree_variant_lambda_zero(B):
     ot = PT.tree_from_gpu(tree, PT.oracle_params(B.params(), depth), extent)
     T_or = O.register(ot, Zs, iters=10, lam_c=0.0)
     r, t = PT.pose_errors(T_gpu, T_or, extent)
+    assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (r, t)
+
+
+# ---- configs as stated: corner scene at <= 30 deg / t <= 0.1 (10k points,
+# depth 3), and the structured-light depth pair (~276k points, depth 4)
+def _per_round(B, p, depth, iters=30, rounds=None):
+    tree, Zt, Zs, T_gpu, hist = _gpu_run(B, p, depth, iters)
+    extent = tree.root()["extent"]
+    ot = PT.tree_from_gpu(tree, PT.oracle_params(B.params(), depth), extent)
+    errs = PT.per_round_teacher_forced(ot, Zs, hist, extent, rounds)
+    return tree, Zt, Zs, T_gpu, errs, extent
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_corner_30deg_per_round_teacher_forced(B, seed):
+    """Every one of 30 rounds, started from the GPU's own previous pose on the
+    GPU's tree, matches one oracle round (Algorithm 1 + Eq. 9-16) within
+    0.01 deg / 1e-4 extent, whether or not the trajectory converges."""
+    p = synth.corner_pair(seed)
+    _, _, _, T_gpu, errs, extent = _per_round(B, p, 3)
+    worst_r = max(e[1] for e in errs)
+    worst_t = max(e[2] for e in errs)
+    print(f"corner seed {seed}: worst per-round {worst_r:.2e} deg / {worst_t:.2e};"
+          f" GPU vs truth {PT.pose_errors(T_gpu, p['T_gt'], extent)}")
+    assert worst_r < PT.ROT_TOL_DEG and worst_t < PT.TRANS_TOL_REL, errs
+
+
+def test_corner_30deg_free_running_where_well_conditioned(B):
+    """Free-running (oracle build + register against GPU build + register)
+    on the seeds 0..9 of the 30-degree corner configuration whose trajectory
+    is determined to FP32 precision: the oracle run on the input perturbed
+    by 1e-7 relative (about FP32 rounding) ends within a quarter of the
+    tolerance of the unperturbed oracle run.  On this scene the method as
+    read does not reach the ground truth from these poses (its fixed point
+    moves even with source = target), and most trajectories amplify a 1e-7
+    perturbation to 0.01-0.3 deg over 30 rounds; those seeds are compared
+    round by round by the teacher-forced test instead."""
+    prm_o = PT.oracle_params(B.params(), 3)
+    compared = 0
+    for seed in range(10):
+        p = synth.corner_pair(seed)
+        tree, Zt, Zs, T_gpu, _ = _gpu_run(B, p, 3, 30)
+        ot = O.build_tree(Zt, prm_o)
+        T_or = O.register(ot, Zs, iters=30)
+        rng = np.random.default_rng(seed)
+        Ztp = Zt * (1.0 + PT.COND_PERTURB * rng.standard_normal(Zt.shape))
+        Zsp = Zs * (1.0 + PT.COND_PERTURB * rng.standard_normal(Zs.shape))
+        T_p = O.register(O.build_tree(Ztp, prm_o), Zsp, iters=30)
+        cr, ct = PT.pose_errors(T_or, T_p, ot.extent)
+        r, t = PT.pose_errors(T_gpu, T_or, ot.extent)
+        print(f"corner seed {seed}: oracle response to 1e-7 input perturbation {cr:.1e} deg / {ct:.1e}; "
+              f"GPU vs oracle {r:.1e} deg / {t:.1e}")
+        if cr > PT.ROT_TOL_DEG / 4 or ct > PT.TRANS_TOL_REL / 4:
+            continue
+        compared += 1
+        assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (seed, r, t)
+    assert compared >= 1
+
+
+def test_depth_pair_per_round_teacher_forced(B):
+    """Config-3 structured-light pair (depth 4, ~276k points): every round of
+    30 against one oracle round from the GPU's previous pose."""
+    p = synth.depth_pair(0)
+    _, _, _, T_gpu, errs, extent = _per_round(B, p, 4)
+    worst_r = max(e[1] for e in errs)
+    worst_t = max(e[2] for e in errs)
+    print(f"depth pair: worst per-round {worst_r:.2e} deg / {worst_t:.2e};"
+          f" GPU vs truth {PT.pose_errors(T_gpu, p['T_gt'], extent)}")
+    assert worst_r < PT.ROT_TOL_DEG and worst_t < PT.TRANS_TOL_REL, errs
+
+
+def test_depth_pair_free_running(B):
+    """Config-3 pair free-running: oracle build + register against GPU build +
+    register (final pose)."""
+    p = synth.depth_pair(0)
+    tree, Zt, Zs, T_gpu, _ = _gpu_run(B, p, 4, 30)
+    prm_o = PT.oracle_params(B.params(), 4)
+    ot = O.build_tree(Zt, prm_o)
+    T_or = O.register(ot, Zs, iters=30)
+    r, t = PT.pose_errors(T_gpu, T_or, ot.extent)
+    print("depth pair free-running GPU vs oracle:", r, t, "oracle vs truth:",
+          PT.pose_errors(T_or, p["T_gt"], ot.extent))
     assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (r, t)
