@@ -19,6 +19,40 @@ def _rand_spd(rng, scale=1.0):
     return scale * (A @ A.T + 0.3 * np.eye(3))
 
 
+# ------------------------------------------------- root statistics (Sec. 3)
+def test_root_stats_closed_form_box_vertices():
+    """The whole-cloud Gaussian that seeds the tree (Children(-1) of
+    Algorithm 1 are fitted inside it) and the extent that sets the
+    regulariser: the 8 vertices of an axis-aligned box with sides (2, 4, 6)
+    centred at c, each repeated k times, have mean c, population covariance
+    diag(1, 4, 9) (every coordinate is +-half a side with equal weight;
+    the N-1 sample form would give 8k/(8k-1) times that) and bounding-box
+    diagonal sqrt(2^2 + 4^2 + 6^2) = sqrt(56); a rigid motion moves the mean
+    with it, rotates the covariance to R diag R^T and leaves the extent of
+    an axis-aligned box's bounding box unchanged under a translation."""
+    c = np.array([0.3, -1.2, 5.0])
+    half = np.array([1.0, 2.0, 3.0])
+    V = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)], float)
+    for k in (1, 3):
+        Z = np.repeat(c + V * half, k, axis=0)
+        mu, Sig, ext = O.root_stats(Z)
+        assert np.allclose(mu, c, atol=1e-14)
+        assert np.allclose(Sig, np.diag([1.0, 4.0, 9.0]), atol=1e-13)
+        assert abs(ext - np.sqrt(56.0)) < 1e-13
+    # rotated box: covariance R diag R^T; the bounding box of the rotated
+    # vertices is wider than the box (extent = diagonal of that box)
+    R = S.axis_angle_matrix(np.array([0.0, 0.0, 1.0]), np.pi / 2)
+    Z = (c + V * half) @ R.T
+    mu, Sig, ext = O.root_stats(Z)
+    assert np.allclose(mu, R @ c, atol=1e-13)
+    assert np.allclose(Sig, np.diag([4.0, 1.0, 9.0]), atol=1e-13)  # x and y sides swapped
+    assert abs(ext - np.sqrt(56.0)) < 1e-13
+    R45 = S.axis_angle_matrix(np.array([0.0, 0.0, 1.0]), np.pi / 4)
+    _, _, ext45 = O.root_stats((V * half) @ R45.T)
+    # extents of the rotated rectangle's bounding box along x and y: (2 + 4)/sqrt(2) each
+    assert abs(ext45 - np.sqrt(2 * (6.0 / np.sqrt(2)) ** 2 + 6.0 ** 2)) < 1e-12
+
+
 # ---------------------------------------------------------------- Eq. 2 / Eq. 3
 def test_log_gauss_matches_scipy_density():
     """Eq. 2: the oracle's Gaussian log-density equals scipy's independent
