@@ -480,6 +480,7 @@ def batched_section(args, B, synth, torch, prm):
     with torch.cuda.stream(s):
         tune_ms = B.hgmm_batch_autotune(bat.handle, pts, T, prm, None, ITERS, stream=s)
     shape, clusters = B.hgmm_batch_get_shape(bat.handle)
+    build_shape, build_ms = B.hgmm_batch_get_build_shape(bat.handle)
 
     def run():
         B.hgmm_batch_register(bat.handle, pts, T, prm, None, ITERS, stream=s, pair_status=st)
@@ -542,6 +543,11 @@ def batched_section(args, B, synth, torch, prm):
         "pairs_le_0p1deg_per_s": float(np.sum(ok_b)) / (ms / 1e3),
         "ms_per_batch": ms, "cluster_ctas": shape, "clusters": clusters,
         "autotune_ms_by_cluster_ctas_1_2_4_8": tune_ms, "graph": note,
+        "build_shape_by_bucket": {f"bucket{k}_{lab}": {"warp_item_parents": int(build_shape[k][0]),
+                                                       "mstep_cta_runs": int(build_shape[k][1]),
+                                                       "offsets_cta_items": int(build_shape[k][2])}
+                                  for k, lab in enumerate(("tgt_lt_20k", "tgt_20k_80k", "tgt_ge_80k"))},
+        "autotune_ms_default_vs_tuned_build_shape": build_ms,
         "plain_pairs_per_s": len(sub) / (plain_ms / 1e3), "plain_subset": len(sub),
         "plain_pairs_le_0p1deg_per_s": float(np.sum(ok_p)) / (plain_ms / 1e3),
         "speedup_vs_plain": (n / (ms / 1e3)) / (len(sub) / (plain_ms / 1e3)),

@@ -314,10 +314,33 @@ int hgmm_batch_plan_ranges(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_
 int hgmm_batch_set_shape(hgmm_batch* b, int32_t cluster_ctas);
 int hgmm_batch_get_shape(const hgmm_batch* b, int32_t* cluster_ctas, int32_t* clusters);
 
-/* Autotuner: runs the planned batch (arguments as hgmm_batch_register) once
- * untimed and once timed with CUDA events for every cluster shape, keeps
- * the fastest and writes the four times (ms; -1 if a shape cannot be
- * resident) to h_ms4.  Synchronous. */
+/* Build shape of the pairs of one size bucket (by target points: bucket 0
+ * below 20,000, bucket 1 below 80,000, bucket 2 the rest): a level runs one
+ * warp per E-step work item when it has at least warp_item_parents x
+ * (cluster CTAs) parents (else each CTA takes a contiguous chunk of items);
+ * a parent's M-step runs on a whole CTA from mstep_cta_runs E-step runs up
+ * (else on one warp); its child offsets on a whole CTA from
+ * offsets_cta_items items up (else on one warp).  The shapes change only the
+ * summation order of the E-step and M-step sums.  Defaults 4, 8, 64.
+ * Applies to the current plan and later ones.  Errors: HGMM_EINVAL. */
+#define HGMM_BATCH_BUCKETS 3
+int hgmm_batch_set_build_shape(hgmm_batch* b, int32_t bucket, int32_t warp_item_parents,
+                               int32_t mstep_cta_runs, int32_t offsets_cta_items);
+/* The three build-shape values of each bucket (9 int32, bucket-major) and
+ * the last autotune's whole-batch times (2 float, ms): default build shape
+ * at the chosen cluster shape, tuned build shape (-1 before any autotune). */
+int hgmm_batch_get_build_shape(const hgmm_batch* b, int32_t* h_shape9, float* h_ms2);
+
+/* Autotuner over the planned batch (arguments as hgmm_batch_register;
+ * synchronous).  (1) Cluster shape: every shape runs the whole batch once
+ * untimed and once timed (CUDA events) at the default build shape; the
+ * fastest is kept and the four times (ms; -1 if a shape cannot be
+ * resident) go to h_ms4.  (2) Build shape per size bucket, one value at a
+ * time over a fixed candidate list: each candidate runs on every pair, the
+ * launch records each pair's device time, and every bucket keeps the
+ * candidate whose pairs took the least total time.  (3) The tuned build
+ * shape is kept only if the whole batch is at least as fast as with the
+ * default one (both times: hgmm_batch_get_build_shape). */
 int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params* p,
                         const double* d_T_init, int32_t iters, void* stream, double* d_T_out,
                         float* h_ms4);

@@ -96,6 +96,8 @@ def _load():
         "hgmm_batch_get_shape": (ctypes.c_int, [vp, P(i32), P(i32)]),
         "hgmm_batch_register": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp, vp]),
         "hgmm_batch_debug_tree": (ctypes.c_int, [vp, i32, i32, vp, i64]),
+        "hgmm_batch_set_build_shape": (ctypes.c_int, [vp, i32, i32, i32, i32]),
+        "hgmm_batch_get_build_shape": (ctypes.c_int, [vp, vp, vp]),
         "hgmm_batch_debug_root": (ctypes.c_int, [vp, i32, vp]),
         "hgmm_batch_autotune": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp]),
         "hgmm_trace_read": (ctypes.c_int, [vp, vp, i64, P(i32), P(i32)]),
@@ -428,6 +430,25 @@ def hgmm_batch_autotune(h, points, T_out, prm: hgmm_params | None = None, T_init
                                     int(iters), _stream_ptr(stream), _dptr(T_out), ms),
            "hgmm_batch_autotune")
     return list(ms)
+
+
+HGMM_BATCH_BUCKETS = 3
+
+
+def hgmm_batch_set_build_shape(h, bucket: int, warp_item_parents: int, mstep_cta_runs: int,
+                               offsets_cta_items: int) -> None:
+    _check(_lib.hgmm_batch_set_build_shape(h, int(bucket), int(warp_item_parents), int(mstep_cta_runs),
+                                           int(offsets_cta_items)), "hgmm_batch_set_build_shape")
+
+
+def hgmm_batch_get_build_shape(h):
+    """((3, 3) int32 build shape per size bucket, [default ms, tuned ms] of the
+    last autotune)."""
+    sh = np.zeros(9, np.int32)
+    ms = np.zeros(2, np.float32)
+    _check(_lib.hgmm_batch_get_build_shape(h, ctypes.c_void_p(sh.ctypes.data), ctypes.c_void_p(ms.ctypes.data)),
+           "hgmm_batch_get_build_shape")
+    return sh.reshape(3, 3), [float(ms[0]), float(ms[1])]
 
 
 def hgmm_batch_objective(h, out, stream=None):

@@ -56,6 +56,8 @@ struct BatchArgs {
     double* T_out;              // [n_pairs x 16]
     double* T_hist;             // [n_pairs x iters x 16] pose after every round, or null
     int* ws_pair;               // [clusters] pair whose tree each workspace holds
+    const int* knobs;           // [n_pairs x 3] build phase shape of each pair (BuildCtx fields)
+    unsigned long long* pair_ns;  // [n_pairs] each pair's run time in ns, or null
     int* pair_status;           // [n_pairs] HGMM error code per pair
     double* obj;                // [n_pairs] Eq. 11 objective of the last round, or null
     __nv_bfloat16* feat;        // [n_pairs x 640] target-cloud features, or null
@@ -100,7 +102,11 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair
     const float4* src = a.points + a.src_rng[2 * pair];
     const int n_s = int(a.src_rng[2 * pair + 1] - a.src_rng[2 * pair]);
     const int depth = a.depth[pair];
-    if (rank == 0 && threadIdx.x == 0) a.ws_pair[cid] = pair;
+    unsigned long long t_start = 0;
+    if (rank == 0 && threadIdx.x == 0) {
+        a.ws_pair[cid] = pair;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+    }
     double* T_hist = a.T_hist ? a.T_hist + int64_t(16) * a.iters * pair : nullptr;
     // ---- the target's tree (shared with the single-pair build kernel)
     {
@@ -132,6 +138,9 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair
         x.item_off = w.item_off;
         x.root_part = w.root_part;
         x.status = w.status;
+        x.warp_item_parents = a.knobs[3 * pair];
+        x.mstep_cta_runs = a.knobs[3 * pair + 1];
+        x.offsets_cta_items = a.knobs[3 * pair + 2];
         build_levels<COMP>(x, rank, cs, bs, [&]() {
             cl.sync();
             return true;
@@ -232,6 +241,11 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair
                                   : (st & ST_TIMEOUT)    ? HGMM_ETIMEOUT
                                   : (st & ST_DEGENERATE) ? HGMM_EDEGENERATE
                                                          : HGMM_OK;
+            if (a.pair_ns) {
+                unsigned long long t_end;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+                a.pair_ns[pair] = t_end - t_start;
+            }
         }
     }
 }
@@ -289,6 +303,13 @@ struct hgmm_batch {
     double* d_T_scratch = nullptr;  // poses of a features-only run
     int min_depth = 0;              // of the current plan
     std::vector<int> h_depth;       // of the current plan, per pair
+    std::vector<int> h_bucket;      // of the current plan, per pair (target size bucket)
+    // build phase shape per size bucket (warp-item parents factor, M-step CTA
+    // runs, child-offset CTA items) and per pair on the device
+    int knobs[HGMM_BATCH_BUCKETS][3];
+    int* d_knobs = nullptr;
+    unsigned long long* d_pair_ns = nullptr;
+    float tune_ms[2] = {-1.f, -1.f};  // last autotune: default shape, tuned shape (ms per batch)
 };
 
 namespace {
@@ -382,7 +403,13 @@ int hgmm_batch_create(int64_t max_points, int32_t max_depth, int32_t max_pairs, 
            balloc(b, &b->d_src_rng, 2 * int64_t(max_pairs)) && balloc(b, &b->d_depth, max_pairs) &&
            balloc(b, &b->d_order, max_pairs) && balloc(b, &b->d_queue, 1) &&
            balloc(b, &b->d_pair_status, max_pairs) && balloc(b, &b->d_obj, max_pairs) &&
-           balloc(b, &b->d_T_scratch, 16 * int64_t(max_pairs)) && balloc(b, &b->d_ws_pair, mc);
+           balloc(b, &b->d_T_scratch, 16 * int64_t(max_pairs)) && balloc(b, &b->d_ws_pair, mc) &&
+           balloc(b, &b->d_knobs, 3 * int64_t(max_pairs)) && balloc(b, &b->d_pair_ns, max_pairs);
+    for (int k = 0; k < HGMM_BATCH_BUCKETS; ++k) {
+        b->knobs[k][0] = BUILD_WARP_ITEM_PARENTS;
+        b->knobs[k][1] = BUILD_MSTEP_CTA_RUNS;
+        b->knobs[k][2] = BUILD_OFFSETS_CTA_ITEMS;
+    }
     if (good)
         good = cudaMemcpy(b->d_ws, ws.data(), mc * sizeof(BatchWs), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemset(b->d_ws_pair, 0xff, mc * sizeof(int)) == cudaSuccess;
@@ -404,6 +431,28 @@ void hgmm_batch_destroy(hgmm_batch* b) {
     cudaSetDevice(cur);
     delete b;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Size bucket of a pair by its target cloud: [0, 20k), [20k, 80k), [80k, ...).
+int size_bucket(int64_t n_tgt) { return n_tgt < 20000 ? 0 : (n_tgt < 80000 ? 1 : 2); }
+
+// Every planned pair's build shape from its bucket's knobs (synchronous).
+int upload_knobs(hgmm_batch* b) {
+    if (b->n_pairs < 1) return HGMM_OK;
+    std::vector<int> k(3 * size_t(b->n_pairs));
+    for (int i = 0; i < b->n_pairs; ++i)
+        for (int j = 0; j < 3; ++j) k[3 * i + j] = b->knobs[b->h_bucket[i]][j];
+    return cudaMemcpy(b->d_knobs, k.data(), k.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess
+               ? HGMM_OK
+               : HGMM_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
 
 int hgmm_batch_plan_ranges(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_rng,
                            const int64_t* h_src_rng, const int32_t* h_depth) {
@@ -434,7 +483,9 @@ int hgmm_batch_plan_ranges(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_
     b->n_pairs = n_pairs;
     b->min_depth = min_depth;
     b->h_depth.assign(h_depth, h_depth + n_pairs);
-    return HGMM_OK;
+    b->h_bucket.resize(n_pairs);
+    for (int i = 0; i < n_pairs; ++i) b->h_bucket[i] = size_bucket(h_tgt_rng[2 * i + 1] - h_tgt_rng[2 * i]);
+    return upload_knobs(b);
 }
 
 int hgmm_batch_plan(hgmm_batch* b, int32_t n_pairs, const int64_t* h_tgt_off,
@@ -494,6 +545,8 @@ int launch_batch(hgmm_batch* b, const float* d_points, const hgmm_params* p, con
     a.T_out = d_T_out;
     a.T_hist = iters > 0 ? d_T_hist : nullptr;
     a.ws_pair = b->d_ws_pair;
+    a.knobs = b->d_knobs;
+    a.pair_ns = b->d_pair_ns;
     a.pair_status = d_pair_status ? d_pair_status : b->d_pair_status;
     a.obj = b->d_obj;
     a.feat = d_feat;
@@ -609,36 +662,120 @@ int hgmm_batch_autotune(hgmm_batch* b, const float* d_points, const hgmm_params*
                         float* h_ms4) {
     if (!b || b->n_pairs < 1) return HGMM_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int shapes[4] = {1, 2, 4, 8};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HGMM_ECUDA;
+    int rc = HGMM_OK;
+    // one untimed run, then one timed run of the whole batch (ms; -1 on failure)
+    auto timed = [&]() -> float {
+        float ms = -1.f;
+        rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr, nullptr);
+        if (rc != HGMM_OK) return ms;
+        cudaEventRecord(e0, s);
+        rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr, nullptr);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = HGMM_ECUDA;
+        else cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // 1. cluster shape, with every bucket at the default build shape
+    int saved[HGMM_BATCH_BUCKETS][3];
+    std::memcpy(saved, b->knobs, sizeof(saved));
+    for (int k = 0; k < HGMM_BATCH_BUCKETS; ++k) {
+        b->knobs[k][0] = BUILD_WARP_ITEM_PARENTS;
+        b->knobs[k][1] = BUILD_MSTEP_CTA_RUNS;
+        b->knobs[k][2] = BUILD_OFFSETS_CTA_ITEMS;
+    }
+    if ((rc = upload_knobs(b)) != HGMM_OK) return rc;
+    const int shapes[4] = {1, 2, 4, 8};
     float best = 1e30f;
     int best_cs = b->cluster_ctas;
-    int rc = HGMM_OK;
     for (int k = 0; k < 4 && rc == HGMM_OK; ++k) {
         b->cluster_ctas = shapes[k];
-        float ms = -1.f;
-        if (clusters_for(shapes[k], true) > 0) {
-            // one untimed run, then one timed run of the whole batch
-            rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr, nullptr);
-            if (rc == HGMM_OK) {
-                cudaEventRecord(e0, s);
-                rc = hgmm_batch_register(b, d_points, p, d_T_init, iters, stream, d_T_out, nullptr, nullptr);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) rc = HGMM_ECUDA;
-                else cudaEventElapsedTime(&ms, e0, e1);
-            }
-        }
+        const float ms = clusters_for(shapes[k], true) > 0 ? timed() : -1.f;
         if (h_ms4) h_ms4[k] = ms;
         if (ms > 0.f && ms < best) {
             best = ms;
             best_cs = shapes[k];
         }
     }
+    b->cluster_ctas = best_cs;
+    b->tune_ms[0] = best;
+    // 2. build shape per size bucket, one knob at a time: every candidate runs
+    // on all pairs, and each bucket keeps the candidate whose pairs took the
+    // least time in total (per-pair device timings of the persistent launch)
+    static const int cand[3][5] = {{1, 2, 4, 8, 1 << 20}, {2, 4, 8, 16, 1 << 20}, {16, 32, 64, 256, 1 << 20}};
+    std::vector<unsigned long long> ns(b->n_pairs);
+    for (int knob = 0; knob < 3 && rc == HGMM_OK; ++knob) {
+        double best_t[HGMM_BATCH_BUCKETS];
+        int best_v[HGMM_BATCH_BUCKETS];
+        for (int k = 0; k < HGMM_BATCH_BUCKETS; ++k) {
+            best_t[k] = 1e300;
+            best_v[k] = b->knobs[k][knob];
+        }
+        const int chosen[HGMM_BATCH_BUCKETS] = {b->knobs[0][knob], b->knobs[1][knob], b->knobs[2][knob]};
+        for (int c = 0; c < 5 && rc == HGMM_OK; ++c) {
+            for (int k = 0; k < HGMM_BATCH_BUCKETS; ++k) b->knobs[k][knob] = cand[knob][c];
+            if ((rc = upload_knobs(b)) != HGMM_OK) break;
+            if (timed() < 0.f) break;
+            if (cudaMemcpy(ns.data(), b->d_pair_ns, ns.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost) != cudaSuccess) {
+                rc = HGMM_ECUDA;
+                break;
+            }
+            double tot[HGMM_BATCH_BUCKETS] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < b->n_pairs; ++i) tot[b->h_bucket[i]] += double(ns[i]);
+            for (int k = 0; k < HGMM_BATCH_BUCKETS; ++k)
+                if (tot[k] < best_t[k]) {
+                    best_t[k] = tot[k];
+                    best_v[k] = cand[knob][c];
+                }
+        }
+        for (int k = 0; k < HGMM_BATCH_BUCKETS; ++k) b->knobs[k][knob] = rc == HGMM_OK ? best_v[k] : chosen[k];
+    }
+    if (rc == HGMM_OK) rc = upload_knobs(b);
+    // 3. the tuned shape against the default one, whole batch; keep the faster
+    if (rc == HGMM_OK) {
+        const float tuned = timed();
+        b->tune_ms[1] = tuned;
+        if (rc == HGMM_OK && !(tuned > 0.f && tuned <= best)) {
+            for (int k = 0; k < HGMM_BATCH_BUCKETS; ++k) {
+                b->knobs[k][0] = BUILD_WARP_ITEM_PARENTS;
+                b->knobs[k][1] = BUILD_MSTEP_CTA_RUNS;
+                b->knobs[k][2] = BUILD_OFFSETS_CTA_ITEMS;
+            }
+            rc = upload_knobs(b);
+        }
+    }
+    if (rc != HGMM_OK) {
+        std::memcpy(b->knobs, saved, sizeof(saved));
+        upload_knobs(b);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->cluster_ctas = best_cs;
     return rc;
+}
+
+int hgmm_batch_set_build_shape(hgmm_batch* b, int32_t bucket, int32_t warp_item_parents,
+                               int32_t mstep_cta_runs, int32_t offsets_cta_items) {
+    if (!b || bucket < 0 || bucket >= HGMM_BATCH_BUCKETS || warp_item_parents < 1 || mstep_cta_runs < 1 ||
+        offsets_cta_items < 1)
+        return HGMM_EINVAL;
+    b->knobs[bucket][0] = warp_item_parents;
+    b->knobs[bucket][1] = mstep_cta_runs;
+    b->knobs[bucket][2] = offsets_cta_items;
+    return upload_knobs(b);
+}
+
+int hgmm_batch_get_build_shape(const hgmm_batch* b, int32_t* h_shape9, float* h_ms2) {
+    if (!b) return HGMM_EINVAL;
+    if (h_shape9)
+        for (int k = 0; k < HGMM_BATCH_BUCKETS; ++k)
+            for (int j = 0; j < 3; ++j) h_shape9[3 * k + j] = b->knobs[k][j];
+    if (h_ms2) {
+        h_ms2[0] = b->tune_ms[0];
+        h_ms2[1] = b->tune_ms[1];
+    }
+    return HGMM_OK;
 }
 
 }  // extern "C"

@@ -1285,7 +1285,16 @@ struct BuildCtx {
     int* item_off;
     float* root_part;            // cs x 32
     int* status;
+    // shape of the phases (the batched form tunes them per cloud size):
+    int warp_item_parents;       // one warp per E-step item when parents >= this x CTAs
+    int mstep_cta_runs;          // a parent's M-step on a whole CTA from this many runs
+    int offsets_cta_items;       // a parent's child offsets on a whole CTA from this many items
 };
+
+// Default phase shape of build_levels.
+constexpr int BUILD_WARP_ITEM_PARENTS = 4;
+constexpr int BUILD_MSTEP_CTA_RUNS = 8;
+constexpr int BUILD_OFFSETS_CTA_ITEMS = 64;
 
 // The top-down build (Sec. 3, Sec. 4.1 and the readings of the hot path) run
 // by cs CTAs of rank 0..cs-1 that meet at sync() between phases: root
@@ -1332,7 +1341,7 @@ __device__ bool build_levels(const BuildCtx& x, int rank, int cs, BuildSmem& bs,
         const int K = stop_here ? x.stop_iters : x.em_iters;
         // many small parents per CTA: one warp per item, every item its own
         // run (C = 1); otherwise each CTA takes a chunk of C items
-        const bool warp_items = n_par >= 4 * cs;
+        const bool warp_items = n_par >= x.warp_item_parents * cs;
         const int Crun = warp_items ? 1 : C;
         for (int k = 0; k < K; ++k) {
             if (warp_items)
@@ -1344,14 +1353,14 @@ __device__ bool build_levels(const BuildCtx& x, int rank, int cs, BuildSmem& bs,
             if (!sync()) return false;
             for (int p = prank; p < n_par; p += cs) {
                 const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
-                if (i0 < i1 && (i1 - 1) / Crun - i0 / Crun + 1 >= 8)
+                if (i0 < i1 && (i1 - 1) / Crun - i0 / Crun + 1 >= x.mstep_cta_runs)
                     mstep_parent<COMP>(l, x.n, p, i0, i1, Crun, x.partials, x.seg_count, x.root,
                                        x.n_min, x.stat, x.est, x.status, bs.msm);
             }
             __syncthreads();
             for (int p = prank + cs * warp; p < n_par; p += cs * wpb) {
                 const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
-                if (i0 < i1 && (i1 - 1) / Crun - i0 / Crun + 1 < 8)
+                if (i0 < i1 && (i1 - 1) / Crun - i0 / Crun + 1 < x.mstep_cta_runs)
                     mstep_parent_warp<COMP>(l, x.n, p, i0, i1, Crun, x.partials, x.seg_count, x.root,
                                             x.n_min, x.stat, x.est, x.status, bs.wmom[warp]);
             }
@@ -1364,13 +1373,13 @@ __device__ bool build_levels(const BuildCtx& x, int rank, int cs, BuildSmem& bs,
         if (!sync()) return false;
         for (int p = prank; p < n_par; p += cs) {  // parents with many items: a whole CTA
             const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
-            if (i1 - i0 >= 64) child_offsets_cta(l, p, i0, i1, items(i0).start, x.item_cnt, x.item_off,
+            if (i1 - i0 >= x.offsets_cta_items) child_offsets_cta(l, p, i0, i1, items(i0).start, x.item_cnt, x.item_off,
                                                  x.seg_start, x.seg_count, bs.os);
         }
         __syncthreads();
         for (int p = prank + cs * warp; p < n_par; p += cs * wpb) {
             const int i0 = __ldcg(x.item_range + 2 * p), i1 = __ldcg(x.item_range + 2 * p + 1);
-            if (i1 - i0 >= 64) continue;
+            if (i1 - i0 >= x.offsets_cta_items) continue;
             const int pstart = i0 < i1 ? items(i0).start
                                        : (l == 0 ? 0 : __ldcg(x.seg_start + level_offset(l - 1) + p));
             child_offsets_warp(l, p, i0, i1, pstart, x.item_cnt, x.item_off, x.seg_start, x.seg_count);

@@ -117,3 +117,45 @@ def test_batch_plan_rejects_bad_pairs(B):
         B.hgmm_batch_plan(bat.handle, np.array([0, 100], np.int64),
                           np.array([100, 200], np.int64), [5])
     assert e.value.code == B.HGMM_EINVAL
+
+
+def test_batch_build_shapes_agree_and_autotune_reports(B):
+    """Every build shape the autotuner can choose (warp-per-item E-step
+    threshold, M-step and child-offset CTA thresholds per size bucket) gives
+    the same first-round pose as the default shape up to the summation order
+    of the E-step and M-step sums; the autotuner reports its choice and the
+    whole-batch times of the default and tuned shapes."""
+    import torch
+    pairs = _pairs(3, 9, 2000, 120000)
+    buf, t_off, s_off = _layout(pairs)
+    n = len(pairs)
+    pts = torch.from_numpy(buf).cuda()
+    bat = B.Batch(int(max(np.diff(t_off).max(), np.diff(s_off).max())), 4, n)
+    B.hgmm_batch_plan(bat.handle, t_off, s_off, [p["depth"] for p in pairs])
+    B.hgmm_batch_set_shape(bat.handle, 2)
+
+    def run():
+        T = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
+        st = torch.full((n,), 99, dtype=torch.int32, device="cuda")
+        B.hgmm_batch_register(bat.handle, pts, T, iters=1, pair_status=st)
+        torch.cuda.synchronize()
+        assert np.all(st.cpu().numpy() == 0)
+        return T.cpu().numpy().reshape(n, 4, 4)
+
+    ref = run()
+    for shape in ((1, 2, 16), (1 << 20, 1 << 20, 1 << 20), (2, 16, 256), (8, 4, 32)):
+        for k in range(B.HGMM_BATCH_BUCKETS):
+            B.hgmm_batch_set_build_shape(bat.handle, k, *shape)
+        T = run()
+        for i, p in enumerate(pairs):
+            ext = np.linalg.norm(p["tgt"].max(0) - p["tgt"].min(0))
+            r, t = PT.pose_errors(T[i], ref[i], ext)
+            assert r < 1e-4 and t < 1e-6, (shape, i, r, t)
+    with pytest.raises(B.HgmmError):
+        B.hgmm_batch_set_build_shape(bat.handle, 3, 4, 8, 64)
+    Tt = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
+    ms = B.hgmm_batch_autotune(bat.handle, pts, Tt, iters=3)
+    shape, ms2 = B.hgmm_batch_get_build_shape(bat.handle)
+    print("cluster times", ms, "build shape per bucket", shape.tolist(), "default / tuned ms", ms2)
+    assert ms2[0] > 0 and ms2[1] > 0
+    assert np.all(shape >= 1)
