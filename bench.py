@@ -924,6 +924,9 @@ def main():
     ap.add_argument("--profile-mlp", action="store_true",
                     help="only run the proposal network (5 forwards of 8192 pairs, 3 training "
                          "steps of 1024), for a profiler")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="P",
+                    help="only run the batched launch on the first P pairs of the batched workload "
+                         "(2 launches: warm-up, then the one to capture), for a profiler")
     ap.add_argument("--ncu", action="store_true",
                     help="only run warm-up + eager steps (for an ncu launch list)")
     args = ap.parse_args()
@@ -935,6 +938,8 @@ def main():
         return reference_main(args, rank, world)
     if args.profile_mlp:
         return profile_mlp_main()
+    if args.profile_batch:
+        return profile_batch_main(args)
     if args.profile_variants:
         return profile_variants_main(args)
     if args.profile_build:
@@ -975,6 +980,43 @@ def profile_variants_main(args):
         tree.register_descent(src, B.HGMM_DESCENT_ML_LOCAL, 0.0, iters=2, full_eq7=True)
     tree.sync()
     print(json.dumps({"profile_variants": True, "J": flat.export()["J"]}))
+    return 0
+
+
+def profile_batch_main(args):
+    """The batched launch alone on the first P pairs of the bench's batched
+    workload (same seed, depth, cluster shape 8), twice; prints the
+    algorithmic bytes of one launch: every EM iteration of every level reads
+    each target point (16 B), the hand-off reads it again and writes it, and
+    every registration round reads each source point (16 B)."""
+    import torch
+    from paper_1807_02587_gb300 import binding as B
+    from paper_1807_02587_gb300 import synth
+    pairs = synth.batched_pairs(args.seed + 100, count=256)[: args.profile_batch]
+    tb = [synth.to_float4(p["tgt"]) for p in pairs]
+    sb = [synth.to_float4(p["src"]) for p in pairs]
+    t_off = np.concatenate([[0], np.cumsum([x.shape[0] for x in tb])]).astype(np.int64)
+    s_off = (np.concatenate([[0], np.cumsum([x.shape[0] for x in sb])]) + t_off[-1]).astype(np.int64)
+    n = len(pairs)
+    pts = torch.from_numpy(np.concatenate(tb + sb)).cuda()
+    bat = B.Batch(int(max(np.diff(t_off).max(), np.diff(s_off).max())), 4, n)
+    B.hgmm_batch_plan(bat.handle, t_off, s_off, [p["depth"] for p in pairs])
+    B.hgmm_batch_set_shape(bat.handle, 8)
+    T = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
+    prm = B.params()
+    for _ in range(2):
+        B.hgmm_batch_register(bat.handle, pts, T, prm, None, ITERS)
+    torch.cuda.synchronize()
+    nt = np.diff(t_off)
+    ns = np.diff(s_off)
+    depth = np.array([p["depth"] for p in pairs])
+    estep = int(np.sum(16 * nt * prm.em_iters * depth))
+    handoff = int(np.sum(2 * 16 * nt * depth))
+    reg = int(np.sum(16 * ns * ITERS))
+    print(json.dumps({"profile_batch": True, "pairs": n, "target_points": int(nt.sum()),
+                      "source_points": int(ns.sum()), "device_bytes_inputs": int(pts.numel() * 4),
+                      "algorithmic_bytes_per_launch": {"estep": estep, "handoff": handoff,
+                                                       "register": reg, "total": estep + handoff + reg}}))
     return 0
 
 

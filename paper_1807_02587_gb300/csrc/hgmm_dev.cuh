@@ -1501,8 +1501,13 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
     const float r12 = Rt_sm[5], r20 = Rt_sm[6], r21 = Rt_sm[7], r22 = Rt_sm[8];
     const float tx = Rt_sm[9], ty = Rt_sm[10], tz = Rt_sm[11];
     const int wpb = blockDim.x >> 5;
-    const int warps_total = ncta * wpb;
-    for (int base = (cta * wpb + warp) * 32; base < n; base += warps_total * 32) {
+    // 32-point chunks dealt round-robin to the CTAs (chunk j to CTA j mod
+    // ncta), then to the CTA's warps: every CTA, and so every SM, gets the
+    // same number of chunks to within one, drawn from the whole cloud (the
+    // descent's depth, and so a chunk's cost, varies along a scan)
+    const int nchunk = (n + 31) >> 5;
+    for (int ch = cta + ncta * warp; ch < nchunk; ch += ncta * wpb) {
+        const int base = ch * 32;
         const int i = base + lane;
         const bool valid = i < n;
         float4 z = valid ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);

@@ -15,6 +15,8 @@
 //   dW1 = dZ1^T x               M = 256, N = 1280, K = batch
 //   db = column sums of dZ1, dZ2, dY (two-pass, fixed order: deterministic)
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <mutex>
 
 #include <algorithm>
 #include <cmath>
@@ -384,10 +386,51 @@ int gemm_launch(const GemmArgs& g, int slices, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
 }
 
-// D = A B^T with the fused epilogue of g.  N <= 16 runs 128 x 16 tiles,
-// larger N 128 x 128 tiles.  When the tiles alone cannot fill the GPU and K
-// is long (the weight gradients: K = batch), K is cut into 64-multiple
-// slices whose FP32 partials go to ws and are summed in a fixed order.
+// cuTensorMapEncodeTiled from the driver (resolved once), or null.
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of a K-contiguous BF16 operand (rows x K, row stride rs
+// elements): dimensions (K, rows), box 64 x box_rows, 128-byte swizzle,
+// zeros outside the matrix.
+bool encode_operand(CUtensorMap* tm, const bf16* base, long long rs, int rows, int K, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(rs) * sizeof(bf16)};
+    const cuuint32_t box[2] = {cuuint32_t(tc::GEMM_BK), cuuint32_t(box_rows)};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+int gemm_tma_launch(const GemmArgs& g, const CUtensorMap& ta, const CUtensorMap& tb, cudaStream_t s) {
+    const dim3 grid((g.M + tc::GEMM_BM - 1) / tc::GEMM_BM, (g.N + BN - 1) / BN);
+    tc::k_gemm_tma<BN><<<grid, tc::GEMM_THREADS, tc::tma_smem_bytes(BN), s>>>(ta, tb, g);
+    return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
+}
+
+// D = A B^T with the fused epilogue of g.  Both operands K-contiguous and
+// no K slices: the warp-specialised TMA kernel.  Otherwise the cp.async
+// kernel: N <= 16 runs 128 x 16 tiles, larger N 128 x 128 tiles; when the
+// tiles alone cannot fill the GPU and K is long (the weight gradients: K =
+// batch), K is cut into 64-multiple slices whose FP32 partials go to ws and
+// are summed in a fixed order.
 int gemm(GemmArgs g, cudaStream_t s, float* ws = nullptr, long long ws_cap = 0) {
     if (g.M < 1 || g.N < 1 || g.K < 1 || !operand_ok(g.A, g.a_m, g.a_k, g.M, g.K) ||
         !operand_ok(g.B, g.b_n, g.b_k, g.N, g.K))
@@ -399,6 +442,16 @@ int gemm(GemmArgs g, cudaStream_t s, float* ws = nullptr, long long ws_cap = 0) 
     if (ws && g.epi == tc::EPI_F32 && tiles < 128) slices = std::min(std::min(MAX_SLICES, kt), (304 + tiles - 1) / tiles);
     g.k_split = ((kt + slices - 1) / slices) * tc::GEMM_BK;
     slices = (g.K + g.k_split - 1) / g.k_split;
+    if (slices <= 1 && g.a_k == 1 && g.b_k == 1) {
+        // (operand_ok has checked 16-byte bases and row strides % 8 == 0)
+        CUtensorMap ta, tb;
+        if (encode_operand(&ta, g.A, g.a_m, g.M, g.K, tc::GEMM_BM) &&
+            encode_operand(&tb, g.B, g.b_n, g.N, g.K, bn)) {
+            g.k_split = g.K;
+            g.split_stride = 0;
+            return bn == 16 ? gemm_tma_launch<16>(g, ta, tb, s) : gemm_tma_launch<128>(g, ta, tb, s);
+        }
+    }
     if (slices <= 1) {
         g.split_stride = 0;
         return bn == 16 ? gemm_launch<16>(g, 1, s) : gemm_launch<128>(g, 1, s);
@@ -462,7 +515,11 @@ bool set_gemm_smem() {
     return cudaFuncSetAttribute(tc::k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::gemm_smem_bytes(128)) == cudaSuccess &&
            cudaFuncSetAttribute(tc::k_gemm_bf16<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::gemm_smem_bytes(16)) == cudaSuccess;
+                                tc::gemm_smem_bytes(16)) == cudaSuccess &&
+           cudaFuncSetAttribute(tc::k_gemm_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::tma_smem_bytes(128)) == cudaSuccess &&
+           cudaFuncSetAttribute(tc::k_gemm_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::tma_smem_bytes(16)) == cudaSuccess;
 }
 
 int check_dev(const hgmm_mlp* m) {

@@ -271,6 +271,133 @@ __global__ void k_barrier_timeout_probe(unsigned* bar, int* status, long long li
     }
 }
 
+// ------------------------------------------------ source reorder (large clouds)
+// A large source cloud in arbitrary order sends each warp's 32 points down
+// ~20 different paths of the tree, so the descent adds its moments with one
+// atomic group per node and warp.  Before the rounds, such a cloud is
+// counting-sorted (into a library buffer) by the cell of a 16 x 16 x 16 grid
+// over the target's extent that it occupies under the starting pose, in
+// Morton order, so that a warp's points are neighbours and share most of
+// their path.  The node moments are exact integer sums of per-warp FP32
+// group sums, so the order of the points changes the result only by the
+// FP32 rounding of those group sums.
+constexpr int REORDER_MIN_POINTS = 1 << 20;
+constexpr int REORDER_BITS = 4;                           // cells per axis: 16
+constexpr int REORDER_KEYS = 1 << (3 * REORDER_BITS);     // 4096
+constexpr int REORDER_THREADS = 256;
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // bits b -> 3b (4 bits)
+    v &= 0xFu;
+    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6);
+}
+
+// Morton key of a transformed point's cell in the box mean +- extent / 2.
+__device__ __forceinline__ uint32_t cell_key(float x, float y, float w, float cx, float cy, float cz,
+                                             float inv_cell) {
+    auto q = [&](float v, float c) {
+        const float f = (v - c) * inv_cell + float(1 << (REORDER_BITS - 1));
+        const int k = f >= 0.f ? int(f) : 0;  // NaN -> 0
+        return uint32_t(k > (1 << REORDER_BITS) - 1 ? (1 << REORDER_BITS) - 1 : k);
+    };
+    return spread3(q(x, cx)) | (spread3(q(y, cy)) << 1) | (spread3(q(w, cz)) << 2);
+}
+
+// Contiguous range of points of CTA b (of nb).
+__device__ __forceinline__ void cta_range(int n, int b, int nb, int& lo, int& hi) {
+    lo = int((int64_t(b) * n) / nb);
+    hi = int((int64_t(b + 1) * n) / nb);
+}
+
+// Pass 1: each point's key (to keys) and each CTA's key counts (cnt[b][key]).
+__global__ void __launch_bounds__(REORDER_THREADS) k_src_keys(const float4* __restrict__ src, int n,
+                                                              const RootDev* __restrict__ root,
+                                                              const float* __restrict__ Rt,
+                                                              uint32_t* __restrict__ keys, int* __restrict__ cnt) {
+    __shared__ int h[REORDER_KEYS];
+    __shared__ float R[12];
+    for (int k = threadIdx.x; k < REORDER_KEYS; k += blockDim.x) h[k] = 0;
+    if (threadIdx.x < 12) R[threadIdx.x] = Rt[threadIdx.x];
+    __syncthreads();
+    const float cx = float(root->mu[0]), cy = float(root->mu[1]), cz = float(root->mu[2]);
+    const float ext = float(root->extent);
+    const float inv_cell = ext > 0.f ? float(1 << REORDER_BITS) / ext : 0.f;
+    int lo, hi;
+    cta_range(n, blockIdx.x, gridDim.x, lo, hi);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const float4 z = src[i];
+        const float x = fmaf(R[0], z.x, fmaf(R[1], z.y, fmaf(R[2], z.z, R[9])));
+        const float y = fmaf(R[3], z.x, fmaf(R[4], z.y, fmaf(R[5], z.z, R[10])));
+        const float w = fmaf(R[6], z.x, fmaf(R[7], z.y, fmaf(R[8], z.z, R[11])));
+        const uint32_t key = cell_key(x, y, w, cx, cy, cz, inv_cell);
+        keys[i] = key;
+        atomicAdd(&h[key], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < REORDER_KEYS; k += blockDim.x) cnt[int64_t(blockIdx.x) * REORDER_KEYS + k] = h[k];
+}
+
+// Pass 2a (one thread per key): cnt[b][key] becomes the exclusive prefix
+// over the CTAs b of that key's counts, and tot[key] the key's total.
+__global__ void k_src_colscan(int* __restrict__ cnt, int nb, int* __restrict__ tot) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= REORDER_KEYS) return;
+    int s = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int c = cnt[int64_t(b) * REORDER_KEYS + k];
+        cnt[int64_t(b) * REORDER_KEYS + k] = s;
+        s += c;
+    }
+    tot[k] = s;
+}
+
+// Pass 2b (one CTA of 1024 threads): tot[key] becomes the exclusive prefix
+// over the keys (keys in order, CTAs in order within a key).
+__global__ void __launch_bounds__(1024) k_src_keyscan(int* __restrict__ tot) {
+    constexpr int PER = REORDER_KEYS / 1024;
+    __shared__ int part[1024];
+    int v[PER], s = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        v[j] = tot[threadIdx.x * PER + j];
+        s += v[j];
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int u = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += u;
+        __syncthreads();
+    }
+    int base = part[threadIdx.x] - s;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        tot[threadIdx.x * PER + j] = base;
+        base += v[j];
+    }
+}
+
+// Pass 3: every point to its key's next slot of its CTA (shared-memory
+// counters: the order within a CTA's key is not fixed, so neither are the
+// per-warp FP32 group sums, to their rounding).
+__global__ void __launch_bounds__(REORDER_THREADS) k_src_scatter(const float4* __restrict__ src, int n,
+                                                                 const uint32_t* __restrict__ keys,
+                                                                 const int* __restrict__ cnt,
+                                                                 const int* __restrict__ base,
+                                                                 float4* __restrict__ dst) {
+    __shared__ int pos[REORDER_KEYS];
+    for (int k = threadIdx.x; k < REORDER_KEYS; k += blockDim.x)
+        pos[k] = base[k] + cnt[int64_t(blockIdx.x) * REORDER_KEYS + k];
+    __syncthreads();
+    int lo, hi;
+    cta_range(n, blockIdx.x, gridDim.x, lo, hi);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint32_t key = keys[i] & (REORDER_KEYS - 1);
+        const int slot = atomicAdd(&pos[key], 1);
+        if (slot >= 0 && slot < n) dst[slot] = src[i];
+    }
+}
+
 __global__ void k_copy_T(const double* __restrict__ T, double* __restrict__ out) {
     if (threadIdx.x < 16) out[threadIdx.x] = T[threadIdx.x];
 }
@@ -597,6 +724,23 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         k_reg_init<<<(n_nodes + 255) / 256, 256, 0, s>>>(T_init, n_nodes, lam_c, t->stat, t->est,
                                                           t->reg_acc, t->reg_T, t->reg_Rt,
                                                           t->reg_bar, t->reg_obj);
+    }
+    // a large source that fits the tree's free point buffer is reordered
+    // first: keys in the dead hand-off codes, per-CTA counts and key totals
+    // in the build's partials (both free after the build)
+    // (CTAs: two per SM, fewer if the counts would not fit)
+    const int reorder_ctas =
+        int(std::min<int64_t>(2 * t->n_sm, t->max_items * NPART * 2 / REORDER_KEYS - 1));
+    if (iters > 0 && n >= REORDER_MIN_POINTS && n64 <= t->cap && reorder_ctas >= 32) {
+        ProfScope ps_(t, K_REG_INIT, s);
+        float4* sorted = t->pts[t->depth & 1];
+        int* cnt = reinterpret_cast<int*>(t->partials);
+        int* tot = cnt + int64_t(reorder_ctas) * REORDER_KEYS;
+        k_src_keys<<<reorder_ctas, REORDER_THREADS, 0, s>>>(src, n, t->root, t->reg_Rt, t->codes, cnt);
+        k_src_colscan<<<REORDER_KEYS / 256, 256, 0, s>>>(cnt, reorder_ctas, tot);
+        k_src_keyscan<<<1, 1024, 0, s>>>(tot);
+        k_src_scatter<<<reorder_ctas, REORDER_THREADS, 0, s>>>(src, n, t->codes, cnt, tot, sorted);
+        src = sorted;
     }
     if (iters > 0) {
         RegArgs a;

@@ -191,3 +191,36 @@ def test_depth_pair_free_running(B):
     print("depth pair free-running GPU vs oracle:", r, t, "oracle vs truth:",
           PT.pose_errors(T_or, p["T_gt"], ot.extent))
     assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (r, t)
+
+
+def test_large_unordered_source_is_reordered_without_changing_the_result(B):
+    """A source of at least 2^20 points is counting-sorted by its path
+    through the top of the tree before the rounds.  The node moments are
+    exact integer sums of per-warp FP32 group sums, so the order of the
+    source points moves the pose only by the rounding of those group sums:
+    the same cloud in two random orders gives the same 3 rounds to 1e-6 deg
+    and 1e-8 of the extent, and the first round matches one oracle round on
+    the GPU's tree."""
+    import torch
+    rng = np.random.default_rng(5)
+    p = synth.primitive_pair(17, 1_200_000, max_deg=3.0, max_t=0.02)
+    tgt, Zt = PT.device_cloud(p["tgt"])
+    src4 = synth.to_float4(p["src"])
+    tree = B.Tree(src4.shape[0], 4)
+    tree.build(tgt, 4)
+    outs = []
+    for perm in (rng.permutation(src4.shape[0]), rng.permutation(src4.shape[0])):
+        src = torch.from_numpy(np.ascontiguousarray(src4[perm])).cuda()
+        hist = torch.zeros((3, 4, 4), dtype=torch.float64, device="cuda")
+        tree.register(src, iters=3, T_hist=hist)
+        tree.sync()
+        outs.append(hist.cpu().numpy())
+    extent = tree.root()["extent"]
+    for k in range(3):
+        r, t = PT.pose_errors(outs[0][k], outs[1][k], extent)
+        assert r < 1e-6 and t < 1e-8, (k, r, t)
+    ot = PT.tree_from_gpu(tree, PT.oracle_params(B.params(), 4), extent)
+    Zs = src4[:, :3].astype(np.float64)
+    T_o = O.register(ot, Zs, iters=1)
+    r, t = PT.pose_errors(outs[0][0], T_o, extent)
+    assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (r, t)
