@@ -200,3 +200,52 @@ def test_batch_pair_independent_of_plan(B, run):
         B.hgmm_batch_register(run["bat"].handle, run["pts"], T1, iters=ITERS)
         torch.cuda.synchronize()
         assert np.array_equal(T1.cpu().numpy().reshape(4, 4), run["T"][i]), i
+
+
+def test_learned_refinement_per_round_against_oracle(B):
+    """The learned-proposal configuration: SO(3) pairs of 50k-point clouds,
+    the shipped network's proposal (features -> forward -> decode) as the
+    starting pose, refined at depth 4 for 30 rounds by the batched engine.
+    Every round against one oracle round (Algorithm 1 + Eq. 9-16) on the
+    batched tree from the batched pose of the round before (the first from
+    the proposal itself); free-running against the oracle's registration
+    from the same proposal where the oracle reaches the truth within 0.1
+    deg."""
+    import os
+    import torch
+    from paper_1807_02587_gb300 import proposal as P
+    params = np.load(os.path.join(os.path.dirname(P.__file__), "weights", "proposal_mlp.npz"))["params"]
+    net = B.Mlp(8)
+    B.hgmm_mlp_set_params(net.handle, params)
+    ps = P.so3_test_pairs(9090, 4, 50000)
+    eng = P.Engine(ps, depth=4)
+    T0 = P.propose(net, eng)
+    hist = torch.zeros((ps.n, ITERS, 16), dtype=torch.float64, device="cuda")
+    T = torch.zeros((ps.n, 16), dtype=torch.float64, device="cuda")
+    st = torch.full((ps.n,), 99, dtype=torch.int32, device="cuda")
+    B.hgmm_batch_register(eng.rb.handle, ps.points, T, T_init=T0, iters=ITERS, pair_status=st, T_hist=hist)
+    torch.cuda.synchronize()
+    assert np.all(st.cpu().numpy() == 0)
+    T0 = T0.cpu().numpy().reshape(ps.n, 4, 4)
+    hist = hist.cpu().numpy().reshape(ps.n, ITERS, 4, 4)
+    pts = ps.points.cpu().numpy()[:, :3].astype(np.float64)
+    compared = 0
+    for i in range(ps.n):
+        tr = _export(B, eng.rb, i, 4)
+        ot = _oracle_tree(B, tr, 4)
+        Zs = pts[ps.src_rng[i, 0]:ps.src_rng[i, 1]]
+        extent = tr["root"]["extent"]
+        errs = PT.per_round_teacher_forced(ot, Zs, hist[i], extent, ROUNDS_LARGE, T0=T0[i])
+        print(f"pair {i}: proposal {PT.pose_errors(T0[i], ps.T_gt[i], extent)[0]:.2f} deg from the truth, "
+              f"worst round {max(e[1] for e in errs):.1e} deg / {max(e[2] for e in errs):.1e}")
+        assert all(e[1] < PT.ROT_TOL_DEG and e[2] < PT.TRANS_TOL_REL for e in errs), (i, errs)
+        Zt = pts[ps.tgt_rng[i, 0]:ps.tgt_rng[i, 1]]
+        ob = O.build_tree(Zt, PT.oracle_params(B.params(), 4))
+        T_or = O.register(ob, Zs, T_init=T0[i], iters=ITERS)
+        if PT.pose_errors(T_or, ps.T_gt[i], ob.extent)[0] > 0.1:
+            continue
+        compared += 1
+        r, t = PT.pose_errors(hist[i, -1], T_or, ob.extent)
+        print(f"pair {i}: free-running refinement vs oracle {r:.1e} deg / {t:.1e}")
+        assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (i, r, t)
+    assert compared >= 1
