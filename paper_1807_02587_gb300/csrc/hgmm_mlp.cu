@@ -318,6 +318,243 @@ __global__ void k_compose(int n, const double* __restrict__ A, const double* __r
             o[4 * r + c] = a[4 * r] * b[c] + a[4 * r + 1] * b[4 + c] + a[4 * r + 2] * b[8 + c] + a[4 * r + 3] * b[12 + c];
 }
 
+
+// ---------------------------------------------------------------------------
+// The whole forward pass of one 128-row block in one launch (warp-specialised
+// tcgen05 with TMEM accumulators and TMA operand streams):
+//   layer 1: acc1 (TMEM columns 0..255) = X[128 x 1280] W1^T, 20 K-steps of
+//            TMA-fed 128 x 64 / 256 x 64 tiles in a 4-stage ring;
+//   epilogue warps: h1 = relu(acc1 + b1) as BF16 to H1 (global, for the
+//            backward pass; skipped when H1 is null) and into shared memory
+//            in the 128-byte-swizzled K-major layout that TMA would write,
+//            as layer 2's A operand;
+//   layer 2: acc2 (columns 256..511) = h1 W2^T, W2 tiles streamed by TMA;
+//   epilogue: h2 likewise (H2 if not null, and shared memory over h1);
+//   layer 3: acc3 (columns 0..15) = h2 W3^T (W3 padded to 16 rows);
+//   epilogue: Y = acc3 + b3 (9 columns, FP32).
+// Warps 0-3 are the epilogue (warp w owns TMEM lanes 32w..32w+31, i.e.
+// rows), one thread of warp 4 issues the TMA loads, one thread of warp 5
+// the MMAs.  Every wait is bounded; on a timeout the kernel records the
+// error, lets every role run out (commits and arrivals still happen) and
+// drains its loads in flight before it frees TMEM.
+constexpr int FW_THREADS = 192;
+constexpr int FW_S1 = 4;                          // layer-1 stages
+constexpr int FW_A = 128 * 128;                   // 128 rows x 64 BF16
+constexpr int FW_B = 256 * 128;                   // 256 rows x 64 BF16
+constexpr int FW_STAGE1 = FW_A + FW_B;            // 48 KB
+constexpr int FW_H = 4 * FW_A;                    // 128 x 256 BF16: four 64-wide K chunks (64 KB)
+constexpr int FW_W2_OFF = FW_H;                   // two 32 KB W2 stages after the h buffer
+constexpr int FW_W3_OFF = FW_W2_OFF + 2 * FW_B;   // four 16 x 64 W3 tiles (8 KB)
+constexpr int FW_W3_TILE = 16 * 128;
+constexpr int FW_SMEM = FW_S1 * FW_STAGE1 + 1024; // the h buffer and W2/W3 reuse the layer-1 ring
+static_assert(FW_W3_OFF + 4 * FW_W3_TILE <= FW_S1 * FW_STAGE1, "layer 2/3 buffers inside the ring");
+
+// Row r's 16-byte unit u of a 64-wide K chunk in the 128-byte swizzled layout.
+__device__ __forceinline__ uint32_t sw128_offset(int r, int u) {
+    return uint32_t(r * 128 + ((u ^ (r & 7)) << 4));
+}
+
+// Epilogue of one hidden layer: relu(acc + bias) for this thread's row (all
+// 256 columns) to the global row (16-byte stores, if grow is not null) and
+// to the shared h buffer.
+__device__ __forceinline__ void fw_hidden_epilogue(uint32_t tacc, const float* __restrict__ bias,
+                                                   bf16* __restrict__ grow, uint32_t hbuf, int r) {
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+        float v[64];
+        tc::tmem_ld64(tacc + uint32_t(c * 64), v);
+        const float4* b4 = reinterpret_cast<const float4*>(bias + c * 64);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float4 ba = __ldg(b4 + 2 * u), bb = __ldg(b4 + 2 * u + 1);
+            const float x[8] = {v[8 * u] + ba.x, v[8 * u + 1] + ba.y, v[8 * u + 2] + ba.z, v[8 * u + 3] + ba.w,
+                                v[8 * u + 4] + bb.x, v[8 * u + 5] + bb.y, v[8 * u + 6] + bb.z, v[8 * u + 7] + bb.w};
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const __nv_bfloat162 p2 = __floats2bfloat162_rn(fmaxf(x[2 * h], 0.f), fmaxf(x[2 * h + 1], 0.f));
+                w[h] = *reinterpret_cast<const uint32_t*>(&p2);
+            }
+            if (grow) reinterpret_cast<uint4*>(grow + c * 64)[u] = make_uint4(w[0], w[1], w[2], w[3]);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                         :: "r"(hbuf + uint32_t(c * FW_A) + sw128_offset(r, u)), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                            "r"(w[3]) : "memory");
+        }
+    }
+}
+
+__device__ __forceinline__ bool fw_wait(uint64_t* bar, uint32_t parity, int* fail) {
+    if (*(volatile int*)fail) return false;
+    if (tc::mbar_wait_bounded(bar, parity, tc::MBAR_SPIN_LIMIT)) return true;
+    atomicExch(fail, 1);
+    return false;
+}
+
+__global__ void __launch_bounds__(FW_THREADS, 1)
+k_mlp_forward(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
+              const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmW3,
+              const float* __restrict__ b1, const float* __restrict__ b2, const float* __restrict__ b3p,
+              bf16* __restrict__ H1, bf16* __restrict__ H2, float* __restrict__ Y, int batch,
+              int* __restrict__ err) {
+    extern __shared__ unsigned char fw_raw[];
+    __shared__ __align__(8) uint64_t full1[FW_S1], empty1[FW_S1], full2[2], empty2[2];
+    __shared__ __align__(8) uint64_t full3, done1, done2, done3, h1_ready, h2_ready;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int fail;
+    const uint32_t base = (tc::smem_u32(fw_raw) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * 128;
+    constexpr int NK1 = IN / 64, NK2 = HID / 64;
+    constexpr uint32_t ID1 = tc::idesc_bf16_f32(128, HID), ID3 = tc::idesc_bf16_f32(128, OUTP);
+    if (warp == 4) {
+        tc::tmem_alloc(&tmem_slot, 512);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 160) {
+        for (int i = 0; i < FW_S1; ++i) {
+            tc::mbar_init(&full1[i], 1);
+            tc::mbar_init(&empty1[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full2[i], 1);
+            tc::mbar_init(&empty2[i], 1);
+        }
+        tc::mbar_init(&full3, 1);
+        tc::mbar_init(&done1, 1);
+        tc::mbar_init(&done2, 1);
+        tc::mbar_init(&done3, 1);
+        tc::mbar_init(&h1_ready, 128);
+        tc::mbar_init(&h2_ready, 128);
+        fail = 0;
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&tmX);
+        tc::prefetch_tmap(&tmW1);
+        tc::prefetch_tmap(&tmW2);
+        tc::prefetch_tmap(&tmW3);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t hbuf = base;
+    int issued1 = 0, issued2 = 0;
+    bool issued3 = false;
+    if (threadIdx.x == 128) {
+        // ---- producer
+        for (int kt = 0; kt < NK1; ++kt) {
+            const int st = kt % FW_S1;
+            if (kt >= FW_S1 && !fw_wait(&empty1[st], ((kt / FW_S1) - 1) & 1, &fail)) break;
+            const uint32_t sa = base + st * FW_STAGE1;
+            tc::mbar_arrive_expect_tx(&full1[st], uint32_t(FW_STAGE1));
+            tc::tma_load_2d(sa, &tmX, kt * 64, m0, &full1[st]);
+            tc::tma_load_2d(sa + FW_A, &tmW1, kt * 64, 0, &full1[st]);
+            issued1 = kt + 1;
+        }
+        // layer 2 and 3 operands go where the layer-1 ring was: after its MMAs
+        if (issued1 == NK1 && fw_wait(&done1, 0, &fail)) {
+            tc::mbar_arrive_expect_tx(&full3, uint32_t(4 * FW_W3_TILE));
+            for (int kt = 0; kt < NK2; ++kt)
+                tc::tma_load_2d(base + FW_W3_OFF + kt * FW_W3_TILE, &tmW3, kt * 64, 0, &full3);
+            issued3 = true;
+            for (int kt = 0; kt < NK2; ++kt) {
+                const int st = kt & 1;
+                if (kt >= 2 && !fw_wait(&empty2[st], ((kt >> 1) - 1) & 1, &fail)) break;
+                tc::mbar_arrive_expect_tx(&full2[st], uint32_t(FW_B));
+                tc::tma_load_2d(base + FW_W2_OFF + st * FW_B, &tmW2, kt * 64, 0, &full2[st]);
+                issued2 = kt + 1;
+            }
+        }
+    } else if (threadIdx.x == 160) {
+        // ---- MMA issuer
+        bool ok = true;
+        for (int kt = 0; kt < NK1 && ok; ++kt) {
+            const int st = kt % FW_S1;
+            ok = fw_wait(&full1[st], (kt / FW_S1) & 1, &fail);
+            if (!ok) break;
+            tc::fence_after_sync();
+            const uint32_t sa = base + st * FW_STAGE1;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc::mma_bf16(tmem, tc::smem_desc_sw128(sa + kk * 32), tc::smem_desc_sw128(sa + FW_A + kk * 32), ID1,
+                             (kt | kk) != 0 ? 1u : 0u);
+            tc::mma_commit(&empty1[st]);
+        }
+        tc::mma_commit(&done1);
+        ok = ok && fw_wait(&h1_ready, 0, &fail);
+        for (int kt = 0; kt < NK2 && ok; ++kt) {
+            const int st = kt & 1;
+            ok = fw_wait(&full2[st], (kt >> 1) & 1, &fail);
+            if (!ok) break;
+            tc::fence_after_sync();
+            const uint32_t sb = base + FW_W2_OFF + st * FW_B;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc::mma_bf16(tmem + 256u, tc::smem_desc_sw128(hbuf + kt * FW_A + kk * 32),
+                             tc::smem_desc_sw128(sb + kk * 32), ID1, (kt | kk) != 0 ? 1u : 0u);
+            tc::mma_commit(&empty2[st]);
+        }
+        tc::mma_commit(&done2);
+        ok = ok && fw_wait(&h2_ready, 0, &fail) && fw_wait(&full3, 0, &fail);
+        if (ok) {
+            tc::fence_after_sync();
+            for (int kt = 0; kt < NK2; ++kt)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc::mma_bf16(tmem, tc::smem_desc_sw128(hbuf + kt * FW_A + kk * 32),
+                                 tc::smem_desc_sw128(base + FW_W3_OFF + kt * FW_W3_TILE + kk * 32), ID3,
+                                 (kt | kk) != 0 ? 1u : 0u);
+        }
+        tc::mma_commit(&done3);
+    } else if (warp < 4) {
+        // ---- epilogue: thread = tile row
+        const int r = warp * 32 + lane;
+        const int m = m0 + r;
+        const bool row_ok = m < batch;
+        const uint32_t lanes = uint32_t(warp * 32) << 16;
+        // warp-uniform decisions: the TMEM loads below are warp-collective
+        const bool ok1 = __all_sync(0xffffffffu, fw_wait(&done1, 0, &fail));
+        if (ok1) {
+            tc::fence_after_sync();
+            fw_hidden_epilogue(tmem + lanes, b1, (H1 && row_ok) ? H1 + int64_t(m) * HID : nullptr, hbuf, r);
+            tc::fence_before_sync();
+        }
+        tc::fence_proxy_async();  // the h buffer, written here, is read by the tensor core
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(&h1_ready)) : "memory");
+        const bool ok2 = __all_sync(0xffffffffu, ok1 && fw_wait(&done2, 0, &fail));
+        if (ok2) {
+            tc::fence_after_sync();
+            fw_hidden_epilogue(tmem + lanes + 256u, b2, (H2 && row_ok) ? H2 + int64_t(m) * HID : nullptr, hbuf, r);
+            tc::fence_before_sync();
+        }
+        tc::fence_proxy_async();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(&h2_ready)) : "memory");
+        const bool ok3 = __all_sync(0xffffffffu, ok2 && fw_wait(&done3, 0, &fail));
+        if (ok3) {
+            tc::fence_after_sync();
+            float v[16];
+            tc::tmem_ld16(tmem + lanes, v);
+            if (row_ok)
+#pragma unroll
+                for (int j = 0; j < OUT; ++j) Y[int64_t(m) * OUT + j] = v[j] + b3p[j];
+        }
+    }
+    __syncwarp();
+    if (threadIdx.x == 128) {
+        // loads issued but never consumed: let them land before the CTA exits
+        for (int kt = max(0, issued1 - FW_S1); kt < issued1; ++kt)
+            tc::mbar_wait_bounded(&full1[kt % FW_S1], (kt / FW_S1) & 1, tc::MBAR_SPIN_LIMIT);
+        for (int kt = max(0, issued2 - 2); kt < issued2; ++kt)
+            tc::mbar_wait_bounded(&full2[kt & 1], (kt >> 1) & 1, tc::MBAR_SPIN_LIMIT);
+        if (issued3) tc::mbar_wait_bounded(&full3, 0, tc::MBAR_SPIN_LIMIT);
+    }
+    if (threadIdx.x == 160) tc::mbar_wait_bounded(&done3, 0, tc::MBAR_SPIN_LIMIT);  // MMAs in flight
+    __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int*)&fail) atomicOr(err, ERR_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 4) tc::tmem_dealloc(tmem, 512);
+}
+
 }  // namespace
 }  // namespace hgmm
 
@@ -489,7 +726,22 @@ GemmArgs gargs(const bf16* A, long long a_m, long long a_k, const bf16* B, long 
     return g;
 }
 
-int forward_impl(hgmm_mlp* m, const bf16* X, int batch, float* Y, cudaStream_t s) {
+// The fused forward (one launch for the three layers; the hidden layers go
+// to m->H1 / m->H2 only when the backward pass needs them), or HGMM_ECUDA if
+// its tensor maps cannot be encoded (the caller then runs the three GEMMs).
+int forward_fused(hgmm_mlp* m, const bf16* X, int batch, float* Y, cudaStream_t s, bool keep_hidden) {
+    CUtensorMap tx, t1, t2, t3;
+    if (!encode_operand(&tx, X, IN, batch, IN, 128) || !encode_operand(&t1, m->W1, IN, HID, IN, HID) ||
+        !encode_operand(&t2, m->W2, HID, HID, HID, HID) || !encode_operand(&t3, m->W3, HID, OUTP, HID, OUTP))
+        return HGMM_ECUDA;
+    k_mlp_forward<<<(batch + 127) / 128, FW_THREADS, FW_SMEM, s>>>(tx, t1, t2, t3, m->P + OFF_B1, m->P + OFF_B2,
+                                                                 m->b3p, keep_hidden ? m->H1 : nullptr,
+                                                                 keep_hidden ? m->H2 : nullptr, Y, batch, m->err);
+    return cudaGetLastError() == cudaSuccess ? HGMM_OK : HGMM_ECUDA;
+}
+
+int forward_impl(hgmm_mlp* m, const bf16* X, int batch, float* Y, cudaStream_t s, bool keep_hidden = true) {
+    if (forward_fused(m, X, batch, Y, s, keep_hidden) == HGMM_OK) return HGMM_OK;
     GemmArgs g = gargs(X, IN, 1, m->W1, IN, 1, batch, HID, IN, tc::EPI_BIAS_RELU_BF16, m->err);
     g.bias = m->P + OFF_B1;
     g.out_bf16 = m->H1;
@@ -519,7 +771,8 @@ bool set_gemm_smem() {
            cudaFuncSetAttribute(tc::k_gemm_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::tma_smem_bytes(128)) == cudaSuccess &&
            cudaFuncSetAttribute(tc::k_gemm_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::tma_smem_bytes(16)) == cudaSuccess;
+                                tc::tma_smem_bytes(16)) == cudaSuccess &&
+           cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM) == cudaSuccess;
 }
 
 int check_dev(const hgmm_mlp* m) {
@@ -608,7 +861,8 @@ int hgmm_mlp_read_grads(hgmm_mlp* m, float* h_grads, int64_t count) {
 int hgmm_mlp_forward(hgmm_mlp* m, const uint16_t* d_x, int32_t batch, float* d_y, void* stream) {
     if (!m || !d_x || !d_y || batch < 1 || batch > m->max_batch || !a16(d_x)) return HGMM_EINVAL;
     if (int rc = check_dev(m)) return rc;
-    return forward_impl(m, reinterpret_cast<const bf16*>(d_x), batch, d_y, static_cast<cudaStream_t>(stream));
+    return forward_impl(m, reinterpret_cast<const bf16*>(d_x), batch, d_y, static_cast<cudaStream_t>(stream),
+                        false);
 }
 
 int hgmm_mlp_gradients(hgmm_mlp* m, const uint16_t* d_x, const float* d_labels, const int32_t* d_index,
