@@ -1461,19 +1461,24 @@ __device__ __forceinline__ int warp_group_sum(int key, float (&v)[NV]) {
     const unsigned peers = __match_any_sync(FULL, key);
     const int rank = __popc(peers & ((1u << lane) - 1u));
     const int gsize = __popc(peers);
+    const int gmax = __reduce_max_sync(FULL, unsigned(gsize));
     const unsigned higher = lane == 31 ? 0u : (peers & ~((2u << lane) - 1u));
+    // the member st ranks above this lane (this lane if there is none): the
+    // next member, then doubled by one shuffle per step (the member 2 st
+    // above is the one st above the member st above), valid wherever it is
+    // used (rank + st < gsize)
+    int nxt = higher ? __ffs(higher) - 1 : lane;
 #pragma unroll
     for (int st = 1; st < 32; st <<= 1) {
-        unsigned h = higher;  // lane holding rank + st within my group
-        for (int k = 1; k < st; ++k) h &= h - 1u;
-        const int srcl = h ? __ffs(h) - 1 : lane;
+        if (st >= gmax) break;  // warp-uniform: no group has a member st above
         float o[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) o[q] = __shfl_sync(FULL, v[q], srcl);
+        for (int q = 0; q < NV; ++q) o[q] = __shfl_sync(FULL, v[q], nxt);
         if ((rank & (2 * st - 1)) == 0 && rank + st < gsize) {
 #pragma unroll
             for (int q = 0; q < NV; ++q) v[q] += o[q];
         }
+        nxt = __shfl_sync(FULL, nxt, nxt);
     }
     return rank;
 }
@@ -1522,7 +1527,7 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             float sc8[8];
             float best = -CUDART_INF_F;
             int bi = -1;
-            float bx = 0.f, by = 0.f, bz = 0.f, bstop = 0.f;  // the best child's mean, stop flag
+            float bstop = 0.f;  // the best child's stop flag (its mean is read once, after the descent)
             const bool staged = first < STAGED_NODES;
             const float4* blk = sm_est + (staged ? staged_slot(int(first)) : 0);
 #pragma unroll
@@ -1540,9 +1545,6 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
                 if (sc > best) {
                     best = sc;
                     bi = c;
-                    bx = ea.x;
-                    by = ea.y;
-                    bz = ea.z;
                     bstop = ec.z;
                 }
             }
@@ -1553,10 +1555,13 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             gamma = rcp_fast(sum);
             chosen = int(first + bi);
             local = 8 * local + bi;
-            cmx = bx; cmy = by; cmz = bz;
             if (bstop != 0.f) break;  // Complexity <= lambda_c
         }
         const bool has = chosen >= 0;
+        if (has) {
+            const float4 cm = chosen < STAGED_NODES ? sm_est[staged_slot(chosen)] : __ldg(&est[chosen].a);
+            cmx = cm.x; cmy = cm.y; cmz = cm.z;
+        }
         float v0 = has ? gamma : 0.f;
         float v1 = has ? gamma * (x - cmx) : 0.f;
         float v2 = has ? gamma * (y - cmy) : 0.f;
@@ -1685,13 +1690,19 @@ __host__ __device__ constexpr int up6(int i, int j) { return i * 6 - (i * (i - 1
 // them: lane L < 21 holds upper-packed entry L of H, lanes 21..26 hold g (the
 // layout of tot), and symmetric Gaussian elimination without pivoting (H is
 // positive definite) updates every entry of the trailing block and of g with
-// one multiply and one FMA per pivot; back substitution runs on the g lanes.
-// Pivots are checked with integer compares of their bit patterns (positive,
-// finite, above 1e-15 of the largest diagonal).  T <- dR T + dt with dR from
-// Rodrigues' formula, all in FP64.  Returns false (uniformly) for a
-// non-positive or tiny pivot, leaving T unchanged.
-__device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt, double* T_hist,
-                                         int iter) {
+// one multiply and one FMA per pivot; back substitution runs on the g lanes
+// (rows scaled by their pivot's reciprocal: one FMA per step).  Pivots are
+// checked with integer compares of their bit patterns (positive, finite,
+// above 1e-15 of the largest diagonal, inside [2^-1000, 2^1000]).
+// T <- dR T + dt with dR from Rodrigues' formula, all in FP64.  Returns false
+// (uniformly) for a failed pivot, leaving T unchanged.
+// T_SHARED: T (and Rt) live in this CTA's shared memory (every CTA of the
+// registration solves the same system itself, so the pose needs no
+// publication); T_copy / Rt_copy, if given, receive the new pose too (the
+// global copies one CTA keeps for the caller).
+template <bool T_SHARED = false>
+__device__ __forceinline__ bool warp_solve_update(const double* tot, double* T, float* Rt, double* T_hist,
+                                         int iter, double* T_copy = nullptr, float* Rt_copy = nullptr) {
     const int lane = threadIdx.x & 31;
     // (row, column) of this lane's entry; column 6 = right-hand side, row -1 = idle
     int ri = -1, rj = 0;
@@ -1712,9 +1723,13 @@ __device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt
     double a = lane < 27 ? tot[lane] : 0.0;
     // this lane's column of the current pose, loaded now so that the L2
     // latency overlaps the elimination (entry (rr, cc) below)
-    const int e = lane < 12 ? lane : 11;
+    // (lanes 16..27 hold the same entries as lanes 0..11: the pose update
+    // below splits its dot products and series between the two halves)
+    const int e = (lane & 15) < 12 ? (lane & 15) : 11;
     const int rr = e >> 2, cc = e & 3;
-    const double t0 = __ldcg(T + cc), t1 = __ldcg(T + 4 + cc), t2 = __ldcg(T + 8 + cc);
+    const double t0 = T_SHARED ? T[cc] : __ldcg(T + cc);
+    const double t1 = T_SHARED ? T[4 + cc] : __ldcg(T + 4 + cc);
+    const double t2 = T_SHARED ? T[8 + cc] : __ldcg(T + 8 + cc);
     // pivot threshold from the largest diagonal entry, in FP32
     float dm = (ri >= 0 && rj == ri) ? float(a) : 0.f;
 #pragma unroll
@@ -1725,18 +1740,21 @@ __device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt
     for (int k = 0; k < 6; ++k) {
         const double p = __shfl_sync(FULL, a, up6(k, k));
         const long long pb = __double_as_longlong(p);
-        if (!(pb > thr && pb < 0x7FF0000000000000LL)) return false;
-        // reciprocal: FP32 seed (relative error <= 2^-23) and one Newton
-        // step (-> ~2^-46, far below what the FP32-summed terms carry);
-        // exponent kept inside the FP32 range by the guard, the rare
-        // outsider takes the division
-        const int ex = int((pb >> 52) & 0x7FF) - 1023;
+        // a pivot must be positive, above the threshold and inside
+        // [2^-1000, 2^1000] (far beyond any scale the terms reach)
+        if (!(pb > thr && pb > 0x0170000000000000LL && pb < 0x7E70000000000000LL)) return false;
+        // reciprocal: the multi-function unit's FP64 approximation
+        // (rcp.approx.ftz.f64; measured on this part: relative error below
+        // 2^-19.9) refined by one third-order step of the iteration for 1/p,
+        // r (1 + e + e^2) with e = 1 - p r (error e^3 < 2^-59, below FP64
+        // rounding; a Newton step, r (1 + e), would stop at 2^-39.8): no
+        // FP32 <-> FP64 conversions and no division subroutine on the
+        // elimination's critical path
         double rp;
-        if (ex > -120 && ex < 120) {
-            rp = double(__frcp_rn(float(p)));
-            rp = rp * fma(-p, rp, 2.0);
-        } else {
-            rp = 1.0 / p;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(rp) : "d"(p));
+        {
+            const double e = fma(-p, rp, 1.0);
+            rp = fma(rp, fma(e, e, e), rp);
         }
         r[k] = rp;
         const bool upd = ri > k;
@@ -1744,55 +1762,85 @@ __device__ inline bool warp_solve_update(const double* tot, double* T, float* Rt
         const int s2 = upd ? (rj < 6 ? up6(k, rj) : 21 + k) : 0;
         const double aki = __shfl_sync(FULL, a, s1);
         const double akj = __shfl_sync(FULL, a, s2);
-        const double f = aki * rp;
-        if (upd) a = fma(-f, akj, a);
+        // a_ij -= (a_ki a_kj) / p: the product does not wait for the
+        // reciprocal, so one FMA follows it on the chain
+        const double t = aki * akj;
+        if (upd) a = fma(-t, rp, a);
     }
-    // back substitution: x_k = b'_k / U_kk, then b'_i -= U_ik x_k (i < k)
+    // back substitution on rows scaled by their pivot's reciprocal (one
+    // multiply on every lane): W_ik = U_ik / U_ii, c_i = b'_i / U_ii, then
+    // x_k = c_k and c_i -= W_ik x_k (i < k), one FMA per step
+    double rri = r[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k) rri = ri == k ? r[k] : rri;
+    a *= rri;
     double x[6];
 #pragma unroll
     for (int k = 5; k >= 0; --k) {
-        const double xk = __shfl_sync(FULL, a, 21 + k) * r[k];
+        const double xk = __shfl_sync(FULL, a, 21 + k);
         x[k] = xk;
         const bool upd = rj == 6 && ri < k;
-        const double uik = __shfl_sync(FULL, a, upd ? up6(ri, k) : 0);
-        if (upd) a = fma(-uik, xk, a);
+        const double wik = __shfl_sync(FULL, a, upd ? up6(ri, k) : 0);
+        if (upd) a = fma(-wik, xk, a);
     }
     // dR = I + a K + b K^2 (Rodrigues), K = [w]x, K^2 = w w^T - |w|^2 I, in
     // FP64: a and b must keep their exact trigonometric relation or dR drifts
     // off the rotation group.  Lane e < 12 forms entry (r, c) of
     // dR T + dt = T + a K T + b (w (w^T T) - |w|^2 T) + dt without forming dR.
-    const double th2 = fma(x[0], x[0], fma(x[1], x[1], x[2] * x[2]));
-    double ca, cb;
+    // Every FP64 warp instruction costs the same whatever its lanes do, so
+    // the three dot products share one FMA chain (lanes 0..11: (w^T T)_c,
+    // lanes 16..27: (K T)_rc, lane 12: |w|^2) and a and b one series
+    // (lanes 0..15: a, lanes 16..31: b).
+    const bool hi = lane >= 16;
+    const double trc = rr == 0 ? t0 : (rr == 1 ? t1 : t2);
+    double p0, p1, p2, q0, q1, q2;
+    if (lane == 12) {
+        p0 = q0 = x[0]; p1 = q1 = x[1]; p2 = q2 = x[2];
+    } else if (hi) {
+        // (K T)_rc: row r of K = [w]x has one zero
+        p0 = rr == 0 ? -x[2] : (rr == 1 ? x[2] : -x[1]);
+        p1 = rr == 0 ? x[1] : (rr == 1 ? -x[0] : x[0]);
+        q0 = rr == 0 ? t1 : t0;
+        q1 = rr == 0 ? t2 : (rr == 1 ? t2 : t1);
+        p2 = 0.0; q2 = 0.0;
+    } else {
+        p0 = x[0]; p1 = x[1]; p2 = x[2];
+        q0 = t0; q1 = t1; q2 = t2;
+    }
+    const double dot = fma(p0, q0, fma(p1, q1, p2 * q2));
+    const double th2 = __shfl_sync(FULL, dot, 12);
+    const double kt = __shfl_sync(FULL, dot, e + 16);
+    const double wt = dot;  // (w^T T)_c on lanes 0..11
+    double ser;
     if (th2 < 1e-4) {  // series truncated after th2^2: error < th2^3 / 5040
-        ca = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120));
-        cb = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720));
+        ser = fma(th2, fma(th2, hi ? 1.0 / 720 : 1.0 / 120, hi ? -1.0 / 24 : -1.0 / 6), hi ? 0.5 : 1.0);
     } else if (th2 < 0.25) {
-        ca = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880 +
-             th2 * (-1.0 / 39916800 + th2 * (1.0 / 6227020800.0))))));
-        cb = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720 + th2 * (-1.0 / 40320 + th2 * (1.0 / 3628800 +
-             th2 * (-1.0 / 479001600 + th2 * (1.0 / 87178291200.0))))));
+        // a = sum_k (-th2)^k / (2k+1)!, b = sum_k (-th2)^k / (2k+2)!, k <= 6
+        ser = hi ? 1.0 / 87178291200.0 : 1.0 / 6227020800.0;
+        ser = fma(th2, ser, hi ? -1.0 / 479001600 : -1.0 / 39916800);
+        ser = fma(th2, ser, hi ? 1.0 / 3628800 : 1.0 / 362880);
+        ser = fma(th2, ser, hi ? -1.0 / 40320 : -1.0 / 5040);
+        ser = fma(th2, ser, hi ? 1.0 / 720 : 1.0 / 120);
+        ser = fma(th2, ser, hi ? -1.0 / 24 : -1.0 / 6);
+        ser = fma(th2, ser, hi ? 0.5 : 1.0);
     } else {
         const double th = sqrt(th2);
-        ca = sin(th) / th;
-        cb = (1.0 - cos(th)) / th2;
+        ser = hi ? (1.0 - cos(th)) / th2 : sin(th) / th;
     }
-    const double trc = rr == 0 ? t0 : (rr == 1 ? t1 : t2);
-    // (K T)_rc: row r of K = [w]x has one zero
-    const double ka = rr == 0 ? -x[2] : (rr == 1 ? x[2] : -x[1]);
-    const double kb = rr == 0 ? x[1] : (rr == 1 ? -x[0] : x[0]);
-    const double ta = rr == 0 ? t1 : t0;
-    const double tb = rr == 0 ? t2 : (rr == 1 ? t2 : t1);
-    const double kt = fma(ka, ta, kb * tb);
-    const double wt = fma(x[0], t0, fma(x[1], t1, x[2] * t2));  // (w^T T)_c
+    const double ca = ser;
+    const double cb = __shfl_sync(FULL, ser, e + 16);
     const double wr = rr == 0 ? x[0] : (rr == 1 ? x[1] : x[2]);
     const double u = fma(wr, wt, -th2 * trc);
-    double acc = cc == 3 ? trc + x[3 + rr] : trc;
+    const double xt = rr == 0 ? x[3] : (rr == 1 ? x[4] : x[5]);
+    double acc = trc + (cc == 3 ? xt : 0.0);
     acc = fma(ca, kt, acc);
     acc = fma(cb, u, acc);
     __syncwarp();
     if (lane < 12) {
         T[e] = acc;
         Rt[cc == 3 ? 9 + rr : rr * 3 + cc] = float(acc);
+        if (T_copy) T_copy[e] = acc;
+        if (Rt_copy) Rt_copy[cc == 3 ? 9 + rr : rr * 3 + cc] = float(acc);
         if (T_hist) T_hist[16 * iter + e] = acc;
     }
     if (T_hist && lane >= 12 && lane < 16) T_hist[16 * iter + lane] = lane == 15 ? 1.0 : 0.0;
@@ -1861,6 +1909,40 @@ __device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned tar
     }
     __syncthreads();
     return ok_wait != 0;
+}
+
+// One thread adds one to a monotonic counter as a release (after a
+// __syncthreads): the CTA's earlier global writes and atomics are visible to
+// any thread that sees the new count through wait_acquire.  fence.acq_rel is
+// the lighter release fence of the PTX memory model (no sequentially
+// consistent order is needed here); it is cumulative over the barrier.
+__device__ __forceinline__ void arrive_release(unsigned* word) {
+    asm volatile("fence.acq_rel.gpu;\n\tred.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(word) : "memory");
+}
+
+// wait_at_least with relaxed polls and one acquire fence once the count is
+// reached (the counterpart of arrive_release); bounded, ST_TIMEOUT on expiry.
+__device__ __forceinline__ bool wait_acquire(const unsigned* word, unsigned target, int* status,
+                                             long long limit) {
+    __shared__ int ok_acq;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        long long spins = 0;
+        unsigned v;
+        for (;;) {
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(word) : "memory");
+            if (int(v - target) >= 0) break;
+            if (++spins > limit) {
+                atomicOr(status, ST_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        ok_acq = ok;
+    }
+    __syncthreads();
+    return ok_acq != 0;
 }
 
 // Grid-wide barrier of a cooperative launch on a monotonic arrival counter

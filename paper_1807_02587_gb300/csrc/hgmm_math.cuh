@@ -59,27 +59,36 @@ __device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2)
 }
 
 // ---------------------------------------------------------------- FP64 helpers
-// On sm_103 a dependent FP64 FMA costs ~64 cycles and the library FP64
-// division / square root several hundred, so FP64 reciprocals and inverse
-// square roots are seeded in FP32 and refined by Newton steps in FP64
-// (quadratic convergence: 2^-22 -> ~1e-13 -> full precision).
-__device__ __forceinline__ double rcp_f64(double x) {
-    const double ax = fabs(x);
-    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
-    double y = double(__frcp_rn(float(x)));
-    y = y * fma(-x, y, 2.0);
-    y = y * fma(-x, y, 2.0);
-    return y;
+// On sm_103 every FP64 warp instruction holds the SM sub-partition's FP64
+// pipe ~64 cycles and the library FP64 division / square root take several
+// hundred, so FP64 reciprocals and inverse square roots start from the
+// multi-function unit's FP64 approximations (rcp.approx.ftz.f64 /
+// rsqrt.approx.ftz.f64, relative error about 2^-20 on this part) and take one
+// third-order correction step in FP64: for 1/x, r (1 + e + e^2) with
+// e = 1 - x r; for 1/sqrt(x), y (1 + e/2 + 3 e^2/8) with e = 1 - x y^2 (the
+// truncated binomial series of (1 - e)^-1 and (1 - e)^-1/2).  The remainder
+// is O(e^3) < 2^-58, below FP64 rounding, in three and five FP64
+// instructions.  Inputs outside [2^-1000, 2^1000] (and zero, negative
+// square-root arguments, infinities, NaN) take the library routine.
+__device__ __forceinline__ bool f64_normal_range(double x) {
+    const int be = (__double2hiint(x) >> 20) & 0x7FF;
+    return be >= 23 && be <= 2023;
 }
 
-// one Newton step: relative error <= ~1e-13 (used where the result feeds
-// FP32 constants, Cholesky pivots or Jacobi rotation factors)
+__device__ __forceinline__ double rcp_f64(double x) {
+    if (!f64_normal_range(x)) return 1.0 / x;
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
 __device__ __forceinline__ double rsqrt_f64(double x) {
-    if (!(x > 1e-30 && x < 1e30)) return rsqrt(x);
-    const double h = 0.5 * x;
-    double y = double(rsqrtf(float(x)));
-    y = y * fma(-h * y, y, 1.5);
-    return y;
+    if (__double2hiint(x) < 0 || !f64_normal_range(x)) return rsqrt(x);
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x * y, y, 1.0);
+    return fma(y, e * fma(e, 0.375, 0.5), y);
 }
 
 // ---------------------------------------------------------------- FP64 3x3

@@ -14,9 +14,11 @@
 //               node's contribution pi* B P B^T, pi* B P (mu_j - mu*) with
 //               B = [[mu*]_x; I] to the 6x6 normal equations of Eq. 16 (the
 //               three weighted point-to-plane rows of Eq. 13-16 summed in
-//               closed form: sum_l (1/lambda_l) n_l n_l^T = P, Eq. 10).  FP64.
-//               The last CTA to finish reduces the per-CTA sums in a fixed
-//               order, solves (Cholesky) and composes T <- dT T.
+//               closed form: sum_l (1/lambda_l) n_l n_l^T = P, Eq. 10).
+//               Every CTA then reduces the per-CTA sums in the same fixed
+//               order, solves the system in FP64 (symmetric elimination) and
+//               composes T <- dT T itself: the same inputs and instructions
+//               give every CTA the same pose, with no publication step.
 #include <algorithm>
 #include <cstdio>
 
@@ -47,6 +49,7 @@ __global__ void k_reg_init(const double* __restrict__ T_init, int n_nodes, float
             if (k != 1) bar[k] = 0u;  // bar[1] is a generation: any start value works
         *obj = 0.0;
     }
+    if (i < REG_SM_ORDER) bar[8 + i] = 0u;  // per-SM arrival counters of k_register
 }
 
 struct RegArgs {
@@ -87,19 +90,28 @@ __device__ __forceinline__ void trace_mark(unsigned long long* tr, int it, int e
 // The whole registration loop in one cooperative launch.  Per round:
 //   A. Algorithm 1 for every source point (fixed-point node moments)
 //   -- every CTA arrives on a counter; only the CTAs that own nodes wait --
-//   B. per node with mass: its normal-equation and objective terms (FP32), compensated
-//      block sums -> one partial per CTA; the last CTA to finish
-//   C. reduces the partials in a fixed order, solves the 6x6 system in FP64,
-//      composes T <- dT T and publishes the round number as the pose generation
-//   -- every CTA waits for that generation, then reads the new T --
-// All counters are monotonic over the launch (zeroed by k_reg_init), so no
-// CTA resets a word that another may still be reading; every wait is bounded.
+//   B. per node with mass: its normal-equation and objective terms (FP32),
+//      compensated block sums -> one partial per node-owning CTA, then an
+//      arrival on a second counter
+//   -- every CTA waits for all partials --
+//   C. every CTA reduces the partials in the same fixed order and solves the
+//      6x6 system in FP64 itself: identical inputs and instructions give every
+//      CTA the same bits, so the new pose needs no publication round trip.
+//      CTA 0 keeps the global copies (T, R|t, per-round history, objective).
+// Trace events per round and CTA: 0 round start, 1 arrival, 2 all arrivals
+// seen (node CTAs), 3 partial published (node CTAs), 4 all partials seen,
+// 5 pose solved.  All counters are monotonic over the launch (zeroed by
+// k_reg_init), so no CTA resets a word that another may still be reading;
+// every wait is bounded.
 __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     __shared__ float Rt_sm[12];
+    __shared__ double T_sm[12];
     __shared__ float2 sm[REG_THREADS / 32][NTERM];
     __shared__ float2 fin[8][NTERM];
     __shared__ double tot[NTERM];
-    __shared__ bool last;
+    __shared__ unsigned slots_sm[REG_THREADS / 32];
+    __shared__ unsigned order_sm;
+    __shared__ int solver_sm;
     // dynamic: the staged top levels (3 float4 per node, padded), then the CTA's
     // fixed-point histogram of their moments (4 words per node)
     extern __shared__ float4 reg_dyn[];
@@ -107,147 +119,167 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     unsigned long long* hist = reinterpret_cast<unsigned long long*>(reg_dyn + STAGED_F4);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ns = a.n_nodes < STAGED_NODES ? a.n_nodes : STAGED_NODES;
+    const int nb_nodes = (a.n_nodes + blockDim.x - 1) / blockDim.x;
+    const bool lead = blockIdx.x == 0;
     // the top levels of the tree are read by every point: stage them once
-    // for all rounds (the stop flags were set by k_reg_init before launch)
+    // for all rounds (the stop flags were set by k_reg_init before launch);
+    // the starting pose (k_reg_init) into shared memory
     {
         stage_nodes(sm_est, a.est, ns);
         for (int i = threadIdx.x; i < 4 * STAGED_NODES; i += blockDim.x) hist[i] = 0ull;
+        if (threadIdx.x < 12) {
+            T_sm[threadIdx.x] = __ldcg(a.T + threadIdx.x);
+            Rt_sm[threadIdx.x] = __ldcg(a.Rt + threadIdx.x);
+        }
+        // The solve is a chain of FP64 warp instructions, each holding its
+        // scheduler's FP64 pipe ~64 cycles, and the two CTAs of an SM solve
+        // at the same moment: they take warps on different schedulers
+        // (warp slot mod 4), chosen from the order in which they arrived on
+        // their SM (a per-SM counter; only the speed depends on it).
+        if (lane == 0) {
+            unsigned slot;
+            asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
+            slots_sm[warp] = slot;
+        }
+        if (threadIdx.x == 0) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            order_sm = atomicAdd(a.bar + 8 + (smid & (REG_SM_ORDER - 1)), 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned target = (2u * order_sm) & 3u;
+            int pick = 0;
+            for (int w = REG_THREADS / 32 - 1; w >= 0; --w)
+                if ((slots_sm[w] & 3u) == target) pick = w;
+            solver_sm = pick;
+        }
         __syncthreads();
     }
+    const int solver = solver_sm;
     const double ext = a.root->extent > 0.0 ? a.root->extent : 1.0;
     const float qscale = float(FIX / ext);  // fixed-point units per metre
     for (int it = 0; it < a.iters; ++it) {
         trace_mark(a.trace, it, 0);
-        if (threadIdx.x < 12) Rt_sm[threadIdx.x] = __ldcg(a.Rt + threadIdx.x);
-        __syncthreads();
         descend_points(a.src, a.n, a.est, sm_est, a.depth, Rt_sm, qscale, a.acc, blockIdx.x, gridDim.x,
                        hist);
         __syncthreads();
         flush_node_hist(hist, ns, a.acc);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();  // this CTA's moment atomics before its arrival
-            atomicAdd(a.bar + 4, 1u);
-        }
+        if (threadIdx.x == 0) arrive_release(a.bar + 4);  // this CTA's moment atomics before it
         trace_mark(a.trace, it, 1);
         // ---- B: node terms (only the CTAs that own nodes take part)
-        const int nb_nodes = (a.n_nodes + blockDim.x - 1) / blockDim.x;
         if (blockIdx.x < nb_nodes) {
-        if (!wait_at_least(a.bar + 4, unsigned(it + 1) * gridDim.x, a.status, BARRIER_SPIN_LIMIT)) return;
-        trace_mark(a.trace, it, 2);
-        float v[32], c[32];  // NTERM terms, padded to a warp's width
+            if (!wait_acquire(a.bar + 4, unsigned(it + 1) * gridDim.x, a.status, BARRIER_SPIN_LIMIT)) return;
+            trace_mark(a.trace, it, 2);
+            // at most one node per thread (nb_nodes x blockDim.x >= n_nodes):
+            // its terms start the compensated pairs (errors zero)
+            float v[32], c[32];  // NTERM terms, padded to a warp's width
 #pragma unroll
-        for (int k = 0; k < 32; ++k) { v[k] = 0.f; c[k] = 0.f; }
-        double* dbg = it == a.iters - 1 ? a.dbg : nullptr;
-        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_nodes; g += nb_nodes * blockDim.x) {
-            long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            for (int k = 0; k < 32; ++k) { v[k] = 0.f; c[k] = 0.f; }
+            double* dbg = it == a.iters - 1 ? a.dbg : nullptr;
+            const int g = blockIdx.x * blockDim.x + threadIdx.x;
+            if (g < a.n_nodes) {
+                // the node's constants are loaded with its moments (one L2
+                // round trip instead of two)
+                const float4 cm = __ldg(&a.est[g].a);
+                const float4 r0 = __ldg(a.rnode + 3 * g), r1 = __ldg(a.rnode + 3 * g + 1);
+                const float4 r2 = __ldg(a.rnode + 3 * g + 2);
+                long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+                {
+                    // integer sums of the replicas: exact, order-free
+                    const ulonglong2* rp = reinterpret_cast<const ulonglong2*>(
+                        a.acc + 4 * int64_t(g) * ACC_REPLICAS);
+                    ulonglong2 q[2 * ACC_REPLICAS];
+#pragma unroll
+                    for (int r = 0; r < 2 * ACC_REPLICAS; ++r) q[r] = __ldcg(rp + r);
+                    unsigned long long any = 0ull;
+#pragma unroll
+                    for (int r = 0; r < ACC_REPLICAS; ++r) {
+                        a0 += (long long)q[2 * r].x;
+                        a1 += (long long)q[2 * r].y;
+                        a2 += (long long)q[2 * r + 1].x;
+                        a3 += (long long)q[2 * r + 1].y;
+                        any |= q[2 * r].x | q[2 * r].y | q[2 * r + 1].x | q[2 * r + 1].y;
+                    }
+                    if (any) {
+                        ulonglong2* wp = reinterpret_cast<ulonglong2*>(a.acc + 4 * int64_t(g) * ACC_REPLICAS);
+#pragma unroll
+                        for (int r = 0; r < 2 * ACC_REPLICAS; ++r) wp[r] = make_ulonglong2(0ull, 0ull);
+                    }
+                }
+                float M0 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
+                if (a0 > 0) {
+                    M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
+                    const float inv = 1.0f / (qscale * M0);
+                    o0 = float(a1) * inv;
+                    o1 = float(a2) * inv;
+                    o2 = float(a3) * inv;
+                    node_terms(r0, r1, r2, cm, M0, o0, o1, o2, M0 / float(a.n), v);
+                }
+                if (dbg) {
+                    dbg[4 * g + 0] = double(a0) * INV_FIX;
+                    dbg[4 * g + 1] = double(M0) * (double(cm.x) + double(o0));
+                    dbg[4 * g + 2] = double(M0) * (double(cm.y) + double(o1));
+                    dbg[4 * g + 3] = double(M0) * (double(cm.z) + double(o2));
+                }
+            }
             {
-                // integer sums of the replicas: exact, order-free
-                const ulonglong2* rp = reinterpret_cast<const ulonglong2*>(
-                    a.acc + 4 * int64_t(g) * ACC_REPLICAS);
-                ulonglong2 q[2 * ACC_REPLICAS];
-#pragma unroll
-                for (int r = 0; r < 2 * ACC_REPLICAS; ++r) q[r] = __ldcg(rp + r);
-                unsigned long long any = 0ull;
-#pragma unroll
-                for (int r = 0; r < ACC_REPLICAS; ++r) {
-                    a0 += (long long)q[2 * r].x;
-                    a1 += (long long)q[2 * r].y;
-                    a2 += (long long)q[2 * r + 1].x;
-                    a3 += (long long)q[2 * r + 1].y;
-                    any |= q[2 * r].x | q[2 * r].y | q[2 * r + 1].x | q[2 * r + 1].y;
-                }
-                if (any) {
-                    ulonglong2* wp = reinterpret_cast<ulonglong2*>(a.acc + 4 * int64_t(g) * ACC_REPLICAS);
-#pragma unroll
-                    for (int r = 0; r < 2 * ACC_REPLICAS; ++r) wp[r] = make_ulonglong2(0ull, 0ull);
-                }
-            }
-            const float4 cm = a.est[g].a;
-            float M0 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
-            if (a0 > 0) {
-                float w[NTERM];
-                M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
-                const float inv = 1.0f / (qscale * M0);
-                o0 = float(a1) * inv;
-                o1 = float(a2) * inv;
-                o2 = float(a3) * inv;
-                node_terms(a.rnode[3 * g], a.rnode[3 * g + 1], a.rnode[3 * g + 2], cm, M0, o0, o1,
-                           o2, M0 / float(a.n), w);
-#pragma unroll
-                for (int k = 0; k < NTERM; ++k) pair_add(v[k], c[k], w[k], 0.f);
-            }
-            if (dbg) {
-                dbg[4 * g + 0] = double(a0) * INV_FIX;
-                dbg[4 * g + 1] = double(M0) * (double(cm.x) + double(o0));
-                dbg[4 * g + 2] = double(M0) * (double(cm.y) + double(o1));
-                dbg[4 * g + 3] = double(M0) * (double(cm.z) + double(o2));
-            }
-        }
-        {
-            float ws, we;
-            warp_reduce_scatter32(v, c, ws, we);
-            if (lane < NTERM) sm[warp][lane] = make_float2(ws, we);
-        }
-        __syncthreads();
-        if (threadIdx.x < NTERM) {
-            float S = 0.f, C = 0.f;
-            for (int w = 0; w < REG_THREADS / 32; ++w) pair_add(S, C, sm[w][threadIdx.x].x, sm[w][threadIdx.x].y);
-            a.part[NTERM * blockIdx.x + threadIdx.x] = make_float2(S, C);
-        }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) last = (atomicAdd(a.bar + 2, 1u) == unsigned(it + 1) * nb_nodes - 1);
-        __syncthreads();
-        trace_mark(a.trace, it, 3);
-        if (last) {
-            // ---- C: fixed-order reduction, FP64 solve, pose update
-            __threadfence();
-            const int nb = nb_nodes;
-            // all partial loads in flight at once (8 groups of NTERM threads),
-            // then a fixed-order combine
-            if (threadIdx.x < 8 * NTERM) {
-                const int k = threadIdx.x % NTERM, q = threadIdx.x / NTERM;
-                float S = 0.f, C = 0.f;
-                float2 xs[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int b = q + 8 * j;
-                    xs[j] = b < nb ? __ldcg(&a.part[NTERM * b + k]) : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) pair_add(S, C, xs[j].x, xs[j].y);
-                for (int b = q + 64; b < nb; b += 8) {
-                    const float2 x = __ldcg(&a.part[NTERM * b + k]);
-                    pair_add(S, C, x.x, x.y);
-                }
-                fin[q][k] = make_float2(S, C);
+                float ws, we;
+                warp_reduce_scatter32(v, c, ws, we);
+                if (lane < NTERM) sm[warp][lane] = make_float2(ws, we);
             }
             __syncthreads();
             if (threadIdx.x < NTERM) {
                 float S = 0.f, C = 0.f;
-                for (int q = 0; q < 8; ++q) pair_add(S, C, fin[q][threadIdx.x].x, fin[q][threadIdx.x].y);
-                tot[threadIdx.x] = double(S) + double(C);
+                for (int w = 0; w < REG_THREADS / 32; ++w) pair_add(S, C, sm[w][threadIdx.x].x, sm[w][threadIdx.x].y);
+                a.part[NTERM * blockIdx.x + threadIdx.x] = make_float2(S, C);
             }
             __syncthreads();
-            if (threadIdx.x == 32 && a.obj) *a.obj = tot[NTERM - 1];
-            if (warp == 0) {
-                const bool solved = warp_solve_update(tot, a.T, a.Rt, a.T_hist, it);
-                if (!solved && lane == 0) {
-                    atomicOr(a.status, ST_DEGENERATE);  // T kept for this round
-                    if (a.T_hist)
-                        for (int k = 0; k < 16; ++k) a.T_hist[16 * it + k] = __ldcg(a.T + k);
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence();  // the new T and R|t before the generation
-                    atomicExch(a.bar + 3, unsigned(it + 1));
-                }
-            }
-            trace_mark(a.trace, it, 4);
+            if (threadIdx.x == 0) arrive_release(a.bar + 2);  // partial and cleared moments before it
+            trace_mark(a.trace, it, 3);
         }
-        }  // node-owning CTAs
-        if (!wait_at_least(a.bar + 3, unsigned(it + 1), a.status, BARRIER_SPIN_LIMIT)) return;
+        // ---- C: every CTA: fixed-order reduction, FP64 solve, pose update
+        if (!wait_acquire(a.bar + 2, unsigned(it + 1) * nb_nodes, a.status, BARRIER_SPIN_LIMIT)) return;
+        trace_mark(a.trace, it, 4);
+        // all partial loads in flight at once (8 groups of NTERM threads),
+        // then a fixed-order combine
+        if (threadIdx.x < 8 * NTERM) {
+            const int k = threadIdx.x % NTERM, q = threadIdx.x / NTERM;
+            float S = 0.f, C = 0.f;
+            float2 xs[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int b = q + 8 * j;
+                xs[j] = b < nb_nodes ? __ldcg(&a.part[NTERM * b + k]) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) pair_add(S, C, xs[j].x, xs[j].y);
+            for (int b = q + 64; b < nb_nodes; b += 8) {
+                const float2 x = __ldcg(&a.part[NTERM * b + k]);
+                pair_add(S, C, x.x, x.y);
+            }
+            fin[q][k] = make_float2(S, C);
+        }
+        __syncthreads();
+        if (warp == solver) {
+            // the eight group sums in order, by the warp that solves
+            if (lane < NTERM) {
+                float S = 0.f, C = 0.f;
+                for (int q = 0; q < 8; ++q) pair_add(S, C, fin[q][lane].x, fin[q][lane].y);
+                tot[lane] = double(S) + double(C);
+            }
+            __syncwarp();
+            if (lead && lane == 0 && a.obj) *a.obj = tot[NTERM - 1];
+            const bool solved = warp_solve_update<true>(tot, T_sm, Rt_sm, lead ? a.T_hist : nullptr, it,
+                                                        lead ? a.T : nullptr, lead ? a.Rt : nullptr);
+            if (!solved && lead && lane == 0) {
+                atomicOr(a.status, ST_DEGENERATE);  // T kept for this round
+                if (a.T_hist)
+                    for (int k = 0; k < 16; ++k) a.T_hist[16 * it + k] = k < 12 ? T_sm[k] : (k == 15 ? 1.0 : 0.0);
+            }
+        }
+        __syncthreads();
         trace_mark(a.trace, it, 5);
     }
 }
