@@ -161,7 +161,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->reg_part, NTERM * nb);
     good &= dalloc(&t->rnode, 3 * t->max_nodes);
     good &= dalloc(&t->trace, int64_t(TRACE_MAX_ITERS) * t->reg_grid * 6);
-    good &= dalloc(&t->reg_bar, 8 + REG_SM_ORDER);
+    good &= dalloc(&t->reg_bar, 8);
     good &= dalloc(&t->reg_T, 16);
     good &= dalloc(&t->reg_Rt, 12);
     good &= dalloc(&t->reg_dbg, 4 * t->max_nodes);
@@ -174,7 +174,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
         return HGMM_ENOMEM;
     }
     good &= ok(cudaMemset(t->status, 0, sizeof(int)), "cudaMemset");
-    good &= ok(cudaMemset(t->reg_bar, 0, (8 + REG_SM_ORDER) * sizeof(unsigned)), "cudaMemset");
+    good &= ok(cudaMemset(t->reg_bar, 0, 8 * sizeof(unsigned)), "cudaMemset");
     good &= ok(cudaMemset(t->root_counter, 0, sizeof(unsigned)), "cudaMemset");
     good &= ok(cudaMemset(t->mcnt, 0, MSTEP_SLICED_PARENTS * sizeof(unsigned)), "cudaMemset");
     good &= ok(cudaMemset(t->reg_acc, 0, 4 * ACC_REPLICAS * t->max_nodes * sizeof(unsigned long long)),

@@ -43,7 +43,6 @@ constexpr int MSTEP_THREADS = 128;    // registration M-step CTA
 constexpr int NTERM = 28;             // per-round sums: 21 of H, 6 of g, the objective
 constexpr int TRACE_MAX_ITERS = 64;   // rounds the registration trace can hold
 constexpr int ACC_REPLICAS = 1;       // copies of each node's registration moments
-constexpr int REG_SM_ORDER = 256;     // per-SM arrival counters of the registration (SM id mod 256)
 constexpr int MSTEP_SLICES = 8;        // run slices per parent in the level-wide M-step
 constexpr int MSTEP_SLICED_PARENTS = 64;  // levels with at most this many parents are sliced
 constexpr int MSTEP_SLICE_MIN_RUNS = 32;  // ... when a parent has about this many runs or more
@@ -179,7 +178,7 @@ struct hgmm_tree {
     unsigned long long* reg_acc2 = nullptr; // nodes x 6 fixed-point second moments (full Eq. 7)
     float2* reg_part = nullptr;             // blocks x 27 (sum, compensation)
     float4* rnode = nullptr;                // nodes x 3: P (6), mu - mu32 (3), FP32
-    unsigned* reg_bar = nullptr;            // grid barrier words (8), then REG_SM_ORDER per-SM counters
+    unsigned* reg_bar = nullptr;            // grid barrier words (8)
     double* reg_T = nullptr;                // 16 doubles current T
     float* reg_Rt = nullptr;                // 12 floats (R row-major, t)
     double* reg_dbg = nullptr;              // nodes x 4 (last round)

@@ -49,7 +49,6 @@ __global__ void k_reg_init(const double* __restrict__ T_init, int n_nodes, float
             if (k != 1) bar[k] = 0u;  // bar[1] is a generation: any start value works
         *obj = 0.0;
     }
-    if (i < REG_SM_ORDER) bar[8 + i] = 0u;  // per-SM arrival counters of k_register
 }
 
 struct RegArgs {
@@ -109,9 +108,6 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     __shared__ float2 sm[REG_THREADS / 32][NTERM];
     __shared__ float2 fin[8][NTERM];
     __shared__ double tot[NTERM];
-    __shared__ unsigned slots_sm[REG_THREADS / 32];
-    __shared__ unsigned order_sm;
-    __shared__ int solver_sm;
     // dynamic: the staged top levels (3 float4 per node, padded), then the CTA's
     // fixed-point histogram of their moments (4 words per node)
     extern __shared__ float4 reg_dyn[];
@@ -131,32 +127,8 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
             T_sm[threadIdx.x] = __ldcg(a.T + threadIdx.x);
             Rt_sm[threadIdx.x] = __ldcg(a.Rt + threadIdx.x);
         }
-        // The solve is a chain of FP64 warp instructions, each holding its
-        // scheduler's FP64 pipe ~64 cycles, and the two CTAs of an SM solve
-        // at the same moment: they take warps on different schedulers
-        // (warp slot mod 4), chosen from the order in which they arrived on
-        // their SM (a per-SM counter; only the speed depends on it).
-        if (lane == 0) {
-            unsigned slot;
-            asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
-            slots_sm[warp] = slot;
-        }
-        if (threadIdx.x == 0) {
-            unsigned smid;
-            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-            order_sm = atomicAdd(a.bar + 8 + (smid & (REG_SM_ORDER - 1)), 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const unsigned target = (2u * order_sm) & 3u;
-            int pick = 0;
-            for (int w = REG_THREADS / 32 - 1; w >= 0; --w)
-                if ((slots_sm[w] & 3u) == target) pick = w;
-            solver_sm = pick;
-        }
         __syncthreads();
     }
-    const int solver = solver_sm;
     const double ext = a.root->extent > 0.0 ? a.root->extent : 1.0;
     const float qscale = float(FIX / ext);  // fixed-point units per metre
     for (int it = 0; it < a.iters; ++it) {
@@ -262,7 +234,7 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
             fin[q][k] = make_float2(S, C);
         }
         __syncthreads();
-        if (warp == solver) {
+        if (warp == 0) {
             // the eight group sums in order, by the warp that solves
             if (lane < NTERM) {
                 float S = 0.f, C = 0.f;
