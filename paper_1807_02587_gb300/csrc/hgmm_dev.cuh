@@ -143,9 +143,10 @@ __device__ __forceinline__ void root_final_cta(const float* __restrict__ part, i
         if (__float_as_int(F[24]) > 0) atomicOr(status, ST_NONFINITE);
         const float4 z0 = pts[0];
         const double nn = double(n);
+        const double rn = rcp_f64(nn);  // one reciprocal instead of nine divisions
         double m1[3], m2[6];
-        for (int a = 0; a < 3; ++a) m1[a] = (double(F[2 * a]) + double(F[2 * a + 1])) / nn;
-        for (int v = 0; v < 6; ++v) m2[v] = (double(F[6 + 2 * v]) + double(F[7 + 2 * v])) / nn;
+        for (int a = 0; a < 3; ++a) m1[a] = (double(F[2 * a]) + double(F[2 * a + 1])) * rn;
+        for (int v = 0; v < 6; ++v) m2[v] = (double(F[6 + 2 * v]) + double(F[7 + 2 * v])) * rn;
         root->n = nn;
         root->mu[0] = double(z0.x) + m1[0];
         root->mu[1] = double(z0.y) + m1[1];
