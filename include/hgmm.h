@@ -370,6 +370,13 @@ int hgmm_batch_debug_tree(const hgmm_batch* b, int32_t pair, int32_t level, doub
                           int64_t cap);
 int hgmm_batch_debug_root(const hgmm_batch* b, int32_t pair, double* h_root12);
 
+/* Tracing (no counterpart in the paper): each pair's device run time in the
+ * last hgmm_batch_register / hgmm_batch_features launch, nanoseconds of the
+ * global timer from the moment its cluster took the pair to the moment it
+ * wrote the pair's pose (n_pairs uint64 to h_ns, cap entries at most).
+ * Synchronous.  Errors: HGMM_EINVAL, HGMM_ECAPACITY, HGMM_ECUDA. */
+int hgmm_batch_pair_ns(const hgmm_batch* b, uint64_t* h_ns, int64_t cap);
+
 /* Per pair of the last hgmm_batch_register: the Eq. 11 objective of its
  * last round (as hgmm_register_objective), n_pairs float64 to d_obj. */
 int hgmm_batch_objective(const hgmm_batch* b, double* d_obj, void* stream);

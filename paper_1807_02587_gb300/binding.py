@@ -98,6 +98,7 @@ def _load():
         "hgmm_batch_debug_tree": (ctypes.c_int, [vp, i32, i32, vp, i64]),
         "hgmm_batch_set_build_shape": (ctypes.c_int, [vp, i32, i32, i32, i32]),
         "hgmm_batch_get_build_shape": (ctypes.c_int, [vp, vp, vp]),
+        "hgmm_batch_pair_ns": (ctypes.c_int, [vp, vp, i64]),
         "hgmm_batch_debug_root": (ctypes.c_int, [vp, i32, vp]),
         "hgmm_batch_autotune": (ctypes.c_int, [vp, vp, P(hgmm_params), vp, i32, vp, vp, vp]),
         "hgmm_trace_read": (ctypes.c_int, [vp, vp, i64, P(i32), P(i32)]),
@@ -403,6 +404,13 @@ def hgmm_batch_register(h, points, T_out, prm: hgmm_params | None = None, T_init
                                     int(iters), _stream_ptr(stream), _dptr(T_out),
                                     _dptr(pair_status), _dptr(T_hist)), "hgmm_batch_register")
     return T_out
+
+
+def hgmm_batch_pair_ns(h, n_pairs: int) -> np.ndarray:
+    """Each pair's device run time (ns) in the last batched launch."""
+    out = np.zeros(n_pairs, np.uint64)
+    _check(_lib.hgmm_batch_pair_ns(h, ctypes.c_void_p(out.ctypes.data), int(n_pairs)), "hgmm_batch_pair_ns")
+    return out
 
 
 def hgmm_batch_debug_tree(h, pair: int, level: int) -> dict:

@@ -766,6 +766,17 @@ int hgmm_batch_set_build_shape(hgmm_batch* b, int32_t bucket, int32_t warp_item_
     return upload_knobs(b);
 }
 
+int hgmm_batch_pair_ns(const hgmm_batch* b, uint64_t* h_ns, int64_t cap) {
+    if (!b || !h_ns) return HGMM_EINVAL;
+    if (cap < b->n_pairs) return HGMM_ECAPACITY;
+    if (b->n_pairs == 0) return HGMM_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return HGMM_ECUDA;
+    return cudaMemcpy(h_ns, b->d_pair_ns, size_t(b->n_pairs) * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost) == cudaSuccess
+               ? HGMM_OK
+               : HGMM_ECUDA;
+}
+
 int hgmm_batch_get_build_shape(const hgmm_batch* b, int32_t* h_shape9, float* h_ms2) {
     if (!b) return HGMM_EINVAL;
     if (h_shape9)

@@ -1491,17 +1491,21 @@ __device__ __forceinline__ int warp_group_sum4(int key, float& v0, float& v1, fl
     return rank;
 }
 
+// KEYS: key_out receives each point's chosen node (all ones: none), for the
+// source reorder between the first and the second round.
 // hist (shared memory, 4 x STAGED_NODES fixed-point words, zero on entry, or
 // null): the groups whose node is one of the staged top levels add into the
 // CTA's own histogram instead of global memory; flush_node_hist then moves it
 // to the global accumulators with one atomic per touched word.  The top
 // levels are where most points stop on large planar structures, so this
 // keeps thousands of warps from serialising on a few hot addresses.
+template <bool KEYS = false>
 __device__ __forceinline__ void descend_points(const float4* __restrict__ src, int n,
                                                const NodeEst* __restrict__ est, const float4* sm_est,
                                                int depth, const float* Rt_sm, float qscale,
                                                unsigned long long* __restrict__ acc, int cta, int ncta,
-                                               unsigned long long* hist = nullptr) {
+                                               unsigned long long* hist = nullptr,
+                                               uint32_t* __restrict__ key_out = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float r00 = Rt_sm[0], r01 = Rt_sm[1], r02 = Rt_sm[2], r10 = Rt_sm[3], r11 = Rt_sm[4];
     const float r12 = Rt_sm[5], r20 = Rt_sm[6], r21 = Rt_sm[7], r22 = Rt_sm[8];
@@ -1563,6 +1567,7 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             const float4 cm = chosen < STAGED_NODES ? sm_est[staged_slot(chosen)] : __ldg(&est[chosen].a);
             cmx = cm.x; cmy = cm.y; cmz = cm.z;
         }
+        if (KEYS && valid) key_out[i] = has ? uint32_t(chosen) : 0xFFFFFFFFu;  // the point's node
         float v0 = has ? gamma : 0.f;
         float v1 = has ? gamma * (x - cmx) : 0.f;
         float v2 = has ? gamma * (y - cmy) : 0.f;

@@ -70,6 +70,7 @@ struct RegArgs {
     double* dbg;
     int* status;
     unsigned long long* trace;  // optional: [iter][cta][TRACE_EVENTS] globaltimer ns
+    uint32_t* keys;             // k_register<true>: each point's chosen node (one-round launches)
 };
 
 constexpr int TRACE_EVENTS = 6;
@@ -102,6 +103,9 @@ __device__ __forceinline__ void trace_mark(unsigned long long* tr, int it, int e
 // 5 pose solved.  All counters are monotonic over the launch (zeroed by
 // k_reg_init), so no CTA resets a word that another may still be reading;
 // every wait is bounded.
+// KEYS: the launch records each point's chosen node in a.keys (a one-round
+// launch before the source reorder).
+template <bool KEYS>
 __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     __shared__ float Rt_sm[12];
     __shared__ double T_sm[12];
@@ -133,8 +137,8 @@ __global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
     const float qscale = float(FIX / ext);  // fixed-point units per metre
     for (int it = 0; it < a.iters; ++it) {
         trace_mark(a.trace, it, 0);
-        descend_points(a.src, a.n, a.est, sm_est, a.depth, Rt_sm, qscale, a.acc, blockIdx.x, gridDim.x,
-                       hist);
+        descend_points<KEYS>(a.src, a.n, a.est, sm_est, a.depth, Rt_sm, qscale, a.acc, blockIdx.x, gridDim.x,
+                             hist, a.keys);
         __syncthreads();
         flush_node_hist(hist, ns, a.acc);
         __syncthreads();
@@ -278,33 +282,16 @@ __global__ void k_barrier_timeout_probe(unsigned* bar, int* status, long long li
 // ------------------------------------------------ source reorder (large clouds)
 // A large source cloud in arbitrary order sends each warp's 32 points down
 // ~20 different paths of the tree, so the descent adds its moments with one
-// atomic group per node and warp.  Before the rounds, such a cloud is
-// counting-sorted (into a library buffer) by the cell of a 16 x 16 x 16 grid
-// over the target's extent that it occupies under the starting pose, in
-// Morton order, so that a warp's points are neighbours and share most of
-// their path.  The node moments are exact integer sums of per-warp FP32
-// group sums, so the order of the points changes the result only by the
-// FP32 rounding of those group sums.
+// atomic group per node and warp and its child loads diverge.  Such a cloud
+// runs its first round in the caller's order, with every point's chosen node
+// recorded; it is then counting-sorted by that node (into a library buffer)
+// and runs the remaining rounds in that order, where the 32 points of a warp
+// mostly follow one path.  The node moments are exact integer sums of
+// per-warp FP32 group sums, so the order of the points changes the result
+// only by the FP32 rounding of those group sums.
 constexpr int REORDER_MIN_POINTS = 1 << 20;
-constexpr int REORDER_BITS = 4;                           // cells per axis: 16
-constexpr int REORDER_KEYS = 1 << (3 * REORDER_BITS);     // 4096
+constexpr int REORDER_KEYS = 8192;  // node ids of trees up to depth 4 (4,680 nodes); the last: no node
 constexpr int REORDER_THREADS = 256;
-
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // bits b -> 3b (4 bits)
-    v &= 0xFu;
-    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6);
-}
-
-// Morton key of a transformed point's cell in the box mean +- extent / 2.
-__device__ __forceinline__ uint32_t cell_key(float x, float y, float w, float cx, float cy, float cz,
-                                             float inv_cell) {
-    auto q = [&](float v, float c) {
-        const float f = (v - c) * inv_cell + float(1 << (REORDER_BITS - 1));
-        const int k = f >= 0.f ? int(f) : 0;  // NaN -> 0
-        return uint32_t(k > (1 << REORDER_BITS) - 1 ? (1 << REORDER_BITS) - 1 : k);
-    };
-    return spread3(q(x, cx)) | (spread3(q(y, cy)) << 1) | (spread3(q(w, cz)) << 2);
-}
 
 // Contiguous range of points of CTA b (of nb).
 __device__ __forceinline__ void cta_range(int n, int b, int nb, int& lo, int& hi) {
@@ -312,30 +299,15 @@ __device__ __forceinline__ void cta_range(int n, int b, int nb, int& lo, int& hi
     hi = int((int64_t(b + 1) * n) / nb);
 }
 
-// Pass 1: each point's key (to keys) and each CTA's key counts (cnt[b][key]).
-__global__ void __launch_bounds__(REORDER_THREADS) k_src_keys(const float4* __restrict__ src, int n,
-                                                              const RootDev* __restrict__ root,
-                                                              const float* __restrict__ Rt,
-                                                              uint32_t* __restrict__ keys, int* __restrict__ cnt) {
+// Pass 1: each CTA's key counts (cnt[b][key]) over its contiguous range.
+__global__ void __launch_bounds__(REORDER_THREADS) k_src_count(const uint32_t* __restrict__ keys, int n,
+                                                               int* __restrict__ cnt) {
     __shared__ int h[REORDER_KEYS];
-    __shared__ float R[12];
     for (int k = threadIdx.x; k < REORDER_KEYS; k += blockDim.x) h[k] = 0;
-    if (threadIdx.x < 12) R[threadIdx.x] = Rt[threadIdx.x];
     __syncthreads();
-    const float cx = float(root->mu[0]), cy = float(root->mu[1]), cz = float(root->mu[2]);
-    const float ext = float(root->extent);
-    const float inv_cell = ext > 0.f ? float(1 << REORDER_BITS) / ext : 0.f;
     int lo, hi;
     cta_range(n, blockIdx.x, gridDim.x, lo, hi);
-    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const float4 z = src[i];
-        const float x = fmaf(R[0], z.x, fmaf(R[1], z.y, fmaf(R[2], z.z, R[9])));
-        const float y = fmaf(R[3], z.x, fmaf(R[4], z.y, fmaf(R[5], z.z, R[10])));
-        const float w = fmaf(R[6], z.x, fmaf(R[7], z.y, fmaf(R[8], z.z, R[11])));
-        const uint32_t key = cell_key(x, y, w, cx, cy, cz, inv_cell);
-        keys[i] = key;
-        atomicAdd(&h[key], 1);
-    }
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[keys[i] & (REORDER_KEYS - 1)], 1);
     __syncthreads();
     for (int k = threadIdx.x; k < REORDER_KEYS; k += blockDim.x) cnt[int64_t(blockIdx.x) * REORDER_KEYS + k] = h[k];
 }
@@ -730,52 +702,68 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
                                                           t->reg_bar, t->reg_obj);
     }
     // a large source that fits the tree's free point buffer is reordered
-    // first: keys in the dead hand-off codes, per-CTA counts and key totals
-    // in the build's partials (both free after the build)
-    // (CTAs: two per SM, fewer if the counts would not fit)
+    // after its first round: node keys in the dead hand-off codes, per-CTA
+    // counts and key totals in the build's partials (both free after the
+    // build); CTAs: two per SM, fewer if the counts would not fit
     const int reorder_ctas =
         int(std::min<int64_t>(2 * t->n_sm, t->max_items * NPART * 2 / REORDER_KEYS - 1));
-    if (iters > 0 && n >= REORDER_MIN_POINTS && n64 <= t->cap && reorder_ctas >= 32) {
-        ProfScope ps_(t, K_REG_INIT, s);
-        float4* sorted = t->pts[t->depth & 1];
-        int* cnt = reinterpret_cast<int*>(t->partials);
-        int* tot = cnt + int64_t(reorder_ctas) * REORDER_KEYS;
-        k_src_keys<<<reorder_ctas, REORDER_THREADS, 0, s>>>(src, n, t->root, t->reg_Rt, t->codes, cnt);
-        k_src_colscan<<<REORDER_KEYS / 256, 256, 0, s>>>(cnt, reorder_ctas, tot);
-        k_src_keyscan<<<1, 1024, 0, s>>>(tot);
-        k_src_scatter<<<reorder_ctas, REORDER_THREADS, 0, s>>>(src, n, t->codes, cnt, tot, sorted);
-        src = sorted;
-    }
-    if (iters > 0) {
+    const bool reorder = iters > 1 && n >= REORDER_MIN_POINTS && n64 <= t->cap && reorder_ctas >= 32 &&
+                         n_nodes < REORDER_KEYS && !t->trace_on;
+    auto launch = [&](const float4* pts, int rounds, double* hist, uint32_t* keys) -> int {
         RegArgs a;
-        a.src = src;
+        a.src = pts;
         a.n = n;
         a.est = t->est;
         a.rnode = t->rnode;
         a.root = t->root;
         a.depth = t->depth;
         a.n_nodes = n_nodes;
-        a.iters = iters;
+        a.iters = rounds;
         a.acc = t->reg_acc;
         a.part = t->reg_part;
         a.bar = t->reg_bar;
         a.T = t->reg_T;
         a.Rt = t->reg_Rt;
-        a.T_hist = T_hist;
+        a.T_hist = hist;
         a.dbg = t->reg_dbg;
         a.obj = t->reg_obj;
         a.status = t->status;
-        a.trace = (t->trace_on && iters <= TRACE_MAX_ITERS) ? t->trace : nullptr;
-        if (a.trace) cudaMemsetAsync(t->trace, 0, size_t(iters) * t->reg_grid * TRACE_EVENTS * 8, s);
-        t->trace_iters = a.trace ? iters : 0;
+        a.keys = keys;
+        a.trace = (t->trace_on && rounds <= TRACE_MAX_ITERS) ? t->trace : nullptr;
+        if (a.trace) cudaMemsetAsync(t->trace, 0, size_t(rounds) * t->reg_grid * TRACE_EVENTS * 8, s);
+        t->trace_iters = a.trace ? rounds : 0;
         void* args[] = {&a};
         ProfScope ps_(t, K_DESCEND, s);
-        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_register, dim3(t->reg_grid),
-                                                          dim3(REG_THREADS), args, REG_DYN_SMEM, s);
+        const void* fn = keys ? (const void*)k_register<true> : (const void*)k_register<false>;
+        const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(t->reg_grid), dim3(REG_THREADS), args,
+                                                          REG_DYN_SMEM, s);
         if (e != cudaSuccess) {
             fprintf(stderr, "hgmm: cooperative launch failed: %s\n", cudaGetErrorString(e));
             return HGMM_ECUDA;
         }
+        return HGMM_OK;
+    };
+    if (reorder) {
+        // round 1 in the caller's order, recording each point's node
+        if (int rc = launch(src, 1, T_hist, t->codes)) return rc;
+        {
+            ProfScope ps_(t, K_REG_INIT, s);
+            float4* sorted = t->pts[t->depth & 1];
+            int* cnt = reinterpret_cast<int*>(t->partials);
+            int* tot = cnt + int64_t(reorder_ctas) * REORDER_KEYS;
+            k_src_count<<<reorder_ctas, REORDER_THREADS, 0, s>>>(t->codes, n, cnt);
+            k_src_colscan<<<REORDER_KEYS / 256, 256, 0, s>>>(cnt, reorder_ctas, tot);
+            k_src_keyscan<<<1, 1024, 0, s>>>(tot);
+            k_src_scatter<<<reorder_ctas, REORDER_THREADS, 0, s>>>(src, n, t->codes, cnt, tot, sorted);
+            src = sorted;
+            // the remaining rounds start from the pose after round 1
+            k_reg_init<<<(n_nodes + 255) / 256, 256, 0, s>>>(t->reg_T, n_nodes, lam_c, t->stat, t->est,
+                                                              t->reg_acc, t->reg_T, t->reg_Rt,
+                                                              t->reg_bar, t->reg_obj);
+        }
+        if (int rc = launch(src, iters - 1, T_hist ? T_hist + 16 : nullptr, nullptr)) return rc;
+    } else if (iters > 0) {
+        if (int rc = launch(src, iters, T_hist, nullptr)) return rc;
     }
     if (T_out) {
         ProfScope ps_(t, K_COPY_T, s);
@@ -832,14 +820,19 @@ int hgmm_register_descent_impl(hgmm_tree* t, const float4* src, int64_t n64, con
 }
 
 int hgmm_register_grid(int n_sm) {
-    int per_sm = 0;
-    // static + dynamic shared memory exceeds the 48 KB default: opt in
-    if (cudaFuncSetAttribute(k_register, cudaFuncAttributeMaxDynamicSharedMemorySize, int(REG_DYN_SMEM)) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_register, REG_THREADS, REG_DYN_SMEM) != cudaSuccess ||
-        per_sm < 1)
-        return 0;
-    return n_sm * (per_sm < 2 ? per_sm : 2);  // <= co-resident CTAs (cooperative launch)
+    // static + dynamic shared memory exceeds the 48 KB default: opt in; the
+    // grid must be co-resident for both variants of the kernel
+    int per_sm = 2;
+    const void* fns[2] = {(const void*)k_register<false>, (const void*)k_register<true>};
+    for (const void* fn : fns) {
+        int k = 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(REG_DYN_SMEM)) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fn, REG_THREADS, REG_DYN_SMEM) != cudaSuccess || k < 1)
+            return 0;
+        per_sm = std::min(per_sm, k);
+    }
+    return n_sm * per_sm;  // <= co-resident CTAs (cooperative launch)
 }
 
 int hgmm_trace_read_impl(hgmm_tree* t, unsigned long long* h, int64_t cap) {

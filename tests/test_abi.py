@@ -34,7 +34,8 @@ def test_header_declares_the_boundary():
                  "hgmm_mlp_train_step", "hgmm_pose_decode", "hgmm_pose_select",
                  "hgmm_register_objective", "hgmm_flat_register", "hgmm_flat_fit", "hgmm_register_descent",
                  "hgmm_debug_posteriors", "hgmm_propose", "hgmm_batch_debug_tree", "hgmm_batch_debug_root",
-                 "hgmm_fit_level0_noalloc", "hgmm_batch_set_build_shape", "hgmm_batch_get_build_shape"]:
+                 "hgmm_fit_level0_noalloc", "hgmm_batch_set_build_shape", "hgmm_batch_get_build_shape",
+                 "hgmm_batch_pair_ns"]:
         assert must in names
 
 
@@ -80,6 +81,7 @@ def test_host_side_argument_checks(lib):
     assert B._lib.hgmm_batch_debug_root(None, 0, None) == B.HGMM_EINVAL
     assert B._lib.hgmm_batch_set_build_shape(None, 0, 4, 8, 64) == B.HGMM_EINVAL
     assert B._lib.hgmm_batch_get_build_shape(None, None, None) == B.HGMM_EINVAL
+    assert B._lib.hgmm_batch_pair_ns(None, None, 0) == B.HGMM_EINVAL
     assert B.HGMM_MLP_PARAMS == 256 * 1280 + 256 + 256 * 256 + 256 + 9 * 256 + 9
     d = B.hgmm_descent(B.HGMM_DESCENT_MULTIPATH, 0.01, -1.0, 0)
     assert B._lib.hgmm_register_descent(None, None, 100, None, 3, ctypes.byref(d), None, None, None) == B.HGMM_EINVAL

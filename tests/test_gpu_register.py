@@ -194,13 +194,14 @@ def test_depth_pair_free_running(B):
 
 
 def test_large_unordered_source_is_reordered_without_changing_the_result(B):
-    """A source of at least 2^20 points is counting-sorted by its path
-    through the top of the tree before the rounds.  The node moments are
-    exact integer sums of per-warp FP32 group sums, so the order of the
-    source points moves the pose only by the rounding of those group sums:
-    the same cloud in two random orders gives the same 3 rounds to 1e-6 deg
-    and 1e-8 of the extent, and the first round matches one oracle round on
-    the GPU's tree."""
+    """A source of at least 2^20 points runs its first round in the given
+    order, recording each point's node, and is then counting-sorted by that
+    node for the remaining rounds.  The node moments are exact integer sums
+    of per-warp FP32 group sums, so the order of the source points moves the
+    pose only by the rounding of those group sums: the same cloud in two
+    random orders gives the same 3 rounds to 1e-6 deg and 1e-8 of the extent;
+    the first round matches one oracle round on the GPU's tree, and so does
+    the second (after the reorder) from the GPU's pose after the first."""
     import torch
     rng = np.random.default_rng(5)
     p = synth.primitive_pair(17, 1_200_000, max_deg=3.0, max_t=0.02)
@@ -223,4 +224,7 @@ def test_large_unordered_source_is_reordered_without_changing_the_result(B):
     Zs = src4[:, :3].astype(np.float64)
     T_o = O.register(ot, Zs, iters=1)
     r, t = PT.pose_errors(outs[0][0], T_o, extent)
+    assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (r, t)
+    T_o2 = O.register(ot, Zs, T_init=outs[0][0], iters=1)
+    r, t = PT.pose_errors(outs[0][1], T_o2, extent)
     assert r < PT.ROT_TOL_DEG and t < PT.TRANS_TOL_REL, (r, t)
