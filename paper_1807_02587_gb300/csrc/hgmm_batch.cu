@@ -89,6 +89,75 @@ struct RegSmem {
 constexpr size_t BATCH_DYN_SMEM =
     STAGED_F4 * sizeof(float4) + 4 * STAGED_NODES * sizeof(unsigned long long);
 
+// Sources of at least this many points are reordered by their first-round
+// node before the second round (below that the sort costs about what it saves).
+constexpr int BATCH_REORDER_MIN = 16384;
+
+// Counting sort of the pair's source points by the node each reached in the
+// first round (keys: node id, all ones = none -> key n_nodes), by the
+// cluster's CTAs: each CTA counts the keys of its contiguous range into
+// shared memory (h, n_nodes + 1 ints), every CTA reads all the cluster's
+// counts through distributed shared memory and scans them in key order (key,
+// then CTA rank), and each CTA scatters its range to the key's next slot.  The
+// order within a key follows shared-memory atomics; the descent's moments are
+// exact fixed-point sums, so the pose does not depend on it.
+__device__ void sort_source_by_node(const float4* __restrict__ src, int n, int n_nodes,
+                                    const uint32_t* __restrict__ keys, float4* __restrict__ dst, int rank,
+                                    int cs, cg::cluster_group& cl, int* h) {
+    __shared__ int scan_w[EST_THREADS / 32];
+    const int nk = n_nodes + 1;
+    const int lo = int((int64_t(rank) * n) / cs), hi = int((int64_t(rank + 1) * n) / cs);
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint32_t k = keys[i];
+        atomicAdd(&h[k < uint32_t(n_nodes) ? int(k) : n_nodes], 1);
+    }
+    cl.sync();  // every CTA's counts complete
+    // thread t owns keys [t * per, (t + 1) * per): totals over the cluster
+    // and the counts of the CTAs before this one
+    const int per = (nk + int(blockDim.x) - 1) / int(blockDim.x);
+    const int k0 = min(nk, int(threadIdx.x) * per), k1 = min(nk, k0 + per);
+    int mine = 0;
+    for (int k = k0; k < k1; ++k)
+        for (int r = 0; r < cs; ++r) mine += cl.map_shared_rank(h, r)[k];
+    // exclusive scan of the threads' totals (warp shuffles, then warp totals)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) scan_w[warp] = incl;
+    __syncthreads();
+    int base = incl - mine;
+    for (int w = 0; w < warp; ++w) base += scan_w[w];
+    // first slot of each owned key for this CTA: keys before it (all CTAs),
+    // then this key's points in the CTAs before this one
+    int pos[32];
+    int run = base;
+    for (int k = k0, j = 0; k < k1; ++k, ++j) {
+        int before = 0, tot = 0;
+        for (int r = 0; r < cs; ++r) {
+            const int c = cl.map_shared_rank(h, r)[k];
+            tot += c;
+            if (r < rank) before += c;
+        }
+        pos[j] = run + before;
+        run += tot;
+    }
+    cl.sync();  // every CTA has read the counts: they may be overwritten
+    for (int k = k0, j = 0; k < k1; ++k, ++j) h[k] = pos[j];
+    __syncthreads();
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint32_t k = keys[i];
+        const int slot = atomicAdd(&h[k < uint32_t(n_nodes) ? int(k) : n_nodes], 1);
+        if (slot >= 0 && slot < n) dst[slot] = src[i];
+    }
+    cl.sync();  // the sorted cloud is complete for the whole cluster
+}
+
 // One pair, run by all CTAs of this cluster.
 template <bool COMP>
 __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair, cg::cluster_group& cl,
@@ -170,10 +239,22 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair
     cl.sync();
     const double ext = __ldcg(&w.root->extent) > 0.0 ? __ldcg(&w.root->extent) : 1.0;
     const float qscale = float(FIX / ext);
+    // large sources: nodes recorded in the first round (the hand-off codes are
+    // free after the build), the cloud sorted by them into a ping-pong buffer
+    // before the second; the sort borrows the staged nodes' shared memory
+    const bool sort_src = a.iters >= 2 && n_s >= BATCH_REORDER_MIN &&
+                          n_nodes + 1 <= int(STAGED_F4 * sizeof(float4) / sizeof(int));
     for (int it = 0; it < a.iters; ++it) {
+        if (it == 1 && sort_src) {
+            sort_source_by_node(src, n_s, n_nodes, w.codes, w.pts[0], rank, cs, cl,
+                                reinterpret_cast<int*>(sm_est));
+            src = w.pts[0];
+            stage_nodes(sm_est, w.est, n_nodes < STAGED_NODES ? n_nodes : STAGED_NODES);
+        }
         if (threadIdx.x < 12) rgs.Rt[threadIdx.x] = __ldcg(w.Rt + threadIdx.x);
         __syncthreads();
-        descend_points(src, n_s, w.est, sm_est, depth, rgs.Rt, qscale, w.acc, rank, cs, hist);
+        descend_points<true>(src, n_s, w.est, sm_est, depth, rgs.Rt, qscale, w.acc, rank, cs, hist,
+                             it == 0 && sort_src ? w.codes : nullptr);
         __syncthreads();
         flush_node_hist(hist, n_nodes < STAGED_NODES ? n_nodes : STAGED_NODES, w.acc);
         cl.sync();

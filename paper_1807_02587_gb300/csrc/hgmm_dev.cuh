@@ -1450,14 +1450,14 @@ __device__ __forceinline__ void load_child(const NodeEst* __restrict__ est, cons
     }
 }
 
-// Sums (v0..v3) over the lanes of the warp that hold the same key (all 32
+// Sums (v[0..NV)) over the lanes of the warp that hold the same key (all 32
 // lanes call it): a pairwise tree over the members' ranks (fixed order, so
 // deterministic).  Returns the lane's rank in its group; rank 0 holds the
-// group's sums, which it then adds to the node's fixed-point moments with
-// one atomic per value (integer adds are exact, so the node totals do not
-// depend on the order in which groups arrive).
-template <int NV>
-__device__ __forceinline__ int warp_group_sum(int key, float (&v)[NV]) {
+// group's sums.  The registration descent sums 64-bit fixed-point values
+// (exact: the node totals depend neither on the order in which groups arrive
+// nor on how the points are grouped into warps).
+template <int NV, typename V = float>
+__device__ __forceinline__ int warp_group_sum(int key, V (&v)[NV]) {
     const int lane = threadIdx.x & 31;
     const unsigned peers = __match_any_sync(FULL, key);
     const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -1472,7 +1472,7 @@ __device__ __forceinline__ int warp_group_sum(int key, float (&v)[NV]) {
 #pragma unroll
     for (int st = 1; st < 32; st <<= 1) {
         if (st >= gmax) break;  // warp-uniform: no group has a member st above
-        float o[NV];
+        V o[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) o[q] = __shfl_sync(FULL, v[q], nxt);
         if ((rank & (2 * st - 1)) == 0 && rank + st < gsize) {
@@ -1484,15 +1484,8 @@ __device__ __forceinline__ int warp_group_sum(int key, float (&v)[NV]) {
     return rank;
 }
 
-__device__ __forceinline__ int warp_group_sum4(int key, float& v0, float& v1, float& v2, float& v3) {
-    float v[4] = {v0, v1, v2, v3};
-    const int rank = warp_group_sum<4>(key, v);
-    v0 = v[0]; v1 = v[1]; v2 = v[2]; v3 = v[3];
-    return rank;
-}
-
-// KEYS: key_out receives each point's chosen node (all ones: none), for the
-// source reorder between the first and the second round.
+// KEYS: key_out (if not null) receives each point's chosen node (all ones:
+// none), for the source reorder between the first and the second round.
 // hist (shared memory, 4 x STAGED_NODES fixed-point words, zero on entry, or
 // null): the groups whose node is one of the staged top levels add into the
 // CTA's own histogram instead of global memory; flush_node_hist then moves it
@@ -1567,21 +1560,27 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             const float4 cm = chosen < STAGED_NODES ? sm_est[staged_slot(chosen)] : __ldg(&est[chosen].a);
             cmx = cm.x; cmy = cm.y; cmz = cm.z;
         }
-        if (KEYS && valid) key_out[i] = has ? uint32_t(chosen) : 0xFFFFFFFFu;  // the point's node
-        float v0 = has ? gamma : 0.f;
-        float v1 = has ? gamma * (x - cmx) : 0.f;
-        float v2 = has ? gamma * (y - cmy) : 0.f;
-        float v3 = has ? gamma * (w - cmz) : 0.f;
-        const int rank = warp_group_sum4(chosen, v0, v1, v2, v3);
+        if (KEYS && key_out && valid) key_out[i] = has ? uint32_t(chosen) : 0xFFFFFFFFu;  // the point's node
+        // each point's moments as fixed-point integers before any sum: the
+        // per-warp group sums and the node totals are then exact integer
+        // sums, independent of the order of the points
+        long long q[4] = {0, 0, 0, 0};
+        if (has) {
+            q[0] = to_fix(gamma * 4294967296.0f);
+            q[1] = to_fix(gamma * (x - cmx) * qscale);
+            q[2] = to_fix(gamma * (y - cmy) * qscale);
+            q[3] = to_fix(gamma * (w - cmz) * qscale);
+        }
+        const int rank = warp_group_sum<4, long long>(chosen, q);
         if (has && rank == 0) {
             unsigned long long* dst =
                 (hist && chosen < STAGED_NODES)
                     ? hist + 4 * chosen
                     : acc + 4 * (int64_t(chosen) * ACC_REPLICAS + (cta & (ACC_REPLICAS - 1)));
-            atomicAdd(dst + 0, (unsigned long long)to_fix(v0 * 4294967296.0f));
-            atomicAdd(dst + 1, (unsigned long long)to_fix(v1 * qscale));
-            atomicAdd(dst + 2, (unsigned long long)to_fix(v2 * qscale));
-            atomicAdd(dst + 3, (unsigned long long)to_fix(v3 * qscale));
+            atomicAdd(dst + 0, (unsigned long long)q[0]);
+            atomicAdd(dst + 1, (unsigned long long)q[1]);
+            atomicAdd(dst + 2, (unsigned long long)q[2]);
+            atomicAdd(dst + 3, (unsigned long long)q[3]);
         }
     }
 }

@@ -286,9 +286,9 @@ __global__ void k_barrier_timeout_probe(unsigned* bar, int* status, long long li
 // runs its first round in the caller's order, with every point's chosen node
 // recorded; it is then counting-sorted by that node (into a library buffer)
 // and runs the remaining rounds in that order, where the 32 points of a warp
-// mostly follow one path.  The node moments are exact integer sums of
-// per-warp FP32 group sums, so the order of the points changes the result
-// only by the FP32 rounding of those group sums.
+// mostly follow one path.  The node moments are exact integer sums of the
+// points' fixed-point moments, so the order of the points does not change
+// the result at all.
 constexpr int REORDER_MIN_POINTS = 1 << 20;
 constexpr int REORDER_KEYS = 8192;  // node ids of trees up to depth 4 (4,680 nodes); the last: no node
 constexpr int REORDER_THREADS = 256;
@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(1024) k_src_keyscan(int* __restrict__ tot) {
 }
 
 // Pass 3: every point to its key's next slot of its CTA (shared-memory
-// counters: the order within a CTA's key is not fixed, so neither are the
-// per-warp FP32 group sums, to their rounding).
+// counters: the order within a CTA's key is not fixed, which the exact
+// fixed-point moments of the descent do not see).
 __global__ void __launch_bounds__(REORDER_THREADS) k_src_scatter(const float4* __restrict__ src, int n,
                                                                  const uint32_t* __restrict__ keys,
                                                                  const int* __restrict__ cnt,
@@ -387,7 +387,7 @@ __global__ void k_copy_T(const double* __restrict__ T, double* __restrict__ out)
 // as in Algorithm 1) and pushes the child the variant keeps (the
 // maximum-likelihood one, or every live child whose expectation reaches
 // tau), or, if it has no live child, is emitted itself.  Emissions of the
-// warp's step are summed per node (warp_group_sum4) and added to the node's
+// warp's step are summed per node (warp_group_sum) and added to the node's
 // fixed-point moments.  The stack bound 8 x depth holds for any tau: a step
 // removes one entry and adds at most 8, and a level never holds more than 7
 // pending siblings.
