@@ -1571,7 +1571,24 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
             q[2] = to_fix(gamma * (y - cmy) * qscale);
             q[3] = to_fix(gamma * (w - cmz) * qscale);
         }
-        const int rank = warp_group_sum<4, long long>(chosen, q);
+        int rank;
+        if (__all_sync(FULL, chosen == __shfl_sync(FULL, chosen, 0))) {
+            // one group (every point of the warp chose the same node, as
+            // most do once the source is in node order): warp reductions of
+            // two biased limbs per value, q + 2^40 = l0 + 2^21 l1 with
+            // l0 < 2^21, l1 <= 2^20, so the 32-lane sums stay below 2^26:
+            // the same exact integer totals as the group tree
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const unsigned long long u = (unsigned long long)(q[v] + (1ll << 40));
+                const unsigned s0 = __reduce_add_sync(FULL, unsigned(u) & 0x1FFFFFu);
+                const unsigned s1 = __reduce_add_sync(FULL, unsigned(u >> 21));
+                q[v] = (long long)s0 + ((long long)s1 << 21) - (32ll << 40);
+            }
+            rank = lane;
+        } else {
+            rank = warp_group_sum<4, long long>(chosen, q);
+        }
         if (has && rank == 0) {
             unsigned long long* dst =
                 (hist && chosen < STAGED_NODES)

@@ -102,6 +102,16 @@ def test_batch_autotune_and_nonfinite_pair(B):
     assert s[3] == B.HGMM_ENONFINITE
     assert np.all(s[[0, 1, 2, 4, 5]] == 0)
     assert np.all(np.isfinite(T.cpu().numpy()[[0, 1, 2, 4, 5]]))
+    # per-pair device times of that launch: every pair ran, none longer than
+    # the launch itself (timed on the host around a synchronised launch)
+    import time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.hgmm_batch_register(bat.handle, both, T, iters=5, pair_status=st)
+    torch.cuda.synchronize()
+    wall_ns = (time.perf_counter() - t0) * 1e9
+    ns = B.hgmm_batch_pair_ns(bat.handle, 6)
+    assert np.all(ns > 0) and np.all(ns < wall_ns), (ns, wall_ns)
 
 
 def test_batch_plan_rejects_bad_pairs(B):
