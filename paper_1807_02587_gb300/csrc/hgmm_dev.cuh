@@ -1520,18 +1520,16 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
         int chosen = -1;
         float gamma = 0.f, cmx = 0.f, cmy = 0.f, cmz = 0.f;
         int local = 0;  // index within its level of the current search node
+        int off = 0;    // first node of the level (32-bit: a depth-5 tree has 37,448 nodes)
         for (int l = 0; l < depth && valid; ++l) {
-            const int64_t first = d_level_offset(l) + 8 * int64_t(local);
+            const int first = off + 8 * local;
+            off = 8 * off + 8;  // the next level's first node
             float sc8[8];
             float best = -CUDART_INF_F;
             int bi = -1;
             float bstop = 0.f;  // the best child's stop flag (its mean is read once, after the descent)
-            const bool staged = first < STAGED_NODES;
-            const float4* blk = sm_est + (staged ? staged_slot(int(first)) : 0);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float4 ea, eb, ec;
-                load_child(est, blk, staged, first, c, ea, eb, ec);
+            // one child's log2 score from its three records, and the running argmax
+            auto score = [&](int c, const float4 ea, const float4 eb, const float4 ec) {
                 const float ex = x - ea.x, ey = y - ea.y, ez = w - ea.z;
                 const float d0 = eb.x * ex;
                 const float d1 = fmaf(eb.z, ey, eb.y * ex);
@@ -1545,13 +1543,24 @@ __device__ __forceinline__ void descend_points(const float4* __restrict__ src, i
                     bi = c;
                     bstop = ec.z;
                 }
+            };
+            // the staged levels (the same level for every lane still
+            // descending) read shared memory, deeper levels the cache
+            if (first < STAGED_NODES) {
+                const float4* blk = sm_est + staged_slot(first);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) score(c, blk[3 * c], blk[3 * c + 1], blk[3 * c + 2]);
+            } else {
+                const NodeEst* e = est + first;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) score(c, __ldg(&e[c].a), __ldg(&e[c].b), __ldg(&e[c].c));
             }
             if (bi < 0) break;  // the current node has no live children
             float sum = 0.f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) sum += ex2_fast(sc8[c] - best);
             gamma = rcp_fast(sum);
-            chosen = int(first + bi);
+            chosen = first + bi;
             local = 8 * local + bi;
             if (bstop != 0.f) break;  // Complexity <= lambda_c
         }
