@@ -53,7 +53,7 @@ KERNEL_WORK = {
     "scatter": {"bytes": 44, "flops": 0, "unit": "target point"},
     "register": {"bytes": 16, "flops": None, "unit": "source point"},
 }
-REGISTER_TRAFFIC_BYTES = 1959936
+REGISTER_TRAFFIC_BYTES = 1966336
 DESCEND_FLOPS_PER_LEVEL = 8 * 18 + 8 * 2 + 8  # 8 child scores, 8 exp2 + sum, rcp
 DESCEND_FLOPS_FIXED = 18 + 12  # transform, fixed-point conversion
 
