@@ -33,9 +33,10 @@
  *     every call must run with that device current.
  *   - No entry point except hgmm_tree_create / hgmm_tree_destroy allocates or
  *     frees device memory, so build + register can be captured in a CUDA graph
- *     (the registration is one cooperative launch).
- *   - Device-side waits are bounded: the registration's arrival and pose
- *     generation waits give up after about a second, record HGMM_ETIMEOUT and
+ *     (the registration is one cooperative launch; two, around an on-device
+ *     reorder, for sources of 2^20 points or more).
+ *   - Device-side waits are bounded: the registration's arrival and partial-
+ *     count waits give up after about a second, record HGMM_ETIMEOUT and
  *     return.
  */
 #ifndef HGMM_H
@@ -126,6 +127,10 @@ int hgmm_build(hgmm_tree* t, const float* d_points, int64_t n, int32_t depth,
  * lam_c = 0 disables the early stop (the paper's "GMM-Tree" variant).  The
  * final T is written to d_T_out (16 float64, device).  If d_T_hist is not
  * NULL it receives the T after every round (iters x 16 float64, device).
+ * The node moments are exact fixed-point sums of every point's moments, so
+ * the result does not depend on the order of the source points; a source of
+ * 2^20 points or more (up to max_points) is sorted by its first-round nodes
+ * into the tree's free point buffer for the remaining rounds.
  * Errors: HGMM_EINVAL, HGMM_ECUDA; singular normal equations are reported by
  * hgmm_sync as HGMM_EDEGENERATE (T is then left unchanged in that round). */
 int hgmm_register(hgmm_tree* t, const float* d_src, int64_t n,
@@ -239,14 +244,14 @@ int hgmm_profile_read(hgmm_tree* t, int32_t kernel, const char** name, double* t
                       int64_t* launches);
 
 /* Registration phase trace: with hgmm_trace(t, 1) the next hgmm_register
- * (up to 64 rounds) records, per round and per CTA of its cooperative launch,
- * 6 %globaltimer stamps in ns: round start; descent and moment flush done
- * (the CTA's arrival); all arrivals seen (only the CTAs that own nodes wait
- * for them, 0 elsewhere); node terms done (0 on CTAs without nodes); solve
- * done (only the CTA that solved, 0 elsewhere); the round's pose generation
- * seen.  hgmm_trace_read synchronises and copies iters x ctas x 6 int64
- * (cap = capacity in int64) and reports the dimensions.  Tracing only adds
- * the stamps; results are unchanged. */
+ * (up to 64 rounds, in one launch: no source reorder while tracing) records,
+ * per round and per CTA of its cooperative launch, 6 %globaltimer stamps in
+ * ns: round start; descent and moment flush done (the CTA's arrival); all
+ * arrivals seen (only the CTAs that own nodes wait for them, 0 elsewhere);
+ * node terms published (0 on CTAs without nodes); all partials seen; the
+ * CTA's solve and pose update done.  hgmm_trace_read synchronises and copies
+ * iters x ctas x 6 int64 (cap = capacity in int64) and reports the
+ * dimensions.  Tracing only adds the stamps; results are unchanged. */
 int hgmm_trace(hgmm_tree* t, int32_t enable);
 int hgmm_trace_read(hgmm_tree* t, int64_t* h_events, int64_t cap, int32_t* iters,
                     int32_t* ctas);
