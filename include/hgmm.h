@@ -32,7 +32,8 @@
  *   - The tree lives on the device that was current at hgmm_tree_create and
  *     every call must run with that device current.
  *   - No entry point except hgmm_tree_create / hgmm_tree_destroy allocates or
- *     frees device memory, so build + register can be captured in a CUDA graph
+ *     frees device memory (hgmm_register_pair_host creates the CUDA stream and
+ *     graph it replays), so build + register can be captured in a CUDA graph
  *     (the registration is one cooperative launch; two, around an on-device
  *     reorder, for sources of 2^20 points or more).
  *   - Device-side waits are bounded: the registration's arrival and partial-
@@ -188,7 +189,12 @@ int hgmm_sync(hgmm_tree* t, void* stream);
  * source (n x 4 float32 each, host; pinned memory is fastest) to the tree's
  * device staging buffers, build the target's tree, register the source from
  * h_T_init (NULL = identity) and copy the result to h_T_out (16 float64,
- * host).  Synchronous.  Errors: as hgmm_build, hgmm_register, hgmm_sync. */
+ * host).  The first call of a shape (point counts, depth, parameters, rounds,
+ * with or without h_T_init) captures the build and the registration into a
+ * CUDA graph on a stream the tree owns; later calls of that shape replay it
+ * (one launch instead of about 80); another shape replaces it.  Not while
+ * profiling or tracing.  Synchronous.  Errors: as hgmm_build, hgmm_register,
+ * hgmm_sync. */
 int hgmm_register_pair_host(hgmm_tree* t, const float* h_tgt, int64_t n_tgt,
                             const float* h_src, int64_t n_src, int32_t depth,
                             const hgmm_params* p, const double* h_T_init,

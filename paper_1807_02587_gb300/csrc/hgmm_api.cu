@@ -43,6 +43,8 @@ void free_tree(hgmm_tree* t) {
     cudaGetDevice(&cur);
     cudaSetDevice(t->device);
     clear_prof(t);
+    if (t->pair_exec) cudaGraphExecDestroy(t->pair_exec);
+    if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
     void* ptrs[] = {t->est, t->stat, t->seg_start, t->seg_count, t->pts[0], t->pts[1],
                     t->codes, t->items, t->item_range, t->meta, t->partials, t->item_cnt,
                     t->item_off, t->slice_tot, t->root, t->root_part, t->root_counter, t->em_cnt, t->mslices, t->mcnt, t->status, t->reg_acc, t->reg_acc2, t->reg_part,
@@ -281,11 +283,61 @@ int hgmm_register_pair_host(hgmm_tree* t, const float* h_tgt, int64_t n_tgt, con
             return HGMM_ECUDA;
         dTi = t->stage_T;
     }
-    int rc = hgmm_build(t, reinterpret_cast<const float*>(t->stage_tgt), n_tgt, depth, HGMM_J, p, stream);
-    if (rc) return rc;
-    rc = hgmm_register(t, reinterpret_cast<const float*>(t->stage_src), n_src, dTi, iters, -1.f,
-                       stream, t->stage_T + 16, nullptr);
-    if (rc) return rc;
+    hgmm_params prm;
+    if (p) prm = *p;
+    else hgmm_params_default(&prm);
+    auto enqueue = [&](void* st) -> int {
+        int rc = hgmm_build(t, reinterpret_cast<const float*>(t->stage_tgt), n_tgt, depth, HGMM_J, &prm, st);
+        if (rc) return rc;
+        return hgmm_register(t, reinterpret_cast<const float*>(t->stage_src), n_src, dTi, iters, -1.f, st,
+                             t->stage_T + 16, nullptr);
+    };
+    // the build and the registration as one CUDA graph, captured for this
+    // shape on the tree's own stream (the caller's may be the legacy default
+    // stream, which cannot be captured) and replayed on the caller's stream:
+    // the ~80 kernels of a step cost one launch.  Not while profiling or
+    // tracing (their events and stamps are per launch).
+    const int64_t key[5] = {n_tgt, n_src, depth, iters, h_T_init ? 1 : 0};
+    bool use_graph = !t->prof_on && !t->trace_on && !t->pair_graph_failed;
+    if (use_graph) {
+        const bool same = t->pair_exec && std::memcmp(key, t->pair_key, sizeof(key)) == 0 &&
+                          std::memcmp(&prm, &t->pair_prm, sizeof(prm)) == 0;
+        if (!same) {
+            if (t->pair_exec) {
+                cudaGraphExecDestroy(t->pair_exec);
+                t->pair_exec = nullptr;
+            }
+            if (!t->cap_stream && !ok(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking), "stream"))
+                return HGMM_ECUDA;
+            // the staging copies above (on s) come before the captured work
+            if (!ok(cudaStreamSynchronize(s), "sync")) return HGMM_ECUDA;
+            cudaGraph_t g = nullptr;
+            if (!ok(cudaStreamBeginCapture(t->cap_stream, cudaStreamCaptureModeThreadLocal), "capture"))
+                return HGMM_ECUDA;
+            const int rc = enqueue(t->cap_stream);
+            const cudaError_t ec = cudaStreamEndCapture(t->cap_stream, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ec != cudaSuccess || !g || cudaGraphInstantiate(&t->pair_exec, g, 0) != cudaSuccess) {
+                (void)cudaGetLastError();
+                if (g) cudaGraphDestroy(g);
+                t->pair_exec = nullptr;
+                t->pair_graph_failed = true;  // this tree runs the host API eagerly from now on
+                use_graph = false;
+            } else {
+                cudaGraphDestroy(g);
+                std::memcpy(t->pair_key, key, sizeof(key));
+                t->pair_prm = prm;
+            }
+        }
+    }
+    if (use_graph) {
+        if (!ok(cudaGraphLaunch(t->pair_exec, s), "graph launch")) return HGMM_ECUDA;
+    } else if (int rc = enqueue(stream)) {
+        return rc;
+    }
     if (!ok(cudaMemcpyAsync(h_T_out, t->stage_T + 16, 16 * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"))
         return HGMM_ECUDA;
     return hgmm_sync(t, stream);

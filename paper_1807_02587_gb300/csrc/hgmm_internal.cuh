@@ -193,6 +193,13 @@ struct hgmm_tree {
     float4* stage_tgt = nullptr;
     float4* stage_src = nullptr;
     double* stage_T = nullptr;              // 32 doubles: T_init, T_out
+    // host API: build + register of the last shape as a CUDA graph (captured
+    // on the tree's own stream), replayed by later calls of the same shape
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t pair_exec = nullptr;
+    int64_t pair_key[5] = {-1, -1, -1, -1, -1};  // n_tgt, n_src, depth, iters, T_init given
+    hgmm_params pair_prm{};
+    bool pair_graph_failed = false;
 };
 
 // Brackets one kernel launch with a CUDA event pair when profiling is on.

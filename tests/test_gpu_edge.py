@@ -112,17 +112,34 @@ def test_invalid_arguments(B):
 
 
 def test_host_entry_point_matches_device_path(B):
+    """The host-buffer entry point captures the build and the registration
+    of a shape into a CUDA graph on its first call and replays it later: the
+    first call, a replay, a call of another shape (a new capture) and the
+    first shape again all give the device path's bits."""
     import torch
     p = synth.corner_pair(11, n=6000, max_deg=3.0, max_t=0.02)
+    q = synth.corner_pair(12, n=5000, max_deg=3.0, max_t=0.02)
     tree = B.Tree(6000, 3)
-    T_host = B.hgmm_register_pair_host(tree.handle, synth.to_float4(p["tgt"]),
-                                       synth.to_float4(p["src"]), 3, B.params(), None, 12)
-    tgt, _ = PT.device_cloud(p["tgt"])
-    src, _ = PT.device_cloud(p["src"])
-    tree.build(tgt, 3)
-    T_dev = tree.register(src, iters=12).cpu().numpy()
-    tree.sync()
-    assert np.array_equal(T_host, T_dev)
+
+    def host(pair):
+        return B.hgmm_register_pair_host(tree.handle, synth.to_float4(pair["tgt"]),
+                                         synth.to_float4(pair["src"]), 3, B.params(), None, 12)
+
+    outs = [host(p), host(p), host(q), host(p)]
+
+    def device(pair):
+        tgt, _ = PT.device_cloud(pair["tgt"])
+        src, _ = PT.device_cloud(pair["src"])
+        tree.build(tgt, 3)
+        T = tree.register(src, iters=12).cpu().numpy()
+        tree.sync()
+        return T
+
+    T_p, T_q = device(p), device(q)
+    for k in (0, 1, 3):
+        assert np.array_equal(outs[k], T_p), k
+    assert np.array_equal(outs[2], T_q)
+    assert not np.array_equal(T_p, T_q)
 
 
 def test_bounded_wait_times_out_without_fault(B):
