@@ -43,6 +43,12 @@ __device__ __forceinline__ float rcp_fast(float x) {
     return y;
 }
 
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---------------------------------------------------------------- FP32 sums
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
@@ -172,11 +178,16 @@ __device__ inline void eig3(const double S[6], double lam[3], double V[9]) {
             const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
             const float apq = a[p][q];
             if (apq == 0.f) continue;
-            const float theta = (a[q][q] - a[p][p]) / (2.f * apq);
-            float t = 1.f / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            // the rotation from the multi-function unit's approximations
+            // (relative errors ~2^-22): this phase only brings the matrix
+            // near diagonal, and the FP64 sweeps below finish from whatever
+            // orthonormal basis it reaches
+            const float theta = (a[q][q] - a[p][p]) * rcp_fast(2.f * apq);
+            const float h = fmaf(theta, theta, 1.f);
+            float t = rcp_fast(fabsf(theta) + h * rsqrt_fast(h));  // 1 / (|theta| + sqrt(theta^2 + 1))
             if (theta < 0.f) t = -t;
-            if (fabsf(theta) > 1e18f) t = 0.5f / theta;
-            const float c = rsqrtf(t * t + 1.f), s = t * c;
+            if (fabsf(theta) > 1e18f) t = 0.5f * rcp_fast(theta);
+            const float c = rsqrt_fast(fmaf(t, t, 1.f)), s = t * c;
             a[p][p] -= t * apq;
             a[q][q] += t * apq;
             a[p][q] = a[q][p] = 0.f;
