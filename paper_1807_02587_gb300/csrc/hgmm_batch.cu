@@ -77,6 +77,7 @@ namespace {
 static_assert(ACC_REPLICAS == 1, "the batched node terms read one accumulator copy per node");
 
 struct RegSmem {
+    double T[12];  // the pair's pose (every CTA of the cluster solves the same system)
     float Rt[12];
     float2 sm[EST_THREADS / 32][NTERM];
     double tot[NTERM];
@@ -244,6 +245,10 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair
     // before the second; the sort borrows the staged nodes' shared memory
     const bool sort_src = a.iters >= 2 && n_s >= BATCH_REORDER_MIN &&
                           n_nodes + 1 <= int(STAGED_F4 * sizeof(float4) / sizeof(int));
+    if (threadIdx.x < 12) {
+        rgs.T[threadIdx.x] = __ldcg(w.T + threadIdx.x);
+        rgs.Rt[threadIdx.x] = __ldcg(w.Rt + threadIdx.x);
+    }
     for (int it = 0; it < a.iters; ++it) {
         if (it == 1 && sort_src) {
             sort_source_by_node(src, n_s, n_nodes, w.codes, w.pts[0], rank, cs, cl,
@@ -251,7 +256,6 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair
             src = w.pts[0];
             stage_nodes(sm_est, w.est, n_nodes < STAGED_NODES ? n_nodes : STAGED_NODES);
         }
-        if (threadIdx.x < 12) rgs.Rt[threadIdx.x] = __ldcg(w.Rt + threadIdx.x);
         __syncthreads();
         descend_points<true>(src, n_s, w.est, sm_est, depth, rgs.Rt, qscale, w.acc, rank, cs, hist,
                              it == 0 && sort_src ? w.codes : nullptr);
@@ -262,21 +266,22 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair
 #pragma unroll
         for (int k = 0; k < 32; ++k) { v[k] = 0.f; c[k] = 0.f; }
         for (int g = rank * blockDim.x + threadIdx.x; g < n_nodes; g += cs * blockDim.x) {
-            const long long a0 = (long long)__ldcg(w.acc + 4 * g + 0);
-            if (a0 == 0) continue;
-            const long long a1 = (long long)__ldcg(w.acc + 4 * g + 1);
-            const long long a2 = (long long)__ldcg(w.acc + 4 * g + 2);
-            const long long a3 = (long long)__ldcg(w.acc + 4 * g + 3);
-            w.acc[4 * g + 0] = 0ull;
-            w.acc[4 * g + 1] = 0ull;
-            w.acc[4 * g + 2] = 0ull;
-            w.acc[4 * g + 3] = 0ull;
-            if (a0 < 0) continue;
+            // the node's moments and constants in one round trip
+            const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(w.acc + 4 * int64_t(g));
+            const ulonglong2 q0 = __ldcg(ap), q1 = __ldcg(ap + 1);
+            const float4 r0 = __ldcg(w.rnode + 3 * g), r1 = __ldcg(w.rnode + 3 * g + 1);
+            const float4 r2 = __ldcg(w.rnode + 3 * g + 2), cm = __ldcg(&w.est[g].a);
+            const long long a0 = (long long)q0.x;
+            if ((q0.x | q0.y | q1.x | q1.y) == 0ull) continue;
+            ulonglong2* wp = reinterpret_cast<ulonglong2*>(w.acc + 4 * int64_t(g));
+            wp[0] = make_ulonglong2(0ull, 0ull);
+            wp[1] = make_ulonglong2(0ull, 0ull);
+            if (a0 <= 0) continue;
             const float M0 = float(a0) * 2.3283064365386963e-10f;  // 2^-32
             const float inv = 1.0f / (qscale * M0);
             float tn[NTERM];
-            node_terms(w.rnode[3 * g], w.rnode[3 * g + 1], w.rnode[3 * g + 2], w.est[g].a, M0,
-                       float(a1) * inv, float(a2) * inv, float(a3) * inv, M0 / float(n_s), tn);
+            node_terms(r0, r1, r2, cm, M0, float((long long)q0.y) * inv, float((long long)q1.x) * inv,
+                       float((long long)q1.y) * inv, M0 / float(n_s), tn);
 #pragma unroll
             for (int k = 0; k < NTERM; ++k) pair_add(v[k], c[k], tn[k], 0.f);
         }
@@ -292,28 +297,32 @@ __device__ void run_pair(const BatchArgs& a, const BatchWs& w, int cid, int pair
             w.reg_part[NTERM * rank + threadIdx.x] = make_float2(S, C);
         }
         cl.sync();
-        if (rank == 0) {
-            if (threadIdx.x < NTERM) {
-                float S = 0.f, C = 0.f;
-                for (int b = 0; b < cs; ++b) {
-                    const float2 x = __ldcg(&w.reg_part[NTERM * b + threadIdx.x]);
-                    pair_add(S, C, x.x, x.y);
-                }
-                rgs.tot[threadIdx.x] = double(S) + double(C);
+        // every CTA of the cluster reduces the partials in the same order and
+        // solves the same system (identical bits), so the new pose needs no
+        // hand-over through global memory and no further barrier: the next
+        // round's partials are written only after its first barrier, which
+        // every CTA reaches after this solve.  Rank 0 keeps the global copies.
+        if (threadIdx.x < NTERM) {
+            float S = 0.f, C = 0.f;
+            for (int b = 0; b < cs; ++b) {
+                const float2 x = __ldcg(&w.reg_part[NTERM * b + threadIdx.x]);
+                pair_add(S, C, x.x, x.y);
             }
-            __syncthreads();
-            if (threadIdx.x == 32 && a.obj && it == a.iters - 1) a.obj[pair] = rgs.tot[NTERM - 1];
-            if (warp == 0) {
-                const bool solved = warp_solve_update(rgs.tot, w.T, w.Rt, T_hist, it);
-                if (!solved && lane == 0) {
-                    atomicOr(w.status, ST_DEGENERATE);
-                    if (T_hist)
-                        for (int k = 0; k < 16; ++k) T_hist[16 * it + k] = w.T[k];
-                }
+            rgs.tot[threadIdx.x] = double(S) + double(C);
+        }
+        __syncthreads();
+        if (rank == 0 && threadIdx.x == 32 && a.obj && it == a.iters - 1) a.obj[pair] = rgs.tot[NTERM - 1];
+        if (warp == 0) {
+            const bool solved = warp_solve_update<true>(rgs.tot, rgs.T, rgs.Rt, rank == 0 ? T_hist : nullptr, it,
+                                                        rank == 0 ? w.T : nullptr, nullptr);
+            if (!solved && rank == 0 && lane == 0) {
+                atomicOr(w.status, ST_DEGENERATE);
+                if (T_hist)
+                    for (int k = 0; k < 16; ++k) T_hist[16 * it + k] = k < 12 ? rgs.T[k] : (k == 15 ? 1.0 : 0.0);
             }
         }
-        cl.sync();
     }
+    cl.sync();  // rank 0's final pose is written
     if (rank == 0 && threadIdx.x < 16) {
         a.T_out[16 * pair + threadIdx.x] = __ldcg(w.T + threadIdx.x);
         if (threadIdx.x == 0) {
