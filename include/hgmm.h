@@ -129,9 +129,12 @@ int hgmm_build(hgmm_tree* t, const float* d_points, int64_t n, int32_t depth,
  * final T is written to d_T_out (16 float64, device).  If d_T_hist is not
  * NULL it receives the T after every round (iters x 16 float64, device).
  * The node moments are exact fixed-point sums of every point's moments, so
- * the result does not depend on the order of the source points; a source of
- * 2^20 points or more (up to max_points) is sorted by its first-round nodes
- * into the tree's free point buffer for the remaining rounds.
+ * the result does not depend on the order of the source points, nor on how
+ * many CTAs the launch has; a source of 2^20 points or more (up to
+ * max_points) is sorted by its first-round nodes into the tree's free point
+ * buffer for the remaining rounds, and one of 2^21 points or more runs with
+ * three CTAs per SM instead of two (more warps for a throughput-bound
+ * descent; the same bits).
  * Errors: HGMM_EINVAL, HGMM_ECUDA; singular normal equations are reported by
  * hgmm_sync as HGMM_EDEGENERATE (T is then left unchanged in that round). */
 int hgmm_register(hgmm_tree* t, const float* d_src, int64_t n,

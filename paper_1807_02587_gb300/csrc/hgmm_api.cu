@@ -120,7 +120,9 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     const int64_t parents = max_depth >= 2 ? level_size(max_depth - 2) : 1;
     t->max_items = (max_points + TILE - 1) / TILE + parents;
     t->est_grid = t->n_sm * 3;  // three k_estep CTAs fit on an SM
-    t->reg_grid = hgmm_register_grid(t->n_sm);
+    t->reg_grid = hgmm_register_grid(t->n_sm, 2);
+    t->reg_grid_wide = hgmm_register_grid(t->n_sm, 3);
+    if (t->reg_grid_wide == 0) cudaGetLastError();  // large sources keep the two-per-SM build
     t->em_coop_grid = hgmm_em_coop_grid(t->n_sm, t->est_grid);
     if (!hgmm_estep_smem_attr()) {
         cudaGetLastError();
@@ -133,7 +135,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     }
     // one normal-equation partial per registration CTA, or per 32 nodes in
     // the descent variants
-    const int64_t nb = std::max<int64_t>(t->reg_grid, (t->max_nodes + 31) / 32);
+    const int64_t nb = std::max<int64_t>(std::max(t->reg_grid, t->reg_grid_wide), (t->max_nodes + 31) / 32);
     bool good = true;
     good &= dalloc(&t->est, t->max_nodes);
     good &= dalloc(&t->stat, t->max_nodes);
@@ -162,7 +164,7 @@ int hgmm_tree_create(int64_t max_points, int32_t max_depth, hgmm_tree** out) {
     good &= dalloc(&t->reg_acc2, 6 * t->max_nodes);
     good &= dalloc(&t->reg_part, NTERM * nb);
     good &= dalloc(&t->rnode, 3 * t->max_nodes);
-    good &= dalloc(&t->trace, int64_t(TRACE_MAX_ITERS) * t->reg_grid * 6);
+    good &= dalloc(&t->trace, int64_t(TRACE_MAX_ITERS) * std::max(t->reg_grid, t->reg_grid_wide) * 6);
     good &= dalloc(&t->reg_bar, 8);
     good &= dalloc(&t->reg_T, 16);
     good &= dalloc(&t->reg_Rt, 12);
@@ -423,7 +425,7 @@ int hgmm_trace_read(hgmm_tree* t, int64_t* h_events, int64_t cap, int32_t* iters
                     int32_t* ctas) {
     if (!t || !h_events) return HGMM_EINVAL;
     if (iters) *iters = t->trace_iters;
-    if (ctas) *ctas = t->reg_grid;
+    if (ctas) *ctas = t->trace_grid;
     return hgmm_trace_read_impl(t, reinterpret_cast<unsigned long long*>(h_events), cap);
 }
 

@@ -143,7 +143,8 @@ struct hgmm_tree {
     int64_t max_nodes = 0;
     int est_grid = 0;   // CTAs of the persistent build E-step
     int em_coop_grid = 0;  // co-resident CTAs of the cooperative per-level EM kernel (0: unavailable)
-    int reg_grid = 0;   // CTAs of the descent
+    int reg_grid = 0;       // CTAs of the registration kernel, two per SM
+    int reg_grid_wide = 0;  // three per SM, for large sources (0: not co-resident)
     // last build
     int64_t n = 0;
     int depth = 0;
@@ -187,7 +188,8 @@ struct hgmm_tree {
     bool prof_on = false;
     bool trace_on = false;
     int trace_iters = 0;
-    unsigned long long* trace = nullptr;  // TRACE_MAX_ITERS x reg_grid x 6
+    int trace_grid = 0;  // CTAs of the traced launch
+    unsigned long long* trace = nullptr;  // TRACE_MAX_ITERS x max(reg_grid, reg_grid_wide) x 6
     std::vector<hgmm::ProfRecord> prof;
     // host-API staging
     float4* stage_tgt = nullptr;
@@ -231,7 +233,7 @@ int hgmm_register_descent_impl(hgmm_tree* t, const float4* src, int64_t n, const
                                double* T_hist);
 int hgmm_export_labels_impl(hgmm_tree* t, int level, int* d_out, cudaStream_t s);
 int hgmm_debug_posteriors_impl(hgmm_tree* t, int level, float* h_gamma);
-int hgmm_register_grid(int n_sm);
+int hgmm_register_grid(int n_sm, int per_sm);
 int hgmm_em_coop_grid(int n_sm, int est_grid);
 bool hgmm_estep_smem_attr();
 int hgmm_barrier_timeout_probe_impl(hgmm_tree* t, long long limit, cudaStream_t s);

@@ -75,7 +75,12 @@ struct RegArgs {
 
 constexpr int TRACE_EVENTS = 6;
 constexpr size_t REG_DYN_SMEM = STAGED_F4 * sizeof(float4) + 4 * STAGED_NODES * sizeof(unsigned long long);
-static_assert(REG_DYN_SMEM <= 96 * 1024, "two k_register CTAs must fit on one SM");
+// three CTAs per SM (dynamic + ~4 KB static + 1 KB reserved each) within 228 KB
+static_assert(3 * (REG_DYN_SMEM + 5 * 1024) <= 228 * 1024, "three k_register CTAs must fit on one SM");
+// sources from this size on take the three-CTAs-per-SM build (measured: 1M
+// points run 10 rounds in 0.65 ms with two CTAs per SM against 0.68 with
+// three; 4M in 1.58 against 1.42; 16M in 6.0 against 5.2)
+constexpr int REG_WIDE_MIN_POINTS = 1 << 21;
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -105,8 +110,13 @@ __device__ __forceinline__ void trace_mark(unsigned long long* tr, int it, int e
 // every wait is bounded.
 // KEYS: the launch records each point's chosen node in a.keys (a one-round
 // launch before the source reorder).
-template <bool KEYS>
-__global__ void __launch_bounds__(REG_THREADS, 2) k_register(RegArgs a) {
+// MINB: co-resident CTAs per SM the build is register-limited for.  Two (128
+// registers) for sources of a few points per thread, where each round is a
+// latency chain and the node terms and the solve want the registers; three
+// (80) for large sources, whose descent is throughput-bound and gains from
+// the extra warps (a few bytes of spills, outside the descent).
+template <bool KEYS, int MINB>
+__global__ void __launch_bounds__(REG_THREADS, MINB) k_register(RegArgs a) {
     __shared__ float Rt_sm[12];
     __shared__ double T_sm[12];
     __shared__ float2 sm[REG_THREADS / 32][NTERM];
@@ -709,6 +719,8 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         int(std::min<int64_t>(2 * t->n_sm, t->max_items * NPART * 2 / REORDER_KEYS - 1));
     const bool reorder = iters > 1 && n >= REORDER_MIN_POINTS && n64 <= t->cap && reorder_ctas >= 32 &&
                          n_nodes < REORDER_KEYS && !t->trace_on;
+    const bool wide = n >= REG_WIDE_MIN_POINTS && t->reg_grid_wide > 0;
+    const int grid = wide ? t->reg_grid_wide : t->reg_grid;
     auto launch = [&](const float4* pts, int rounds, double* hist, uint32_t* keys) -> int {
         RegArgs a;
         a.src = pts;
@@ -730,12 +742,14 @@ int hgmm_register_impl(hgmm_tree* t, const float4* src, int64_t n64, const doubl
         a.status = t->status;
         a.keys = keys;
         a.trace = (t->trace_on && rounds <= TRACE_MAX_ITERS) ? t->trace : nullptr;
-        if (a.trace) cudaMemsetAsync(t->trace, 0, size_t(rounds) * t->reg_grid * TRACE_EVENTS * 8, s);
+        if (a.trace) cudaMemsetAsync(t->trace, 0, size_t(rounds) * grid * TRACE_EVENTS * 8, s);
         t->trace_iters = a.trace ? rounds : 0;
+        t->trace_grid = a.trace ? grid : 0;
         void* args[] = {&a};
         ProfScope ps_(t, K_DESCEND, s);
-        const void* fn = keys ? (const void*)k_register<true> : (const void*)k_register<false>;
-        const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(t->reg_grid), dim3(REG_THREADS), args,
+        const void* fn = wide ? (keys ? (const void*)k_register<true, 3> : (const void*)k_register<false, 3>)
+                              : (keys ? (const void*)k_register<true, 2> : (const void*)k_register<false, 2>);
+        const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(REG_THREADS), args,
                                                           REG_DYN_SMEM, s);
         if (e != cudaSuccess) {
             fprintf(stderr, "hgmm: cooperative launch failed: %s\n", cudaGetErrorString(e));
@@ -819,24 +833,29 @@ int hgmm_register_descent_impl(hgmm_tree* t, const float4* src, int64_t n64, con
     return HGMM_OK;
 }
 
-int hgmm_register_grid(int n_sm) {
+int hgmm_register_grid(int n_sm, int per_sm) {
     // static + dynamic shared memory exceeds the 48 KB default: opt in; the
-    // grid must be co-resident for both variants of the kernel
-    int per_sm = 2;
-    const void* fns[2] = {(const void*)k_register<false>, (const void*)k_register<true>};
+    // grid must be co-resident for both variants (KEYS) of the build asked
+    // for; 0 if that build does not reach per_sm CTAs per SM (the caller then
+    // keeps to the two-per-SM build)
+    if (per_sm != 2 && per_sm != 3) return 0;
+    const void* fns[2] = {per_sm == 3 ? (const void*)k_register<false, 3> : (const void*)k_register<false, 2>,
+                          per_sm == 3 ? (const void*)k_register<true, 3> : (const void*)k_register<true, 2>};
+    int got = per_sm;
     for (const void* fn : fns) {
         int k = 0;
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(REG_DYN_SMEM)) !=
                 cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fn, REG_THREADS, REG_DYN_SMEM) != cudaSuccess || k < 1)
             return 0;
-        per_sm = std::min(per_sm, k);
+        got = std::min(got, k);
     }
-    return n_sm * per_sm;  // <= co-resident CTAs (cooperative launch)
+    if (per_sm == 3 && got < 3) return 0;
+    return n_sm * got;  // <= co-resident CTAs (cooperative launch)
 }
 
 int hgmm_trace_read_impl(hgmm_tree* t, unsigned long long* h, int64_t cap) {
-    const int64_t need = int64_t(t->trace_iters) * t->reg_grid * TRACE_EVENTS;
+    const int64_t need = int64_t(t->trace_iters) * t->trace_grid * TRACE_EVENTS;
     if (cap < need) return HGMM_ECAPACITY;
     if (need == 0) return HGMM_OK;
     if (cudaDeviceSynchronize() != cudaSuccess) return HGMM_ECUDA;

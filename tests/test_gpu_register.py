@@ -215,10 +215,12 @@ def test_registration_does_not_depend_on_the_order_of_the_source_points(B):
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
-def test_large_unordered_source_is_reordered_without_changing_the_result(B):
+@pytest.mark.parametrize("n", [1_200_000, 2_200_000])
+def test_large_unordered_source_is_reordered_without_changing_the_result(B, n):
     """A source of at least 2^20 points runs its first round in the given
     order, recording each point's node, and is then counting-sorted by that
-    node for the remaining rounds.  The node moments are exact integer sums
+    node for the remaining rounds (from 2^21 points with three registration
+    CTAs per SM instead of two).  The node moments are exact integer sums
     of the points' fixed-point moments, so the order of the source points
     does not change the pose: the same cloud in two random orders gives the
     same 3 rounds bit for bit; the first round matches one oracle round on
@@ -226,7 +228,7 @@ def test_large_unordered_source_is_reordered_without_changing_the_result(B):
     pose after the first."""
     import torch
     rng = np.random.default_rng(5)
-    p = synth.primitive_pair(17, 1_200_000, max_deg=3.0, max_t=0.02)
+    p = synth.primitive_pair(17, n, max_deg=3.0, max_t=0.02)
     tgt, Zt = PT.device_cloud(p["tgt"])
     src4 = synth.to_float4(p["src"])
     tree = B.Tree(src4.shape[0], 4)
