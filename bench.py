@@ -912,6 +912,9 @@ def main():
     ap.add_argument("--profile-build", type=int, default=0, metavar="N",
                     help="only build the depth-4 tree of an N-point plane/box/sphere cloud 3 times, "
                          "for a profiler")
+    ap.add_argument("--profile-register", type=int, default=0, metavar="N",
+                    help="only register the N-point cloud, moved as in the large-build section, to its "
+                         "depth-4 tree 3 times (10 rounds each), for a profiler")
     ap.add_argument("--no-large-build", action="store_true")
     ap.add_argument("--no-odometry", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -952,7 +955,38 @@ def main():
         tree.sync()
         print(json.dumps({"profile_build": True, "points": int(dev.shape[0])}))
         return 0
+    if args.profile_register:
+        return profile_register_main(args)
     return gpu_main(args, rank, world, local_rank)
+
+
+def profile_register_main(args):
+    """Registration of a large cloud for an external profiler: the N-point
+    plane/box/sphere cloud moved by the large-build section's motion (2
+    degrees, 1 % of the extent), registered to its depth-4 tree 3 times with
+    10 rounds.  A source of 2^20 points or more takes two k_register launches
+    per call (the one-round launch that records the nodes, then the other
+    nine rounds on the reordered source)."""
+    import torch
+    from paper_1807_02587_gb300 import binding as B
+    from paper_1807_02587_gb300 import synth
+    dev = large_cloud(args.profile_register, args.seed)
+    n = int(dev.shape[0])
+    tree = B.Tree(n, 4)
+    tree.build(dev, 4)
+    extent = tree.root()["extent"]
+    T_gt = synth.rigid(synth.axis_angle_matrix([1.0, -2.0, 3.0], np.deg2rad(2.0)),
+                       np.full(3, 0.01 * extent / np.sqrt(3)))
+    Ti = torch.from_numpy(np.linalg.inv(T_gt)).to(device="cuda", dtype=torch.float32)
+    src = dev.clone()
+    src[:, :3] = dev[:, :3] @ Ti[:3, :3].T + Ti[:3, 3]
+    for _ in range(3):
+        T = tree.register(src, iters=10)
+    tree.sync()
+    T = T.cpu().numpy()
+    print(json.dumps({"profile_register": True, "points": n,
+                      "rot_err_deg_vs_truth": _rot_err(T[:3, :3], T_gt[:3, :3])}))
+    return 0
 
 
 def profile_variants_main(args):
